@@ -1,0 +1,222 @@
+"""CPU oracle for the finite-automaton DNA pattern scan — TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg (and its ``--impl reference`` arm) may import this package.  The product
+path (``paper_1506_08612_gb300``) never imports it, and the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain C, compiled here with gcc); this
+module only marshals numpy arrays.  Functions:
+
+* ``find_brute(text, pattern)`` — the result by its definition (Sec. II-A):
+  every window compared; returns ``(count, positions)``.
+* ``dfa_delta(pattern)`` — the string-matching automaton's transition function
+  built from its definition (Sec. II-A).
+* ``dfa_scan(text, delta, m)`` — sequential automaton walk.
+* ``alg1_scan(text, delta, m, p, v)`` — Algorithm 1's decomposition (Sec. III-A).
+* ``stt_ascii(strings, finals)`` — sparse 256-column STT (Sec. III-B, Table I).
+* ``kmer_census(text, k)`` and ``valid_windows(text, k)``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``_build/liboracle.so`` (OpenMP when available)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", src, "-o", tmp]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       stdout=subprocess.PIPE, stderr=subprocess.PIPE)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        i64, i32 = ctypes.c_int64, ctypes.c_int32
+        lib.oracle_find_brute.argtypes = [u8p, i64, u8p, i32, i64p, i64]
+        lib.oracle_find_brute.restype = i64
+        lib.oracle_dfa_delta.argtypes = [u8p, i32, i32p]
+        lib.oracle_dfa_delta.restype = ctypes.c_int
+        lib.oracle_dfa_scan.argtypes = [u8p, i64, i32p, i32, i64p, i64]
+        lib.oracle_dfa_scan.restype = i64
+        lib.oracle_alg1_lane_starts.argtypes = [i64, i64, i64, i64, i64p]
+        lib.oracle_alg1_lane_starts.restype = ctypes.c_int
+        lib.oracle_alg1_scan.argtypes = [u8p, i64, i32p, i32, i64, i64, i32, i64p, i64, i64p]
+        lib.oracle_alg1_scan.restype = i64
+        lib.oracle_stt_ascii.argtypes = [u8p, i32p, i32p, i32, i32p, i32, i32p, i32p, i32p]
+        lib.oracle_stt_ascii.restype = i32
+        lib.oracle_kmer_census.argtypes = [u8p, i64, i32, u64p]
+        lib.oracle_kmer_census.restype = ctypes.c_int
+        lib.oracle_valid_windows.argtypes = [u8p, i64, i32]
+        lib.oracle_valid_windows.restype = i64
+        lib.oracle_num_threads.argtypes = []
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _bytes(x) -> np.ndarray:
+    if isinstance(x, (bytes, bytearray)):
+        return np.frombuffer(bytes(x), dtype=np.uint8).copy()
+    if isinstance(x, str):
+        return np.frombuffer(x.encode("ascii"), dtype=np.uint8).copy()
+    a = np.ascontiguousarray(x, dtype=np.uint8)
+    return a
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+class OracleError(ValueError):
+    pass
+
+
+def find_brute(text, pattern, cap: int | None = None):
+    """(count, sorted int64 start positions) of every occurrence, by definition."""
+    t = _bytes(text)
+    p = _bytes(pattern)
+    lib = _load()
+    n = int(t.size)
+    if cap is None:
+        cnt = lib.oracle_find_brute(_p(t, ctypes.c_uint8), n, _p(p, ctypes.c_uint8), int(p.size),
+                                    None, 0)
+        if cnt < 0:
+            raise OracleError("invalid pattern")
+        cap = cnt
+    pos = np.empty(max(int(cap), 1), dtype=np.int64)
+    cnt = lib.oracle_find_brute(_p(t, ctypes.c_uint8), n, _p(p, ctypes.c_uint8), int(p.size),
+                                _p(pos, ctypes.c_int64), int(cap))
+    if cnt < 0:
+        raise OracleError("invalid pattern")
+    return int(cnt), pos[: min(int(cnt), int(cap))].copy()
+
+
+def count_brute(text, pattern) -> int:
+    t = _bytes(text)
+    p = _bytes(pattern)
+    cnt = _load().oracle_find_brute(_p(t, ctypes.c_uint8), int(t.size), _p(p, ctypes.c_uint8),
+                                    int(p.size), None, 0)
+    if cnt < 0:
+        raise OracleError("invalid pattern")
+    return int(cnt)
+
+
+def dfa_delta(pattern) -> np.ndarray:
+    """delta as an (m+1, 4) int32 array, columns A, C, G, T."""
+    p = _bytes(pattern)
+    m = int(p.size)
+    d = np.zeros((m + 1) * 4, dtype=np.int32)
+    if m < 1 or _load().oracle_dfa_delta(_p(p, ctypes.c_uint8), m, _p(d, ctypes.c_int32)) != 0:
+        raise OracleError("invalid pattern")
+    return d.reshape(m + 1, 4)
+
+
+def dfa_scan(text, delta: np.ndarray, m: int, cap: int | None = None):
+    t = _bytes(text)
+    d = np.ascontiguousarray(delta, dtype=np.int32).ravel()
+    lib = _load()
+    if cap is None:
+        cap = lib.oracle_dfa_scan(_p(t, ctypes.c_uint8), int(t.size), _p(d, ctypes.c_int32), m,
+                                  None, 0)
+    pos = np.empty(max(int(cap), 1), dtype=np.int64)
+    cnt = lib.oracle_dfa_scan(_p(t, ctypes.c_uint8), int(t.size), _p(d, ctypes.c_int32), m,
+                              _p(pos, ctypes.c_int64), int(cap))
+    return int(cnt), pos[: min(int(cnt), int(cap))].copy()
+
+
+def alg1_lane_starts(n: int, p: int, v: int, chunk: int = 0) -> list[int]:
+    out = np.zeros(v, dtype=np.int64)
+    if _load().oracle_alg1_lane_starts(n, p, v, chunk, _p(out, ctypes.c_int64)) != 0:
+        raise OracleError("invalid arguments")
+    return [int(x) for x in out]
+
+
+def alg1_scan(text, delta: np.ndarray, m: int, p: int, v: int, nthreads: int = 1,
+              want_positions: bool = True):
+    """Algorithm 1: returns (count, positions or None, automaton steps)."""
+    t = _bytes(text)
+    d = np.ascontiguousarray(delta, dtype=np.int32).ravel()
+    lib = _load()
+    steps = ctypes.c_int64(0)
+    if not want_positions:
+        cnt = lib.oracle_alg1_scan(_p(t, ctypes.c_uint8), int(t.size), _p(d, ctypes.c_int32), m,
+                                   p, v, nthreads, None, 0, ctypes.byref(steps))
+        return int(cnt), None, int(steps.value)
+    cnt = lib.oracle_alg1_scan(_p(t, ctypes.c_uint8), int(t.size), _p(d, ctypes.c_int32), m,
+                               p, v, nthreads, None, 0, None)
+    if cnt < 0:
+        raise OracleError("invalid arguments")
+    pos = np.empty(max(int(cnt), 1), dtype=np.int64)
+    cnt = lib.oracle_alg1_scan(_p(t, ctypes.c_uint8), int(t.size), _p(d, ctypes.c_int32), m,
+                               p, v, nthreads, _p(pos, ctypes.c_int64), int(cnt),
+                               ctypes.byref(steps))
+    return int(cnt), pos[: int(cnt)].copy(), int(steps.value)
+
+
+def stt_ascii(strings, finals=None):
+    """Sparse ASCII STT of the failure-less automaton of ``strings``.
+
+    Returns (stt[int32 states x 256], f, state_strings) where state_strings[q]
+    is the (upper-case) string of state q.
+    """
+    strs = [s.encode() if isinstance(s, str) else bytes(s) for s in strings]
+    if finals is None:
+        finals = [True] * len(strs)
+    buf = np.frombuffer(b"".join(strs), dtype=np.uint8).copy()
+    lens = np.array([len(s) for s in strs], dtype=np.int32)
+    fin = np.array([1 if f else 0 for f in finals], dtype=np.int32)
+    cap = int(lens.sum()) + 1
+    stt = np.zeros(cap * 256, dtype=np.int32)
+    src = np.zeros(cap, dtype=np.int32)
+    ln = np.zeros(cap, dtype=np.int32)
+    f = ctypes.c_int32(0)
+    ns = _load().oracle_stt_ascii(_p(buf, ctypes.c_uint8), _p(lens, ctypes.c_int32),
+                                  _p(fin, ctypes.c_int32), len(strs), _p(stt, ctypes.c_int32), cap,
+                                  ctypes.byref(f), _p(src, ctypes.c_int32), _p(ln, ctypes.c_int32))
+    if ns < 0:
+        raise OracleError("invalid strings")
+    upper = [s.upper() for s in strs]
+    names = [upper[src[q]][: ln[q]].decode() for q in range(ns)]
+    return stt[: ns * 256].reshape(ns, 256).copy(), int(f.value), names
+
+
+def kmer_census(text, k: int) -> np.ndarray:
+    t = _bytes(text)
+    h = np.zeros(4 ** k, dtype=np.uint64)
+    if _load().oracle_kmer_census(_p(t, ctypes.c_uint8), int(t.size), k, _p(h, ctypes.c_uint64)) != 0:
+        raise OracleError("invalid k")
+    return h
+
+
+def valid_windows(text, k: int) -> int:
+    t = _bytes(text)
+    return int(_load().oracle_valid_windows(_p(t, ctypes.c_uint8), int(t.size), k))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())

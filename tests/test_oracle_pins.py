@@ -1,0 +1,398 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU).
+
+Each group below checks the oracle against something the paper or the
+mathematics fixes — printed values, closed forms, textbook algorithms,
+library routines, invariants — chosen so that a dropped term, an off-by-one
+or a transposed operand in ``oracle.c`` fails at least one of them.
+"""
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import GOLDEN
+
+BASES = b"ACGT"
+
+
+def _golden_lines(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                yield line
+
+
+# --------------------------------------------------------------------------
+# fixed facts of the problem statement (Sec. II-A)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("line", list(_golden_lines("fixed_facts.txt")))
+def test_fixed_facts(line):
+    text, pat, cnt, pos = line.split()
+    expect = [] if pos == "-" else [int(x) for x in pos.split(",")]
+    c, p = oracle.find_brute(text.encode(), pat.encode())
+    assert c == int(cnt) and list(p) == expect
+    d = oracle.dfa_delta(pat.encode())
+    c2, p2 = oracle.dfa_scan(text.encode(), d, len(pat))
+    assert c2 == int(cnt) and list(p2) == expect
+
+
+# --------------------------------------------------------------------------
+# closed forms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,m", [(1, 1), (6, 4), (100, 1), (100, 7), (1000, 64), (63, 64)])
+def test_homopolymer_closed_form(n, m):
+    c, p = oracle.find_brute(b"A" * n, b"A" * m)
+    assert c == max(0, n - m + 1)
+    assert list(p) == list(range(max(0, n - m + 1)))
+
+
+@pytest.mark.parametrize("pat,r", [(b"AAAC", 10), (b"ACGT", 7), (b"GATTACA", 5), (b"C", 9)])
+def test_border_free_repeat(pat, r):
+    # a pattern with no proper border occurs in P^r exactly at the multiples of m
+    c, p = oracle.find_brute(pat * r, pat)
+    assert c == r and list(p) == [i * len(pat) for i in range(r)]
+
+
+@pytest.mark.parametrize("k,r", [(1, 10), (2, 10), (3, 4), (5, 5)])
+def test_periodic_repeat(k, r):
+    # (AC)^k inside (AC)^r occurs at every even offset 0, 2, .., 2(r-k)
+    c, p = oracle.find_brute(b"AC" * r, b"AC" * k)
+    assert c == r - k + 1 and list(p) == list(range(0, 2 * (r - k) + 1, 2))
+
+
+def test_no_bases_no_matches():
+    for t in (b"N" * 50, b"n" * 50, b"\n" * 9, bytes(range(256)) * 2):
+        for pat in (b"A", b"T", b"ACGT", b"AAA"):
+            # only the 8 base bytes can match; bytes(range(256)) holds each of
+            # A and a twice per copy and no run of two bases
+            want = t.upper().count(pat) if len(pat) == 1 else 0
+            assert oracle.count_brute(t, pat) == want
+
+
+def test_empty_and_short_texts():
+    assert oracle.find_brute(b"", b"A")[0] == 0
+    assert oracle.find_brute(b"ACG", b"ACGT")[0] == 0
+    assert oracle.find_brute(b"ACGT", b"ACGT")[0] == 1
+
+
+def test_invalid_patterns_rejected():
+    for bad in (b"", b"ACGN", b"AC-T", b"\x00"):
+        with pytest.raises(oracle.OracleError):
+            oracle.find_brute(b"ACGT", bad)
+
+
+def test_expected_count_uniform_text():
+    # E[count] of a fixed non-self-overlapping 6-mer in uniform text is
+    # (n - 5) / 4^6, variance ~ the mean; allow 6 standard deviations.
+    n = 4_000_000
+    t = synth.uniform_text(n, seed=123)
+    for pat in (b"ACGTTG", b"GATTAC"):
+        mu = (n - 5) / 4096
+        assert abs(oracle.count_brute(t, pat) - mu) < 6 * mu ** 0.5
+
+
+# --------------------------------------------------------------------------
+# agreement with a library routine: the regex engine (overlapping look-ahead)
+# --------------------------------------------------------------------------
+
+def _regex_find(text: bytes, pat: bytes):
+    folded = bytes(text).upper()            # ASCII-only upper-casing
+    return [mt.start() for mt in re.finditer(b"(?=" + re.escape(pat.upper()) + b")", folded)]
+
+
+def test_exhaustive_tiny_texts_vs_regex():
+    alphabet = b"ACGTNa"
+    pats = [b"A", b"C", b"AA", b"AC", b"CA", b"AAA", b"ACA", b"TGT"]
+    for L in range(0, 7):
+        for tup in itertools.product(alphabet, repeat=L):
+            t = bytes(tup)
+            for pat in pats:
+                c, p = oracle.find_brute(t, pat)
+                r = _regex_find(t, pat)
+                assert c == len(r) and list(p) == r, (t, pat)
+
+
+def test_random_texts_vs_regex():
+    for seed in range(20):
+        t = synth.random_text(3000, seed, b"ACGTacgtNn\n")
+        for m in range(1, 13):
+            pat = synth.pattern(m, 1000 + seed * 13 + m)
+            c, p = oracle.find_brute(t, pat)
+            r = _regex_find(t.tobytes(), pat)
+            assert c == len(r) and list(p) == r
+
+
+# --------------------------------------------------------------------------
+# the automaton: definitional table vs the Knuth-Morris-Pratt construction
+# --------------------------------------------------------------------------
+
+def _kmp_delta(pat: bytes) -> np.ndarray:
+    """Automaton from the KMP prefix function (an independent construction):
+    delta(q, a) = q+1 if q < m and P[q] = a, else delta(pi[q-1], a) (q > 0),
+    else 0."""
+    m = len(pat)
+    pi = [0] * m
+    k = 0
+    for i in range(1, m):
+        while k and pat[i] != pat[k]:
+            k = pi[k - 1]
+        if pat[i] == pat[k]:
+            k += 1
+        pi[i] = k
+    d = np.zeros((m + 1, 4), dtype=np.int32)
+    for q in range(m + 1):
+        for b, a in enumerate(BASES):
+            if q < m and pat[q] == a:
+                d[q, b] = q + 1
+            elif q == 0:
+                d[q, b] = 0
+            else:
+                d[q, b] = d[pi[q - 1], b]
+    return d
+
+
+def test_delta_equals_kmp_exhaustive_m_le_6():
+    for m in range(1, 7):
+        for tup in itertools.product(BASES, repeat=m):
+            pat = bytes(tup)
+            assert np.array_equal(oracle.dfa_delta(pat), _kmp_delta(pat)), pat
+
+
+def test_delta_equals_kmp_random_long():
+    for m in (7, 13, 31, 32, 64, 100):
+        for s in range(5):
+            pat = synth.pattern(m, 77 + 7 * m + s)
+            assert np.array_equal(oracle.dfa_delta(pat), _kmp_delta(pat))
+
+
+def test_delta_structure():
+    pat = b"GATTACA"
+    d = oracle.dfa_delta(pat)
+    m = len(pat)
+    for q in range(m):                       # forward edges
+        assert d[q, BASES.index(pat[q])] == q + 1
+    assert (d <= np.arange(m + 1)[:, None] + 1).all()
+    assert (d[0] == [1 if a == pat[0] else 0 for a in BASES]).all()
+    hom = oracle.dfa_delta(b"AAAA")
+    assert hom[4, 0] == 4 and (hom[:, 1:] == 0).all()
+    assert oracle.dfa_delta(b"acgt").tolist() == oracle.dfa_delta(b"ACGT").tolist()
+
+
+def test_dfa_scan_equals_brute_random():
+    for seed in range(10):
+        t = synth.genome_text(20000, seed, mask_mean=40, n_gap_mean=900, n_run_mean=60)
+        for m in (1, 2, 3, 4, 5, 8, 12, 16):
+            pat = synth.pattern(m, 5000 + seed * 31 + m)
+            d = oracle.dfa_delta(pat)
+            c1, p1 = oracle.find_brute(t, pat)
+            c2, p2 = oracle.dfa_scan(t, d, m)
+            assert c1 == c2 and np.array_equal(p1, p2)
+
+
+# --------------------------------------------------------------------------
+# Table I (Sec. III-B): the sparse ASCII STT layout and values
+# --------------------------------------------------------------------------
+
+def test_table_I_sparse_stt():
+    lines = list(_golden_lines("table_I.txt"))
+    cols = [int(x) for x in lines[0].split()[1:]]
+    assert cols == [ord("A"), ord("C"), ord("G"), ord("T")]
+    rows, corrections = {}, {}
+    final_from = None
+    for ln in lines[1:]:
+        if ln.startswith("final_from"):
+            final_from = int(ln.split()[1])
+            continue
+        head, _, fix = ln.partition("!")
+        parts = head.split()
+        q, name, vals = int(parts[0]), parts[1], [int(x) for x in parts[2:6]]
+        rows[q] = ("" if name == "e" else name.upper(), vals)
+        if fix.strip():
+            col, change = fix.strip().split("=")
+            printed, corrected = (int(x) for x in change.split("->"))
+            corrections[(q, "ACGT".index(col))] = (printed, corrected)
+    names_paper = {q: rows[q][0] for q in rows}
+    stt, f, names = oracle.stt_ascii(["acg", "act", "cta", "t"], [True, True, True, False])
+    assert sorted(names) == sorted(names_paper.values())
+    assert names.index("ACG") >= f and f == final_from   # finals numbered last
+    ours = {nm: q for q, nm in enumerate(names)}
+    for q, (nm, vals) in rows.items():
+        row = stt[ours[nm]]
+        for j, c in enumerate(cols):
+            want = vals[j]
+            if (q, j) in corrections:
+                printed, corrected = corrections[(q, j)]
+                assert printed == want
+                want = corrected
+            assert names[row[c]] == names_paper[want], (nm, "ACGT"[j])
+            assert row[c + 32] == row[c]                   # lower-case column
+        others = [c for c in range(256) if c not in cols and c - 32 not in cols]
+        assert (row[others] == 0).all()                    # every other column -> q0
+
+
+def test_stt_single_pattern_matches_delta():
+    for pat in (b"ACGT", b"AAAA", b"GATTACA", synth.pattern(20, 9)):
+        stt, f, names = oracle.stt_ascii([pat])
+        d = oracle.dfa_delta(pat)
+        m = len(pat)
+        assert f == m and len(names) == m + 1
+        # single pattern: prefix numbering is the prefix length
+        assert [len(nm) for nm in names] == list(range(m + 1))
+        assert np.array_equal(stt[:, list(BASES)], d)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 (Sec. III-A): decomposition with m-1 overlap
+# --------------------------------------------------------------------------
+
+def test_fig2b_lane_starts():
+    for ln in _golden_lines("fig2b_lanes.txt"):
+        n, p, v, ch, starts = ln.split()
+        assert oracle.alg1_lane_starts(int(n), int(p), int(v), int(ch)) == \
+            [int(x) for x in starts.split(",")]
+
+
+@pytest.mark.parametrize("p,v", [(1, 1), (1, 4), (3, 1), (4, 4), (7, 3), (60, 16), (240, 16),
+                                 (5000, 1), (2, 5000)])
+def test_alg1_equals_brute(p, v):
+    t = synth.genome_text(30011, 5, mask_mean=50, n_gap_mean=3000, n_run_mean=100)
+    for m in (1, 2, 4, 8, 13, 16, 33, 64):
+        pat = synth.pattern(m, 900 + m)
+        c1, p1 = oracle.find_brute(t, pat)
+        c2, p2, _ = oracle.alg1_scan(t, oracle.dfa_delta(pat), m, p, v)
+        assert c1 == c2 and np.array_equal(p1, p2), (m, p, v)
+
+
+def test_alg1_dense_matches_cross_every_border():
+    t = b"A" * 4099
+    for m in (1, 3, 4, 17):
+        for p, v in ((1, 1), (4, 4), (16, 8), (1000, 3)):
+            c, pos, _ = oracle.alg1_scan(t, oracle.dfa_delta(b"A" * m), m, p, v)
+            assert c == 4099 - m + 1 and list(pos) == list(range(4099 - m + 1))
+
+
+def test_alg1_overlap_cost():
+    # each of the P non-empty pieces except the last re-scans m-1 bytes of
+    # its successor: steps = n + (P - 1)(m - 1) when every piece ends at
+    # least m - 1 bytes before n.
+    n = 1 << 16
+    t = synth.uniform_text(n, 3)
+    for m, p, v in ((8, 4, 4), (64, 16, 16), (2, 240, 16), (33, 7, 3)):
+        pat = synth.pattern(m, 4)
+        _, _, steps = oracle.alg1_scan(t, oracle.dfa_delta(pat), m, p, v, want_positions=False)
+        assert steps == n + (p * v - 1) * (m - 1)
+
+
+# --------------------------------------------------------------------------
+# metamorphic relations
+# --------------------------------------------------------------------------
+
+COMP = bytes.maketrans(b"ACGTacgt", b"TGCAtgca")
+
+
+def _genome(seed, n=50000):
+    return synth.genome_text(n, seed, mask_mean=30, n_gap_mean=5000, n_run_mean=200).tobytes()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_metamorphic(seed):
+    t = _genome(seed)
+    n = len(t)
+    flip = synth.uniform_ints(n, 2, seed, stream=3).astype(bool)
+    arr = np.frombuffer(t, dtype=np.uint8).copy()
+    letters = np.isin(arr, np.frombuffer(b"ACGTacgt", np.uint8))
+    arr[flip & letters] ^= 0x20
+    t_case = arr.tobytes()
+    for m in (1, 3, 4, 6, 9):
+        pat = synth.pattern(m, 300 + seed * 10 + m)
+        c, p = oracle.find_brute(t, pat)
+        # case of the text does not matter
+        assert np.array_equal(oracle.find_brute(t_case, pat)[1], p)
+        # complementing text and pattern keeps every occurrence
+        assert np.array_equal(oracle.find_brute(t.translate(COMP), pat.translate(COMP))[1], p)
+        # reversing text and pattern mirrors the positions
+        cr, pr = oracle.find_brute(t[::-1], pat[::-1])
+        assert cr == c and sorted(n - m - int(i) for i in pr) == list(p)
+        # an N between two texts separates them
+        half = n // 2
+        c1, p1 = oracle.find_brute(t[:half], pat)
+        c2, p2 = oracle.find_brute(t[half:], pat)
+        cj, pj = oracle.find_brute(t[:half] + b"N" + t[half:], pat)
+        assert cj == c1 + c2
+        assert list(pj) == list(p1) + [int(x) + half + 1 for x in p2]
+
+
+# --------------------------------------------------------------------------
+# k-mer census
+# --------------------------------------------------------------------------
+
+def _de_bruijn(k: int) -> bytes:
+    """Linear de Bruijn sequence B(4, k) (Fredricksen-Kessler-Maiorana
+    construction): every k-mer over ACGT occurs exactly once."""
+    a = [0] * (k + 1)
+    seq = []
+
+    def db(t, p):
+        if t > k:
+            if k % p == 0:
+                seq.extend(a[1:p + 1])
+        else:
+            a[t] = a[t - p]
+            db(t + 1, p)
+            for j in range(a[t - p] + 1, 4):
+                a[t] = j
+                db(t + 1, t)
+    db(1, 1)
+    seq = seq + seq[: k - 1]
+    return bytes(BASES[i] for i in seq)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6])
+def test_census_de_bruijn(k):
+    h = oracle.kmer_census(_de_bruijn(k), k)
+    assert (h == 1).all()
+
+
+def test_census_invariants():
+    t = _genome(11, 200000)
+    for k in (1, 2, 4, 6):
+        h = oracle.kmer_census(t, k)
+        assert int(h.sum()) == oracle.valid_windows(t, k)
+    h6 = oracle.kmer_census(t, 6)
+    for s in range(30):
+        pat = synth.pattern(6, 40 + s)
+        code = 0
+        for ch in pat:
+            code = code * 4 + BASES.index(ch)
+        assert int(h6[code]) == oracle.count_brute(t, pat)
+
+
+def test_valid_windows_closed_form():
+    # runs of bases of lengths L_i separated by N: sum max(0, L_i - k + 1)
+    runs = [0, 1, 5, 6, 7, 100, 3]
+    t = b"N".join(b"A" * L for L in runs)
+    for k in (1, 3, 6, 7):
+        assert oracle.valid_windows(t, k) == sum(max(0, L - k + 1) for L in runs)
+
+
+# --------------------------------------------------------------------------
+# planted occurrences of long patterns
+# --------------------------------------------------------------------------
+
+def test_planted_long_patterns_found():
+    n = 1 << 20
+    t = synth.genome_text(n, 8)
+    for m in (16, 32, 64):
+        pat = synth.pattern(m, 50 + m)
+        pos = np.unique(synth.uniform_ints(200, n - m, 60 + m) // (2 * m) * (2 * m))
+        synth.plant(t, pat, pos)
+        c, p = oracle.find_brute(t, pat)
+        assert set(pos.tolist()) <= set(p.tolist())
+        assert c == oracle.dfa_scan(t, oracle.dfa_delta(pat), m)[0]
