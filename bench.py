@@ -1,0 +1,378 @@
+"""Benchmark of the finite-automaton DNA pattern scan on GB300.
+
+Workload (one "step" = the whole hot path over one batch): a 3.2 GB
+genome-like synthetic text (GC 0.41, ~50% soft-masked lower case in runs of
+mean 300, ~5% N in blocks of mean 50 kb; seed 2) resident in HBM, and five
+patterns of lengths 4, 8, 16, 32, 64 (uniform A/C/G/T, seeds 3..7), one
+launch per pattern, each producing the exact count and the sorted int64
+start positions.  The automata are built once before timing (host setup).
+
+Metric: GB/s of DNA text scanned per pattern (n bytes x patterns / time).
+The text (3.2 GB) is far larger than L2 (129 MB), so no flush is needed
+between steps.  ``e2e`` repeats the step through the host-buffer entry point
+(pinned host text in, host positions out, copies inside the timed region).
+``roofline`` reports the find kernel's algorithmic bytes (text + 8 B per
+position written) per launch over its CUDA-event duration against the
+measured HBM copy bandwidth.  ``cpu_baseline`` times the CPU oracle's
+Algorithm 1 scan on the host cores on a bounded sample of the same text.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) each rank scans its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GB/s of DNA text scanned per pattern"
+UNIT = "GB/s"
+PATTERN_LENGTHS = (4, 8, 16, 32, 64)
+PATTERN_SEEDS = (3, 4, 5, 6, 7)
+TEXT_BYTES = 3_200_000_000
+TEXT_SEED = 2
+WORKLOAD = "genome-scale single-pattern scan"
+DOMINANT_KERNEL = "k_find<1,256>"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=TEXT_BYTES)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cfg", default="", help="json launch config (layout/threads/chunk/loader)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def config_dict(n, world, cfg):
+    return {"workload": WORKLOAD, "text_bytes": n, "text": "GC 0.41, 50% soft-masked (runs mean 300),"
+            " 5% N (blocks mean 50 kb), seed 2", "patterns": list(PATTERN_LENGTHS),
+            "pattern_seeds": list(PATTERN_SEEDS), "outputs": "count + sorted int64 start positions",
+            "launches_per_step": len(PATTERN_LENGTHS), "l2": "inputs larger than L2 (no flush)",
+            "parallelism": f"replicas x{world}", "launch_config": cfg or "library default"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1506_08612_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cpp", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "k_find_genome3200MB.txt")
+    try:
+        kv = {}
+        with open(p) as f:
+            for ln in f:
+                if ":" in ln and not ln.startswith("#"):
+                    k, _, v = ln.partition(":")
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_digest") != kernel_source_digest():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ CPU side
+
+def cpu_baseline(text_np, patterns, budget_s=12.0, scale_n=None):
+    """The oracle's Algorithm 1 scan (OpenMP over every host core) on a
+    bounded prefix of the same text; GB/s of text per pattern."""
+    import oracle
+    cores = oracle.num_threads()
+    deltas = [(oracle.dfa_delta(p), len(p)) for p in patterns]
+    probe = min(text_np.size, 32_000_000)
+    t0 = time.perf_counter()
+    for d, m in deltas:
+        oracle.alg1_scan(text_np[:probe], d, m, p=cores * 8, v=16, nthreads=cores, want_positions=False)
+    dt = time.perf_counter() - t0
+    rate = probe * len(deltas) / dt
+    sample = int(min(text_np.size, max(probe, rate * budget_s / len(deltas))))
+    t0 = time.perf_counter()
+    for d, m in deltas:
+        oracle.alg1_scan(text_np[:sample], d, m, p=cores * 8, v=16, nthreads=cores, want_positions=True)
+    dt = time.perf_counter() - t0
+    gbs = sample * len(deltas) / dt / 1e9
+    return {"value": round(gbs, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} bytes of the {text_np.size}-byte text x {len(deltas)} patterns,"
+                      f" Algorithm 1 (p={cores * 8} chunks, v=16 lanes, m-1 overlap), count + positions,"
+                      f" {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    import synth
+    n = args.n
+    patterns = [synth.pattern(m, s) for m, s in zip(PATTERN_LENGTHS, PATTERN_SEEDS)]
+    import oracle
+    cores = oracle.num_threads()
+    # each step: a bounded prefix of the workload, sized for ~a few seconds
+    sample = min(n, 400_000_000)
+    text = synth.genome_text(sample, TEXT_SEED)
+    deltas = [(oracle.dfa_delta(p), len(p)) for p in patterns]
+
+    def step():
+        for d, m in deltas:
+            oracle.alg1_scan(text, d, m, p=cores * 8, v=16, nthreads=cores, want_positions=True)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = sample * len(deltas) * args.steps / dt / 1e9
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "impl": "reference",
+            "config": config_dict(n, world, None),
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {sample} bytes of the text x {len(deltas)} patterns per step,"
+                                       " Algorithm 1 with OpenMP"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU side
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1506_08612_gb300 as dd
+    import synth
+
+    cfg = json.loads(args.cfg) if args.cfg else None
+    n = args.n
+    seed = TEXT_SEED + 1000 * rank         # each rank scans its own replica
+    host = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    synth.genome_text(n, seed, out=host.numpy())
+    text = host.to(dev, non_blocking=False)
+    patterns = [synth.pattern(m, s) for m, s in zip(PATTERN_LENGTHS, PATTERN_SEEDS)]
+    tables = [dd.dfa_build(p) for p in patterns]
+    stream = torch.cuda.current_stream(dev)
+
+    # exact counts first (sizes the position buffers), untimed
+    counts = [dd.count(text, t, cfg=cfg) for t in tables]
+    caps = [max(16, c) for c in counts]
+    pos = [torch.empty(c, dtype=torch.int64, device=dev) for c in caps]
+    cnt = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in tables]
+    ws = torch.empty(dd.dfa_find_workspace_bytes(n, cfg), dtype=torch.uint8, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in tables]
+
+    def step():
+        for i, t in enumerate(tables):
+            dd.dfa_find(text, t, pos[i], cnt[i], ws, cfg=cfg, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    for i in range(len(tables)):
+        rc, c = dd.dfa_find_status(ws, cnt[i], caps[i], stream=stream)
+        assert rc == dd.DFA_OK and c == counts[i], (i, rc, c, counts[i])
+
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step()
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        torch.distributed.barrier()
+    for i in range(len(tables)):
+        assert int(cnt[i].item()) == counts[i]
+    ms_per_step = total_ms / args.steps
+    bytes_per_step = n * len(tables)
+    value = bytes_per_step * world / (ms_per_step * 1e-3) / 1e9
+
+    # dominant kernel roofline: every launch is the same kernel; time each one
+    # over a separate pass of K launches with events on the launching stream
+    k_ms = []
+    for _ in range(args.steps):
+        for i, t in enumerate(tables):
+            ev[i][0].record(stream)
+            dd.dfa_find(text, t, pos[i], cnt[i], ws, cfg=cfg, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        k_ms.append([ev[i][0].elapsed_time(ev[i][1]) for i in range(len(tables))])
+    mean_launch_ms = float(np.mean(k_ms))
+    algo_bytes = n + 8 * float(np.mean(counts))
+    achieved = algo_bytes / (mean_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+            "kernel": DOMINANT_KERNEL, "peak_kind": f"{peak_kind} (hbm_gbs copy bandwidth)",
+            "per_pattern_ms": [round(float(np.mean([r[i] for r in k_ms])), 4) for i in range(len(tables))],
+            "algorithmic_bytes_per_launch": "n + 8 * count (text read once, positions written)"}
+
+    e2e = None
+    if not args.no_e2e:
+        seg = 256 << 20
+        stage = torch.empty(dd.dfa_host_stage_bytes(seg, max(caps)), dtype=torch.uint8, device=dev)
+        hpos = [torch.empty(c, dtype=torch.int64, pin_memory=True) for c in caps]
+        for i, t in enumerate(tables):
+            dd.dfa_find_host(host, t, hpos[i], stage, seg, stream=stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            for i, t in enumerate(tables):
+                rc, c = dd.dfa_find_host(host, t, hpos[i], stage, seg, stream=stream)
+                assert c == counts[i]
+                d2h += 8 * c + 8
+        dt = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([dt], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": round(bytes_per_step * world * args.steps / dt / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(bytes_per_step), "d2h_bytes_per_step": int(d2h // args.steps),
+               "entry_point": "dfa_find_host (pinned host text, segments of 256 MiB, copies overlapped)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        cpu = cpu_baseline(host.numpy(), patterns)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic", "config": config_dict(n, world, cfg), "clocks": clk,
+                "e2e": e2e, "gpu_launches": args.steps * len(tables), "roofline": roof,
+                "cpu_baseline": cpu, "counts": counts}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

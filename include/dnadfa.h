@@ -1,0 +1,185 @@
+/*
+ * dnadfa — finite-automaton DNA pattern scan on GB300 (sm_103a): C ABI.
+ *
+ * The method is the automaton scan of Memeti & Pllana, "Accelerating DNA
+ * Sequence Analysis using Intel Xeon Phi" (2015): a failure-less automaton
+ * (Sec. III-B, Fig. 4) walks the text once, the text being split into chunks
+ * that carry m-1 bytes of overlap so that occurrences across chunk borders
+ * are found exactly once (Algorithm 1, Sec. III-A, Fig. 2a).  This library
+ * runs that walk in hand-written CUDA kernels; every call below is a plain C
+ * function on plain pointers and sizes.
+ *
+ * Conventions shared by every entry point
+ *   - Text: raw bytes.  A, C, G, T match in either case; every other byte
+ *     (N, IUPAC codes, newline, >= 128) matches nothing and resets the
+ *     automaton to q0, as the sparse table of Sec. III-B does for every
+ *     column outside the alphabet.
+ *   - Results: the number of occurrences of the pattern, overlaps included
+ *     (Sec. II-A problem statement), and their 0-based START positions in
+ *     ascending order (Algorithm 1 reports the index of the last matched
+ *     character; start = that index - m + 1).
+ *   - Memory: "d_" arguments are device pointers owned by the caller, on the
+ *     device that is current when the call is made; "h_" arguments are host
+ *     pointers.  Tables (dfa_table) are owned by the library.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Device entry points only enqueue work: they return
+ *     before it runs, do not synchronise, and allocate no memory.
+ *   - Errors: every int-returning function returns a DFA_* code and never
+ *     aborts the process.  Argument errors are detected before anything is
+ *     enqueued.
+ *   - Alignment: a text pointer that is 16-byte aligned gets the vectorised
+ *     path; any other pointer is accepted and scanned with byte loads.
+ */
+#ifndef DNADFA_H
+#define DNADFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define DFA_OK 0          /* success */
+#define DFA_EINVAL 1      /* bad argument: NULL pointer, n < 0, m out of range, bad pattern byte */
+#define DFA_ETRUNC 2      /* more occurrences than the position buffer holds (count is still exact) */
+#define DFA_ETIMEOUT 3    /* a bounded device-side wait gave up; results of that call are invalid */
+#define DFA_ECUDA 4       /* a CUDA runtime call failed */
+#define DFA_EWORKSPACE 5  /* workspace smaller than dfa_find_workspace_bytes() asks for */
+#define DFA_ENOMEM 6      /* host or device allocation failed (dfa_build only) */
+
+/* Longest pattern accepted.  States 0..m must fit a byte and the tables of
+ * the fast layouts must fit in one SM's shared memory. */
+#define DFA_MAX_M 64
+
+/* Opaque automaton for one pattern: host tables plus a device copy on the
+ * device that was current at dfa_build.  Library-owned; free with dfa_free. */
+typedef struct dfa_table dfa_table;
+
+/*
+ * Build the automaton of one pattern (Sec. III-B, Fig. 4; single pattern).
+ *   pattern: m bytes from {A,C,G,T,a,c,g,t} (case is folded); need not be
+ *            NUL-terminated.
+ *   m:       1 <= m <= DFA_MAX_M.
+ *   out:     receives the new table.
+ * The transition function is delta(q, a) = the length of the longest prefix
+ * of the pattern that is a suffix of (its first q bytes)·a, for q = 0..m; the
+ * one final state is m, numbered last (Sec. III-B).  The device copy is
+ * allocated and uploaded synchronously on the current device.
+ * Errors: DFA_EINVAL (NULL, m out of range, non-base byte), DFA_ENOMEM,
+ * DFA_ECUDA.
+ */
+int dfa_build(const char* pattern, int32_t m, dfa_table** out);
+
+/* Release a table (host and device memory).  NULL is ignored.  The caller
+ * must make sure no enqueued call still uses it. */
+void dfa_free(dfa_table* table);
+
+/* Pattern length m of a table, or -1 for NULL. */
+int32_t dfa_pattern_length(const dfa_table* table);
+
+/*
+ * Copy the table's sparse ASCII state transition table (Sec. III-B, Table I
+ * layout) to host memory: (m+1) rows of 256 bytes, row q column c holding
+ * delta(q, c); only the columns of A, C, G, T and a, c, g, t are non-zero.
+ *   h_stt: host buffer of at least (m+1)*256 bytes; bytes: its size.
+ * Errors: DFA_EINVAL.
+ */
+int dfa_export_stt(const dfa_table* table, uint8_t* h_stt, int64_t bytes);
+
+/*
+ * Launch configuration (the knobs the autotuner sets).  Zero fields take the
+ * library's defaults.
+ *   layout:  0 = default; 1 = four-step composite table over 2-bit codes
+ *            (u16 entries, (m+1)*256); 2 = the paper's sparse ASCII STT
+ *            (u8 entries, (m+1)*256, one lookup per byte: Sec. III-B).
+ *   threads: threads per CTA (64..1024, multiple of 32).
+ *   chunk:   bytes walked per thread per tile (multiple of 16, 16..32768),
+ *            each chunk carrying m-1 bytes of overlap (Algorithm 1).
+ *   loader:  0 = default; 1 = direct 16-byte global loads; 2 = TMA-staged
+ *            tiles (cp.async.bulk.tensor into shared memory).
+ *   ctas_per_sm: persistent CTAs per SM (0 = as many as fit).
+ */
+typedef struct dfa_config {
+    int32_t layout;
+    int32_t threads;
+    int32_t chunk;
+    int32_t loader;
+    int32_t ctas_per_sm;
+} dfa_config;
+
+/*
+ * Count every occurrence (overlaps included) of the table's pattern in
+ * d_text[0..n) and store the count in *d_count (device, uint64), overwriting
+ * it.  n < m gives 0.  Asynchronous on `stream`; allocates nothing.
+ * Matches the paper's "count" output of Algorithm 1.
+ *   cfg: launch configuration or NULL for the defaults.
+ * Errors: DFA_EINVAL (NULL pointers with n > 0, n < 0, bad cfg), DFA_ECUDA.
+ */
+int dfa_count(const uint8_t* d_text, int64_t n, const dfa_table* table, uint64_t* d_count,
+              const dfa_config* cfg, void* stream);
+
+/* Bytes of device workspace that dfa_find needs for a text of n bytes under
+ * `cfg` (NULL = defaults).  Returns -1 for bad arguments. */
+int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg);
+
+/*
+ * Count and locate every occurrence (overlaps included) of the table's
+ * pattern in d_text[0..n) (Algorithm 1: "count of pattern matches and their
+ * location").  Writes the exact count to *d_count (device, uint64) and the
+ * first min(count, cap) start positions, ascending, to d_pos[0..cap) (device,
+ * int64).  When count > cap the extra positions are dropped and
+ * dfa_find_status reports DFA_ETRUNC.
+ *   d_work / work_bytes: caller-owned device workspace of at least
+ *            dfa_find_workspace_bytes(n, cfg) bytes (tile descriptors for the
+ *            ordered single-pass compaction and a status word).  Its contents
+ *            need no initialisation; one workspace must not be shared by two
+ *            calls that may overlap on the device.
+ * Asynchronous on `stream`; allocates nothing.
+ * Errors: DFA_EINVAL, DFA_EWORKSPACE, DFA_ECUDA.  Device-side outcomes
+ * (truncation, a wait that gave up) are read with dfa_find_status.
+ */
+int dfa_find(const uint8_t* d_text, int64_t n, const dfa_table* table, int64_t* d_pos,
+             int64_t cap, uint64_t* d_count, void* d_work, int64_t work_bytes,
+             const dfa_config* cfg, void* stream);
+
+/*
+ * Synchronise `stream` and report the device-side outcome of the last
+ * dfa_find that used d_work: DFA_ETIMEOUT if a bounded wait gave up,
+ * DFA_ETRUNC if *d_count > cap, else DFA_OK (DFA_ECUDA on a CUDA error).
+ * If h_count is not NULL it receives *d_count.
+ */
+int dfa_find_status(const void* d_work, const uint64_t* d_count, int64_t cap,
+                    uint64_t* h_count, void* stream);
+
+/*
+ * End-to-end form with HOST buffers: the text is copied to the device in
+ * segments (each carrying the m-1 byte overlap of Algorithm 1 from its
+ * predecessor), scanned while the next segment is in flight, and the
+ * positions copied back.  Blocking: returns when *h_count and h_pos are
+ * final.
+ *   h_text: host text (pinned memory gives full copy bandwidth).
+ *   h_pos / cap: host buffer for up to cap start positions (NULL, 0 = count
+ *            only).
+ *   d_stage / stage_bytes: caller-owned device staging memory; at least
+ *            dfa_host_stage_bytes(seg, cap) bytes, where seg is the segment
+ *            size in bytes (>= 1 MiB).
+ * Returns DFA_ETRUNC when count > cap, else as dfa_find.
+ */
+int64_t dfa_host_stage_bytes(int64_t seg, int64_t cap);
+int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int64_t* h_pos,
+                  int64_t cap, uint64_t* h_count, void* d_stage, int64_t stage_bytes,
+                  int64_t seg, void* stream);
+
+/* Static text for a return code. */
+const char* dfa_strerror(int code);
+
+/* Library version string. */
+const char* dfa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DNADFA_H */

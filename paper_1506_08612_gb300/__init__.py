@@ -1,0 +1,204 @@
+"""GB300-native finite-automaton DNA pattern scan (Memeti & Pllana 2015).
+
+Thin Python binding over the C ABI of ``include/dnadfa.h`` (``libdnadfa.so``,
+built in place from ``csrc/``).  Every step of the scan runs in the library's
+CUDA kernels; this module only marshals arguments: PyTorch tensors supply
+device memory and the current CUDA stream.  The names follow the C ABI:
+
+* ``dfa_build(pattern) -> Table`` / ``dfa_free(table)``
+* ``dfa_count(text, table, count)`` — count occurrences (overlaps included)
+* ``dfa_find(text, table, positions, count, workspace)`` — count and sorted
+  start positions, single pass
+* ``dfa_find_status(workspace, count, cap)`` — device-side outcome
+* ``dfa_find_host(...)`` — host buffers in, host buffers out (copies inside)
+
+plus ``find``/``count`` conveniences that allocate their outputs with torch.
+There is no CPU fallback: importing this package fails if the CUDA library
+cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import (DFA_ECUDA, DFA_EINVAL, DFA_ENOMEM, DFA_ETIMEOUT, DFA_ETRUNC,
+                      DFA_EWORKSPACE, DFA_MAX_M, DFA_OK, LIBRARY_PATH, dfa_config)
+
+_lib = _native.lib
+
+__all__ = ["Table", "DfaError", "dfa_build", "dfa_free", "dfa_export_stt", "dfa_count",
+           "dfa_find", "dfa_find_workspace_bytes", "dfa_find_status", "dfa_host_stage_bytes",
+           "dfa_find_host", "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
+           "DFA_OK", "DFA_EINVAL", "DFA_ETRUNC", "DFA_ETIMEOUT", "DFA_ECUDA", "DFA_EWORKSPACE",
+           "DFA_ENOMEM", "DFA_MAX_M"]
+
+
+class DfaError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {dfa_strerror(code)} (code {code})" if what else dfa_strerror(code))
+
+
+def dfa_strerror(code: int) -> str:
+    return _lib.dfa_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != DFA_OK:
+        raise DfaError(rc, what)
+    return rc
+
+
+def _cfg(cfg):
+    if cfg is None:
+        return None
+    if isinstance(cfg, dict):
+        cfg = dfa_config(**{k: int(v) for k, v in cfg.items()})
+    return ctypes.byref(cfg)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+class Table:
+    """Automaton of one pattern (library-owned host + device tables)."""
+
+    def __init__(self, pattern):
+        if isinstance(pattern, str):
+            pattern = pattern.encode("ascii")
+        pattern = bytes(pattern)
+        h = ctypes.c_void_p()
+        _check(_lib.dfa_build(pattern, len(pattern), ctypes.byref(h)), "dfa_build")
+        self._h = h
+        self.pattern = pattern.upper()
+        self.m = len(pattern)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise ValueError("table already freed")
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.dfa_free(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dfa_build(pattern) -> Table:
+    return Table(pattern)
+
+
+def dfa_free(table: Table) -> None:
+    table.free()
+
+
+def dfa_export_stt(table: Table) -> np.ndarray:
+    """The paper's sparse ASCII STT, (m+1, 256) uint8 (Sec. III-B, Table I)."""
+    out = np.zeros((table.m + 1) * 256, dtype=np.uint8)
+    _check(_lib.dfa_export_stt(table.handle, out.ctypes.data_as(ctypes.c_void_p), out.size),
+           "dfa_export_stt")
+    return out.reshape(table.m + 1, 256)
+
+
+def dfa_count(text, table: Table, count, cfg=None, stream=None) -> None:
+    """Enqueue a count; ``count`` is a 1-element int64 device tensor."""
+    _check(_lib.dfa_count(_ptr(text), int(text.numel()), table.handle, _ptr(count), _cfg(cfg),
+                          _stream(stream)), "dfa_count")
+
+
+def dfa_find_workspace_bytes(n: int, cfg=None) -> int:
+    return int(_lib.dfa_find_workspace_bytes(int(n), _cfg(cfg)))
+
+
+def dfa_find(text, table: Table, positions, count, workspace, cfg=None, stream=None,
+             n: int | None = None) -> None:
+    """Enqueue count + sorted start positions (int64 device tensor, capacity =
+    its length) into ``count`` (1-element int64 device tensor)."""
+    cap = int(positions.numel()) if positions is not None else 0
+    nbytes = int(text.numel()) if n is None else int(n)
+    _check(_lib.dfa_find(_ptr(text), nbytes, table.handle, _ptr(positions), cap, _ptr(count),
+                         _ptr(workspace), int(workspace.numel() * workspace.element_size()),
+                         _cfg(cfg), _stream(stream)), "dfa_find")
+
+
+def dfa_find_status(workspace, count, cap: int, stream=None):
+    """Synchronise and return (return code, count)."""
+    h = ctypes.c_uint64(0)
+    rc = _lib.dfa_find_status(_ptr(workspace), _ptr(count), int(cap), ctypes.byref(h),
+                              _stream(stream))
+    return rc, int(h.value)
+
+
+def dfa_host_stage_bytes(seg: int, cap: int) -> int:
+    return int(_lib.dfa_host_stage_bytes(int(seg), int(cap)))
+
+
+def dfa_find_host(h_text, table: Table, h_positions, stage, seg: int, stream=None):
+    """Host buffers in and out: ``h_text`` a CPU uint8 tensor (pinned for full
+    copy bandwidth), ``h_positions`` a CPU int64 tensor (or None), ``stage``
+    a device uint8 tensor of dfa_host_stage_bytes(seg, cap) bytes.
+    Returns (return code, count)."""
+    cap = int(h_positions.numel()) if h_positions is not None else 0
+    h = ctypes.c_uint64(0)
+    rc = _lib.dfa_find_host(_ptr(h_text), int(h_text.numel()), table.handle, _ptr(h_positions), cap,
+                            ctypes.byref(h), _ptr(stage), int(stage.numel()), int(seg),
+                            _stream(stream))
+    if rc not in (DFA_OK, DFA_ETRUNC):
+        raise DfaError(rc, "dfa_find_host")
+    return rc, int(h.value)
+
+
+# ----------------------------------------------------------- conveniences
+
+def _as_table(p):
+    return p if isinstance(p, Table) else Table(p)
+
+
+def count(text, pattern, cfg=None) -> int:
+    """Synchronous count on the current stream (allocates its output)."""
+    import torch
+    t = _as_table(pattern)
+    out = torch.zeros(1, dtype=torch.int64, device=text.device)
+    dfa_count(text, t, out, cfg=cfg)
+    return int(out.item())
+
+
+def find(text, pattern, cap: int | None = None, cfg=None):
+    """Synchronous find: returns (count, int64 positions tensor on device).
+    With cap=None the buffer grows until every position fits."""
+    import torch
+    t = _as_table(pattern)
+    dev = text.device
+    if cap is None:
+        cap = max(1024, text.numel() // 4096)
+    while True:
+        pos = torch.empty(max(int(cap), 1), dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        ws = torch.empty(dfa_find_workspace_bytes(text.numel(), cfg), dtype=torch.uint8, device=dev)
+        dfa_find(text, t, pos[:cap], cnt, ws, cfg=cfg)
+        rc, c = dfa_find_status(ws, cnt, cap)
+        if rc == DFA_OK:
+            return c, pos[:c]
+        if rc == DFA_ETRUNC:
+            cap = c
+            continue
+        raise DfaError(rc, "dfa_find")

@@ -1,0 +1,896 @@
+// Finite-automaton DNA pattern scan for GB300 (sm_103a): kernels and C ABI.
+//
+// The walk is the one of Algorithm 1 (Memeti & Pllana 2015, Sec. III-A):
+// the text is cut into per-thread chunks, each thread walks its chunk from
+// q0 and carries on m-1 bytes into its successor's chunk (Fig. 2a), so every
+// occurrence is found by exactly the thread whose chunk holds its start.
+// GPU-first choices (the paper's Xeon Phi design is prior art):
+//   * a warp's 32 lanes play the role of the paper's SIMD lanes (Fig. 2b),
+//     each lane walking its own contiguous chunk;
+//   * the transition table lives in shared memory; the default layout is a
+//     four-step composite table over 2-bit base codes, so one lookup
+//     advances the automaton by four bytes; the paper's sparse 256-column
+//     STT (Sec. III-B, Table I) is kept as a selectable layout;
+//   * text arrives in 16-byte vector loads; bytes outside A/C/G/T/a/c/g/t
+//     are detected four at a time and reset the walk to q0 (Sec. III-B);
+//   * counts are reduced by warp shuffles, then one atomic per CTA;
+//   * positions are compacted in text order in one pass: tiles are taken in
+//     order from an atomic ticket, a CTA scans its threads' counts, learns
+//     its tile's global offset by decoupled look-back over its predecessors'
+//     published sums, and writes its positions there.  Every wait is bounded
+//     and reports DFA_ETIMEOUT instead of hanging.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "dnadfa_internal.h"
+
+using namespace dnadfa;
+
+namespace {
+
+constexpr int kLayoutK4 = 1;
+constexpr int kLayoutStt = 2;
+constexpr int kSlots = 16;                  // staged positions per thread per tile
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = kFlagAgg - 1;
+constexpr unsigned kSpinLimit = 1u << 21;   // ~2 s with the back-off below
+constexpr int kWorkHeader = 2;              // [0] ticket, [1] status
+
+struct ScanArgs {
+    const uint8_t* text;
+    int64_t n;            // readable bytes
+    int64_t n_own;        // occurrences must start before n_own (<= n)
+    int64_t chunk;        // bytes per thread per tile, multiple of 16
+    int64_t ntiles;
+    const uint8_t* tab;   // device table allocation
+    int32_t m;
+    int32_t k4_bytes, d1_bytes, stt_bytes;
+    int32_t aligned;      // text is 16-byte aligned
+    unsigned long long* count;
+    int64_t* pos;
+    int64_t cap;
+    int64_t pos_base;                     // added to every position written
+    const unsigned long long* base_in;    // running total of earlier segments (or null)
+    unsigned long long* work;             // [ticket, status, desc[ntiles]]
+};
+
+struct SmemTab {
+    const uint16_t* k4;
+    const uint8_t* d1;
+    const uint8_t* stt;
+    uint32_t m;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ uint4 ldg16(const uint4* p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Zero iff all four bytes of x are bases (A C G T a c g t), see code_valid.
+__device__ __forceinline__ uint32_t word_bad(uint32_t x)
+{
+    uint32_t t = (x >> 2) & ~(x >> 1) & 0x01010101u;
+    return ((x ^ (t * 0x11u)) & 0xD9D9D9D9u) ^ 0x41414141u;
+}
+
+// Four automaton steps on the four bases of x, from the state in byte 0 of e.
+// (x & 0x06060606) holds the 2-bit codes at bits 8k+1; the multiply gathers
+// them, first byte lowest, into bits 24..31 without carries; byte_perm forms
+// the table index (state << 8) | code4.
+__device__ __forceinline__ uint32_t k4_next(const uint16_t* __restrict__ k4, uint32_t e, uint32_t x)
+{
+    uint32_t code = (x & 0x06060606u) * 0x00820820u;
+    uint32_t idx = __byte_perm(code, e, 0x7743u);
+    return k4[idx];
+}
+
+// One automaton step on one raw byte (any byte value).
+__device__ __forceinline__ uint32_t byte_next(const uint8_t* __restrict__ d1, uint32_t q, uint32_t c)
+{
+    uint32_t t = (c >> 2) & ~(c >> 1) & 1u;
+    bool ok = ((c ^ (t * 0x11u)) & 0xD9u) == 0x41u;
+    uint32_t nq = d1[q * 4u + ((c >> 1) & 3u)];
+    return ok ? nq : 0u;
+}
+
+// Bits i (i < 4) of an accept mask whose end offset r + i is below lim.
+__device__ __forceinline__ uint32_t lim_mask(uint32_t r, uint32_t lim)
+{
+    if (lim <= r) return 0u;
+    uint32_t d = lim - r;
+    return d >= 4 ? 0xFu : ((1u << d) - 1u);
+}
+
+// ---------------------------------------------------------------- sinks
+
+struct CountSink {
+    static constexpr bool kRecord = false;
+    __device__ __forceinline__ void put(uint32_t) {}
+};
+
+// Stages end offsets (relative to the chunk start) in shared memory,
+// slot j of thread t at slots[j * stride + t].
+struct SlotSink {
+    static constexpr bool kRecord = true;
+    uint16_t* slots;
+    uint32_t stride;
+    uint32_t n;
+    bool over;
+    __device__ __forceinline__ void put(uint32_t off)
+    {
+        if (n < (uint32_t)kSlots)
+            slots[n * stride] = (uint16_t)off;
+        else
+            over = true;
+        n++;
+    }
+};
+
+// Writes positions straight to global memory (overflow re-walk).
+struct GlobalSink {
+    static constexpr bool kRecord = true;
+    int64_t* pos;
+    int64_t cap;
+    int64_t idx;
+    int64_t start0;       // start position of end offset 0
+    __device__ __forceinline__ void put(uint32_t off)
+    {
+        if (idx < cap) pos[idx] = start0 + (int64_t)off;
+        idx++;
+    }
+};
+
+// ---------------------------------------------------------------- walk
+
+template <int LAYOUT, bool LIM, class Sink>
+struct Walker {
+    const SmemTab& T;
+    Sink& sink;
+    uint32_t e;      // K4: entry (state in byte 0); STT: state
+    uint32_t cnt;
+
+    __device__ __forceinline__ void accept_mask(uint32_t acc, uint32_t r)
+    {
+        if (Sink::kRecord) {
+            while (acc) {
+                uint32_t i = __ffs(acc) - 1;
+                sink.put(r + i);
+                acc &= acc - 1;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void word_k4(uint32_t x, uint32_t r, uint32_t lim)
+    {
+        e = k4_next(T.k4, e, x);
+        if (LIM) {
+            uint32_t acc = ((e >> K4_ACC_SHIFT) & 0xFu) & lim_mask(r, lim);
+            cnt += __popc(acc);
+            accept_mask(acc, r);
+        } else {
+            cnt += e >> K4_CNT_SHIFT;
+            if (Sink::kRecord) {
+                uint32_t acc = (e >> K4_ACC_SHIFT) & 0xFu;
+                if (acc) accept_mask(acc, r);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void byte_d1(uint32_t c, uint32_t r, uint32_t lim)
+    {
+        e = byte_next(T.d1, e, c);
+        if (e == T.m && (!LIM || r < lim)) {
+            cnt++;
+            if (Sink::kRecord) sink.put(r);
+        }
+    }
+
+    __device__ __forceinline__ void word_stt(uint32_t x, uint32_t r, uint32_t lim)
+    {
+#pragma unroll
+        for (uint32_t i = 0; i < 4; i++) {
+            e = T.stt[__byte_perm(x, e, 0x7740u | i)];
+            if (e == T.m && (!LIM || r + i < lim)) {
+                cnt++;
+                if (Sink::kRecord) sink.put(r + i);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void vec(uint4 v, uint32_t r, uint32_t lim)
+    {
+        if (LAYOUT == kLayoutK4) {
+            uint32_t bad = word_bad(v.x) | word_bad(v.y) | word_bad(v.z) | word_bad(v.w);
+            if (bad == 0u) {
+                word_k4(v.x, r, lim);
+                word_k4(v.y, r + 4, lim);
+                word_k4(v.z, r + 8, lim);
+                word_k4(v.w, r + 12, lim);
+            } else {
+                e &= 0xFFu;
+                uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+#pragma unroll
+                    for (int i = 0; i < 4; i++) byte_d1((w[k] >> (8 * i)) & 0xFFu, r + 4 * k + i, lim);
+            }
+        } else {
+            word_stt(v.x, r, lim);
+            word_stt(v.y, r + 4, lim);
+            word_stt(v.z, r + 8, lim);
+            word_stt(v.w, r + 12, lim);
+        }
+    }
+};
+
+// Walk the chunk [s, e) of the text: from q0 at s through min(e + m - 1, n),
+// counting (and handing to the sink) the occurrences that start in [s, e),
+// i.e. whose last byte lies below e + m - 1.  Returns the count.
+template <int LAYOUT, class Sink>
+__device__ uint32_t walk_chunk(const ScanArgs& a, const SmemTab& T, int64_t s, int64_t e, Sink& sink)
+{
+    const uint32_t m = T.m;
+    const int64_t len = e - s;
+    const uint32_t lim = (uint32_t)len + m - 1;               // end offsets must be < lim
+    const uint32_t h16 = (m - 1 + 15) & ~15u;                 // halo rounded to vectors
+    if (a.aligned && len == a.chunk && s + len + h16 <= a.n) {
+        const uint4* p = reinterpret_cast<const uint4*>(a.text + s);
+        const int nv = (int)(len >> 4);
+        Walker<LAYOUT, false, Sink> w{T, sink, 0u, 0u};
+        uint4 cur = ldg16(p);
+#pragma unroll 1
+        for (int i = 0; i < nv - 1; i++) {
+            uint4 nxt = ldg16(p + i + 1);
+            w.vec(cur, (uint32_t)i << 4, 0);
+            cur = nxt;
+        }
+        w.vec(cur, (uint32_t)(nv - 1) << 4, 0);
+        Walker<LAYOUT, true, Sink> h{T, sink, w.e, w.cnt};
+        for (uint32_t r = (uint32_t)len; r < (uint32_t)len + h16; r += 16)
+            h.vec(ldg16(reinterpret_cast<const uint4*>(a.text + s + r)), r, lim);
+        return h.cnt;
+    }
+    // boundary chunk: byte loads, exact bounds
+    const int64_t hi = min(e + (int64_t)m - 1, a.n);
+    uint32_t q = 0, cnt = 0;
+    for (int64_t j = s; j < hi; j++) {
+        uint32_t c = a.text[j];
+        if (LAYOUT == kLayoutK4)
+            q = byte_next(T.d1, q, c);
+        else
+            q = T.stt[(q << 8) | c];
+        if (q == m) {
+            cnt++;
+            if (Sink::kRecord) sink.put((uint32_t)(j - s));
+        }
+    }
+    return cnt;
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ SmemTab load_tables(const ScanArgs& a, uint8_t* smem)
+{
+    SmemTab T;
+    T.m = (uint32_t)a.m;
+    int bytes, src_off;
+    if (LAYOUT == kLayoutK4) {
+        bytes = a.k4_bytes + a.d1_bytes;
+        src_off = 0;
+        T.k4 = reinterpret_cast<const uint16_t*>(smem);
+        T.d1 = smem + a.k4_bytes;
+        T.stt = nullptr;
+    } else {
+        bytes = a.stt_bytes;
+        src_off = a.k4_bytes + a.d1_bytes;
+        T.k4 = nullptr;
+        T.d1 = nullptr;
+        T.stt = smem;
+    }
+    const uint4* src = reinterpret_cast<const uint4*>(a.tab + src_off);
+    uint4* dst = reinterpret_cast<uint4*>(smem);
+    for (int i = threadIdx.x; i < (bytes >> 4); i += blockDim.x) dst[i] = src[i];
+    return T;
+}
+
+__device__ __forceinline__ int table_smem_bytes_dev(const ScanArgs& a, int layout)
+{
+    return layout == kLayoutK4 ? a.k4_bytes + a.d1_bytes : a.stt_bytes;
+}
+
+// ---------------------------------------------------------------- kernels
+
+template <int LAYOUT, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_count(const ScanArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ unsigned long long s_warp[THREADS / 32];
+    const SmemTab T = load_tables<LAYOUT>(a, smem);
+    __syncthreads();
+    const int64_t tb = (int64_t)THREADS * a.chunk;
+    unsigned long long total = 0;
+    CountSink sink;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const int64_t s = tile * tb + (int64_t)threadIdx.x * a.chunk;
+        if (s < a.n_own) total += walk_chunk<LAYOUT>(a, T, s, min(s + a.chunk, a.n_own), sink);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = total;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long v = threadIdx.x < THREADS / 32 ? s_warp[threadIdx.x] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0 && v) atomicAdd(a.count, v);
+    }
+}
+
+// Decoupled look-back: publish this tile's sum, add up predecessors' sums
+// until one with an inclusive prefix is found, publish the inclusive prefix.
+// Returns the tile's exclusive offset.  Every wait is bounded; on give-up
+// bit 0 of the status word is set and the walk back stops.
+__device__ unsigned long long lookback(unsigned long long* work, int64_t tile, unsigned long long total)
+{
+    unsigned long long* desc = work + kWorkHeader;
+    if (tile == 0) {
+        st_release(desc, kFlagPre | total);
+        return 0ull;
+    }
+    st_release(desc + tile, kFlagAgg | total);
+    unsigned long long excl = 0;
+    for (int64_t j = tile - 1; j >= 0; j--) {
+        unsigned long long d;
+        unsigned spins = 0, ns = 32;
+        while (((d = ld_acquire(desc + j)) >> 62) == 0ull) {
+            if (++spins > kSpinLimit) {
+                atomicOr(reinterpret_cast<unsigned long long*>(work + 1), 1ull);
+                d = kFlagPre;
+                break;
+            }
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+        }
+        excl += d & kValMask;
+        if ((d >> 62) == 2ull) break;
+    }
+    st_release(desc + tile, kFlagPre | (excl + total));
+    return excl;
+}
+
+template <int LAYOUT, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t s_warp[THREADS / 32];
+    __shared__ int64_t s_tile;
+    __shared__ unsigned long long s_off;
+    const SmemTab T = load_tables<LAYOUT>(a, smem);
+    uint16_t* slots = reinterpret_cast<uint16_t*>(smem + ((table_smem_bytes_dev(a, LAYOUT) + 15) & ~15));
+    const unsigned long long base = a.base_in ? *a.base_in : 0ull;
+    const int64_t tb = (int64_t)THREADS * a.chunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(a.work, 1ull);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= a.ntiles) break;
+        const int64_t s = tile * tb + (int64_t)threadIdx.x * a.chunk;
+        const int64_t e = min(s + a.chunk, a.n_own);
+        SlotSink sink{slots + threadIdx.x, THREADS, 0u, false};
+        uint32_t cnt = 0;
+        if (s < a.n_own) cnt = walk_chunk<LAYOUT>(a, T, s, e, sink);
+
+        // block-wide exclusive scan of the per-thread counts
+        uint32_t v = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) s_warp[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < THREADS / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < THREADS / 32) s_warp[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t excl = v - cnt + (warp ? s_warp[warp - 1] : 0u);
+        const uint32_t total = s_warp[THREADS / 32 - 1];
+        if (threadIdx.x == 0) s_off = lookback(a.work, tile, total);
+        __syncthreads();
+        const unsigned long long off = s_off;
+        const int64_t g0 = (int64_t)(base + off + excl);
+        const int64_t start0 = a.pos_base + s - (a.m - 1);
+        if (cnt) {
+            if (!sink.over) {
+                for (uint32_t j = 0; j < cnt; j++) {
+                    int64_t g = g0 + j;
+                    if (g < a.cap) a.pos[g] = start0 + slots[j * THREADS + threadIdx.x];
+                }
+            } else if (g0 < a.cap) {
+                GlobalSink gs{a.pos, a.cap, g0, start0};
+                walk_chunk<LAYOUT>(a, T, s, e, gs);
+            }
+        }
+        if (tile == a.ntiles - 1 && threadIdx.x == 0) *a.count = base + off + total;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+#define CUDA_TRY(x)                                   \
+    do {                                              \
+        cudaError_t err_ = (x);                       \
+        if (err_ != cudaSuccess) return DFA_ECUDA;    \
+    } while (0)
+
+struct DeviceInfo {
+    int sms = 0;
+    int smem_optin = 0;
+    bool ok = false;
+};
+
+std::mutex g_mu;
+DeviceInfo g_dev[64];
+
+const DeviceInfo* device_info(int dev)
+{
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceInfo& d = g_dev[dev];
+    if (!d.ok) {
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return nullptr;
+        if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+            return nullptr;
+        d.ok = true;
+    }
+    return &d;
+}
+
+// Per (kernel, device): raise the dynamic shared memory limit once, and cache
+// occupancy by shared memory size.
+struct KernelCache {
+    const void* fn;
+    int dev;
+    int smem;
+    int occ;
+};
+std::vector<KernelCache> g_kc;
+
+int occupancy(const void* fn, int threads, int smem, int dev, int smem_optin)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& k : g_kc)
+        if (k.fn == fn && k.dev == dev && k.smem == smem) return k.occ;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 0;
+    const int dyn_max = smem_optin - (int)fa.sharedSizeBytes;
+    if (smem > dyn_max) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
+        return 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, (size_t)smem) != cudaSuccess)
+        occ = 0;
+    g_kc.push_back({fn, dev, smem, occ});
+    return occ;
+}
+
+struct Resolved {
+    int layout, threads, loader, ctas_per_sm;
+    int64_t chunk;
+};
+
+constexpr int64_t kMinDefaultTile = 256 * 64;   // workspace sizing for cfg == NULL
+
+int resolve(const dfa_config* cfg, int64_t n, int sms, Resolved* r)
+{
+    r->layout = cfg && cfg->layout ? cfg->layout : kLayoutK4;
+    r->threads = cfg && cfg->threads ? cfg->threads : 256;
+    r->loader = cfg && cfg->loader ? cfg->loader : 1;
+    r->ctas_per_sm = cfg ? cfg->ctas_per_sm : 0;
+    if (cfg && cfg->chunk) {
+        r->chunk = cfg->chunk;
+    } else {
+        int64_t per = (int64_t)r->threads * (sms > 0 ? sms : 152) * 8;
+        int64_t c = (n + per - 1) / per;
+        c = (c + 15) & ~(int64_t)15;
+        r->chunk = std::min<int64_t>(std::max<int64_t>(c, kMinDefaultTile / r->threads), 1024);
+    }
+    if (r->layout != kLayoutK4 && r->layout != kLayoutStt) return DFA_EINVAL;
+    if (r->threads != 128 && r->threads != 256 && r->threads != 512) return DFA_EINVAL;
+    if (r->chunk < 16 || r->chunk > 32768 || (r->chunk & 15)) return DFA_EINVAL;
+    if (r->loader != 1) return DFA_EINVAL;
+    if (r->ctas_per_sm < 0 || r->ctas_per_sm > 32) return DFA_EINVAL;
+    return DFA_OK;
+}
+
+typedef void (*KernelFn)(const ScanArgs);
+
+KernelFn pick_count(int layout, int threads)
+{
+    if (layout == kLayoutK4) {
+        if (threads == 128) return k_count<kLayoutK4, 128>;
+        if (threads == 256) return k_count<kLayoutK4, 256>;
+        return k_count<kLayoutK4, 512>;
+    }
+    if (threads == 128) return k_count<kLayoutStt, 128>;
+    if (threads == 256) return k_count<kLayoutStt, 256>;
+    return k_count<kLayoutStt, 512>;
+}
+
+KernelFn pick_find(int layout, int threads)
+{
+    if (layout == kLayoutK4) {
+        if (threads == 128) return k_find<kLayoutK4, 128>;
+        if (threads == 256) return k_find<kLayoutK4, 256>;
+        return k_find<kLayoutK4, 512>;
+    }
+    if (threads == 128) return k_find<kLayoutStt, 128>;
+    if (threads == 256) return k_find<kLayoutStt, 256>;
+    return k_find<kLayoutStt, 512>;
+}
+
+int table_smem(const dfa_table* t, int layout)
+{
+    return layout == kLayoutK4 ? t->view.k4_bytes + t->view.d1_bytes : t->view.stt_bytes;
+}
+
+void fill_args(ScanArgs* a, const uint8_t* text, int64_t n, int64_t n_own, const dfa_table* t,
+               const Resolved& r)
+{
+    memset(a, 0, sizeof(*a));
+    a->text = text;
+    a->n = n;
+    a->n_own = n_own;
+    a->chunk = r.chunk;
+    const int64_t tb = (int64_t)r.threads * r.chunk;
+    a->ntiles = (n_own + tb - 1) / tb;
+    a->tab = static_cast<const uint8_t*>(t->d_mem);
+    a->m = t->m;
+    a->k4_bytes = t->view.k4_bytes;
+    a->d1_bytes = t->view.d1_bytes;
+    a->stt_bytes = t->view.stt_bytes;
+    a->aligned = ((uintptr_t)text & 15u) == 0;
+}
+
+int current_device_info(const DeviceInfo** di, int* dev)
+{
+    if (cudaGetDevice(dev) != cudaSuccess) return DFA_ECUDA;
+    *di = device_info(*dev);
+    return *di ? DFA_OK : DFA_ECUDA;
+}
+
+int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t* d_count,
+                 const dfa_config* cfg, cudaStream_t st)
+{
+    const DeviceInfo* di;
+    int dev;
+    int rc = current_device_info(&di, &dev);
+    if (rc) return rc;
+    if (dev != t->device) return DFA_EINVAL;
+    Resolved r;
+    rc = resolve(cfg, n, di->sms, &r);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st));
+    if (n < t->m) return DFA_OK;
+    ScanArgs a;
+    fill_args(&a, d_text, n, n, t, r);
+    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    KernelFn fn = pick_count(r.layout, r.threads);
+    const int smem = table_smem(t, r.layout);
+    int occ = occupancy((const void*)fn, r.threads, smem, dev, di->smem_optin);
+    if (occ <= 0) return DFA_ECUDA;
+    if (r.ctas_per_sm) occ = std::min(occ, r.ctas_per_sm);
+    int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
+    fn<<<(unsigned)grid, r.threads, smem, st>>>(a);
+    CUDA_TRY(cudaGetLastError());
+    return DFA_OK;
+}
+
+int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
+
+// Shared by dfa_find and the segmented host path.
+int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table* t, int64_t* d_pos,
+                int64_t cap, uint64_t* d_count, const uint64_t* d_base, int64_t pos_base, void* d_work,
+                int64_t work_bytes, const dfa_config* cfg, cudaStream_t st)
+{
+    const DeviceInfo* di;
+    int dev;
+    int rc = current_device_info(&di, &dev);
+    if (rc) return rc;
+    if (dev != t->device) return DFA_EINVAL;
+    Resolved r;
+    rc = resolve(cfg, n_own, di->sms, &r);
+    if (rc) return rc;
+    ScanArgs a;
+    fill_args(&a, d_text, n, n_own, t, r);
+    const int64_t need = work_bytes_for(a.ntiles);
+    if (work_bytes < need) return DFA_EWORKSPACE;
+    CUDA_TRY(cudaMemsetAsync(d_work, 0, (size_t)need, st));
+    if (a.ntiles == 0) {
+        if (d_base)
+            CUDA_TRY(cudaMemcpyAsync(d_count, d_base, 8, cudaMemcpyDeviceToDevice, st));
+        else
+            CUDA_TRY(cudaMemsetAsync(d_count, 0, 8, st));
+        return DFA_OK;
+    }
+    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    a.pos = d_pos;
+    a.cap = d_pos ? cap : 0;
+    a.pos_base = pos_base;
+    a.base_in = reinterpret_cast<const unsigned long long*>(d_base);
+    a.work = static_cast<unsigned long long*>(d_work);
+    KernelFn fn = pick_find(r.layout, r.threads);
+    const int smem = ((table_smem(t, r.layout) + 15) & ~15) + kSlots * r.threads * 2;
+    int occ = occupancy((const void*)fn, r.threads, smem, dev, di->smem_optin);
+    if (occ <= 0) return DFA_ECUDA;
+    if (r.ctas_per_sm) occ = std::min(occ, r.ctas_per_sm);
+    int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
+    fn<<<(unsigned)grid, r.threads, smem, st>>>(a);
+    CUDA_TRY(cudaGetLastError());
+    return DFA_OK;
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+
+extern "C" {
+
+int dfa_build(const char* pattern, int32_t m, dfa_table** out)
+{
+    if (!pattern || !out || m < 1 || m > DFA_MAX_M) return DFA_EINVAL;
+    *out = nullptr;
+    dfa_table* t = new (std::nothrow) dfa_table();
+    if (!t) return DFA_ENOMEM;
+    t->m = m;
+    for (int j = 0; j < m; j++) {
+        uint32_t c = (uint8_t)pattern[j];
+        if (!code_valid(c)) {
+            delete t;
+            return DFA_EINVAL;
+        }
+        t->pattern[j] = (uint8_t)(c & 0xDFu);
+    }
+    int rc = build_host_tables(t);
+    if (rc) {
+        delete t;
+        return rc;
+    }
+    t->view.m = m;
+    t->view.k4_bytes = (m + 1) * 512;
+    t->view.d1_bytes = ((m + 1) * 4 + 15) & ~15;
+    t->view.stt_bytes = (m + 1) * 256;
+    t->d_bytes = (size_t)t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes;
+    if (cudaGetDevice(&t->device) != cudaSuccess || cudaMalloc(&t->d_mem, t->d_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete t;
+        return DFA_ECUDA;
+    }
+    std::vector<uint8_t> img(t->d_bytes, 0);
+    memcpy(img.data(), t->k4.data(), (size_t)t->view.k4_bytes);
+    memcpy(img.data() + t->view.k4_bytes, t->d1.data(), t->d1.size());
+    memcpy(img.data() + t->view.k4_bytes + t->view.d1_bytes, t->stt.data(), t->stt.size());
+    if (cudaMemcpy(t->d_mem, img.data(), t->d_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(t->d_mem);
+        delete t;
+        return DFA_ECUDA;
+    }
+    t->view.base = static_cast<const uint8_t*>(t->d_mem);
+    *out = t;
+    return DFA_OK;
+}
+
+void dfa_free(dfa_table* table)
+{
+    if (!table) return;
+    if (table->d_mem) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != table->device) cudaSetDevice(table->device);
+        cudaFree(table->d_mem);
+        if (cur >= 0 && cur != table->device) cudaSetDevice(cur);
+    }
+    delete table;
+}
+
+int32_t dfa_pattern_length(const dfa_table* table) { return table ? table->m : -1; }
+
+int dfa_export_stt(const dfa_table* table, uint8_t* h_stt, int64_t bytes)
+{
+    if (!table || !h_stt || bytes < (int64_t)table->stt.size()) return DFA_EINVAL;
+    memcpy(h_stt, table->stt.data(), table->stt.size());
+    return DFA_OK;
+}
+
+int dfa_count(const uint8_t* d_text, int64_t n, const dfa_table* table, uint64_t* d_count,
+              const dfa_config* cfg, void* stream)
+{
+    if (!table || !d_count || n < 0 || (n > 0 && !d_text)) return DFA_EINVAL;
+    return launch_count(d_text, n, table, d_count, cfg, static_cast<cudaStream_t>(stream));
+}
+
+int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg)
+{
+    if (n < 0) return -1;
+    int64_t tb;
+    if (cfg && cfg->threads && cfg->chunk) {
+        tb = (int64_t)cfg->threads * cfg->chunk;
+        if (tb <= 0) return -1;
+    } else {
+        tb = kMinDefaultTile;
+    }
+    return work_bytes_for((n + tb - 1) / tb);
+}
+
+int dfa_find(const uint8_t* d_text, int64_t n, const dfa_table* table, int64_t* d_pos, int64_t cap,
+             uint64_t* d_count, void* d_work, int64_t work_bytes, const dfa_config* cfg, void* stream)
+{
+    if (!table || !d_count || !d_work || n < 0 || (n > 0 && !d_text) || cap < 0 ||
+        (cap > 0 && !d_pos))
+        return DFA_EINVAL;
+    return launch_find(d_text, n, n, table, d_pos, cap, d_count, nullptr, 0, d_work, work_bytes, cfg,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int dfa_find_status(const void* d_work, const uint64_t* d_count, int64_t cap, uint64_t* h_count,
+                    void* stream)
+{
+    if (!d_work || !d_count) return DFA_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long hdr[2] = {0, 0};
+    uint64_t cnt = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return DFA_ECUDA;
+    if (cudaMemcpy(hdr, d_work, sizeof(hdr), cudaMemcpyDeviceToHost) != cudaSuccess) return DFA_ECUDA;
+    if (cudaMemcpy(&cnt, d_count, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return DFA_ECUDA;
+    if (h_count) *h_count = cnt;
+    if (hdr[1] & 1ull) return DFA_ETIMEOUT;
+    if ((int64_t)cnt > cap) return DFA_ETRUNC;
+    return DFA_OK;
+}
+
+// Segmented host path: staging = [2 segment buffers][positions][2 counters][workspace]
+static int64_t stage_layout(int64_t seg, int64_t cap, int64_t* seg_stride, int64_t* pos_off,
+                            int64_t* cnt_off, int64_t* work_off)
+{
+    *seg_stride = (seg + DFA_MAX_M + 255) & ~(int64_t)255;
+    *pos_off = 2 * *seg_stride;
+    *cnt_off = *pos_off + ((cap * 8 + 255) & ~(int64_t)255);
+    *work_off = *cnt_off + 256;
+    int64_t wb = dfa_find_workspace_bytes(seg, nullptr);
+    return *work_off + wb;
+}
+
+int64_t dfa_host_stage_bytes(int64_t seg, int64_t cap)
+{
+    if (seg < (1 << 20) || cap < 0) return -1;
+    int64_t a, b, c, d;
+    return stage_layout(seg, cap, &a, &b, &c, &d);
+}
+
+int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int64_t* h_pos, int64_t cap,
+                  uint64_t* h_count, void* d_stage, int64_t stage_bytes, int64_t seg, void* stream)
+{
+    if (!table || !h_count || !d_stage || n < 0 || (n > 0 && !h_text) || cap < 0 ||
+        (cap > 0 && !h_pos) || seg < (1 << 20))
+        return DFA_EINVAL;
+    int64_t seg_stride, pos_off, cnt_off, work_off;
+    int64_t need = stage_layout(seg, cap, &seg_stride, &pos_off, &cnt_off, &work_off);
+    if (stage_bytes < need) return DFA_EWORKSPACE;
+    uint8_t* stage = static_cast<uint8_t*>(d_stage);
+    int64_t* d_pos = cap > 0 ? reinterpret_cast<int64_t*>(stage + pos_off) : nullptr;
+    uint64_t* d_cnt = reinterpret_cast<uint64_t*>(stage + cnt_off);   // two ping-pong counters
+    void* d_work = stage + work_off;
+    const int64_t work_bytes = stage_bytes - work_off;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int m = table->m;
+
+    cudaStream_t cp;
+    cudaEvent_t copied[2], scanned[2];
+    if (cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking) != cudaSuccess) return DFA_ECUDA;
+    int rc = DFA_OK;
+    for (int i = 0; i < 2; i++) {
+        cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&scanned[i], cudaEventDisableTiming);
+    }
+    if (cudaMemsetAsync(d_cnt, 0, 16, st) != cudaSuccess) rc = DFA_ECUDA;
+    // the copy stream starts after the counters are cleared
+    cudaEventRecord(scanned[1], st);
+    cudaEventRecord(scanned[0], st);
+    const int64_t nseg = n > 0 ? (n + seg - 1) / seg : 0;
+    for (int64_t k = 0; k < nseg && rc == DFA_OK; k++) {
+        const int b = (int)(k & 1);
+        const int64_t lo = k * seg;
+        const int64_t own = std::min(seg, n - lo);
+        const int64_t avail = std::min(own + m - 1, n - lo);
+        uint8_t* buf = stage + b * seg_stride;
+        // buffer b was last read by scan k-2
+        if (cudaStreamWaitEvent(cp, scanned[b], 0) != cudaSuccess ||
+            cudaMemcpyAsync(buf, h_text + lo, (size_t)avail, cudaMemcpyHostToDevice, cp) != cudaSuccess ||
+            cudaEventRecord(copied[b], cp) != cudaSuccess || cudaStreamWaitEvent(st, copied[b], 0) != cudaSuccess) {
+            rc = DFA_ECUDA;
+            break;
+        }
+        const uint64_t* base = d_cnt + ((k + 1) & 1);     // previous segment's running total
+        uint64_t* outc = d_cnt + (k & 1);
+        rc = launch_find(buf, avail, own, table, d_pos, cap, outc, k ? base : nullptr, lo, d_work,
+                         work_bytes, nullptr, st);
+        if (rc == DFA_OK && cudaEventRecord(scanned[b], st) != cudaSuccess) rc = DFA_ECUDA;
+    }
+    uint64_t cnt = 0;
+    unsigned long long hdr[2] = {0, 0};
+    if (rc == DFA_OK) {
+        const uint64_t* last = nseg ? d_cnt + ((nseg - 1) & 1) : d_cnt;
+        if (cudaMemcpyAsync(&cnt, last, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hdr, d_work, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = DFA_ECUDA;
+    }
+    if (rc == DFA_OK && cap > 0 && cnt > 0) {
+        int64_t k = std::min<int64_t>((int64_t)cnt, cap);
+        if (cudaMemcpyAsync(h_pos, d_pos, (size_t)k * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = DFA_ECUDA;
+    }
+    cudaStreamSynchronize(cp);
+    for (int i = 0; i < 2; i++) {
+        cudaEventDestroy(copied[i]);
+        cudaEventDestroy(scanned[i]);
+    }
+    cudaStreamDestroy(cp);
+    if (rc != DFA_OK) return rc;
+    *h_count = cnt;
+    if (hdr[1] & 1ull) return DFA_ETIMEOUT;
+    if ((int64_t)cnt > cap) return DFA_ETRUNC;
+    return DFA_OK;
+}
+
+const char* dfa_strerror(int code)
+{
+    switch (code) {
+    case DFA_OK: return "ok";
+    case DFA_EINVAL: return "invalid argument";
+    case DFA_ETRUNC: return "more occurrences than the position buffer holds";
+    case DFA_ETIMEOUT: return "a bounded device-side wait gave up";
+    case DFA_ECUDA: return "CUDA runtime error";
+    case DFA_EWORKSPACE: return "workspace too small";
+    case DFA_ENOMEM: return "out of memory";
+    default: return "unknown error";
+    }
+}
+
+const char* dfa_version(void) { return "dnadfa 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -76,13 +76,22 @@ static int64_t ilog2_q32(uint64_t x)
 
 /* Geometric run length on {1, 2, ...} with the given mean (>= 2), by
  * inversion: L = 1 + floor(log(U) / log(1 - 1/mean)), U uniform on (0,1]. */
-static int64_t geometric(uint64_t draw, uint64_t mean)
+static int64_t geo_scale(uint64_t mean)
+{
+    int64_t b = ilog2_q32(mean) - ilog2_q32(mean - 1);     /* -log2(1-1/mean) in Q32, > 0 */
+    return b > 0 ? b : 1;
+}
+
+static int64_t geometric_b(uint64_t draw, int64_t b)
 {
     uint64_t u = (draw >> 11) + 1;                         /* [1, 2^53] */
     int64_t a = ((int64_t)53 << 32) - ilog2_q32(u);        /* -log2(U) in Q32, >= 0 */
-    int64_t b = ilog2_q32(mean) - ilog2_q32(mean - 1);     /* -log2(1-1/mean) in Q32, > 0 */
-    if (b <= 0) b = 1;
     return 1 + a / b;
+}
+
+static int64_t geometric(uint64_t draw, uint64_t mean)
+{
+    return geometric_b(draw, geo_scale(mean));
 }
 
 int64_t synth_geometric(uint64_t seed, uint64_t stream, uint64_t k, uint64_t mean)
@@ -153,11 +162,12 @@ void synth_genome(uint8_t* out, int64_t n, uint64_t seed, int32_t gc,
     /* soft-mask: alternating unmasked / masked runs, first run unmasked */
     if (mask_mean >= 2) {
         const uint64_t key = sm64_key(seed, 1);
+        const int64_t b = geo_scale(mask_mean);
         uint64_t k = 0;
         int64_t pos = 0;
         int masked = 0;
         while (pos < n) {
-            int64_t len = geometric(sm64_at(key, k++), mask_mean);
+            int64_t len = geometric_b(sm64_at(key, k++), b);
             int64_t end = pos + len < n ? pos + len : n;
             if (masked)
                 for (int64_t i = pos; i < end; i++) out[i] |= 0x20;
@@ -168,11 +178,12 @@ void synth_genome(uint8_t* out, int64_t n, uint64_t seed, int32_t gc,
     /* N blocks: alternating non-N gaps / N runs, first run a gap */
     if (n_gap_mean >= 2 && n_run_mean >= 2) {
         const uint64_t key = sm64_key(seed, 2);
+        const int64_t b_run = geo_scale(n_run_mean), b_gap = geo_scale(n_gap_mean);
         uint64_t k = 0;
         int64_t pos = 0;
         int isn = 0;
         while (pos < n) {
-            int64_t len = geometric(sm64_at(key, k++), isn ? n_run_mean : n_gap_mean);
+            int64_t len = geometric_b(sm64_at(key, k++), isn ? b_run : b_gap);
             int64_t end = pos + len < n ? pos + len : n;
             if (isn) memset(out + pos, 'N', (size_t)(end - pos));
             pos = end;

@@ -1,0 +1,206 @@
+"""Parity of the CUDA scan (through the C ABI) with the CPU oracle.
+
+Counts and positions are integers: the bar is bit-exact equality.
+Every input is seeded and synthetic (``synth``).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import GOLDEN
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = [
+    None,
+    dict(layout=1, threads=128, chunk=16),
+    dict(layout=1, threads=256, chunk=48),
+    dict(layout=1, threads=512, chunk=256),
+    dict(layout=2, threads=256, chunk=64),
+    dict(layout=2, threads=128, chunk=1008),
+]
+
+
+def _dev(gpu, arr):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(arr)).cuda()
+
+
+def _find(gpu, text_dev, pat, cfg=None, cap=None):
+    c, p = gpu.find(text_dev, pat, cap=cap, cfg=cfg)
+    return c, p.cpu().numpy()
+
+
+def _check(gpu, text_np, pat, cfg=None, text_dev=None):
+    if text_dev is None:
+        text_dev = _dev(gpu, text_np)
+    want_c, want_p = oracle.find_brute(text_np, pat)
+    c, p = _find(gpu, text_dev, pat, cfg)
+    assert c == want_c, (len(pat), cfg, c, want_c)
+    assert np.array_equal(p, want_p), (len(pat), cfg)
+    assert gpu.count(text_dev, pat, cfg=cfg) == want_c
+    return want_c
+
+
+def _lines(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def test_fixed_facts(gpu):
+    for text, pat, cnt, pos in _lines("fixed_facts.txt"):
+        t = np.frombuffer(text.encode(), dtype=np.uint8).copy()
+        c, p = _find(gpu, _dev(gpu, t), pat.encode())
+        assert c == int(cnt)
+        assert list(p) == ([] if pos == "-" else [int(x) for x in pos.split(",")])
+
+
+def test_export_stt_is_paper_table(gpu):
+    for pat in (b"ACGT", b"AAAA", b"GATTACA", synth.pattern(64, 3)):
+        stt, f, _ = oracle.stt_ascii([pat])
+        t = gpu.dfa_build(pat)
+        assert np.array_equal(gpu.dfa_export_stt(t).astype(np.int32), stt)
+        assert f == len(pat)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_random_genome_all_lengths(gpu, cfg):
+    # several tiles plus a ragged tail under every configuration
+    n = 300_007
+    t = synth.genome_text(n, 21, mask_mean=60, n_gap_mean=20_000, n_run_mean=700)
+    td = _dev(gpu, t)
+    for m in list(range(1, 17)) + [31, 32, 33, 47, 63, 64]:
+        _check(gpu, t, synth.pattern(m, 100 + m), cfg, td)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS[:4])
+def test_planted_long_patterns(gpu, cfg):
+    n = 1 << 20
+    t = synth.genome_text(n, 8)
+    rng_pos = synth.uniform_ints(400, n - 64, 31)
+    for m in (16, 32, 64):
+        pat = synth.pattern(m, 40 + m)
+        tt = t.copy()
+        pos = np.unique(rng_pos // (2 * m) * (2 * m))
+        synth.plant(tt, pat, pos)
+        assert _check(gpu, tt, pat, cfg) >= len(pos)
+
+
+def test_border_plants(gpu):
+    # occurrences planted at +-m around every chunk / tile border
+    cfg = dict(layout=1, threads=128, chunk=64)
+    n = 128 * 64 * 6 + 77
+    for m in (5, 16, 33, 64):
+        t = synth.genome_text(n, 3, n_gap_mean=0)
+        pat = synth.pattern(m, 7 * m)
+        borders = np.arange(0, n, 64)
+        pos = np.unique(np.clip(np.concatenate([borders - m + 1, borders - 1, borders,
+                                                borders - m // 2]), 0, n - m))
+        pos = pos[np.concatenate([[True], np.diff(pos) >= m])]  # keep them disjoint
+        synth.plant(t, pat, pos)
+        assert _check(gpu, t, pat, cfg) >= len(pos)
+
+
+def test_edge_cases(gpu):
+    import torch
+    # empty text, shorter than the pattern, exactly the pattern
+    empty = torch.empty(0, dtype=torch.uint8, device="cuda")
+    assert gpu.find(empty, b"ACGT")[0] == 0 and gpu.count(empty, b"ACGT") == 0
+    for n in range(0, 40):
+        t = synth.uniform_text(n, n)
+        for m in (1, 3, 8, 17):
+            _check(gpu, t, synth.pattern(m, m + 5))
+    _check(gpu, np.frombuffer(b"ACGT", np.uint8).copy(), b"ACGT")
+    # no bases at all, every byte value
+    _check(gpu, np.full(100_000, ord("N"), np.uint8), b"A")
+    allbytes = np.tile(np.arange(256, dtype=np.uint8), 500)
+    for pat in (b"A", b"C", b"T", b"G", b"AB"[:1]):
+        _check(gpu, allbytes, pat)
+    # lower case only
+    _check(gpu, np.frombuffer(b"acgt" * 10000, np.uint8).copy(), b"GTAC")
+
+
+def test_dense_matches_overflow_and_truncation(gpu):
+    # every position matches: exercises the per-thread staging overflow path
+    n = 200_003
+    t = np.full(n, ord("A"), np.uint8)
+    for cfg in (None, dict(layout=1, threads=128, chunk=1024), dict(layout=2, threads=256, chunk=512)):
+        for m in (1, 4, 64):
+            _check(gpu, t, b"A" * m, cfg)
+    # cap smaller than the count: exact count, first cap positions, ETRUNC
+    import torch
+    td = _dev(gpu, t)
+    tab = gpu.dfa_build(b"AAAA")
+    cap = 1000
+    pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = torch.empty(gpu.dfa_find_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    gpu.dfa_find(td, tab, pos, cnt, ws)
+    rc, c = gpu.dfa_find_status(ws, cnt, cap)
+    assert rc == gpu.DFA_ETRUNC and c == n - 3
+    assert pos.cpu().numpy().tolist() == list(range(cap))
+
+
+def test_misaligned_text(gpu):
+    t = synth.genome_text(100_000, 5, mask_mean=50)
+    td = _dev(gpu, t)
+    for off in (1, 3, 8, 15):
+        sub = t[off:]
+        for m in (4, 8, 33):
+            pat = synth.pattern(m, 60 + m + off)
+            want_c, want_p = oracle.find_brute(sub, pat)
+            c, p = _find(gpu, td[off:], pat)
+            assert c == want_c and np.array_equal(p, want_p)
+
+
+def test_config1_uniform_16MiB_m8(gpu):
+    """The 16 MiB uniform text, m = 8, full positions."""
+    n = 16 * 1024 * 1024
+    t = synth.uniform_text(n, 0)
+    pat = synth.pattern(8, 1)
+    c = _check(gpu, t, pat)
+    assert 100 < c < 500          # ~256 expected
+
+
+def test_host_buffer_path(gpu):
+    import torch
+    n = 5_000_000
+    t = synth.genome_text(n, 9)
+    ht = torch.from_numpy(t).pin_memory()
+    for m in (4, 8, 16):
+        pat = synth.pattern(m, 90 + m)
+        want_c, want_p = oracle.find_brute(t, pat)
+        tab = gpu.dfa_build(pat)
+        for seg in (1 << 20, (1 << 20) + 16 * 1000 + 7, 1 << 23):
+            cap = want_c + 10
+            hp = torch.zeros(cap, dtype=torch.int64)
+            stage = torch.empty(gpu.dfa_host_stage_bytes(seg, cap), dtype=torch.uint8, device="cuda")
+            rc, c = gpu.dfa_find_host(ht, tab, hp, stage, seg)
+            assert rc == gpu.DFA_OK and c == want_c
+            assert np.array_equal(hp[:c].numpy(), want_p)
+
+
+def test_streams_and_concurrency(gpu):
+    import torch
+    t = synth.genome_text(2_000_000, 13)
+    td = _dev(gpu, t)
+    pats = [synth.pattern(m, 500 + m) for m in (4, 6, 8, 12)]
+    want = [oracle.find_brute(t, p) for p in pats]
+    streams = [torch.cuda.Stream() for _ in pats]
+    outs = []
+    for p, s in zip(pats, streams):
+        with torch.cuda.stream(s):
+            tab = gpu.dfa_build(p)
+            cap = 200_000
+            pos = torch.empty(cap, dtype=torch.int64, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            ws = torch.empty(gpu.dfa_find_workspace_bytes(td.numel()), dtype=torch.uint8, device="cuda")
+            gpu.dfa_find(td, tab, pos, cnt, ws)
+            outs.append((tab, pos, cnt, ws, s))
+    for (tab, pos, cnt, ws, s), (wc, wp) in zip(outs, want):
+        rc, c = gpu.dfa_find_status(ws, cnt, pos.numel(), stream=s)
+        assert rc == gpu.DFA_OK and c == wc
+        assert np.array_equal(pos[:c].cpu().numpy(), wp)
