@@ -46,7 +46,7 @@ DOMINANT_KERNEL = "k_find<1,256>"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=TEXT_BYTES)
@@ -87,7 +87,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -128,6 +128,19 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def gpu_smi_id(local):
+    """nvidia-smi identifier of the CUDA device `local` (UUID when known)."""
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(local).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        parts = [p for p in vis.split(",") if p.strip()]
+        return parts[local] if local < len(parts) else str(local)
 
 
 def measured_peak_hbm():
@@ -281,7 +294,7 @@ def run_ours(args):
 
     if world > 1:
         torch.distributed.barrier()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(gpu_smi_id(local))
     clocks.start()
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
@@ -334,9 +347,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        e2e_steps = min(args.steps, 20)
         t0 = time.perf_counter()
         d2h = 0
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             for i, t in enumerate(tables):
                 rc, c = dd.dfa_find_host(host, t, hpos[i], stage, seg, stream=stream)
                 assert c == counts[i]
@@ -346,8 +360,9 @@ def run_ours(args):
             tt = torch.tensor([dt], device=dev)
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             dt = float(tt.item())
-        e2e = {"value": round(bytes_per_step * world * args.steps / dt / 1e9, 3), "unit": UNIT,
-               "h2d_bytes_per_step": int(bytes_per_step), "d2h_bytes_per_step": int(d2h // args.steps),
+        e2e = {"value": round(bytes_per_step * world * e2e_steps / dt / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(bytes_per_step), "d2h_bytes_per_step": int(d2h // e2e_steps),
+               "steps": e2e_steps,
                "entry_point": "dfa_find_host (pinned host text, segments of 256 MiB, copies overlapped)"}
 
     cpu = None

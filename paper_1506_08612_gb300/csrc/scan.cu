@@ -19,6 +19,8 @@
 //     its tile's global offset by decoupled look-back over its predecessors'
 //     published sums, and writes its positions there.  Every wait is bounded
 //     and reports DFA_ETIMEOUT instead of hanging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +28,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "dnadfa_internal.h"
 
@@ -138,11 +141,12 @@ struct SlotSink {
     static constexpr bool kRecord = true;
     uint16_t* slots;
     uint32_t stride;
+    uint32_t cap;
     uint32_t n;
     bool over;
     __device__ __forceinline__ void put(uint32_t off)
     {
-        if (n < (uint32_t)kSlots)
+        if (n < cap)
             slots[n * stride] = (uint16_t)off;
         else
             over = true;
@@ -326,7 +330,7 @@ __device__ __forceinline__ int table_smem_bytes_dev(const ScanArgs& a, int layou
 template <int LAYOUT, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_count(const ScanArgs a)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ unsigned long long s_warp[THREADS / 32];
     const SmemTab T = load_tables<LAYOUT>(a, smem);
     __syncthreads();
@@ -384,7 +388,7 @@ __device__ unsigned long long lookback(unsigned long long* work, int64_t tile, u
 template <int LAYOUT, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint32_t s_warp[THREADS / 32];
     __shared__ int64_t s_tile;
     __shared__ unsigned long long s_off;
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
         if (tile >= a.ntiles) break;
         const int64_t s = tile * tb + (int64_t)threadIdx.x * a.chunk;
         const int64_t e = min(s + a.chunk, a.n_own);
-        SlotSink sink{slots + threadIdx.x, THREADS, 0u, false};
+        SlotSink sink{slots + threadIdx.x, THREADS, (uint32_t)kSlots, 0u, false};
         uint32_t cnt = 0;
         if (s < a.n_own) cnt = walk_chunk<LAYOUT>(a, T, s, e, sink);
 
@@ -446,6 +450,425 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
     }
 }
 
+// ---------------------------------------------------------------- TMA-staged kernel
+//
+// Persistent, warp-specialised form of the same walk.  A tile is 256 rows of
+// C bytes (row r of tile k = text[(256k + r)C, (256k + r + 1)C)); thread r
+// of the walker warps walks row r.  The text is viewed as a 2-D tensor of
+// C-byte rows and streamed by TMA (cp.async.bulk.tensor.2d) in stages of
+// 80 bytes x 256 rows into a ring of shared-memory buffers; a final "halo"
+// stage brings the first 80 bytes of rows r+1, i.e. the m-1 bytes of overlap
+// each row needs (Algorithm 1).  80-byte rows (5 x 16 B, an odd count) make
+// the walkers' 16-byte shared loads conflict-free without swizzling.
+//   warp 8 (producer): takes tile tickets, issues the TMA loads;
+//   warp 9 (scheduler, find only): sums the walker warps' counts of a tile,
+//          publishes them and resolves the tile's global offset by a
+//          warp-parallel decoupled look-back, while the walkers already walk
+//          the next tile; a tile's positions are written one tile later.
+// Rows whose chunk or overlap runs past the full rows of the tensor (the end
+// of the text) are walked from global memory by their thread instead.
+
+constexpr int kRows = 256;
+constexpr int kStageW = 80;
+constexpr int kStageBytes = kRows * kStageW;
+constexpr int kWalkWarps = kRows / 32;
+constexpr int kTmaThreads = kRows + 64;
+constexpr int kTSlots = 8;
+constexpr int kMaxStages = 8;
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+
+struct TmaArgs {
+    ScanArgs a;
+    int64_t nrows_full;   // rows of C bytes fully inside [0, n): the tensor's rows
+    int32_t nst;          // stages in the ring
+    int32_t sps;          // body stages per tile (C / 80)
+    int32_t table_bytes;  // shared bytes of the table, 128-aligned
+    // where a wait that gave up is reported: the find workspace's status
+    // word (bit 1), or bit 63 of the count for a count without workspace
+    unsigned long long* fail_word;
+    unsigned long long fail_bit;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void named_sync_walkers()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kRows) : "memory");
+}
+
+// Bounded wait on an mbarrier phase.  Gives up after ~2 s (status bit 1 and
+// the CTA's abort flag set) or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          const TmaArgs& p)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            atomicOr(p.fail_word, p.fail_bit);
+            return false;
+        }
+    }
+}
+
+// mbar_wait for a whole warp: every lane gets the same outcome, so that an
+// abort racing with a completing phase cannot split the warp.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          const TmaArgs& p)
+{
+    const bool ok = mbar_wait(bar, parity, abort_flag, p);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Warp-parallel decoupled look-back: lane l inspects the descriptor of tile
+// (end - l); the window slides back 32 tiles at a time until it holds an
+// inclusive prefix.  Returns the tile's exclusive offset (all lanes).
+__device__ unsigned long long lookback_warp(unsigned long long* work, int64_t tile,
+                                            unsigned long long total, int lane)
+{
+    unsigned long long* desc = work + kWorkHeader;
+    if (tile == 0) {
+        if (lane == 0) st_release(desc, kFlagPre | total);
+        return 0ull;
+    }
+    if (lane == 0) st_release(desc + tile, kFlagAgg | total);
+    unsigned long long excl = 0;
+    for (int64_t end = tile - 1;; end -= 32) {
+        const int64_t j = end - lane;
+        unsigned long long d = kFlagPre;           // before tile 0: an empty inclusive prefix
+        if (j >= 0) {
+            d = ld_acquire(desc + j);
+            if ((d >> 62) == 0ull) {
+                const long long t0 = clock64();
+                unsigned ns = 32;
+                while (((d = ld_acquire(desc + j)) >> 62) == 0ull) {
+                    if (clock64() - t0 > kWaitCycles) {
+                        atomicOr(work + 1, 1ull);
+                        d = kFlagPre;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 512) ns <<= 1;
+                }
+            }
+        }
+        const unsigned pre = __ballot_sync(0xffffffffu, (d >> 62) == 2ull);
+        const int first = pre ? __ffs(pre) - 1 : 32;
+        unsigned long long v = lane <= first ? (d & kValMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pre) break;
+    }
+    if (lane == 0) st_release(desc + tile, kFlagPre | (excl + total));
+    return excl;
+}
+
+template <bool FIND>
+__device__ __forceinline__ typename std::conditional<FIND, SlotSink, CountSink>::type make_sink(uint16_t* p)
+{
+    if constexpr (FIND)
+        return SlotSink{p, (uint32_t)kRows, (uint32_t)kTSlots, 0u, false};
+    else
+        return CountSink{};
+}
+
+template <int LAYOUT, bool FIND>
+__global__ void __launch_bounds__(kTmaThreads, 2)
+    k_scan_tma(const __grid_constant__ CUtensorMap tmap, const TmaArgs p)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_full[kMaxStages];
+    __shared__ __align__(8) uint64_t s_empty[kMaxStages];
+    __shared__ __align__(8) uint64_t s_counted[2];
+    __shared__ __align__(8) uint64_t s_ready[2];
+    __shared__ int32_t s_stage_tile[kMaxStages];
+    __shared__ int64_t s_tile_of[2];
+    __shared__ uint32_t s_wtot[2][kWalkWarps];
+    __shared__ uint32_t s_woff[2][kWalkWarps];
+    __shared__ unsigned long long s_tile_off[2];
+    __shared__ unsigned long long s_sum[kWalkWarps];
+    __shared__ int s_abort;
+
+    const ScanArgs& a = p.a;
+    const int nst = p.nst;
+    uint8_t* stages = smem;
+    uint8_t* tabmem = smem + (size_t)nst * kStageBytes;
+    const SmemTab T = load_tables<LAYOUT>(a, tabmem);
+    uint16_t* slots = reinterpret_cast<uint16_t*>(tabmem + p.table_bytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < nst; i++) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_empty[i], kWalkWarps);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&s_counted[i], kWalkWarps);
+            mbar_init(&s_ready[i], 1);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    volatile int* abort_flag = &s_abort;
+    const uint32_t sps = (uint32_t)p.sps;
+    const int64_t C = a.chunk;
+
+    if (warp == kWalkWarps) {
+        // ------------------------------------------------------ producer
+        if (lane != 0) return;
+        uint32_t g = 0;
+        bool ok = true;
+        int64_t iter = 0;
+        for (bool done = false; !done && ok;) {
+            // find: tickets in text order (the look-back needs them);
+            // count: a static schedule, no workspace needed
+            const int64_t tile = FIND ? (int64_t)atomicAdd(a.work, 1ull)
+                                      : (int64_t)blockIdx.x + (iter++) * (int64_t)gridDim.x;
+            const bool end = tile >= a.ntiles;
+            const uint32_t nstage = end ? 1u : sps + 1u;
+            for (uint32_t s = 0; s < nstage; s++, g++) {
+                const uint32_t slot = g % nst, use = g / nst;
+                if (use > 0 && !mbar_wait(&s_empty[slot], (use - 1) & 1u, abort_flag, p)) {
+                    ok = false;
+                    break;
+                }
+                if (end) {
+                    s_stage_tile[slot] = -1;
+                    mbar_arrive(&s_full[slot]);
+                    done = true;
+                    g++;
+                    break;
+                }
+                s_stage_tile[slot] = (int32_t)tile;
+                mbar_arrive_expect_tx(&s_full[slot], kStageBytes);
+                const int32_t x = s < sps ? (int32_t)(s * kStageW) : 0;
+                const int32_t y = (int32_t)(tile * kRows) + (s < sps ? 0 : 1);
+                tma_load_2d(stages + (size_t)slot * kStageBytes, &tmap, x, y, &s_full[slot]);
+            }
+        }
+        if (!ok) {
+            // drain the copies still in flight before the CTA's memory goes away
+            for (uint32_t i = g > (uint32_t)nst ? g - nst : 0; i < g; i++) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&s_full[i % nst], (i / nst) & 1u) && clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
+        return;
+    }
+
+    if (warp == kWalkWarps + 1) {
+        // ------------------------------------------------------ scheduler
+        if (!FIND) return;
+        const unsigned long long base = a.base_in ? *a.base_in : 0ull;
+        for (int64_t k = 0;; k++) {
+            const int b = (int)(k & 1);
+            if (!warp_wait(&s_counted[b], (uint32_t)(k >> 1) & 1u, abort_flag, p)) return;
+            const int64_t tile = s_tile_of[b];
+            if (tile < 0) return;
+            const uint32_t wt = lane < kWalkWarps ? s_wtot[b][lane] : 0u;
+            uint32_t inc = wt;
+#pragma unroll
+            for (int o = 1; o < kWalkWarps; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, inc, kWalkWarps - 1);
+            if (lane < kWalkWarps) s_woff[b][lane] = inc - wt;
+            const unsigned long long off = lookback_warp(a.work, tile, total, lane);
+            if (lane == 0) {
+                s_tile_off[b] = base + off;
+                if (tile == a.ntiles - 1) *a.count = base + off + total;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_ready[b]);
+        }
+    }
+
+    // ---------------------------------------------------------- walkers
+    using Sink = typename std::conditional<FIND, SlotSink, CountSink>::type;
+    const int t = threadIdx.x;
+    const uint32_t m = T.m;
+    uint32_t g = 0;
+    int64_t k = 0;
+    unsigned long long total = 0;
+    // the previous tile, whose positions are written once its offset is known
+    uint32_t prev_cnt = 0, prev_excl = 0;
+    bool prev_over = false;
+    int64_t prev_s = 0, prev_e = 0;
+    bool aborted = false;
+
+    auto flush_prev = [&](int64_t kp) -> bool {
+        const int b = (int)(kp & 1);
+        if (!warp_wait(&s_ready[b], (uint32_t)(kp >> 1) & 1u, abort_flag, p)) return false;
+        if (prev_cnt == 0) return true;
+        const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + prev_excl);
+        const int64_t start0 = a.pos_base + prev_s - (int64_t)(m - 1);
+        if (!prev_over) {
+            const uint16_t* sl = slots + (size_t)b * kTSlots * kRows + t;
+            for (uint32_t j = 0; j < prev_cnt; j++) {
+                const int64_t gi = g0 + j;
+                if (gi < a.cap) a.pos[gi] = start0 + sl[j * kRows];
+            }
+        } else if (g0 < a.cap) {
+            GlobalSink gs{a.pos, a.cap, g0, start0};
+            walk_chunk<LAYOUT>(a, T, prev_s, prev_e, gs);
+        }
+        return true;
+    };
+
+    for (;;) {
+        uint32_t slot = g % nst;
+        if (!warp_wait(&s_full[slot], (g / nst) & 1u, abort_flag, p)) {
+            aborted = true;
+            break;
+        }
+        const int32_t tile = s_stage_tile[slot];
+        if (tile < 0) break;
+        const int64_t row = (int64_t)tile * kRows + t;
+        const int64_t s0 = row * C;
+        const bool has = s0 < a.n_own;
+        const int64_t e0 = has ? min(s0 + C, a.n_own) : s0;
+        const bool tma_ok = has && e0 == s0 + C && row + 1 < p.nrows_full;
+        Sink sink = make_sink<FIND>(slots + (size_t)(k & 1) * kTSlots * kRows + t);
+        Walker<LAYOUT, false, Sink> w{T, sink, 0u, 0u};
+        for (uint32_t s = 0; s < sps; s++) {
+            slot = (g + s) % nst;
+            if (s > 0 && !warp_wait(&s_full[slot], ((g + s) / nst) & 1u, abort_flag, p)) {
+                aborted = true;
+                break;
+            }
+            if (tma_ok) {
+                const uint4* src =
+                    reinterpret_cast<const uint4*>(stages + (size_t)slot * kStageBytes + t * kStageW);
+#pragma unroll
+                for (int j = 0; j < kStageW / 16; j++) w.vec(src[j], s * kStageW + j * 16, 0);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_empty[slot]);
+        }
+        if (aborted) break;
+        slot = (g + sps) % nst;
+        if (!warp_wait(&s_full[slot], ((g + sps) / nst) & 1u, abort_flag, p)) {
+            aborted = true;
+            break;
+        }
+        uint32_t cnt = 0;
+        if (tma_ok) {
+            Walker<LAYOUT, true, Sink> h{T, sink, w.e, w.cnt};
+            const uint4* src =
+                reinterpret_cast<const uint4*>(stages + (size_t)slot * kStageBytes + t * kStageW);
+            const uint32_t lim = (uint32_t)C + m - 1;
+            for (uint32_t j = 0; j * 16 < m - 1; j++) h.vec(src[j], (uint32_t)C + j * 16, lim);
+            cnt = h.cnt;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[slot]);
+        g += sps + 1;
+        if (has && !tma_ok) cnt = walk_chunk<LAYOUT>(a, T, s0, e0, sink);
+
+        if (!FIND) {
+            total += cnt;
+        } else {
+            uint32_t v = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            const int b = (int)(k & 1);
+            if (lane == 31) {
+                s_wtot[b][warp] = v;
+                if (warp == 0) s_tile_of[b] = tile;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_counted[b]);
+            if (k >= 1 && !flush_prev(k - 1)) {
+                aborted = true;
+                break;
+            }
+            prev_cnt = cnt;
+            prev_excl = v - cnt;
+            if constexpr (FIND) prev_over = sink.over;
+            prev_s = s0;
+            prev_e = e0;
+        }
+        k++;
+    }
+
+    if (!FIND) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (lane == 0) s_sum[warp] = total;
+        named_sync_walkers();
+        if (t == 0 && !*abort_flag) {
+            unsigned long long v = 0;
+            for (int i = 0; i < kWalkWarps; i++) v += s_sum[i];
+            if (v) atomicAdd(a.count, v);
+        }
+        return;
+    }
+    if (aborted) return;
+    // end of work: tell the scheduler, then write the last tile's positions
+    const int b = (int)(k & 1);
+    if (lane == 0 && warp == 0) s_tile_of[b] = -1;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&s_counted[b]);
+    if (k >= 1) flush_prev(k - 1);
+}
+
 // ---------------------------------------------------------------- host side
 
 #define CUDA_TRY(x)                                   \
@@ -457,6 +880,7 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
 struct DeviceInfo {
     int sms = 0;
     int smem_optin = 0;
+    int smem_per_sm = 0;
     bool ok = false;
 };
 
@@ -472,6 +896,9 @@ const DeviceInfo* device_info(int dev)
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return nullptr;
         if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+            return nullptr;
+        if (cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
             cudaSuccess)
             return nullptr;
         d.ok = true;
@@ -513,26 +940,55 @@ struct Resolved {
 };
 
 constexpr int64_t kMinDefaultTile = 256 * 64;   // workspace sizing for cfg == NULL
+constexpr int kTmaDefaultCtas = 2;
 
-int resolve(const dfa_config* cfg, int64_t n, int sms, Resolved* r)
+// Launch configuration for a scan of n bytes (n_avail readable).  The TMA
+// loader needs a 16-byte aligned text holding at least two full rows.
+int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int sms, Resolved* r)
 {
     r->layout = cfg && cfg->layout ? cfg->layout : kLayoutK4;
-    r->threads = cfg && cfg->threads ? cfg->threads : 256;
-    r->loader = cfg && cfg->loader ? cfg->loader : 1;
     r->ctas_per_sm = cfg ? cfg->ctas_per_sm : 0;
-    if (cfg && cfg->chunk) {
+    if (r->layout != kLayoutK4 && r->layout != kLayoutStt) return DFA_EINVAL;
+    if (r->ctas_per_sm < 0 || r->ctas_per_sm > 32) return DFA_EINVAL;
+    const int req_loader = cfg ? cfg->loader : 0;
+    if (req_loader < 0 || req_loader > 2) return DFA_EINVAL;
+    if (sms <= 0) sms = 152;
+    const bool tma_chunk = !(cfg && cfg->chunk) ||
+                           (cfg->chunk % kStageW == 0 && cfg->chunk >= 2 * kStageW && cfg->chunk <= 80 * 64);
+    if (req_loader == 2 && !tma_chunk) return DFA_EINVAL;
+    if (req_loader == 2 || (req_loader == 0 && tma_chunk)) {
+        // TMA-staged tiles of 256 rows x chunk bytes, chunk a multiple of 80
+        int64_t chunk;
+        if (cfg && cfg->chunk) {
+            chunk = cfg->chunk;
+        } else {
+            const int ctas = sms * (r->ctas_per_sm ? r->ctas_per_sm : kTmaDefaultCtas);
+            const int64_t per = (int64_t)kRows * kStageW * 4 * ctas;
+            int64_t sps = (n + per - 1) / per;
+            sps = std::min<int64_t>(std::max<int64_t>(sps, 2), 16);
+            chunk = sps * kStageW;
+        }
+        const bool ok = aligned && n_avail / chunk >= 2;
+        if (ok || req_loader == 2) {
+            if (!ok) return DFA_EINVAL;
+            r->loader = 2;
+            r->threads = kRows;
+            r->chunk = chunk;
+            return DFA_OK;
+        }
+    }
+    r->loader = 1;
+    r->threads = cfg && cfg->threads ? cfg->threads : 256;
+    if (cfg && cfg->chunk && !(req_loader == 0 && tma_chunk)) {
         r->chunk = cfg->chunk;
     } else {
-        int64_t per = (int64_t)r->threads * (sms > 0 ? sms : 152) * 8;
+        int64_t per = (int64_t)r->threads * sms * 8;
         int64_t c = (n + per - 1) / per;
         c = (c + 15) & ~(int64_t)15;
         r->chunk = std::min<int64_t>(std::max<int64_t>(c, kMinDefaultTile / r->threads), 1024);
     }
-    if (r->layout != kLayoutK4 && r->layout != kLayoutStt) return DFA_EINVAL;
     if (r->threads != 128 && r->threads != 256 && r->threads != 512) return DFA_EINVAL;
     if (r->chunk < 16 || r->chunk > 32768 || (r->chunk & 15)) return DFA_EINVAL;
-    if (r->loader != 1) return DFA_EINVAL;
-    if (r->ctas_per_sm < 0 || r->ctas_per_sm > 32) return DFA_EINVAL;
     return DFA_OK;
 }
 
@@ -565,6 +1021,80 @@ KernelFn pick_find(int layout, int threads)
 int table_smem(const dfa_table* t, int layout)
 {
     return layout == kLayoutK4 ? t->view.k4_bytes + t->view.d1_bytes : t->view.stt_bytes;
+}
+
+typedef void (*TmaKernelFn)(const CUtensorMap, const TmaArgs);
+
+TmaKernelFn pick_tma(int layout, bool find)
+{
+    if (layout == kLayoutK4) return find ? k_scan_tma<kLayoutK4, true> : k_scan_tma<kLayoutK4, false>;
+    return find ? k_scan_tma<kLayoutStt, true> : k_scan_tma<kLayoutStt, false>;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_encode) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return DFA_ECUDA;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    *fn = g_encode;
+    return DFA_OK;
+}
+
+// Launch the TMA-staged kernel for the filled-in arguments `a`.
+int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
+               const DeviceInfo* di, cudaStream_t st)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 encode;
+    int rc = tensor_map_encoder(&encode);
+    if (rc) return rc;
+    const int64_t C = r.chunk;
+    TmaArgs p;
+    p.a = a;
+    p.nrows_full = a.n / C;
+    p.sps = (int32_t)(C / kStageW);
+    p.table_bytes = (table_smem(t, r.layout) + 127) & ~127;
+    p.fail_word = find ? a.work + 1 : a.count;
+    p.fail_bit = find ? 2ull : (1ull << 63);
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
+    cuuint64_t strides[1] = {(cuuint64_t)C};
+    cuuint32_t box[2] = {(cuuint32_t)kStageW, (cuuint32_t)kRows};
+    cuuint32_t estr[2] = {1, 1};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(a.text), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return DFA_ECUDA;
+    TmaKernelFn fn = pick_tma(r.layout, find);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void*)fn) != cudaSuccess) return DFA_ECUDA;
+    const int ctas = r.ctas_per_sm ? r.ctas_per_sm : kTmaDefaultCtas;
+    const int slot_bytes = find ? 2 * kTSlots * kRows * 2 : 0;
+    const int budget = std::min(di->smem_per_sm / ctas - 1024, di->smem_optin) - (int)fa.sharedSizeBytes;
+    int nst = (budget - p.table_bytes - slot_bytes) / kStageBytes;
+    nst = std::min(nst, kMaxStages);
+    if (nst < 2) {
+        nst = std::min((di->smem_optin - (int)fa.sharedSizeBytes - p.table_bytes - slot_bytes) / kStageBytes,
+                       kMaxStages);
+        if (nst < 2) return DFA_EINVAL;
+    }
+    p.nst = nst;
+    const int smem = nst * kStageBytes + p.table_bytes + slot_bytes;
+    int occ = occupancy((const void*)fn, kTmaThreads, smem, dev, di->smem_optin);
+    if (occ <= 0) return DFA_ECUDA;
+    occ = std::min(occ, ctas);
+    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
+    fn<<<(unsigned)grid, kTmaThreads, smem, st>>>(map, p);
+    CUDA_TRY(cudaGetLastError());
+    return DFA_OK;
 }
 
 void fill_args(ScanArgs* a, const uint8_t* text, int64_t n, int64_t n_own, const dfa_table* t,
@@ -601,13 +1131,14 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
     if (rc) return rc;
     if (dev != t->device) return DFA_EINVAL;
     Resolved r;
-    rc = resolve(cfg, n, di->sms, &r);
+    rc = resolve(cfg, n, n, ((uintptr_t)d_text & 15u) == 0, di->sms, &r);
     if (rc) return rc;
     CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st));
     if (n < t->m) return DFA_OK;
     ScanArgs a;
     fill_args(&a, d_text, n, n, t, r);
     a.count = reinterpret_cast<unsigned long long*>(d_count);
+    if (r.loader == 2) return launch_tma(r, a, t, false, dev, di, st);
     KernelFn fn = pick_count(r.layout, r.threads);
     const int smem = table_smem(t, r.layout);
     int occ = occupancy((const void*)fn, r.threads, smem, dev, di->smem_optin);
@@ -632,7 +1163,7 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     if (rc) return rc;
     if (dev != t->device) return DFA_EINVAL;
     Resolved r;
-    rc = resolve(cfg, n_own, di->sms, &r);
+    rc = resolve(cfg, n_own, n, ((uintptr_t)d_text & 15u) == 0, di->sms, &r);
     if (rc) return rc;
     ScanArgs a;
     fill_args(&a, d_text, n, n_own, t, r);
@@ -652,6 +1183,7 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     a.pos_base = pos_base;
     a.base_in = reinterpret_cast<const unsigned long long*>(d_base);
     a.work = static_cast<unsigned long long*>(d_work);
+    if (r.loader == 2) return launch_tma(r, a, t, true, dev, di, st);
     KernelFn fn = pick_find(r.layout, r.threads);
     const int smem = ((table_smem(t, r.layout) + 15) & ~15) + kSlots * r.threads * 2;
     int occ = occupancy((const void*)fn, r.threads, smem, dev, di->smem_optin);

@@ -16,11 +16,17 @@ pytestmark = pytest.mark.gpu
 
 CONFIGS = [
     None,
-    dict(layout=1, threads=128, chunk=16),
-    dict(layout=1, threads=256, chunk=48),
-    dict(layout=1, threads=512, chunk=256),
-    dict(layout=2, threads=256, chunk=64),
-    dict(layout=2, threads=128, chunk=1008),
+    # direct-load kernel (loader 1)
+    dict(loader=1, layout=1, threads=128, chunk=16),
+    dict(loader=1, layout=1, threads=256, chunk=48),
+    dict(loader=1, layout=1, threads=512, chunk=256),
+    dict(loader=1, layout=2, threads=256, chunk=64),
+    dict(loader=1, layout=2, threads=128, chunk=1008),
+    # TMA-staged persistent kernel (loader 2): chunk = 80 x stages per tile
+    dict(loader=2, layout=1, chunk=160),
+    dict(loader=2, layout=1, chunk=400, ctas_per_sm=1),
+    dict(loader=2, layout=2, chunk=240),
+    dict(loader=2, layout=1, chunk=1280),
 ]
 
 
@@ -76,7 +82,7 @@ def test_random_genome_all_lengths(gpu, cfg):
         _check(gpu, t, synth.pattern(m, 100 + m), cfg, td)
 
 
-@pytest.mark.parametrize("cfg", CONFIGS[:4])
+@pytest.mark.parametrize("cfg", CONFIGS[:4] + CONFIGS[6:])
 def test_planted_long_patterns(gpu, cfg):
     n = 1 << 20
     t = synth.genome_text(n, 8)
@@ -89,14 +95,16 @@ def test_planted_long_patterns(gpu, cfg):
         assert _check(gpu, tt, pat, cfg) >= len(pos)
 
 
-def test_border_plants(gpu):
+@pytest.mark.parametrize("cfg,chunk", [(dict(loader=1, layout=1, threads=128, chunk=64), 64),
+                                       (dict(loader=2, layout=1, chunk=160), 160),
+                                       (dict(loader=2, layout=2, chunk=80 * 3), 240)])
+def test_border_plants(gpu, cfg, chunk):
     # occurrences planted at +-m around every chunk / tile border
-    cfg = dict(layout=1, threads=128, chunk=64)
-    n = 128 * 64 * 6 + 77
+    n = 256 * chunk * 6 + 77
     for m in (5, 16, 33, 64):
         t = synth.genome_text(n, 3, n_gap_mean=0)
         pat = synth.pattern(m, 7 * m)
-        borders = np.arange(0, n, 64)
+        borders = np.arange(0, n, chunk)
         pos = np.unique(np.clip(np.concatenate([borders - m + 1, borders - 1, borders,
                                                 borders - m // 2]), 0, n - m))
         pos = pos[np.concatenate([[True], np.diff(pos) >= m])]  # keep them disjoint
@@ -127,7 +135,9 @@ def test_dense_matches_overflow_and_truncation(gpu):
     # every position matches: exercises the per-thread staging overflow path
     n = 200_003
     t = np.full(n, ord("A"), np.uint8)
-    for cfg in (None, dict(layout=1, threads=128, chunk=1024), dict(layout=2, threads=256, chunk=512)):
+    for cfg in (None, dict(loader=1, layout=1, threads=128, chunk=1024),
+                dict(loader=1, layout=2, threads=256, chunk=512), dict(loader=2, chunk=160),
+                dict(loader=2, layout=2, chunk=800)):
         for m in (1, 4, 64):
             _check(gpu, t, b"A" * m, cfg)
     # cap smaller than the count: exact count, first cap positions, ETRUNC
