@@ -452,36 +452,42 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
 
 // ---------------------------------------------------------------- TMA-staged kernel
 //
-// Persistent, warp-specialised form of the same walk.  A tile is 256 rows of
-// C bytes (row r of tile k = text[(256k + r)C, (256k + r + 1)C)); thread r
-// of the walker warps walks row r.  The text is viewed as a 2-D tensor of
-// C-byte rows and streamed by TMA (cp.async.bulk.tensor.2d) in stages of
-// 80 bytes x 256 rows into a ring of shared-memory buffers; a final "halo"
-// stage brings the first 80 bytes of rows r+1, i.e. the m-1 bytes of overlap
-// each row needs (Algorithm 1).  80-byte rows (5 x 16 B, an odd count) make
-// the walkers' 16-byte shared loads conflict-free without swizzling.
-//   warp 8 (producer): takes tile tickets, issues the TMA loads;
-//   warp 9 (scheduler, find only): sums the walker warps' counts of a tile,
-//          publishes them and resolves the tile's global offset by a
-//          warp-parallel decoupled look-back, while the walkers already walk
-//          the next tile; a tile's positions are written one tile later.
+// Persistent, warp-specialised form of the same walk, one CTA per SM.  A
+// tile is 512 rows of C bytes (row r of tile k = text[(512k + r)C, ...+C));
+// walker thread r walks row r.  The text is viewed as a 2-D tensor of C-byte
+// rows.  Each of the 16 walker warps streams its own 32 rows through a
+// private ring of shared-memory stages: its lane 0 issues a TMA load
+// (cp.async.bulk.tensor.2d, 64 bytes x 32 rows, 64-byte swizzle) for the
+// stage that will reuse a slot as soon as the warp has read it, so warps
+// never wait for one another's progress through a tile.  After the C bytes
+// of its rows a warp loads one more "halo" box, the first 64 bytes of rows
+// r+1: the m-1 bytes of overlap each row needs (Algorithm 1).
+//   warp 16 (tickets): hands out tile ids (in text order for find, by a
+//           static schedule for count) through a small ring;
+//   warp 17 (scheduler, find only): sums the walker warps' counts of a tile,
+//           publishes them and resolves the tile's global offset by a
+//           warp-parallel decoupled look-back while the walkers go on; a
+//           tile's positions are written two tiles later, which hides the
+//           look-back's latency.
 // Rows whose chunk or overlap runs past the full rows of the tensor (the end
 // of the text) are walked from global memory by their thread instead.
 
-constexpr int kRows = 256;
-constexpr int kStageW = 80;
-constexpr int kStageBytes = kRows * kStageW;
-constexpr int kWalkWarps = kRows / 32;
+constexpr int kWalkWarps = 16;
+constexpr int kRows = kWalkWarps * 32;
+constexpr int kStageW = 64;
+constexpr int kWarpStage = 32 * kStageW;
 constexpr int kTmaThreads = kRows + 64;
 constexpr int kTSlots = 8;
 constexpr int kMaxStages = 8;
+constexpr int kDefer = 3;
+constexpr int kTicketRing = 8;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
 struct TmaArgs {
     ScanArgs a;
     int64_t nrows_full;   // rows of C bytes fully inside [0, n): the tensor's rows
-    int32_t nst;          // stages in the ring
-    int32_t sps;          // body stages per tile (C / 80)
+    int32_t nst;          // stages in each warp's ring
+    int32_t sps;          // body stages per tile (C / 64)
     int32_t table_bytes;  // shared bytes of the table, 128-aligned
     // where a wait that gave up is reported: the find workspace's status
     // word (bit 1), or bit 63 of the count for a count without workspace
@@ -544,8 +550,8 @@ __device__ __forceinline__ void named_sync_walkers()
     asm volatile("bar.sync 1, %0;" ::"n"(kRows) : "memory");
 }
 
-// Bounded wait on an mbarrier phase.  Gives up after ~2 s (status bit 1 and
-// the CTA's abort flag set) or when another role has aborted.
+// Bounded wait on an mbarrier phase.  Gives up after ~2 s (reported through
+// p.fail_word, and the CTA's abort flag set) or when another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           const TmaArgs& p)
 {
@@ -624,36 +630,46 @@ __device__ __forceinline__ typename std::conditional<FIND, SlotSink, CountSink>:
         return CountSink{};
 }
 
+// One tile's worth of a walker thread's state, kept until its positions are written.
+struct PendingRow {
+    uint32_t cnt, excl;
+    bool over;
+    int64_t s, e;
+};
+
 template <int LAYOUT, bool FIND>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, 1)
     k_scan_tma(const __grid_constant__ CUtensorMap tmap, const TmaArgs p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t s_full[kMaxStages];
-    __shared__ __align__(8) uint64_t s_empty[kMaxStages];
-    __shared__ __align__(8) uint64_t s_counted[2];
-    __shared__ __align__(8) uint64_t s_ready[2];
-    __shared__ int32_t s_stage_tile[kMaxStages];
-    __shared__ int64_t s_tile_of[2];
-    __shared__ uint32_t s_wtot[2][kWalkWarps];
-    __shared__ uint32_t s_woff[2][kWalkWarps];
-    __shared__ unsigned long long s_tile_off[2];
+    __shared__ __align__(8) uint64_t s_full[kWalkWarps][kMaxStages];
+    __shared__ __align__(8) uint64_t s_tready[kTicketRing];
+    __shared__ __align__(8) uint64_t s_tfree[kTicketRing];
+    __shared__ __align__(8) uint64_t s_counted[kDefer];
+    __shared__ __align__(8) uint64_t s_ready[kDefer];
+    __shared__ int64_t s_tiles[kTicketRing];
+    __shared__ int64_t s_tile_of[kDefer];
+    __shared__ uint32_t s_wtot[kDefer][kWalkWarps];
+    __shared__ uint32_t s_woff[kDefer][kWalkWarps];
+    __shared__ unsigned long long s_tile_off[kDefer];
     __shared__ unsigned long long s_sum[kWalkWarps];
     __shared__ int s_abort;
 
     const ScanArgs& a = p.a;
     const int nst = p.nst;
-    uint8_t* stages = smem;
-    uint8_t* tabmem = smem + (size_t)nst * kStageBytes;
+    uint8_t* rings = smem;
+    uint8_t* tabmem = smem + (size_t)kWalkWarps * nst * kWarpStage;
     const SmemTab T = load_tables<LAYOUT>(a, tabmem);
     uint16_t* slots = reinterpret_cast<uint16_t*>(tabmem + p.table_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < nst; i++) {
-            mbar_init(&s_full[i], 1);
-            mbar_init(&s_empty[i], kWalkWarps);
+        for (int w = 0; w < kWalkWarps; w++)
+            for (int i = 0; i < nst; i++) mbar_init(&s_full[w][i], 1);
+        for (int i = 0; i < kTicketRing; i++) {
+            mbar_init(&s_tready[i], 1);
+            mbar_init(&s_tfree[i], kWalkWarps);
         }
-        for (int i = 0; i < 2; i++) {
+        for (int i = 0; i < kDefer; i++) {
             mbar_init(&s_counted[i], kWalkWarps);
             mbar_init(&s_ready[i], 1);
         }
@@ -663,50 +679,24 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     __syncthreads();
     volatile int* abort_flag = &s_abort;
     const uint32_t sps = (uint32_t)p.sps;
+    const uint32_t spt = sps + 1;                 // stages per tile, halo included
     const int64_t C = a.chunk;
 
     if (warp == kWalkWarps) {
-        // ------------------------------------------------------ producer
+        // ------------------------------------------------------ tickets
         if (lane != 0) return;
-        uint32_t g = 0;
-        bool ok = true;
-        int64_t iter = 0;
-        for (bool done = false; !done && ok;) {
-            // find: tickets in text order (the look-back needs them);
-            // count: a static schedule, no workspace needed
-            const int64_t tile = FIND ? (int64_t)atomicAdd(a.work, 1ull)
-                                      : (int64_t)blockIdx.x + (iter++) * (int64_t)gridDim.x;
-            const bool end = tile >= a.ntiles;
-            const uint32_t nstage = end ? 1u : sps + 1u;
-            for (uint32_t s = 0; s < nstage; s++, g++) {
-                const uint32_t slot = g % nst, use = g / nst;
-                if (use > 0 && !mbar_wait(&s_empty[slot], (use - 1) & 1u, abort_flag, p)) {
-                    ok = false;
-                    break;
-                }
-                if (end) {
-                    s_stage_tile[slot] = -1;
-                    mbar_arrive(&s_full[slot]);
-                    done = true;
-                    g++;
-                    break;
-                }
-                s_stage_tile[slot] = (int32_t)tile;
-                mbar_arrive_expect_tx(&s_full[slot], kStageBytes);
-                const int32_t x = s < sps ? (int32_t)(s * kStageW) : 0;
-                const int32_t y = (int32_t)(tile * kRows) + (s < sps ? 0 : 1);
-                tma_load_2d(stages + (size_t)slot * kStageBytes, &tmap, x, y, &s_full[slot]);
-            }
+        for (int64_t kk = 0;; kk++) {
+            const int slot = (int)(kk % kTicketRing);
+            if (kk >= kTicketRing &&
+                !mbar_wait(&s_tfree[slot], (uint32_t)((kk / kTicketRing) - 1) & 1u, abort_flag, p))
+                return;
+            int64_t tile = FIND ? (int64_t)atomicAdd(a.work, 1ull)
+                                : (int64_t)blockIdx.x + kk * (int64_t)gridDim.x;
+            if (tile >= a.ntiles) tile = -1;
+            s_tiles[slot] = tile;
+            mbar_arrive(&s_tready[slot]);
+            if (tile < 0) return;
         }
-        if (!ok) {
-            // drain the copies still in flight before the CTA's memory goes away
-            for (uint32_t i = g > (uint32_t)nst ? g - nst : 0; i < g; i++) {
-                const long long t0 = clock64();
-                while (!mbar_try_wait(&s_full[i % nst], (i / nst) & 1u) && clock64() - t0 < kWaitCycles) {
-                }
-            }
-        }
-        return;
     }
 
     if (warp == kWalkWarps + 1) {
@@ -714,8 +704,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         if (!FIND) return;
         const unsigned long long base = a.base_in ? *a.base_in : 0ull;
         for (int64_t k = 0;; k++) {
-            const int b = (int)(k & 1);
-            if (!warp_wait(&s_counted[b], (uint32_t)(k >> 1) & 1u, abort_flag, p)) return;
+            const int b = (int)(k % kDefer);
+            if (!warp_wait(&s_counted[b], (uint32_t)(k / kDefer) & 1u, abort_flag, p)) return;
             const int64_t tile = s_tile_of[b];
             if (tile < 0) return;
             const uint32_t wt = lane < kWalkWarps ? s_wtot[b][lane] : 0u;
@@ -739,85 +729,116 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 
     // ---------------------------------------------------------- walkers
     using Sink = typename std::conditional<FIND, SlotSink, CountSink>::type;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x;                    // row within the tile
     const uint32_t m = T.m;
-    uint32_t g = 0;
-    int64_t k = 0;
-    unsigned long long total = 0;
-    // the previous tile, whose positions are written once its offset is known
-    uint32_t prev_cnt = 0, prev_excl = 0;
-    bool prev_over = false;
-    int64_t prev_s = 0, prev_e = 0;
+    uint8_t* ring = rings + (size_t)warp * nst * kWarpStage;
+    uint64_t* full = s_full[warp];
+    const uint32_t swz = (uint32_t)(lane >> 1) & 3u;   // 64-byte swizzle of this lane's row
+    int64_t end_k = INT64_MAX;                    // first tile index holding the end marker
+    uint32_t g_issue = 0;                         // next stage to load
     bool aborted = false;
 
-    auto flush_prev = [&](int64_t kp) -> bool {
-        const int b = (int)(kp & 1);
-        if (!warp_wait(&s_ready[b], (uint32_t)(kp >> 1) & 1u, abort_flag, p)) return false;
-        if (prev_cnt == 0) return true;
-        const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + prev_excl);
-        const int64_t start0 = a.pos_base + prev_s - (int64_t)(m - 1);
-        if (!prev_over) {
+    // tile id of this CTA's kk-th tile (warp-collective); false on abort
+    auto tile_id = [&](int64_t kk, int64_t* out) -> bool {
+        const int slot = (int)(kk % kTicketRing);
+        if (!warp_wait(&s_tready[slot], (uint32_t)(kk / kTicketRing) & 1u, abort_flag, p)) return false;
+        *out = s_tiles[slot];
+        return true;
+    };
+    // load the next stage of this warp's rows into the slot it will use
+    auto issue_next = [&]() -> bool {
+        const int64_t kk = g_issue / spt;
+        const uint32_t s = g_issue % spt;
+        if (kk >= end_k) return true;
+        int64_t tile;
+        if (!tile_id(kk, &tile)) return false;
+        if (tile < 0) {
+            end_k = kk;
+            return true;
+        }
+        if (lane == 0) {
+            const uint32_t slot = g_issue % nst;
+            mbar_arrive_expect_tx(&full[slot], kWarpStage);
+            const int32_t x = s < sps ? (int32_t)(s * kStageW) : 0;
+            const int32_t y = (int32_t)(tile * kRows + warp * 32) + (s < sps ? 0 : 1);
+            tma_load_2d(ring + (size_t)slot * kWarpStage, &tmap, x, y, &full[slot]);
+        }
+        g_issue++;
+        return true;
+    };
+
+    for (int i = 0; i < nst && !aborted; i++) aborted = !issue_next();
+
+    unsigned long long total = 0;
+    PendingRow p1{0, 0, false, 0, 0}, p2{0, 0, false, 0, 0};   // tiles k-1 and k-2
+    auto flush = [&](const PendingRow& pr, int64_t kp) -> bool {
+        const int b = (int)(kp % kDefer);
+        if (!warp_wait(&s_ready[b], (uint32_t)(kp / kDefer) & 1u, abort_flag, p)) return false;
+        if (pr.cnt == 0) return true;
+        const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + pr.excl);
+        const int64_t start0 = a.pos_base + pr.s - (int64_t)(m - 1);
+        if (!pr.over) {
             const uint16_t* sl = slots + (size_t)b * kTSlots * kRows + t;
-            for (uint32_t j = 0; j < prev_cnt; j++) {
+            for (uint32_t j = 0; j < pr.cnt; j++) {
                 const int64_t gi = g0 + j;
                 if (gi < a.cap) a.pos[gi] = start0 + sl[j * kRows];
             }
         } else if (g0 < a.cap) {
             GlobalSink gs{a.pos, a.cap, g0, start0};
-            walk_chunk<LAYOUT>(a, T, prev_s, prev_e, gs);
+            walk_chunk<LAYOUT>(a, T, pr.s, pr.e, gs);
         }
         return true;
     };
 
-    for (;;) {
-        uint32_t slot = g % nst;
-        if (!warp_wait(&s_full[slot], (g / nst) & 1u, abort_flag, p)) {
+    uint32_t g = 0;                               // next stage to consume
+    int64_t k = 0;
+    while (!aborted) {
+        int64_t tile;
+        if (!tile_id(k, &tile)) {
             aborted = true;
             break;
         }
-        const int32_t tile = s_stage_tile[slot];
         if (tile < 0) break;
-        const int64_t row = (int64_t)tile * kRows + t;
+        const int64_t row = tile * kRows + t;
         const int64_t s0 = row * C;
         const bool has = s0 < a.n_own;
         const int64_t e0 = has ? min(s0 + C, a.n_own) : s0;
         const bool tma_ok = has && e0 == s0 + C && row + 1 < p.nrows_full;
-        Sink sink = make_sink<FIND>(slots + (size_t)(k & 1) * kTSlots * kRows + t);
+        Sink sink = make_sink<FIND>(slots + (size_t)(k % kDefer) * kTSlots * kRows + t);
         Walker<LAYOUT, false, Sink> w{T, sink, 0u, 0u};
-        for (uint32_t s = 0; s < sps; s++) {
-            slot = (g + s) % nst;
-            if (s > 0 && !warp_wait(&s_full[slot], ((g + s) / nst) & 1u, abort_flag, p)) {
+        uint32_t cnt = 0;
+        for (uint32_t s = 0; s < spt; s++) {
+            const uint32_t slot = g % nst;
+            if (!warp_wait(&full[slot], (g / nst) & 1u, abort_flag, p)) {
                 aborted = true;
                 break;
             }
             if (tma_ok) {
-                const uint4* src =
-                    reinterpret_cast<const uint4*>(stages + (size_t)slot * kStageBytes + t * kStageW);
+                const uint8_t* row_p = ring + (size_t)slot * kWarpStage + lane * kStageW;
+                if (s < sps) {
 #pragma unroll
-                for (int j = 0; j < kStageW / 16; j++) w.vec(src[j], s * kStageW + j * 16, 0);
+                    for (int j = 0; j < kStageW / 16; j++)
+                        w.vec(*reinterpret_cast<const uint4*>(row_p + ((j ^ swz) << 4)), s * kStageW + j * 16, 0);
+                } else {
+                    Walker<LAYOUT, true, Sink> h{T, sink, w.e, w.cnt};
+                    const uint32_t lim = (uint32_t)C + m - 1;
+                    for (uint32_t j = 0; j * 16 < m - 1; j++)
+                        h.vec(*reinterpret_cast<const uint4*>(row_p + ((j ^ swz) << 4)),
+                              (uint32_t)C + j * 16, lim);
+                    cnt = h.cnt;
+                }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&s_empty[slot]);
+            g++;
+            if (!issue_next()) {
+                aborted = true;
+                break;
+            }
         }
         if (aborted) break;
-        slot = (g + sps) % nst;
-        if (!warp_wait(&s_full[slot], ((g + sps) / nst) & 1u, abort_flag, p)) {
-            aborted = true;
-            break;
-        }
-        uint32_t cnt = 0;
-        if (tma_ok) {
-            Walker<LAYOUT, true, Sink> h{T, sink, w.e, w.cnt};
-            const uint4* src =
-                reinterpret_cast<const uint4*>(stages + (size_t)slot * kStageBytes + t * kStageW);
-            const uint32_t lim = (uint32_t)C + m - 1;
-            for (uint32_t j = 0; j * 16 < m - 1; j++) h.vec(src[j], (uint32_t)C + j * 16, lim);
-            cnt = h.cnt;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[slot]);
-        g += sps + 1;
         if (has && !tma_ok) cnt = walk_chunk<LAYOUT>(a, T, s0, e0, sink);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_tfree[k % kTicketRing]);
 
         if (!FIND) {
             total += cnt;
@@ -828,24 +849,31 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
                 uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
                 if (lane >= o) v += y;
             }
-            const int b = (int)(k & 1);
+            const int b = (int)(k % kDefer);
             if (lane == 31) {
                 s_wtot[b][warp] = v;
                 if (warp == 0) s_tile_of[b] = tile;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&s_counted[b]);
-            if (k >= 1 && !flush_prev(k - 1)) {
+            if (k >= 2 && !flush(p2, k - 2)) {
                 aborted = true;
                 break;
             }
-            prev_cnt = cnt;
-            prev_excl = v - cnt;
-            if constexpr (FIND) prev_over = sink.over;
-            prev_s = s0;
-            prev_e = e0;
+            p2 = p1;
+            bool over = false;
+            if constexpr (FIND) over = sink.over;
+            p1 = PendingRow{cnt, v - cnt, over, s0, e0};
         }
         k++;
+    }
+    if (aborted) {
+        // drain this warp's loads still in flight before its memory goes away
+        for (uint32_t i = g; i < g_issue; i++) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&full[i % nst], (i / nst) & 1u) && clock64() - t0 < kWaitCycles) {
+            }
+        }
     }
 
     if (!FIND) {
@@ -861,12 +889,13 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         return;
     }
     if (aborted) return;
-    // end of work: tell the scheduler, then write the last tile's positions
-    const int b = (int)(k & 1);
+    // end of work: tell the scheduler, then write the last two tiles' positions
+    const int b = (int)(k % kDefer);
     if (lane == 0 && warp == 0) s_tile_of[b] = -1;
     __syncwarp();
     if (lane == 0) mbar_arrive(&s_counted[b]);
-    if (k >= 1) flush_prev(k - 1);
+    if (k >= 2 && !flush(p2, k - 2)) return;
+    if (k >= 1) flush(p1, k - 1);
 }
 
 // ---------------------------------------------------------------- host side
@@ -940,7 +969,6 @@ struct Resolved {
 };
 
 constexpr int64_t kMinDefaultTile = 256 * 64;   // workspace sizing for cfg == NULL
-constexpr int kTmaDefaultCtas = 2;
 
 // Launch configuration for a scan of n bytes (n_avail readable).  The TMA
 // loader needs a 16-byte aligned text holding at least two full rows.
@@ -954,7 +982,7 @@ int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int
     if (req_loader < 0 || req_loader > 2) return DFA_EINVAL;
     if (sms <= 0) sms = 152;
     const bool tma_chunk = !(cfg && cfg->chunk) ||
-                           (cfg->chunk % kStageW == 0 && cfg->chunk >= 2 * kStageW && cfg->chunk <= 80 * 64);
+                           (cfg->chunk % kStageW == 0 && cfg->chunk >= 2 * kStageW && cfg->chunk <= kStageW * 64);
     if (req_loader == 2 && !tma_chunk) return DFA_EINVAL;
     if (req_loader == 2 || (req_loader == 0 && tma_chunk)) {
         // TMA-staged tiles of 256 rows x chunk bytes, chunk a multiple of 80
@@ -962,10 +990,9 @@ int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int
         if (cfg && cfg->chunk) {
             chunk = cfg->chunk;
         } else {
-            const int ctas = sms * (r->ctas_per_sm ? r->ctas_per_sm : kTmaDefaultCtas);
-            const int64_t per = (int64_t)kRows * kStageW * 4 * ctas;
+            const int64_t per = (int64_t)kRows * kStageW * 4 * sms;
             int64_t sps = (n + per - 1) / per;
-            sps = std::min<int64_t>(std::max<int64_t>(sps, 2), 16);
+            sps = std::min<int64_t>(std::max<int64_t>(sps, 2), 20);
             chunk = sps * kStageW;
         }
         const bool ok = aligned && n_avail / chunk >= 2;
@@ -1067,31 +1094,24 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
-    cuuint32_t box[2] = {(cuuint32_t)kStageW, (cuuint32_t)kRows};
+    cuuint32_t box[2] = {(cuuint32_t)kStageW, 32u};
     cuuint32_t estr[2] = {1, 1};
     if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(a.text), dims, strides, box,
-               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return DFA_ECUDA;
     TmaKernelFn fn = pick_tma(r.layout, find);
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, (const void*)fn) != cudaSuccess) return DFA_ECUDA;
-    const int ctas = r.ctas_per_sm ? r.ctas_per_sm : kTmaDefaultCtas;
-    const int slot_bytes = find ? 2 * kTSlots * kRows * 2 : 0;
-    const int budget = std::min(di->smem_per_sm / ctas - 1024, di->smem_optin) - (int)fa.sharedSizeBytes;
-    int nst = (budget - p.table_bytes - slot_bytes) / kStageBytes;
-    nst = std::min(nst, kMaxStages);
-    if (nst < 2) {
-        nst = std::min((di->smem_optin - (int)fa.sharedSizeBytes - p.table_bytes - slot_bytes) / kStageBytes,
-                       kMaxStages);
-        if (nst < 2) return DFA_EINVAL;
-    }
+    const int slot_bytes = find ? kDefer * kTSlots * kRows * 2 : 0;
+    const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.table_bytes - slot_bytes;
+    const int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
+    if (nst < 2) return DFA_EINVAL;
     p.nst = nst;
-    const int smem = nst * kStageBytes + p.table_bytes + slot_bytes;
+    const int smem = kWalkWarps * nst * kWarpStage + p.table_bytes + slot_bytes;
     int occ = occupancy((const void*)fn, kTmaThreads, smem, dev, di->smem_optin);
     if (occ <= 0) return DFA_ECUDA;
-    occ = std::min(occ, ctas);
-    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
+    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)di->sms);
     fn<<<(unsigned)grid, kTmaThreads, smem, st>>>(map, p);
     CUDA_TRY(cudaGetLastError());
     return DFA_OK;
