@@ -225,6 +225,55 @@ struct Walker {
         }
     }
 
+    // Slow path for a 16-byte vector holding at least one non-base byte:
+    // word by word, a word of four bases takes the four-step table, a word of
+    // four non-bases resets the walk, anything else goes byte by byte.
+    __device__ __forceinline__ void slow_vec(uint4 v, uint32_t r, uint32_t lim)
+    {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t b = word_bad(w[k]);
+            if (b == 0u) {
+                word_k4(w[k], r + 4 * k, lim);
+            } else if (((((b & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | b) & 0x80808080u) == 0x80808080u) {
+                e = 0u;                       // four non-bases: back to q0, nothing accepted
+            } else {
+                e &= 0xFFu;
+#pragma unroll
+                for (int i = 0; i < 4; i++) byte_d1((w[k] >> (8 * i)) & 0xFFu, r + 4 * k + i, lim);
+            }
+        }
+    }
+
+    // 64 contiguous bytes (four vectors) starting at offset r, one test for
+    // the common case of 64 bases.
+    __device__ __forceinline__ void vec4(uint4 v0, uint4 v1, uint4 v2, uint4 v3, uint32_t r)
+    {
+        if (LAYOUT == kLayoutK4) {
+            const uint32_t bad = word_bad(v0.x) | word_bad(v0.y) | word_bad(v0.z) | word_bad(v0.w) |
+                                 word_bad(v1.x) | word_bad(v1.y) | word_bad(v1.z) | word_bad(v1.w) |
+                                 word_bad(v2.x) | word_bad(v2.y) | word_bad(v2.z) | word_bad(v2.w) |
+                                 word_bad(v3.x) | word_bad(v3.y) | word_bad(v3.z) | word_bad(v3.w);
+            if (bad == 0u) {
+                word_k4(v0.x, r, 0); word_k4(v0.y, r + 4, 0); word_k4(v0.z, r + 8, 0); word_k4(v0.w, r + 12, 0);
+                word_k4(v1.x, r + 16, 0); word_k4(v1.y, r + 20, 0); word_k4(v1.z, r + 24, 0); word_k4(v1.w, r + 28, 0);
+                word_k4(v2.x, r + 32, 0); word_k4(v2.y, r + 36, 0); word_k4(v2.z, r + 40, 0); word_k4(v2.w, r + 44, 0);
+                word_k4(v3.x, r + 48, 0); word_k4(v3.y, r + 52, 0); word_k4(v3.z, r + 56, 0); word_k4(v3.w, r + 60, 0);
+            } else {
+                slow_vec(v0, r, 0);
+                slow_vec(v1, r + 16, 0);
+                slow_vec(v2, r + 32, 0);
+                slow_vec(v3, r + 48, 0);
+            }
+        } else {
+            vec(v0, r, 0);
+            vec(v1, r + 16, 0);
+            vec(v2, r + 32, 0);
+            vec(v3, r + 48, 0);
+        }
+    }
+
     __device__ __forceinline__ void vec(uint4 v, uint32_t r, uint32_t lim)
     {
         if (LAYOUT == kLayoutK4) {
@@ -235,12 +284,7 @@ struct Walker {
                 word_k4(v.z, r + 8, lim);
                 word_k4(v.w, r + 12, lim);
             } else {
-                e &= 0xFFu;
-                uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int k = 0; k < 4; k++)
-#pragma unroll
-                    for (int i = 0; i < 4; i++) byte_d1((w[k] >> (8 * i)) & 0xFFu, r + 4 * k + i, lim);
+                slow_vec(v, r, lim);
             }
         } else {
             word_stt(v.x, r, lim);
@@ -456,19 +500,23 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
 // tile is 512 rows of C bytes (row r of tile k = text[(512k + r)C, ...+C));
 // walker thread r walks row r.  The text is viewed as a 2-D tensor of C-byte
 // rows.  Each of the 16 walker warps streams its own 32 rows through a
-// private ring of shared-memory stages: its lane 0 issues a TMA load
-// (cp.async.bulk.tensor.2d, 64 bytes x 32 rows, 64-byte swizzle) for the
-// stage that will reuse a slot as soon as the warp has read it, so warps
-// never wait for one another's progress through a tile.  After the C bytes
-// of its rows a warp loads one more "halo" box, the first 64 bytes of rows
-// r+1: the m-1 bytes of overlap each row needs (Algorithm 1).
-//   warp 16 (tickets): hands out tile ids (in text order for find, by a
-//           static schedule for count) through a small ring;
+// private ring of shared-memory stages (64 bytes x 32 rows, one TMA box with
+// 64-byte swizzle, cp.async.bulk.tensor.2d), so warps never wait for one
+// another inside a tile.  After the C bytes of its rows a warp receives one
+// more "halo" box, the first 64 bytes of rows r+1: the m-1 bytes of overlap
+// each row needs (Algorithm 1).
+//   warp 16 (producer): lane w keeps walker warp w's ring full, polling the
+//           ring's free slots without blocking; lane 31 hands out tile ids
+//           (in text order for find, by a static schedule for count);
 //   warp 17 (scheduler, find only): sums the walker warps' counts of a tile,
 //           publishes them and resolves the tile's global offset by a
 //           warp-parallel decoupled look-back while the walkers go on; a
 //           tile's positions are written two tiles later, which hides the
 //           look-back's latency.
+// Walker warps only wait for a stage, walk it and release it.  In find mode a
+// sparse pattern (few occurrences expected) is walked without looking at
+// accept bits; a stage whose count moved is walked again from its saved
+// start state to record the positions.  Dense patterns record as they go.
 // Rows whose chunk or overlap runs past the full rows of the tensor (the end
 // of the text) are walked from global memory by their thread instead.
 
@@ -477,10 +525,14 @@ constexpr int kRows = kWalkWarps * 32;
 constexpr int kStageW = 64;
 constexpr int kWarpStage = 32 * kStageW;
 constexpr int kTmaThreads = kRows + 64;
+constexpr int kProducerWarp = kWalkWarps;
+constexpr int kSchedulerWarp = kWalkWarps + 1;
+constexpr int kTicketLane = 31;
 constexpr int kTSlots = 8;
 constexpr int kMaxStages = 8;
 constexpr int kDefer = 3;
 constexpr int kTicketRing = 8;
+constexpr int kDenseMaxM = 6;                     // patterns this short record inline
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
 struct TmaArgs {
@@ -528,6 +580,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Non-blocking probe of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -621,15 +687,6 @@ __device__ unsigned long long lookback_warp(unsigned long long* work, int64_t ti
     return excl;
 }
 
-template <bool FIND>
-__device__ __forceinline__ typename std::conditional<FIND, SlotSink, CountSink>::type make_sink(uint16_t* p)
-{
-    if constexpr (FIND)
-        return SlotSink{p, (uint32_t)kRows, (uint32_t)kTSlots, 0u, false};
-    else
-        return CountSink{};
-}
-
 // One tile's worth of a walker thread's state, kept until its positions are written.
 struct PendingRow {
     uint32_t cnt, excl;
@@ -637,12 +694,13 @@ struct PendingRow {
     int64_t s, e;
 };
 
-template <int LAYOUT, bool FIND>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+template <int LAYOUT, bool FIND, bool DENSE>
+__global__ void __maxnreg__(112)
     k_scan_tma(const __grid_constant__ CUtensorMap tmap, const TmaArgs p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_full[kWalkWarps][kMaxStages];
+    __shared__ __align__(8) uint64_t s_empty[kWalkWarps][kMaxStages];
     __shared__ __align__(8) uint64_t s_tready[kTicketRing];
     __shared__ __align__(8) uint64_t s_tfree[kTicketRing];
     __shared__ __align__(8) uint64_t s_counted[kDefer];
@@ -664,7 +722,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int w = 0; w < kWalkWarps; w++)
-            for (int i = 0; i < nst; i++) mbar_init(&s_full[w][i], 1);
+            for (int i = 0; i < nst; i++) {
+                mbar_init(&s_full[w][i], 1);
+                mbar_init(&s_empty[w][i], 1);
+            }
         for (int i = 0; i < kTicketRing; i++) {
             mbar_init(&s_tready[i], 1);
             mbar_init(&s_tfree[i], kWalkWarps);
@@ -682,30 +743,95 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     const uint32_t spt = sps + 1;                 // stages per tile, halo included
     const int64_t C = a.chunk;
 
-    if (warp == kWalkWarps) {
-        // ------------------------------------------------------ tickets
-        if (lane != 0) return;
-        for (int64_t kk = 0;; kk++) {
-            const int slot = (int)(kk % kTicketRing);
-            if (kk >= kTicketRing &&
-                !mbar_wait(&s_tfree[slot], (uint32_t)((kk / kTicketRing) - 1) & 1u, abort_flag, p))
-                return;
-            int64_t tile = FIND ? (int64_t)atomicAdd(a.work, 1ull)
-                                : (int64_t)blockIdx.x + kk * (int64_t)gridDim.x;
-            if (tile >= a.ntiles) tile = -1;
-            s_tiles[slot] = tile;
-            mbar_arrive(&s_tready[slot]);
-            if (tile < 0) return;
+    if (warp == kProducerWarp) {
+        // ------------------------------------------------------ producer
+        const bool ring_lane = lane < kWalkWarps;
+        uint8_t* ring = rings + (size_t)(ring_lane ? lane : 0) * nst * kWarpStage;
+        int64_t i_k = 0, i_tile = 0;              // ring: tile index and id being loaded
+        uint32_t i_s = 0, i_slot = 0, passes = 0, n_issued = 0;
+        bool ring_done = !ring_lane;
+        int64_t t_k = 0;                          // tickets handed out
+        bool tick_done = lane != kTicketLane;
+        long long idle_since = clock64();
+        bool aborted = false;
+        for (;;) {
+            bool progress = false;
+            if (!tick_done) {
+                const int slot = (int)((uint64_t)t_k % kTicketRing);
+                if (t_k < kTicketRing ||
+                    mbar_test_wait(&s_tfree[slot], (uint32_t)((uint64_t)t_k / kTicketRing - 1) & 1u)) {
+                    int64_t tile = FIND ? (int64_t)atomicAdd(a.work, 1ull)
+                                        : (int64_t)blockIdx.x + t_k * (int64_t)gridDim.x;
+                    if (tile >= a.ntiles) tile = -1;
+                    s_tiles[slot] = tile;
+                    mbar_arrive(&s_tready[slot]);
+                    t_k++;
+                    tick_done = tile < 0;
+                    progress = true;
+                }
+            }
+            for (int burst = 0; burst < 2 && !ring_done; burst++) {
+                if (passes > 0 && !mbar_test_wait(&s_empty[lane][i_slot], (passes - 1) & 1u)) break;
+                if (i_s == 0) {
+                    const int tslot = (int)((uint64_t)i_k % kTicketRing);
+                    if (!mbar_test_wait(&s_tready[tslot], (uint32_t)((uint64_t)i_k / kTicketRing) & 1u)) break;
+                    i_tile = s_tiles[tslot];
+                    if (i_tile < 0) {
+                        ring_done = true;
+                        break;
+                    }
+                }
+                mbar_arrive_expect_tx(&s_full[lane][i_slot], kWarpStage);
+                const int32_t x = i_s < sps ? (int32_t)(i_s * kStageW) : 0;
+                const int32_t y = (int32_t)(i_tile * kRows + lane * 32) + (i_s < sps ? 0 : 1);
+                tma_load_2d(ring + (size_t)i_slot * kWarpStage, &tmap, x, y, &s_full[lane][i_slot]);
+                n_issued++;
+                if (++i_slot == (uint32_t)nst) {
+                    i_slot = 0;
+                    passes++;
+                }
+                if (++i_s == spt) {
+                    i_s = 0;
+                    i_k++;
+                }
+                progress = true;
+            }
+            // every lane reaches the votes below on every pass
+            if (__all_sync(0xffffffffu, ring_done && tick_done)) break;
+            if (progress) {
+                idle_since = clock64();
+            } else if (*abort_flag) {
+                aborted = true;
+            } else if (!(ring_done && tick_done) && clock64() - idle_since > kWaitCycles) {
+                *abort_flag = 1;
+                atomicOr(p.fail_word, p.fail_bit);
+                aborted = true;
+            }
+            if (__any_sync(0xffffffffu, aborted)) {
+                aborted = true;
+                break;
+            }
+            if (!progress) __nanosleep(64);
         }
+        if (aborted && ring_lane) {
+            // wait for this ring's loads still in flight before the CTA's memory goes away
+            const uint32_t first = n_issued > (uint32_t)nst ? n_issued - nst : 0;
+            for (uint32_t f = first; f < n_issued; f++) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&s_full[lane][f % nst], (f / nst) & 1u) && clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
+        return;
     }
 
-    if (warp == kWalkWarps + 1) {
+    if (warp == kSchedulerWarp) {
         // ------------------------------------------------------ scheduler
         if (!FIND) return;
         const unsigned long long base = a.base_in ? *a.base_in : 0ull;
         for (int64_t k = 0;; k++) {
-            const int b = (int)(k % kDefer);
-            if (!warp_wait(&s_counted[b], (uint32_t)(k / kDefer) & 1u, abort_flag, p)) return;
+            const int b = (int)((uint64_t)k % kDefer);
+            if (!warp_wait(&s_counted[b], (uint32_t)((uint64_t)k / kDefer) & 1u, abort_flag, p)) return;
             const int64_t tile = s_tile_of[b];
             if (tile < 0) return;
             const uint32_t wt = lane < kWalkWarps ? s_wtot[b][lane] : 0u;
@@ -728,52 +854,22 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
 
     // ---------------------------------------------------------- walkers
-    using Sink = typename std::conditional<FIND, SlotSink, CountSink>::type;
     const int t = threadIdx.x;                    // row within the tile
     const uint32_t m = T.m;
     uint8_t* ring = rings + (size_t)warp * nst * kWarpStage;
     uint64_t* full = s_full[warp];
-    const uint32_t swz = (uint32_t)(lane >> 1) & 3u;   // 64-byte swizzle of this lane's row
-    int64_t end_k = INT64_MAX;                    // first tile index holding the end marker
-    uint32_t g_issue = 0;                         // next stage to load
+    uint64_t* empty = s_empty[warp];
+    // this lane's row inside a 2 KB box: 64-byte swizzle of its four 16-byte pieces
+    const uint32_t swz = (uint32_t)(lane >> 1) & 3u;
+    const uint32_t o0 = lane * kStageW + ((0u ^ swz) << 4), o1 = lane * kStageW + ((1u ^ swz) << 4);
+    const uint32_t o2 = lane * kStageW + ((2u ^ swz) << 4), o3 = lane * kStageW + ((3u ^ swz) << 4);
     bool aborted = false;
-
-    // tile id of this CTA's kk-th tile (warp-collective); false on abort
-    auto tile_id = [&](int64_t kk, int64_t* out) -> bool {
-        const int slot = (int)(kk % kTicketRing);
-        if (!warp_wait(&s_tready[slot], (uint32_t)(kk / kTicketRing) & 1u, abort_flag, p)) return false;
-        *out = s_tiles[slot];
-        return true;
-    };
-    // load the next stage of this warp's rows into the slot it will use
-    auto issue_next = [&]() -> bool {
-        const int64_t kk = g_issue / spt;
-        const uint32_t s = g_issue % spt;
-        if (kk >= end_k) return true;
-        int64_t tile;
-        if (!tile_id(kk, &tile)) return false;
-        if (tile < 0) {
-            end_k = kk;
-            return true;
-        }
-        if (lane == 0) {
-            const uint32_t slot = g_issue % nst;
-            mbar_arrive_expect_tx(&full[slot], kWarpStage);
-            const int32_t x = s < sps ? (int32_t)(s * kStageW) : 0;
-            const int32_t y = (int32_t)(tile * kRows + warp * 32) + (s < sps ? 0 : 1);
-            tma_load_2d(ring + (size_t)slot * kWarpStage, &tmap, x, y, &full[slot]);
-        }
-        g_issue++;
-        return true;
-    };
-
-    for (int i = 0; i < nst && !aborted; i++) aborted = !issue_next();
 
     unsigned long long total = 0;
     PendingRow p1{0, 0, false, 0, 0}, p2{0, 0, false, 0, 0};   // tiles k-1 and k-2
     auto flush = [&](const PendingRow& pr, int64_t kp) -> bool {
-        const int b = (int)(kp % kDefer);
-        if (!warp_wait(&s_ready[b], (uint32_t)(kp / kDefer) & 1u, abort_flag, p)) return false;
+        const int b = (int)((uint64_t)kp % kDefer);
+        if (!warp_wait(&s_ready[b], (uint32_t)((uint64_t)kp / kDefer) & 1u, abort_flag, p)) return false;
         if (pr.cnt == 0) return true;
         const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + pr.excl);
         const int64_t start0 = a.pos_base + pr.s - (int64_t)(m - 1);
@@ -790,55 +886,95 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         return true;
     };
 
-    uint32_t g = 0;                               // next stage to consume
+    uint32_t c_slot = 0, c_par = 0;               // consume cursor
     int64_t k = 0;
     while (!aborted) {
-        int64_t tile;
-        if (!tile_id(k, &tile)) {
+        const int tslot = (int)((uint64_t)k % kTicketRing);
+        if (!warp_wait(&s_tready[tslot], (uint32_t)((uint64_t)k / kTicketRing) & 1u, abort_flag, p)) {
             aborted = true;
             break;
         }
+        const int64_t tile = s_tiles[tslot];
         if (tile < 0) break;
         const int64_t row = tile * kRows + t;
         const int64_t s0 = row * C;
         const bool has = s0 < a.n_own;
         const int64_t e0 = has ? min(s0 + C, a.n_own) : s0;
         const bool tma_ok = has && e0 == s0 + C && row + 1 < p.nrows_full;
-        Sink sink = make_sink<FIND>(slots + (size_t)(k % kDefer) * kTSlots * kRows + t);
-        Walker<LAYOUT, false, Sink> w{T, sink, 0u, 0u};
+        const int kb = (int)((uint64_t)k % kDefer);
+        SlotSink ss{slots + (size_t)kb * kTSlots * kRows + t, (uint32_t)kRows, (uint32_t)kTSlots, 0u, false};
+        CountSink cs;
+        // the walk: inline recording for dense find, plain counting otherwise
+        Walker<LAYOUT, false, CountSink> w{T, cs, 0u, 0u};
+        Walker<LAYOUT, false, SlotSink> wd{T, ss, 0u, 0u};
         uint32_t cnt = 0;
         for (uint32_t s = 0; s < spt; s++) {
-            const uint32_t slot = g % nst;
-            if (!warp_wait(&full[slot], (g / nst) & 1u, abort_flag, p)) {
+            if (!warp_wait(&full[c_slot], c_par, abort_flag, p)) {
                 aborted = true;
                 break;
             }
             if (tma_ok) {
-                const uint8_t* row_p = ring + (size_t)slot * kWarpStage + lane * kStageW;
+                const uint8_t* rp = ring + (size_t)c_slot * kWarpStage;
+                const uint4 v0 = *reinterpret_cast<const uint4*>(rp + o0);
+                const uint4 v1 = *reinterpret_cast<const uint4*>(rp + o1);
+                const uint4 v2 = *reinterpret_cast<const uint4*>(rp + o2);
+                const uint4 v3 = *reinterpret_cast<const uint4*>(rp + o3);
                 if (s < sps) {
-#pragma unroll
-                    for (int j = 0; j < kStageW / 16; j++)
-                        w.vec(*reinterpret_cast<const uint4*>(row_p + ((j ^ swz) << 4)), s * kStageW + j * 16, 0);
+                    const uint32_t r = s * kStageW;
+                    if (FIND && DENSE) {
+                        wd.vec4(v0, v1, v2, v3, r);
+                    } else {
+                        const uint32_t e_in = w.e, c_in = w.cnt;
+                        w.vec4(v0, v1, v2, v3, r);
+                        if (FIND && w.cnt != c_in) {
+                            // a match in this stage: walk it again to record where
+                            Walker<LAYOUT, false, SlotSink> rw{T, ss, e_in, 0u};
+                            rw.vec4(v0, v1, v2, v3, r);
+                        }
+                    }
                 } else {
-                    Walker<LAYOUT, true, Sink> h{T, sink, w.e, w.cnt};
+                    // the overlap: ends below C + m - 1 belong to this row
                     const uint32_t lim = (uint32_t)C + m - 1;
-                    for (uint32_t j = 0; j * 16 < m - 1; j++)
-                        h.vec(*reinterpret_cast<const uint4*>(row_p + ((j ^ swz) << 4)),
-                              (uint32_t)C + j * 16, lim);
-                    cnt = h.cnt;
+                    if (FIND && DENSE) {
+                        Walker<LAYOUT, true, SlotSink> h{T, ss, wd.e, wd.cnt};
+                        h.vec(v0, (uint32_t)C, lim);
+                        if (m > 17) h.vec(v1, (uint32_t)C + 16, lim);
+                        if (m > 33) h.vec(v2, (uint32_t)C + 32, lim);
+                        if (m > 49) h.vec(v3, (uint32_t)C + 48, lim);
+                        cnt = h.cnt;
+                    } else {
+                        Walker<LAYOUT, true, CountSink> h{T, cs, w.e, w.cnt};
+                        h.vec(v0, (uint32_t)C, lim);
+                        if (m > 17) h.vec(v1, (uint32_t)C + 16, lim);
+                        if (m > 33) h.vec(v2, (uint32_t)C + 32, lim);
+                        if (m > 49) h.vec(v3, (uint32_t)C + 48, lim);
+                        if (FIND && h.cnt != w.cnt) {
+                            Walker<LAYOUT, true, SlotSink> hr{T, ss, w.e, 0u};
+                            hr.vec(v0, (uint32_t)C, lim);
+                            if (m > 17) hr.vec(v1, (uint32_t)C + 16, lim);
+                            if (m > 33) hr.vec(v2, (uint32_t)C + 32, lim);
+                            if (m > 49) hr.vec(v3, (uint32_t)C + 48, lim);
+                        }
+                        cnt = h.cnt;
+                    }
                 }
             }
             __syncwarp();
-            g++;
-            if (!issue_next()) {
-                aborted = true;
-                break;
+            if (lane == 0) mbar_arrive(&empty[c_slot]);
+            if (++c_slot == (uint32_t)nst) {
+                c_slot = 0;
+                c_par ^= 1u;
             }
         }
         if (aborted) break;
-        if (has && !tma_ok) cnt = walk_chunk<LAYOUT>(a, T, s0, e0, sink);
+        if (has && !tma_ok) {
+            if (FIND)
+                cnt = walk_chunk<LAYOUT>(a, T, s0, e0, ss);
+            else
+                cnt = walk_chunk<LAYOUT>(a, T, s0, e0, cs);
+        }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&s_tfree[k % kTicketRing]);
+        if (lane == 0) mbar_arrive(&s_tfree[tslot]);
 
         if (!FIND) {
             total += cnt;
@@ -849,31 +985,20 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
                 if (lane >= o) v += y;
             }
-            const int b = (int)(k % kDefer);
             if (lane == 31) {
-                s_wtot[b][warp] = v;
-                if (warp == 0) s_tile_of[b] = tile;
+                s_wtot[kb][warp] = v;
+                if (warp == 0) s_tile_of[kb] = tile;
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&s_counted[b]);
+            if (lane == 0) mbar_arrive(&s_counted[kb]);
             if (k >= 2 && !flush(p2, k - 2)) {
                 aborted = true;
                 break;
             }
             p2 = p1;
-            bool over = false;
-            if constexpr (FIND) over = sink.over;
-            p1 = PendingRow{cnt, v - cnt, over, s0, e0};
+            p1 = PendingRow{cnt, v - cnt, ss.over, s0, e0};
         }
         k++;
-    }
-    if (aborted) {
-        // drain this warp's loads still in flight before its memory goes away
-        for (uint32_t i = g; i < g_issue; i++) {
-            const long long t0 = clock64();
-            while (!mbar_try_wait(&full[i % nst], (i / nst) & 1u) && clock64() - t0 < kWaitCycles) {
-            }
-        }
     }
 
     if (!FIND) {
@@ -890,7 +1015,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
     if (aborted) return;
     // end of work: tell the scheduler, then write the last two tiles' positions
-    const int b = (int)(k % kDefer);
+    const int b = (int)((uint64_t)k % kDefer);
     if (lane == 0 && warp == 0) s_tile_of[b] = -1;
     __syncwarp();
     if (lane == 0) mbar_arrive(&s_counted[b]);
@@ -1052,10 +1177,15 @@ int table_smem(const dfa_table* t, int layout)
 
 typedef void (*TmaKernelFn)(const CUtensorMap, const TmaArgs);
 
-TmaKernelFn pick_tma(int layout, bool find)
+TmaKernelFn pick_tma(int layout, bool find, int m)
 {
-    if (layout == kLayoutK4) return find ? k_scan_tma<kLayoutK4, true> : k_scan_tma<kLayoutK4, false>;
-    return find ? k_scan_tma<kLayoutStt, true> : k_scan_tma<kLayoutStt, false>;
+    const bool dense = m <= kDenseMaxM;
+    if (layout == kLayoutK4) {
+        if (!find) return k_scan_tma<kLayoutK4, false, false>;
+        return dense ? k_scan_tma<kLayoutK4, true, true> : k_scan_tma<kLayoutK4, true, false>;
+    }
+    if (!find) return k_scan_tma<kLayoutStt, false, false>;
+    return dense ? k_scan_tma<kLayoutStt, true, true> : k_scan_tma<kLayoutStt, true, false>;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -1100,7 +1230,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return DFA_ECUDA;
-    TmaKernelFn fn = pick_tma(r.layout, find);
+    TmaKernelFn fn = pick_tma(r.layout, find, t->m);
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, (const void*)fn) != cudaSuccess) return DFA_ECUDA;
     const int slot_bytes = find ? kDefer * kTSlots * kRows * 2 : 0;

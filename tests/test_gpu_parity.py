@@ -22,10 +22,10 @@ CONFIGS = [
     dict(loader=1, layout=1, threads=512, chunk=256),
     dict(loader=1, layout=2, threads=256, chunk=64),
     dict(loader=1, layout=2, threads=128, chunk=1008),
-    # TMA-staged persistent kernel (loader 2): chunk = 80 x stages per tile
-    dict(loader=2, layout=1, chunk=160),
-    dict(loader=2, layout=1, chunk=400, ctas_per_sm=1),
-    dict(loader=2, layout=2, chunk=240),
+    # TMA-staged persistent kernel (loader 2): chunk = 64 x stages per tile
+    dict(loader=2, layout=1, chunk=128),
+    dict(loader=2, layout=1, chunk=384),
+    dict(loader=2, layout=2, chunk=192),
     dict(loader=2, layout=1, chunk=1280),
 ]
 
@@ -96,8 +96,8 @@ def test_planted_long_patterns(gpu, cfg):
 
 
 @pytest.mark.parametrize("cfg,chunk", [(dict(loader=1, layout=1, threads=128, chunk=64), 64),
-                                       (dict(loader=2, layout=1, chunk=160), 160),
-                                       (dict(loader=2, layout=2, chunk=80 * 3), 240)])
+                                       (dict(loader=2, layout=1, chunk=128), 128),
+                                       (dict(loader=2, layout=2, chunk=64 * 3), 192)])
 def test_border_plants(gpu, cfg, chunk):
     # occurrences planted at +-m around every chunk / tile border
     n = 256 * chunk * 6 + 77
@@ -136,8 +136,8 @@ def test_dense_matches_overflow_and_truncation(gpu):
     n = 200_003
     t = np.full(n, ord("A"), np.uint8)
     for cfg in (None, dict(loader=1, layout=1, threads=128, chunk=1024),
-                dict(loader=1, layout=2, threads=256, chunk=512), dict(loader=2, chunk=160),
-                dict(loader=2, layout=2, chunk=800)):
+                dict(loader=1, layout=2, threads=256, chunk=512), dict(loader=2, chunk=128),
+                dict(loader=2, layout=2, chunk=768)):
         for m in (1, 4, 64):
             _check(gpu, t, b"A" * m, cfg)
     # cap smaller than the count: exact count, first cap positions, ETRUNC
