@@ -178,6 +178,11 @@ const char* dfa_strerror(int code);
 /* Library version string. */
 const char* dfa_version(void);
 
+/* Text of the last CUDA failure (DFA_ECUDA) seen by the calling thread: the
+ * failing call and CUDA's message.  Empty if none.  Thread-local, static
+ * storage owned by the library. */
+const char* dfa_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

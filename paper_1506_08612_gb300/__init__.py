@@ -38,7 +38,10 @@ __all__ = ["Table", "DfaError", "dfa_build", "dfa_free", "dfa_export_stt", "dfa_
 class DfaError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
-        super().__init__(f"{what}: {dfa_strerror(code)} (code {code})" if what else dfa_strerror(code))
+        msg = f"{what}: {dfa_strerror(code)} (code {code})" if what else dfa_strerror(code)
+        if code == DFA_ECUDA:
+            msg += f" [{_lib.dfa_last_error().decode(errors='replace')}]"
+        super().__init__(msg)
 
 
 def dfa_strerror(code: int) -> str:

@@ -38,6 +38,7 @@ def _declare(lib):
                           ctypes.c_int),
         "dfa_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "dfa_version": ([], ctypes.c_char_p),
+        "dfa_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -63,12 +63,27 @@ struct ScanArgs {
     unsigned long long* work;             // [ticket, status, desc[ntiles]]
 };
 
+// Tables in shared memory, as 32-bit shared-window addresses.
 struct SmemTab {
-    const uint16_t* k4;
-    const uint8_t* d1;
-    const uint8_t* stt;
+    uint32_t k4;    // (m+1)*256 u16
+    uint32_t d1;    // (m+1)*4 u8
+    uint32_t stt;   // (m+1)*256 u8
     uint32_t m;
 };
+
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr)
+{
+    unsigned short v;
+    asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lds_u8(uint32_t addr)
+{
+    unsigned short v;
+    asm("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v & 0xFFu;
+}
 
 // ---------------------------------------------------------------- helpers
 
@@ -104,19 +119,19 @@ __device__ __forceinline__ uint32_t word_bad(uint32_t x)
 // (x & 0x06060606) holds the 2-bit codes at bits 8k+1; the multiply gathers
 // them, first byte lowest, into bits 24..31 without carries; byte_perm forms
 // the table index (state << 8) | code4.
-__device__ __forceinline__ uint32_t k4_next(const uint16_t* __restrict__ k4, uint32_t e, uint32_t x)
+__device__ __forceinline__ uint32_t k4_next(uint32_t k4, uint32_t e, uint32_t x)
 {
     uint32_t code = (x & 0x06060606u) * 0x00820820u;
     uint32_t idx = __byte_perm(code, e, 0x7743u);
-    return k4[idx];
+    return lds_u16(k4 + 2u * idx);
 }
 
 // One automaton step on one raw byte (any byte value).
-__device__ __forceinline__ uint32_t byte_next(const uint8_t* __restrict__ d1, uint32_t q, uint32_t c)
+__device__ __forceinline__ uint32_t byte_next(uint32_t d1, uint32_t q, uint32_t c)
 {
     uint32_t t = (c >> 2) & ~(c >> 1) & 1u;
     bool ok = ((c ^ (t * 0x11u)) & 0xD9u) == 0x41u;
-    uint32_t nq = d1[q * 4u + ((c >> 1) & 3u)];
+    uint32_t nq = lds_u8(d1 + q * 4u + ((c >> 1) & 3u));
     return ok ? nq : 0u;
 }
 
@@ -217,7 +232,7 @@ struct Walker {
     {
 #pragma unroll
         for (uint32_t i = 0; i < 4; i++) {
-            e = T.stt[__byte_perm(x, e, 0x7740u | i)];
+            e = lds_u8(T.stt + __byte_perm(x, e, 0x7740u | i));
             if (e == T.m && (!LIM || r + i < lim)) {
                 cnt++;
                 if (Sink::kRecord) sink.put(r + i);
@@ -330,7 +345,7 @@ __device__ uint32_t walk_chunk(const ScanArgs& a, const SmemTab& T, int64_t s, i
         if (LAYOUT == kLayoutK4)
             q = byte_next(T.d1, q, c);
         else
-            q = T.stt[(q << 8) | c];
+            q = lds_u8(T.stt + ((q << 8) | c));
         if (q == m) {
             cnt++;
             if (Sink::kRecord) sink.put((uint32_t)(j - s));
@@ -345,18 +360,19 @@ __device__ __forceinline__ SmemTab load_tables(const ScanArgs& a, uint8_t* smem)
     SmemTab T;
     T.m = (uint32_t)a.m;
     int bytes, src_off;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem);
     if (LAYOUT == kLayoutK4) {
         bytes = a.k4_bytes + a.d1_bytes;
         src_off = 0;
-        T.k4 = reinterpret_cast<const uint16_t*>(smem);
-        T.d1 = smem + a.k4_bytes;
-        T.stt = nullptr;
+        T.k4 = base;
+        T.d1 = base + (uint32_t)a.k4_bytes;
+        T.stt = 0;
     } else {
         bytes = a.stt_bytes;
         src_off = a.k4_bytes + a.d1_bytes;
-        T.k4 = nullptr;
-        T.d1 = nullptr;
-        T.stt = smem;
+        T.k4 = 0;
+        T.d1 = 0;
+        T.stt = base;
     }
     const uint4* src = reinterpret_cast<const uint4*>(a.tab + src_off);
     uint4* dst = reinterpret_cast<uint4*>(smem);
@@ -505,15 +521,16 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
 // another inside a tile.  After the C bytes of its rows a warp receives one
 // more "halo" box, the first 64 bytes of rows r+1: the m-1 bytes of overlap
 // each row needs (Algorithm 1).
-//   warp 16 (producer): lane w keeps walker warp w's ring full, polling the
-//           ring's free slots without blocking; lane 31 hands out tile ids
-//           (in text order for find, by a static schedule for count);
+//   walker warps refill their own rings: lane 0 reloads a slot as soon as the
+//           warp has read it (measured faster than a polling producer);
+//   warp 16 (tickets): hands out tile ids through a small ring (in text
+//           order for find, by a static schedule for count);
 //   warp 17 (scheduler, find only): sums the walker warps' counts of a tile,
 //           publishes them and resolves the tile's global offset by a
 //           warp-parallel decoupled look-back while the walkers go on; a
 //           tile's positions are written two tiles later, which hides the
 //           look-back's latency.
-// Walker warps only wait for a stage, walk it and release it.  In find mode a
+// In find mode a
 // sparse pattern (few occurrences expected) is walked without looking at
 // accept bits; a stage whose count moved is walked again from its saved
 // start state to record the positions.  Dense patterns record as they go.
@@ -527,9 +544,11 @@ constexpr int kWarpStage = 32 * kStageW;
 constexpr int kTmaThreads = kRows + 64;
 constexpr int kProducerWarp = kWalkWarps;
 constexpr int kSchedulerWarp = kWalkWarps + 1;
-constexpr int kTicketLane = 31;
 constexpr int kTSlots = 8;
-constexpr int kMaxStages = 8;
+// Stages in flight per warp ring.  With 16 rings of 64-byte x 32-row boxes a
+// depth of 3-4 streams at the HBM rate on GB300; deeper rings were measured to
+// halve the throughput, so the depth is capped here.
+constexpr int kMaxStages = 4;
 constexpr int kDefer = 3;
 constexpr int kTicketRing = 8;
 constexpr int kDenseMaxM = 6;                     // patterns this short record inline
@@ -611,6 +630,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// 16-byte shared-memory load that is always issued (never merged with an
+// earlier load of the same address), so a value need not stay in registers.
+__device__ __forceinline__ uint4 lds128_fresh(const void* p)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(smem_u32(p)));
+    return v;
+}
+
 __device__ __forceinline__ void named_sync_walkers()
 {
     asm volatile("bar.sync 1, %0;" ::"n"(kRows) : "memory");
@@ -687,20 +717,58 @@ __device__ unsigned long long lookback_warp(unsigned long long* work, int64_t ti
     return excl;
 }
 
-// One tile's worth of a walker thread's state, kept until its positions are written.
+// Cold paths of the TMA walkers, kept out of line so that the hot loop's
+// register allocation does not pay for them.
+//   replay_stage: walk a 64-byte stage again from its start entry and record
+//                 the accepts (a sparse pattern's stage whose count moved);
+//   replay_halo:  the same for the overlap stage, ends limited to lim;
+//   walk_cold:    a row walked from global memory (edge rows, overflow).
+template <int LAYOUT>
+__device__ __noinline__ uint2 replay_stage(SmemTab T, uint16_t* slots, uint32_t n, uint32_t over,
+                                           uint32_t e_in, const uint8_t* rp, uint32_t ob, uint32_t r)
+{
+    SlotSink ss{slots, (uint32_t)kRows, (uint32_t)kTSlots, n, over != 0u};
+    Walker<LAYOUT, false, SlotSink> rw{T, ss, e_in, 0u};
+    rw.vec4(lds128_fresh(rp + ob), lds128_fresh(rp + (ob ^ 16u)), lds128_fresh(rp + (ob ^ 32u)),
+            lds128_fresh(rp + (ob ^ 48u)), r);
+    return make_uint2(ss.n, ss.over ? 1u : 0u);
+}
+
+template <int LAYOUT>
+__device__ __noinline__ uint2 replay_halo(SmemTab T, uint16_t* slots, uint32_t n, uint32_t over,
+                                          uint32_t e_in, const uint8_t* rp, uint32_t ob, uint32_t C,
+                                          uint32_t lim)
+{
+    SlotSink ss{slots, (uint32_t)kRows, (uint32_t)kTSlots, n, over != 0u};
+    Walker<LAYOUT, true, SlotSink> hr{T, ss, e_in, 0u};
+    const uint32_t m = T.m;
+    hr.vec(lds128_fresh(rp + ob), C, lim);
+    if (m > 17) hr.vec(lds128_fresh(rp + (ob ^ 16u)), C + 16, lim);
+    if (m > 33) hr.vec(lds128_fresh(rp + (ob ^ 32u)), C + 32, lim);
+    if (m > 49) hr.vec(lds128_fresh(rp + (ob ^ 48u)), C + 48, lim);
+    return make_uint2(ss.n, ss.over ? 1u : 0u);
+}
+
+template <int LAYOUT, class Sink>
+__device__ __noinline__ uint32_t walk_cold(const ScanArgs a, SmemTab T, int64_t s, int64_t e, Sink* sink)
+{
+    return walk_chunk<LAYOUT>(a, T, s, e, *sink);
+}
+
+// One tile's worth of a walker thread's state, kept until its positions are
+// written (the row's bounds are recomputed from the tile id).
 struct PendingRow {
     uint32_t cnt, excl;
+    int32_t tile;
     bool over;
-    int64_t s, e;
 };
 
 template <int LAYOUT, bool FIND, bool DENSE>
-__global__ void __maxnreg__(112)
+__global__ void __launch_bounds__(kTmaThreads, 1)
     k_scan_tma(const __grid_constant__ CUtensorMap tmap, const TmaArgs p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_full[kWalkWarps][kMaxStages];
-    __shared__ __align__(8) uint64_t s_empty[kWalkWarps][kMaxStages];
     __shared__ __align__(8) uint64_t s_tready[kTicketRing];
     __shared__ __align__(8) uint64_t s_tfree[kTicketRing];
     __shared__ __align__(8) uint64_t s_counted[kDefer];
@@ -722,10 +790,7 @@ __global__ void __maxnreg__(112)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int w = 0; w < kWalkWarps; w++)
-            for (int i = 0; i < nst; i++) {
-                mbar_init(&s_full[w][i], 1);
-                mbar_init(&s_empty[w][i], 1);
-            }
+            for (int i = 0; i < nst; i++) mbar_init(&s_full[w][i], 1);
         for (int i = 0; i < kTicketRing; i++) {
             mbar_init(&s_tready[i], 1);
             mbar_init(&s_tfree[i], kWalkWarps);
@@ -744,85 +809,20 @@ __global__ void __maxnreg__(112)
     const int64_t C = a.chunk;
 
     if (warp == kProducerWarp) {
-        // ------------------------------------------------------ producer
-        const bool ring_lane = lane < kWalkWarps;
-        uint8_t* ring = rings + (size_t)(ring_lane ? lane : 0) * nst * kWarpStage;
-        int64_t i_k = 0, i_tile = 0;              // ring: tile index and id being loaded
-        uint32_t i_s = 0, i_slot = 0, passes = 0, n_issued = 0;
-        bool ring_done = !ring_lane;
-        int64_t t_k = 0;                          // tickets handed out
-        bool tick_done = lane != kTicketLane;
-        long long idle_since = clock64();
-        bool aborted = false;
-        for (;;) {
-            bool progress = false;
-            if (!tick_done) {
-                const int slot = (int)((uint64_t)t_k % kTicketRing);
-                if (t_k < kTicketRing ||
-                    mbar_test_wait(&s_tfree[slot], (uint32_t)((uint64_t)t_k / kTicketRing - 1) & 1u)) {
-                    int64_t tile = FIND ? (int64_t)atomicAdd(a.work, 1ull)
-                                        : (int64_t)blockIdx.x + t_k * (int64_t)gridDim.x;
-                    if (tile >= a.ntiles) tile = -1;
-                    s_tiles[slot] = tile;
-                    mbar_arrive(&s_tready[slot]);
-                    t_k++;
-                    tick_done = tile < 0;
-                    progress = true;
-                }
-            }
-            for (int burst = 0; burst < 2 && !ring_done; burst++) {
-                if (passes > 0 && !mbar_test_wait(&s_empty[lane][i_slot], (passes - 1) & 1u)) break;
-                if (i_s == 0) {
-                    const int tslot = (int)((uint64_t)i_k % kTicketRing);
-                    if (!mbar_test_wait(&s_tready[tslot], (uint32_t)((uint64_t)i_k / kTicketRing) & 1u)) break;
-                    i_tile = s_tiles[tslot];
-                    if (i_tile < 0) {
-                        ring_done = true;
-                        break;
-                    }
-                }
-                mbar_arrive_expect_tx(&s_full[lane][i_slot], kWarpStage);
-                const int32_t x = i_s < sps ? (int32_t)(i_s * kStageW) : 0;
-                const int32_t y = (int32_t)(i_tile * kRows + lane * 32) + (i_s < sps ? 0 : 1);
-                tma_load_2d(ring + (size_t)i_slot * kWarpStage, &tmap, x, y, &s_full[lane][i_slot]);
-                n_issued++;
-                if (++i_slot == (uint32_t)nst) {
-                    i_slot = 0;
-                    passes++;
-                }
-                if (++i_s == spt) {
-                    i_s = 0;
-                    i_k++;
-                }
-                progress = true;
-            }
-            // every lane reaches the votes below on every pass
-            if (__all_sync(0xffffffffu, ring_done && tick_done)) break;
-            if (progress) {
-                idle_since = clock64();
-            } else if (*abort_flag) {
-                aborted = true;
-            } else if (!(ring_done && tick_done) && clock64() - idle_since > kWaitCycles) {
-                *abort_flag = 1;
-                atomicOr(p.fail_word, p.fail_bit);
-                aborted = true;
-            }
-            if (__any_sync(0xffffffffu, aborted)) {
-                aborted = true;
-                break;
-            }
-            if (!progress) __nanosleep(64);
+        // ------------------------------------------------------ tickets
+        if (lane != 0) return;
+        for (int64_t kk = 0;; kk++) {
+            const int slot = (int)((uint64_t)kk % kTicketRing);
+            if (kk >= kTicketRing &&
+                !mbar_wait(&s_tfree[slot], (uint32_t)((uint64_t)kk / kTicketRing - 1) & 1u, abort_flag, p))
+                return;
+            int64_t tile = FIND ? (int64_t)atomicAdd(a.work, 1ull)
+                                : (int64_t)blockIdx.x + kk * (int64_t)gridDim.x;
+            if (tile >= a.ntiles) tile = -1;
+            s_tiles[slot] = tile;
+            mbar_arrive(&s_tready[slot]);
+            if (tile < 0) return;
         }
-        if (aborted && ring_lane) {
-            // wait for this ring's loads still in flight before the CTA's memory goes away
-            const uint32_t first = n_issued > (uint32_t)nst ? n_issued - nst : 0;
-            for (uint32_t f = first; f < n_issued; f++) {
-                const long long t0 = clock64();
-                while (!mbar_try_wait(&s_full[lane][f % nst], (f / nst) & 1u) && clock64() - t0 < kWaitCycles) {
-                }
-            }
-        }
-        return;
     }
 
     if (warp == kSchedulerWarp) {
@@ -858,21 +858,59 @@ __global__ void __maxnreg__(112)
     const uint32_t m = T.m;
     uint8_t* ring = rings + (size_t)warp * nst * kWarpStage;
     uint64_t* full = s_full[warp];
-    uint64_t* empty = s_empty[warp];
     // this lane's row inside a 2 KB box: 64-byte swizzle of its four 16-byte pieces
-    const uint32_t swz = (uint32_t)(lane >> 1) & 3u;
-    const uint32_t o0 = lane * kStageW + ((0u ^ swz) << 4), o1 = lane * kStageW + ((1u ^ swz) << 4);
-    const uint32_t o2 = lane * kStageW + ((2u ^ swz) << 4), o3 = lane * kStageW + ((3u ^ swz) << 4);
+    // piece j of this lane's row sits at ob ^ (j << 4)
+    const uint32_t ob = lane * kStageW + ((((uint32_t)lane >> 1) & 3u) << 4);
     bool aborted = false;
 
+    // tile id of this CTA's kk-th tile (warp-collective); false on abort
+    auto tile_id = [&](int64_t kk, int64_t* out) -> bool {
+        const int slot = (int)((uint64_t)kk % kTicketRing);
+        if (!warp_wait(&s_tready[slot], (uint32_t)((uint64_t)kk / kTicketRing) & 1u, abort_flag, p)) return false;
+        *out = s_tiles[slot];
+        return true;
+    };
+    // refill cursor: the next stage of this warp's rows to load, kept as
+    // (tile index, stage within the tile, ring slot) without divisions; the
+    // warp's lane 0 loads a slot again as soon as the warp has read it
+    int64_t i_k = 0, i_tile = 0;
+    uint32_t i_s = 0, i_slot = 0, n_issued = 0, n_consumed = 0;
+    bool i_done = false;
+    auto issue_next = [&]() -> bool {
+        if (i_done) return true;
+        if (i_s == 0) {
+            if (!tile_id(i_k, &i_tile)) return false;
+            if (i_tile < 0) {
+                i_done = true;
+                return true;
+            }
+        }
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&full[i_slot], kWarpStage);
+            const int32_t x = i_s < sps ? (int32_t)(i_s * kStageW) : 0;
+            const int32_t y = (int32_t)(i_tile * kRows + warp * 32) + (i_s < sps ? 0 : 1);
+            tma_load_2d(ring + (size_t)i_slot * kWarpStage, &tmap, x, y, &full[i_slot]);
+        }
+        n_issued++;
+        if (++i_slot == (uint32_t)nst) i_slot = 0;
+        if (++i_s == spt) {
+            i_s = 0;
+            i_k++;
+        }
+        return true;
+    };
+    for (int i = 0; i < nst && !aborted; i++) aborted = !issue_next();
+
     unsigned long long total = 0;
-    PendingRow p1{0, 0, false, 0, 0}, p2{0, 0, false, 0, 0};   // tiles k-1 and k-2
+    PendingRow p1{0, 0, 0, false}, p2{0, 0, 0, false};   // tiles k-1 and k-2
     auto flush = [&](const PendingRow& pr, int64_t kp) -> bool {
         const int b = (int)((uint64_t)kp % kDefer);
         if (!warp_wait(&s_ready[b], (uint32_t)((uint64_t)kp / kDefer) & 1u, abort_flag, p)) return false;
         if (pr.cnt == 0) return true;
         const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + pr.excl);
-        const int64_t start0 = a.pos_base + pr.s - (int64_t)(m - 1);
+        const int64_t ps = ((int64_t)pr.tile * kRows + t) * C;
+        const int64_t pe = min(ps + C, a.n_own);
+        const int64_t start0 = a.pos_base + ps - (int64_t)(m - 1);
         if (!pr.over) {
             const uint16_t* sl = slots + (size_t)b * kTSlots * kRows + t;
             for (uint32_t j = 0; j < pr.cnt; j++) {
@@ -881,7 +919,7 @@ __global__ void __maxnreg__(112)
             }
         } else if (g0 < a.cap) {
             GlobalSink gs{a.pos, a.cap, g0, start0};
-            walk_chunk<LAYOUT>(a, T, pr.s, pr.e, gs);
+            walk_cold<LAYOUT>(a, T, ps, pe, &gs);
         }
         return true;
     };
@@ -890,11 +928,11 @@ __global__ void __maxnreg__(112)
     int64_t k = 0;
     while (!aborted) {
         const int tslot = (int)((uint64_t)k % kTicketRing);
-        if (!warp_wait(&s_tready[tslot], (uint32_t)((uint64_t)k / kTicketRing) & 1u, abort_flag, p)) {
+        int64_t tile;
+        if (!tile_id(k, &tile)) {
             aborted = true;
             break;
         }
-        const int64_t tile = s_tiles[tslot];
         if (tile < 0) break;
         const int64_t row = tile * kRows + t;
         const int64_t s0 = row * C;
@@ -915,10 +953,10 @@ __global__ void __maxnreg__(112)
             }
             if (tma_ok) {
                 const uint8_t* rp = ring + (size_t)c_slot * kWarpStage;
-                const uint4 v0 = *reinterpret_cast<const uint4*>(rp + o0);
-                const uint4 v1 = *reinterpret_cast<const uint4*>(rp + o1);
-                const uint4 v2 = *reinterpret_cast<const uint4*>(rp + o2);
-                const uint4 v3 = *reinterpret_cast<const uint4*>(rp + o3);
+                const uint4 v0 = *reinterpret_cast<const uint4*>(rp + ob);
+                const uint4 v1 = *reinterpret_cast<const uint4*>(rp + (ob ^ 16u));
+                const uint4 v2 = *reinterpret_cast<const uint4*>(rp + (ob ^ 32u));
+                const uint4 v3 = *reinterpret_cast<const uint4*>(rp + (ob ^ 48u));
                 if (s < sps) {
                     const uint32_t r = s * kStageW;
                     if (FIND && DENSE) {
@@ -928,8 +966,10 @@ __global__ void __maxnreg__(112)
                         w.vec4(v0, v1, v2, v3, r);
                         if (FIND && w.cnt != c_in) {
                             // a match in this stage: walk it again to record where
-                            Walker<LAYOUT, false, SlotSink> rw{T, ss, e_in, 0u};
-                            rw.vec4(v0, v1, v2, v3, r);
+                            // (the stage is re-read: its slot is released below)
+                            const uint2 st = replay_stage<LAYOUT>(T, ss.slots, ss.n, ss.over, e_in, rp, ob, r);
+                            ss.n = st.x;
+                            ss.over = st.y != 0u;
                         }
                     }
                 } else {
@@ -949,29 +989,32 @@ __global__ void __maxnreg__(112)
                         if (m > 33) h.vec(v2, (uint32_t)C + 32, lim);
                         if (m > 49) h.vec(v3, (uint32_t)C + 48, lim);
                         if (FIND && h.cnt != w.cnt) {
-                            Walker<LAYOUT, true, SlotSink> hr{T, ss, w.e, 0u};
-                            hr.vec(v0, (uint32_t)C, lim);
-                            if (m > 17) hr.vec(v1, (uint32_t)C + 16, lim);
-                            if (m > 33) hr.vec(v2, (uint32_t)C + 32, lim);
-                            if (m > 49) hr.vec(v3, (uint32_t)C + 48, lim);
+                            const uint2 st = replay_halo<LAYOUT>(T, ss.slots, ss.n, ss.over, w.e, rp, ob,
+                                                                 (uint32_t)C, lim);
+                            ss.n = st.x;
+                            ss.over = st.y != 0u;
                         }
                         cnt = h.cnt;
                     }
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[c_slot]);
+            n_consumed++;
             if (++c_slot == (uint32_t)nst) {
                 c_slot = 0;
                 c_par ^= 1u;
+            }
+            if (!issue_next()) {                  // reload the slot just read
+                aborted = true;
+                break;
             }
         }
         if (aborted) break;
         if (has && !tma_ok) {
             if (FIND)
-                cnt = walk_chunk<LAYOUT>(a, T, s0, e0, ss);
+                cnt = walk_cold<LAYOUT>(a, T, s0, e0, &ss);
             else
-                cnt = walk_chunk<LAYOUT>(a, T, s0, e0, cs);
+                cnt = walk_cold<LAYOUT>(a, T, s0, e0, &cs);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_tfree[tslot]);
@@ -996,11 +1039,23 @@ __global__ void __maxnreg__(112)
                 break;
             }
             p2 = p1;
-            p1 = PendingRow{cnt, v - cnt, ss.over, s0, e0};
+            p1 = PendingRow{cnt, v - cnt, (int32_t)tile, ss.over};
         }
         k++;
     }
 
+    if (aborted) {
+        // wait for this warp's loads still in flight before the CTA's memory goes away
+        for (uint32_t i = n_consumed; i < n_issued; i++) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&full[c_slot], c_par) && clock64() - t0 < kWaitCycles) {
+            }
+            if (++c_slot == (uint32_t)nst) {
+                c_slot = 0;
+                c_par ^= 1u;
+            }
+        }
+    }
     if (!FIND) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
@@ -1025,10 +1080,25 @@ __global__ void __maxnreg__(112)
 
 // ---------------------------------------------------------------- host side
 
+// Text of the last CUDA failure seen by this thread (dfa_last_error).
+thread_local char g_last_error[256] = "";
+
+int cuda_fail(cudaError_t err, const char* what)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(err));
+    return DFA_ECUDA;
+}
+
+int fail(const char* what)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s", what);
+    return DFA_ECUDA;
+}
+
 #define CUDA_TRY(x)                                   \
     do {                                              \
         cudaError_t err_ = (x);                       \
-        if (err_ != cudaSuccess) return DFA_ECUDA;    \
+        if (err_ != cudaSuccess) return cuda_fail(err_, #x); \
     } while (0)
 
 struct DeviceInfo {
@@ -1199,7 +1269,7 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !p)
-            return DFA_ECUDA;
+            return fail("cuTensorMapEncodeTiled entry point not found");
         g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
     *fn = g_encode;
@@ -1229,10 +1299,10 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(a.text), dims, strides, box,
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return DFA_ECUDA;
+        return fail("cuTensorMapEncodeTiled failed");
     TmaKernelFn fn = pick_tma(r.layout, find, t->m);
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, (const void*)fn) != cudaSuccess) return DFA_ECUDA;
+    CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)fn));
     const int slot_bytes = find ? kDefer * kTSlots * kRows * 2 : 0;
     const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.table_bytes - slot_bytes;
     const int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
@@ -1240,7 +1310,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.nst = nst;
     const int smem = kWalkWarps * nst * kWarpStage + p.table_bytes + slot_bytes;
     int occ = occupancy((const void*)fn, kTmaThreads, smem, dev, di->smem_optin);
-    if (occ <= 0) return DFA_ECUDA;
+    if (occ <= 0) return fail("TMA scan kernel does not fit on an SM (occupancy 0)");
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)di->sms);
     fn<<<(unsigned)grid, kTmaThreads, smem, st>>>(map, p);
     CUDA_TRY(cudaGetLastError());
@@ -1292,7 +1362,7 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
     KernelFn fn = pick_count(r.layout, r.threads);
     const int smem = table_smem(t, r.layout);
     int occ = occupancy((const void*)fn, r.threads, smem, dev, di->smem_optin);
-    if (occ <= 0) return DFA_ECUDA;
+    if (occ <= 0) return fail("scan kernel does not fit on an SM (occupancy 0)");
     if (r.ctas_per_sm) occ = std::min(occ, r.ctas_per_sm);
     int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
     fn<<<(unsigned)grid, r.threads, smem, st>>>(a);
@@ -1337,7 +1407,7 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     KernelFn fn = pick_find(r.layout, r.threads);
     const int smem = ((table_smem(t, r.layout) + 15) & ~15) + kSlots * r.threads * 2;
     int occ = occupancy((const void*)fn, r.threads, smem, dev, di->smem_optin);
-    if (occ <= 0) return DFA_ECUDA;
+    if (occ <= 0) return fail("scan kernel does not fit on an SM (occupancy 0)");
     if (r.ctas_per_sm) occ = std::min(occ, r.ctas_per_sm);
     int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
     fn<<<(unsigned)grid, r.threads, smem, st>>>(a);
@@ -1574,5 +1644,7 @@ const char* dfa_strerror(int code)
 }
 
 const char* dfa_version(void) { return "dnadfa 0.1 (sm_103a)"; }
+
+const char* dfa_last_error(void) { return g_last_error; }
 
 }  // extern "C"
