@@ -513,41 +513,43 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
 // ---------------------------------------------------------------- TMA-staged kernel
 //
 // Persistent, warp-specialised form of the same walk, one CTA per SM.  A
-// tile is 512 rows of C bytes (row r of tile k = text[(512k + r)C, ...+C));
-// walker thread r walks row r.  The text is viewed as a 2-D tensor of C-byte
-// rows.  Each of the 16 walker warps streams its own 32 rows through a
-// private ring of shared-memory stages (64 bytes x 32 rows, one TMA box with
-// 64-byte swizzle, cp.async.bulk.tensor.2d), so warps never wait for one
-// another inside a tile.  After the C bytes of its rows a warp receives one
-// more "halo" box, the first 64 bytes of rows r+1: the m-1 bytes of overlap
-// each row needs (Algorithm 1).
-//   walker warps refill their own rings: lane 0 reloads a slot as soon as the
-//           warp has read it (measured faster than a polling producer);
-//   warp 16 (tickets): hands out tile ids through a small ring (in text
-//           order for find, by a static schedule for count);
-//   warp 17 (scheduler, find only): sums the walker warps' counts of a tile,
+// tile is 512 rows of C bytes (row r of tile k = text[(512k + r)C, ...+C)),
+// walked by 8 warps; each lane walks two rows (32 apart) with their two
+// automaton chains interleaved, which hides the latency of the table lookups.
+// The text is viewed as a 2-D tensor of C-byte rows.  Each walker warp
+// streams its own 64 rows through a private ring of shared-memory stages
+// (64 bytes x 64 rows, one TMA box with 64-byte swizzle,
+// cp.async.bulk.tensor.2d); its lane 0 reloads a slot as soon as the warp has
+// read it, so warps never wait for one another inside a tile.  After the C
+// bytes of its rows a warp receives one more "halo" box, the first 64 bytes
+// of rows r+1: the m-1 bytes of overlap each row needs (Algorithm 1).
+//   warp 8 (tickets): hands out tile ids through a small ring (in text order
+//           for find, by a static schedule for count);
+//   warp 9 (scheduler, find only): sums the walker warps' counts of a tile,
 //           publishes them and resolves the tile's global offset by a
 //           warp-parallel decoupled look-back while the walkers go on; a
 //           tile's positions are written two tiles later, which hides the
 //           look-back's latency.
-// In find mode a
-// sparse pattern (few occurrences expected) is walked without looking at
-// accept bits; a stage whose count moved is walked again from its saved
-// start state to record the positions.  Dense patterns record as they go.
+// In find mode a sparse pattern (few occurrences expected) is walked without
+// looking at accept bits; a stage whose count moved is walked again from its
+// saved start state to record the positions.  Dense patterns record inline.
 // Rows whose chunk or overlap runs past the full rows of the tensor (the end
 // of the text) are walked from global memory by their thread instead.
 
 constexpr int kWalkWarps = 16;
-constexpr int kRows = kWalkWarps * 32;
+constexpr int kRPL = 1;                          // rows walked by each lane (16 warps x 1 row measured best)
+constexpr int kWarpRows = 32 * kRPL;             // rows of one warp's box
+constexpr int kRows = kWalkWarps * kWarpRows;    // rows of a tile
+constexpr int kWalkThreads = kWalkWarps * 32;
 constexpr int kStageW = 64;
-constexpr int kWarpStage = 32 * kStageW;
-constexpr int kTmaThreads = kRows + 64;
+constexpr int kWarpStage = kWarpRows * kStageW;  // one TMA box
+constexpr int kTmaThreads = kWalkThreads + 64;
 constexpr int kProducerWarp = kWalkWarps;
 constexpr int kSchedulerWarp = kWalkWarps + 1;
 constexpr int kTSlots = 8;
-// Stages in flight per warp ring.  With 16 rings of 64-byte x 32-row boxes a
-// depth of 3-4 streams at the HBM rate on GB300; deeper rings were measured to
-// halve the throughput, so the depth is capped here.
+// Stages in flight per warp ring.  With rings of 64-byte rows a depth of 3-4
+// streams at the HBM rate on GB300; deeper rings were measured to lose up to
+// half the throughput, so the depth is capped here.
 constexpr int kMaxStages = 4;
 constexpr int kDefer = 3;
 constexpr int kTicketRing = 8;
@@ -643,7 +645,7 @@ __device__ __forceinline__ uint4 lds128_fresh(const void* p)
 
 __device__ __forceinline__ void named_sync_walkers()
 {
-    asm volatile("bar.sync 1, %0;" ::"n"(kRows) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(kWalkThreads) : "memory");
 }
 
 // Bounded wait on an mbarrier phase.  Gives up after ~2 s (reported through
@@ -755,7 +757,54 @@ __device__ __noinline__ uint32_t walk_cold(const ScanArgs a, SmemTab T, int64_t 
     return walk_chunk<LAYOUT>(a, T, s, e, *sink);
 }
 
-// One tile's worth of a walker thread's state, kept until its positions are
+// The common case of a stage: kRPL rows of 64 bytes each, counted only.
+// The rows' automaton chains are advanced word by word in turn so that their
+// table lookups overlap; a stage holding any non-base byte takes the
+// per-row slow path.  Rows with ok[i] false are walked on whatever bytes the
+// stage holds (every table index stays in range) and their result discarded.
+template <int LAYOUT>
+__device__ __forceinline__ void count_stage(const SmemTab& T, uint32_t (&e)[kRPL], uint32_t (&cnt)[kRPL],
+                                            const uint4 (&v)[kRPL][4], const bool (&ok)[kRPL], uint32_t r)
+{
+    if (LAYOUT == kLayoutK4) {
+        uint32_t bad = 0;
+#pragma unroll
+        for (int i = 0; i < kRPL; i++) {
+            const uint32_t b = word_bad(v[i][0].x) | word_bad(v[i][0].y) | word_bad(v[i][0].z) |
+                               word_bad(v[i][0].w) | word_bad(v[i][1].x) | word_bad(v[i][1].y) |
+                               word_bad(v[i][1].z) | word_bad(v[i][1].w) | word_bad(v[i][2].x) |
+                               word_bad(v[i][2].y) | word_bad(v[i][2].z) | word_bad(v[i][2].w) |
+                               word_bad(v[i][3].x) | word_bad(v[i][3].y) | word_bad(v[i][3].z) |
+                               word_bad(v[i][3].w);
+            bad |= ok[i] ? b : 0u;
+        }
+        if (bad == 0u) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+#pragma unroll
+                    for (int i = 0; i < kRPL; i++) {
+                        const uint32_t x = c == 0 ? v[i][q].x : c == 1 ? v[i][q].y : c == 2 ? v[i][q].z : v[i][q].w;
+                        e[i] = k4_next(T.k4, e[i], x);
+                        cnt[i] += e[i] >> K4_CNT_SHIFT;
+                    }
+                }
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kRPL; i++) {
+        CountSink cs;
+        Walker<LAYOUT, false, CountSink> w{T, cs, e[i], cnt[i]};
+        w.vec4(v[i][0], v[i][1], v[i][2], v[i][3], r);
+        e[i] = w.e;
+        cnt[i] = w.cnt;
+    }
+}
+
+// One tile's worth of a walker row's state, kept until its positions are
 // written (the row's bounds are recomputed from the tile id).
 struct PendingRow {
     uint32_t cnt, excl;
@@ -854,16 +903,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
 
     // ---------------------------------------------------------- walkers
-    const int t = threadIdx.x;                    // row within the tile
     const uint32_t m = T.m;
     uint8_t* ring = rings + (size_t)warp * nst * kWarpStage;
     uint64_t* full = s_full[warp];
-    // this lane's row inside a 2 KB box: 64-byte swizzle of its four 16-byte pieces
-    // piece j of this lane's row sits at ob ^ (j << 4)
+    // row i of this lane is box row 32i + lane; its 16-byte piece j sits at
+    // ob + i*32*64 ^ (j << 4) (64-byte swizzle of the box)
     const uint32_t ob = lane * kStageW + ((((uint32_t)lane >> 1) & 3u) << 4);
+    const uint32_t wrow0 = (uint32_t)warp * kWarpRows + lane;    // row 0 of this lane in the tile
     bool aborted = false;
 
-    // tile id of this CTA's kk-th tile (warp-collective); false on abort
     auto tile_id = [&](int64_t kk, int64_t* out) -> bool {
         const int slot = (int)((uint64_t)kk % kTicketRing);
         if (!warp_wait(&s_tready[slot], (uint32_t)((uint64_t)kk / kTicketRing) & 1u, abort_flag, p)) return false;
@@ -888,7 +936,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         if (lane == 0) {
             mbar_arrive_expect_tx(&full[i_slot], kWarpStage);
             const int32_t x = i_s < sps ? (int32_t)(i_s * kStageW) : 0;
-            const int32_t y = (int32_t)(i_tile * kRows + warp * 32) + (i_s < sps ? 0 : 1);
+            const int32_t y = (int32_t)(i_tile * kRows + warp * kWarpRows) + (i_s < sps ? 0 : 1);
             tma_load_2d(ring + (size_t)i_slot * kWarpStage, &tmap, x, y, &full[i_slot]);
         }
         n_issued++;
@@ -902,24 +950,32 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     for (int i = 0; i < nst && !aborted; i++) aborted = !issue_next();
 
     unsigned long long total = 0;
-    PendingRow p1{0, 0, 0, false}, p2{0, 0, 0, false};   // tiles k-1 and k-2
-    auto flush = [&](const PendingRow& pr, int64_t kp) -> bool {
+    PendingRow p1[kRPL], p2[kRPL];                // tiles k-1 and k-2
+#pragma unroll
+    for (int i = 0; i < kRPL; i++) {
+        p1[i] = PendingRow{0, 0, 0, false};
+        p2[i] = PendingRow{0, 0, 0, false};
+    }
+    auto flush = [&](const PendingRow (&pr)[kRPL], int64_t kp) -> bool {
         const int b = (int)((uint64_t)kp % kDefer);
         if (!warp_wait(&s_ready[b], (uint32_t)((uint64_t)kp / kDefer) & 1u, abort_flag, p)) return false;
-        if (pr.cnt == 0) return true;
-        const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + pr.excl);
-        const int64_t ps = ((int64_t)pr.tile * kRows + t) * C;
-        const int64_t pe = min(ps + C, a.n_own);
-        const int64_t start0 = a.pos_base + ps - (int64_t)(m - 1);
-        if (!pr.over) {
-            const uint16_t* sl = slots + (size_t)b * kTSlots * kRows + t;
-            for (uint32_t j = 0; j < pr.cnt; j++) {
-                const int64_t gi = g0 + j;
-                if (gi < a.cap) a.pos[gi] = start0 + sl[j * kRows];
+#pragma unroll
+        for (int i = 0; i < kRPL; i++) {
+            if (pr[i].cnt == 0) continue;
+            const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + pr[i].excl);
+            const int64_t ps = ((int64_t)pr[i].tile * kRows + wrow0 + 32 * i) * C;
+            const int64_t pe = min(ps + C, a.n_own);
+            const int64_t start0 = a.pos_base + ps - (int64_t)(m - 1);
+            if (!pr[i].over) {
+                const uint16_t* sl = slots + (size_t)b * kTSlots * kRows + wrow0 + 32 * i;
+                for (uint32_t j = 0; j < pr[i].cnt; j++) {
+                    const int64_t gi = g0 + j;
+                    if (gi < a.cap) a.pos[gi] = start0 + sl[j * kRows];
+                }
+            } else if (g0 < a.cap) {
+                GlobalSink gs{a.pos, a.cap, g0, start0};
+                walk_cold<LAYOUT>(a, T, ps, pe, &gs);
             }
-        } else if (g0 < a.cap) {
-            GlobalSink gs{a.pos, a.cap, g0, start0};
-            walk_cold<LAYOUT>(a, T, ps, pe, &gs);
         }
         return true;
     };
@@ -934,67 +990,100 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             break;
         }
         if (tile < 0) break;
-        const int64_t row = tile * kRows + t;
-        const int64_t s0 = row * C;
-        const bool has = s0 < a.n_own;
-        const int64_t e0 = has ? min(s0 + C, a.n_own) : s0;
-        const bool tma_ok = has && e0 == s0 + C && row + 1 < p.nrows_full;
         const int kb = (int)((uint64_t)k % kDefer);
-        SlotSink ss{slots + (size_t)kb * kTSlots * kRows + t, (uint32_t)kRows, (uint32_t)kTSlots, 0u, false};
-        CountSink cs;
-        // the walk: inline recording for dense find, plain counting otherwise
-        Walker<LAYOUT, false, CountSink> w{T, cs, 0u, 0u};
-        Walker<LAYOUT, false, SlotSink> wd{T, ss, 0u, 0u};
-        uint32_t cnt = 0;
+        int64_t s0[kRPL], e0[kRPL];
+        bool has[kRPL], ok[kRPL];
+        uint32_t e[kRPL], cnt[kRPL];
+        SlotSink ss[kRPL];
+#pragma unroll
+        for (int i = 0; i < kRPL; i++) {
+            const int64_t row = tile * kRows + wrow0 + 32 * i;
+            s0[i] = row * C;
+            has[i] = s0[i] < a.n_own;
+            e0[i] = has[i] ? min(s0[i] + C, a.n_own) : s0[i];
+            ok[i] = has[i] && e0[i] == s0[i] + C && row + 1 < p.nrows_full;
+            e[i] = 0;
+            cnt[i] = 0;
+            ss[i] = SlotSink{slots + (size_t)kb * kTSlots * kRows + wrow0 + 32 * i, (uint32_t)kRows,
+                             (uint32_t)kTSlots, 0u, false};
+        }
         for (uint32_t s = 0; s < spt; s++) {
             if (!warp_wait(&full[c_slot], c_par, abort_flag, p)) {
                 aborted = true;
                 break;
             }
-            if (tma_ok) {
-                const uint8_t* rp = ring + (size_t)c_slot * kWarpStage;
-                const uint4 v0 = *reinterpret_cast<const uint4*>(rp + ob);
-                const uint4 v1 = *reinterpret_cast<const uint4*>(rp + (ob ^ 16u));
-                const uint4 v2 = *reinterpret_cast<const uint4*>(rp + (ob ^ 32u));
-                const uint4 v3 = *reinterpret_cast<const uint4*>(rp + (ob ^ 48u));
-                if (s < sps) {
-                    const uint32_t r = s * kStageW;
-                    if (FIND && DENSE) {
-                        wd.vec4(v0, v1, v2, v3, r);
-                    } else {
-                        const uint32_t e_in = w.e, c_in = w.cnt;
-                        w.vec4(v0, v1, v2, v3, r);
-                        if (FIND && w.cnt != c_in) {
-                            // a match in this stage: walk it again to record where
-                            // (the stage is re-read: its slot is released below)
-                            const uint2 st = replay_stage<LAYOUT>(T, ss.slots, ss.n, ss.over, e_in, rp, ob, r);
-                            ss.n = st.x;
-                            ss.over = st.y != 0u;
-                        }
+            const uint8_t* rp = ring + (size_t)c_slot * kWarpStage;
+            if (s < sps) {
+                const uint32_t r = s * kStageW;
+                uint4 v[kRPL][4];
+#pragma unroll
+                for (int i = 0; i < kRPL; i++) {
+                    const uint8_t* q = rp + ob + i * 32 * kStageW;
+                    v[i][0] = *reinterpret_cast<const uint4*>(q);
+                    v[i][1] = *reinterpret_cast<const uint4*>(rp + ((ob + i * 32 * kStageW) ^ 16u));
+                    v[i][2] = *reinterpret_cast<const uint4*>(rp + ((ob + i * 32 * kStageW) ^ 32u));
+                    v[i][3] = *reinterpret_cast<const uint4*>(rp + ((ob + i * 32 * kStageW) ^ 48u));
+                }
+                if (FIND && DENSE) {
+#pragma unroll
+                    for (int i = 0; i < kRPL; i++) {
+                        if (!ok[i]) continue;
+                        Walker<LAYOUT, false, SlotSink> wd{T, ss[i], e[i], cnt[i]};
+                        wd.vec4(v[i][0], v[i][1], v[i][2], v[i][3], r);
+                        e[i] = wd.e;
+                        cnt[i] = wd.cnt;
                     }
                 } else {
-                    // the overlap: ends below C + m - 1 belong to this row
-                    const uint32_t lim = (uint32_t)C + m - 1;
-                    if (FIND && DENSE) {
-                        Walker<LAYOUT, true, SlotSink> h{T, ss, wd.e, wd.cnt};
-                        h.vec(v0, (uint32_t)C, lim);
-                        if (m > 17) h.vec(v1, (uint32_t)C + 16, lim);
-                        if (m > 33) h.vec(v2, (uint32_t)C + 32, lim);
-                        if (m > 49) h.vec(v3, (uint32_t)C + 48, lim);
-                        cnt = h.cnt;
-                    } else {
-                        Walker<LAYOUT, true, CountSink> h{T, cs, w.e, w.cnt};
-                        h.vec(v0, (uint32_t)C, lim);
-                        if (m > 17) h.vec(v1, (uint32_t)C + 16, lim);
-                        if (m > 33) h.vec(v2, (uint32_t)C + 32, lim);
-                        if (m > 49) h.vec(v3, (uint32_t)C + 48, lim);
-                        if (FIND && h.cnt != w.cnt) {
-                            const uint2 st = replay_halo<LAYOUT>(T, ss.slots, ss.n, ss.over, w.e, rp, ob,
-                                                                 (uint32_t)C, lim);
-                            ss.n = st.x;
-                            ss.over = st.y != 0u;
+                    uint32_t e_in[kRPL], c_in[kRPL];
+#pragma unroll
+                    for (int i = 0; i < kRPL; i++) {
+                        e_in[i] = e[i];
+                        c_in[i] = cnt[i];
+                    }
+                    count_stage<LAYOUT>(T, e, cnt, v, ok, r);
+                    if (FIND) {
+#pragma unroll
+                        for (int i = 0; i < kRPL; i++) {
+                            if (ok[i] && cnt[i] != c_in[i]) {
+                                // a match in this stage: walk it again to record where
+                                // (the stage is re-read from its slot, released below)
+                                const uint2 st = replay_stage<LAYOUT>(T, ss[i].slots, ss[i].n, ss[i].over, e_in[i],
+                                                                      rp + i * 32 * kStageW, ob, r);
+                                ss[i].n = st.x;
+                                ss[i].over = st.y != 0u;
+                            }
                         }
-                        cnt = h.cnt;
+                    }
+                }
+            } else {
+                // the overlap: ends below C + m - 1 belong to this row
+                const uint32_t lim = (uint32_t)C + m - 1;
+#pragma unroll
+                for (int i = 0; i < kRPL; i++) {
+                    if (!ok[i]) continue;
+                    const uint8_t* q = rp + i * 32 * kStageW;
+                    const uint4 h0 = *reinterpret_cast<const uint4*>(q + ob);
+                    if (FIND && DENSE) {
+                        Walker<LAYOUT, true, SlotSink> h{T, ss[i], e[i], cnt[i]};
+                        h.vec(h0, (uint32_t)C, lim);
+                        if (m > 17) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 16u)), (uint32_t)C + 16, lim);
+                        if (m > 33) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 32u)), (uint32_t)C + 32, lim);
+                        if (m > 49) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 48u)), (uint32_t)C + 48, lim);
+                        cnt[i] = h.cnt;
+                    } else {
+                        CountSink cs;
+                        Walker<LAYOUT, true, CountSink> h{T, cs, e[i], cnt[i]};
+                        h.vec(h0, (uint32_t)C, lim);
+                        if (m > 17) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 16u)), (uint32_t)C + 16, lim);
+                        if (m > 33) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 32u)), (uint32_t)C + 32, lim);
+                        if (m > 49) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 48u)), (uint32_t)C + 48, lim);
+                        if (FIND && h.cnt != cnt[i]) {
+                            const uint2 st = replay_halo<LAYOUT>(T, ss[i].slots, ss[i].n, ss[i].over, e[i], q, ob,
+                                                                 (uint32_t)C, lim);
+                            ss[i].n = st.x;
+                            ss[i].over = st.y != 0u;
+                        }
+                        cnt[i] = h.cnt;
                     }
                 }
             }
@@ -1010,26 +1099,44 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             }
         }
         if (aborted) break;
-        if (has && !tma_ok) {
-            if (FIND)
-                cnt = walk_cold<LAYOUT>(a, T, s0, e0, &ss);
-            else
-                cnt = walk_cold<LAYOUT>(a, T, s0, e0, &cs);
+#pragma unroll
+        for (int i = 0; i < kRPL; i++) {
+            if (!has[i]) {
+                cnt[i] = 0;
+            } else if (!ok[i]) {
+                ss[i].n = 0;
+                ss[i].over = false;
+                if (FIND)
+                    cnt[i] = walk_cold<LAYOUT>(a, T, s0[i], e0[i], &ss[i]);
+                else {
+                    CountSink cs;
+                    cnt[i] = walk_cold<LAYOUT>(a, T, s0[i], e0[i], &cs);
+                }
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_tfree[tslot]);
 
         if (!FIND) {
-            total += cnt;
-        } else {
-            uint32_t v = cnt;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += y;
+            for (int i = 0; i < kRPL; i++) total += cnt[i];
+        } else {
+            // exclusive offsets of this lane's rows among the warp's rows
+            // (row i of every lane, then row i+1 of every lane)
+            uint32_t excl[kRPL], wsum = 0;
+#pragma unroll
+            for (int i = 0; i < kRPL; i++) {
+                uint32_t v = cnt[i];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += y;
+                }
+                excl[i] = wsum + v - cnt[i];
+                wsum += __shfl_sync(0xffffffffu, v, 31);
             }
-            if (lane == 31) {
-                s_wtot[kb][warp] = v;
+            if (lane == 0) {
+                s_wtot[kb][warp] = wsum;
                 if (warp == 0) s_tile_of[kb] = tile;
             }
             __syncwarp();
@@ -1038,12 +1145,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 aborted = true;
                 break;
             }
-            p2 = p1;
-            p1 = PendingRow{cnt, v - cnt, (int32_t)tile, ss.over};
+#pragma unroll
+            for (int i = 0; i < kRPL; i++) {
+                p2[i] = p1[i];
+                p1[i] = PendingRow{cnt[i], excl[i], (int32_t)tile, ss[i].over};
+            }
         }
         k++;
     }
-
     if (aborted) {
         // wait for this warp's loads still in flight before the CTA's memory goes away
         for (uint32_t i = n_consumed; i < n_issued; i++) {
@@ -1061,7 +1170,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
         if (lane == 0) s_sum[warp] = total;
         named_sync_walkers();
-        if (t == 0 && !*abort_flag) {
+        if (threadIdx.x == 0 && !*abort_flag) {
             unsigned long long v = 0;
             for (int i = 0; i < kWalkWarps; i++) v += s_sum[i];
             if (v) atomicAdd(a.count, v);
@@ -1294,7 +1403,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
-    cuuint32_t box[2] = {(cuuint32_t)kStageW, 32u};
+    cuuint32_t box[2] = {(cuuint32_t)kStageW, (cuuint32_t)kWarpRows};
     cuuint32_t estr[2] = {1, 1};
     if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(a.text), dims, strides, box,
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
