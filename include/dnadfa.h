@@ -49,6 +49,9 @@ extern "C" {
 #define DFA_EWORKSPACE 5  /* workspace smaller than dfa_find_workspace_bytes() asks for */
 #define DFA_ENOMEM 6      /* host or device allocation failed (dfa_build only) */
 
+/* Bit of a count written by dfa_count that marks a device-side failure. */
+#define DFA_COUNT_FAILED (1ull << 63)
+
 /* Longest pattern accepted.  States 0..m must fit a byte and the tables of
  * the fast layouts must fit in one SM's shared memory. */
 #define DFA_MAX_M 64
@@ -116,6 +119,8 @@ typedef struct dfa_config {
  * Matches the paper's "count" output of Algorithm 1.
  *   cfg: launch configuration or NULL for the defaults.
  * Errors: DFA_EINVAL (NULL pointers with n > 0, n < 0, bad cfg), DFA_ECUDA.
+ * Device-side failure: a bounded wait inside the kernel that gave up sets
+ * bit 63 of *d_count (DFA_COUNT_FAILED); the count is then invalid.
  */
 int dfa_count(const uint8_t* d_text, int64_t n, const dfa_table* table, uint64_t* d_count,
               const dfa_config* cfg, void* stream);

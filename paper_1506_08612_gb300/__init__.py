@@ -23,8 +23,8 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import (DFA_ECUDA, DFA_EINVAL, DFA_ENOMEM, DFA_ETIMEOUT, DFA_ETRUNC,
-                      DFA_EWORKSPACE, DFA_MAX_M, DFA_OK, LIBRARY_PATH, dfa_config)
+from ._native import (DFA_COUNT_FAILED, DFA_ECUDA, DFA_EINVAL, DFA_ENOMEM, DFA_ETIMEOUT,
+                      DFA_ETRUNC, DFA_EWORKSPACE, DFA_MAX_M, DFA_OK, LIBRARY_PATH, dfa_config)
 
 _lib = _native.lib
 
@@ -182,7 +182,10 @@ def count(text, pattern, cfg=None) -> int:
     t = _as_table(pattern)
     out = torch.zeros(1, dtype=torch.int64, device=text.device)
     dfa_count(text, t, out, cfg=cfg)
-    return int(out.item())
+    v = int(out.item()) & (2**64 - 1)
+    if v & DFA_COUNT_FAILED:
+        raise DfaError(DFA_ETIMEOUT, "dfa_count")
+    return v
 
 
 def find(text, pattern, cap: int | None = None, cfg=None):

@@ -13,6 +13,7 @@ from . import build as _build
 
 DFA_OK, DFA_EINVAL, DFA_ETRUNC, DFA_ETIMEOUT, DFA_ECUDA, DFA_EWORKSPACE, DFA_ENOMEM = range(7)
 DFA_MAX_M = 64
+DFA_COUNT_FAILED = 1 << 63
 
 
 class dfa_config(ctypes.Structure):

@@ -553,6 +553,13 @@ constexpr int kTSlots = 8;
 constexpr int kMaxStages = 4;
 constexpr int kDefer = 3;
 constexpr int kTicketRing = 8;
+// How many tiles ahead of the slowest walker warp the ticket warp may claim
+// in find mode.  Tickets fix the text order that the look-back follows, so a
+// CTA must not hold tiles it will only start much later (its successors'
+// offsets would wait for them).  A warp still walking tile k prefetches the
+// stages of tiles up to k + 1 + (nst - 1) / (stages per tile), so the host
+// sets ahead = 2 + (nst - 1) / (stages per tile) (TmaArgs::ahead); counting
+// uses a static schedule and runs a full ring ahead.
 constexpr int kDenseMaxM = 6;                     // patterns this short record inline
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
@@ -562,6 +569,7 @@ struct TmaArgs {
     int32_t nst;          // stages in each warp's ring
     int32_t sps;          // body stages per tile (C / 64)
     int32_t table_bytes;  // shared bytes of the table, 128-aligned
+    int32_t ahead;        // find: tiles the ticket warp may claim ahead (see above)
     // where a wait that gave up is reported: the find workspace's status
     // word (bit 1), or bit 63 of the count for a count without workspace
     unsigned long long* fail_word;
@@ -860,11 +868,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     if (warp == kProducerWarp) {
         // ------------------------------------------------------ tickets
         if (lane != 0) return;
+        const int64_t ahead = FIND ? (int64_t)p.ahead : (int64_t)kTicketRing;
         for (int64_t kk = 0;; kk++) {
             const int slot = (int)((uint64_t)kk % kTicketRing);
-            if (kk >= kTicketRing &&
-                !mbar_wait(&s_tfree[slot], (uint32_t)((uint64_t)kk / kTicketRing - 1) & 1u, abort_flag, p))
-                return;
+            // wait until every walker warp is done with tile kk - ahead
+            // (which also frees this slot, since kk - kTicketRing <= kk - ahead)
+            if (kk >= ahead) {
+                const uint64_t kf = (uint64_t)(kk - ahead);
+                if (!mbar_wait(&s_tfree[kf % kTicketRing], (uint32_t)(kf / kTicketRing) & 1u, abort_flag, p))
+                    return;
+            }
             int64_t tile = FIND ? (int64_t)atomicAdd(a.work, 1ull)
                                 : (int64_t)blockIdx.x + kk * (int64_t)gridDim.x;
             if (tile >= a.ntiles) tile = -1;
@@ -1417,6 +1430,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     const int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
     if (nst < 2) return DFA_EINVAL;
     p.nst = nst;
+    p.ahead = std::min(2 + (nst - 1) / (p.sps + 1), kTicketRing);
     const int smem = kWalkWarps * nst * kWarpStage + p.table_bytes + slot_bytes;
     int occ = occupancy((const void*)fn, kTmaThreads, smem, dev, di->smem_optin);
     if (occ <= 0) return fail("TMA scan kernel does not fit on an SM (occupancy 0)");
@@ -1637,7 +1651,7 @@ int dfa_find_status(const void* d_work, const uint64_t* d_count, int64_t cap, ui
     if (cudaMemcpy(hdr, d_work, sizeof(hdr), cudaMemcpyDeviceToHost) != cudaSuccess) return DFA_ECUDA;
     if (cudaMemcpy(&cnt, d_count, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return DFA_ECUDA;
     if (h_count) *h_count = cnt;
-    if (hdr[1] & 1ull) return DFA_ETIMEOUT;
+    if (hdr[1]) return DFA_ETIMEOUT;
     if ((int64_t)cnt > cap) return DFA_ETRUNC;
     return DFA_OK;
 }
@@ -1733,7 +1747,7 @@ int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int6
     cudaStreamDestroy(cp);
     if (rc != DFA_OK) return rc;
     *h_count = cnt;
-    if (hdr[1] & 1ull) return DFA_ETIMEOUT;
+    if (hdr[1]) return DFA_ETIMEOUT;
     if ((int64_t)cnt > cap) return DFA_ETRUNC;
     return DFA_OK;
 }
