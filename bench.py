@@ -40,7 +40,7 @@ PATTERN_SEEDS = (3, 4, 5, 6, 7)
 TEXT_BYTES = 3_200_000_000
 TEXT_SEED = 2
 WORKLOAD = "genome-scale single-pattern scan"
-DOMINANT_KERNEL = "k_find<1,256>"
+DOMINANT_KERNEL = "k_scan_tma<layout 1 (four-step table), find>"
 
 
 def parse():
@@ -167,7 +167,7 @@ def kernel_source_digest():
 def profiled_traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None when the kernel source changed since it was taken."""
-    p = os.path.join(ROOT, "profiles", "k_find_genome3200MB.txt")
+    p = os.path.join(ROOT, "profiles", "k_scan_tma_find_genome.txt")
     try:
         kv = {}
         with open(p) as f:
@@ -177,7 +177,7 @@ def profiled_traffic():
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_source_digest") != kernel_source_digest():
             return None
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv["dram_bytes_per_full_launch"])
     except Exception:
         return None
 

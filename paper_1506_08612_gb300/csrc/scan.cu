@@ -528,8 +528,8 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
 //   warp 9 (scheduler, find only): sums the walker warps' counts of a tile,
 //           publishes them and resolves the tile's global offset by a
 //           warp-parallel decoupled look-back while the walkers go on; a
-//           tile's positions are written two tiles later, which hides the
-//           look-back's latency.
+//           tile's positions are written kDefer - 1 tiles later, which hides
+//           the look-back's latency.
 // In find mode a sparse pattern (few occurrences expected) is walked without
 // looking at accept bits; a stage whose count moved is walked again from its
 // saved start state to record the positions.  Dense patterns record inline.
@@ -546,20 +546,23 @@ constexpr int kWarpStage = kWarpRows * kStageW;  // one TMA box
 constexpr int kTmaThreads = kWalkThreads + 64;
 constexpr int kProducerWarp = kWalkWarps;
 constexpr int kSchedulerWarp = kWalkWarps + 1;
-constexpr int kTSlots = 8;
+constexpr int kTSlots = 8;                       // staged positions per row (sparse patterns)
+constexpr int kTSlotsDense = 16;                 // staged positions per row (dense patterns)
 // Stages in flight per warp ring.  With rings of 64-byte rows a depth of 3-4
 // streams at the HBM rate on GB300; deeper rings were measured to lose up to
 // half the throughput, so the depth is capped here.
 constexpr int kMaxStages = 4;
-constexpr int kDefer = 3;
+constexpr int kDefer = 4;                        // tiles whose positions wait for their offset
 constexpr int kTicketRing = 8;
 // How many tiles ahead of the slowest walker warp the ticket warp may claim
 // in find mode.  Tickets fix the text order that the look-back follows, so a
 // CTA must not hold tiles it will only start much later (its successors'
 // offsets would wait for them).  A warp still walking tile k prefetches the
-// stages of tiles up to k + 1 + (nst - 1) / (stages per tile), so the host
-// sets ahead = 2 + (nst - 1) / (stages per tile) (TmaArgs::ahead); counting
-// uses a static schedule and runs a full ring ahead.
+// stages of tiles up to k + 1 + (nst - 1) / (stages per tile), which needs
+// ahead >= 2 + (nst - 1) / (stages per tile); the host adds one tile of slack
+// so that one slow warp does not hold back the others' prefetch
+// (TmaArgs::ahead).  Counting uses a static schedule and runs a full ring
+// ahead.
 constexpr int kDenseMaxM = 6;                     // patterns this short record inline
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
@@ -838,6 +841,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     __shared__ unsigned long long s_sum[kWalkWarps];
     __shared__ int s_abort;
 
+    constexpr int KS = DENSE ? kTSlotsDense : kTSlots;
     const ScanArgs& a = p.a;
     const int nst = p.nst;
     uint8_t* rings = smem;
@@ -963,12 +967,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     for (int i = 0; i < nst && !aborted; i++) aborted = !issue_next();
 
     unsigned long long total = 0;
-    PendingRow p1[kRPL], p2[kRPL];                // tiles k-1 and k-2
+    // pend[d] holds tile k-1-d, for d = 0 .. kDefer-2
+    PendingRow pend[kDefer - 1][kRPL];
 #pragma unroll
-    for (int i = 0; i < kRPL; i++) {
-        p1[i] = PendingRow{0, 0, 0, false};
-        p2[i] = PendingRow{0, 0, 0, false};
-    }
+    for (int d = 0; d < kDefer - 1; d++)
+#pragma unroll
+        for (int i = 0; i < kRPL; i++) pend[d][i] = PendingRow{0, 0, 0, false};
     auto flush = [&](const PendingRow (&pr)[kRPL], int64_t kp) -> bool {
         const int b = (int)((uint64_t)kp % kDefer);
         if (!warp_wait(&s_ready[b], (uint32_t)((uint64_t)kp / kDefer) & 1u, abort_flag, p)) return false;
@@ -980,7 +984,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             const int64_t pe = min(ps + C, a.n_own);
             const int64_t start0 = a.pos_base + ps - (int64_t)(m - 1);
             if (!pr[i].over) {
-                const uint16_t* sl = slots + (size_t)b * kTSlots * kRows + wrow0 + 32 * i;
+                const uint16_t* sl = slots + (size_t)b * KS * kRows + wrow0 + 32 * i;
                 for (uint32_t j = 0; j < pr[i].cnt; j++) {
                     const int64_t gi = g0 + j;
                     if (gi < a.cap) a.pos[gi] = start0 + sl[j * kRows];
@@ -1017,8 +1021,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             ok[i] = has[i] && e0[i] == s0[i] + C && row + 1 < p.nrows_full;
             e[i] = 0;
             cnt[i] = 0;
-            ss[i] = SlotSink{slots + (size_t)kb * kTSlots * kRows + wrow0 + 32 * i, (uint32_t)kRows,
-                             (uint32_t)kTSlots, 0u, false};
+            ss[i] = SlotSink{slots + (size_t)kb * KS * kRows + wrow0 + 32 * i, (uint32_t)kRows, (uint32_t)KS,
+                             0u, false};
         }
         for (uint32_t s = 0; s < spt; s++) {
             if (!warp_wait(&full[c_slot], c_par, abort_flag, p)) {
@@ -1154,15 +1158,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&s_counted[kb]);
-            if (k >= 2 && !flush(p2, k - 2)) {
+            if (k >= kDefer - 1 && !flush(pend[kDefer - 2], k - (kDefer - 1))) {
                 aborted = true;
                 break;
             }
 #pragma unroll
-            for (int i = 0; i < kRPL; i++) {
-                p2[i] = p1[i];
-                p1[i] = PendingRow{cnt[i], excl[i], (int32_t)tile, ss[i].over};
-            }
+            for (int d = kDefer - 2; d > 0; d--)
+#pragma unroll
+                for (int i = 0; i < kRPL; i++) pend[d][i] = pend[d - 1][i];
+#pragma unroll
+            for (int i = 0; i < kRPL; i++) pend[0][i] = PendingRow{cnt[i], excl[i], (int32_t)tile, ss[i].over};
         }
         k++;
     }
@@ -1191,13 +1196,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         return;
     }
     if (aborted) return;
-    // end of work: tell the scheduler, then write the last two tiles' positions
+    // end of work: tell the scheduler, then write the last tiles' positions
     const int b = (int)((uint64_t)k % kDefer);
     if (lane == 0 && warp == 0) s_tile_of[b] = -1;
     __syncwarp();
     if (lane == 0) mbar_arrive(&s_counted[b]);
-    if (k >= 2 && !flush(p2, k - 2)) return;
-    if (k >= 1) flush(p1, k - 1);
+#pragma unroll
+    for (int d = kDefer - 2; d >= 0; d--)
+        if (k >= d + 1 && !flush(pend[d], k - 1 - d)) return;
 }
 
 // ---------------------------------------------------------------- host side
@@ -1425,12 +1431,13 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     TmaKernelFn fn = pick_tma(r.layout, find, t->m);
     cudaFuncAttributes fa;
     CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)fn));
-    const int slot_bytes = find ? kDefer * kTSlots * kRows * 2 : 0;
+    const int slot_bytes =
+        find ? kDefer * (t->m <= kDenseMaxM ? kTSlotsDense : kTSlots) * kRows * 2 : 0;
     const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.table_bytes - slot_bytes;
     const int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
     if (nst < 2) return DFA_EINVAL;
     p.nst = nst;
-    p.ahead = std::min(2 + (nst - 1) / (p.sps + 1), kTicketRing);
+    p.ahead = std::min(3 + (nst - 1) / (p.sps + 1), kTicketRing);
     const int smem = kWalkWarps * nst * kWarpStage + p.table_bytes + slot_bytes;
     int occ = occupancy((const void*)fn, kTmaThreads, smem, dev, di->smem_optin);
     if (occ <= 0) return fail("TMA scan kernel does not fit on an SM (occupancy 0)");
