@@ -43,6 +43,8 @@ int build_host_tables(dfa_table* t)
     // code4 = d0 | d1<<2 | d2<<4 | d3<<6, d0 the code of the first byte
     std::vector<uint16_t>& k4 = t->k4;
     k4.assign((size_t)S * 256, 0);
+    std::vector<uint8_t>& k4s = t->k4s;
+    k4s.assign((size_t)S * 256, 0);
     for (int q = 0; q < S; q++) {
         for (int code4 = 0; code4 < 256; code4++) {
             int s = q;
@@ -54,6 +56,7 @@ int build_host_tables(dfa_table* t)
             uint32_t pop = (uint32_t)__builtin_popcount(acc);
             k4[(size_t)q * 256 + code4] =
                 (uint16_t)(s | (acc << K4_ACC_SHIFT) | (pop << K4_CNT_SHIFT));
+            k4s[(size_t)q * 256 + code4] = (uint8_t)s;
         }
     }
 

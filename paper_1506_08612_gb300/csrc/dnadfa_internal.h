@@ -32,12 +32,15 @@ constexpr uint32_t K4_CNT_SHIFT = 12;
 
 // Device copy layout, one allocation, every part 16-byte aligned:
 //   [k4: (m+1)*256 u16][d1: (m+1)*4 u8, padded to 16][stt: (m+1)*256 u8]
+//   [k4s: (m+1)*256 u8]
+// k4s is the four-step table holding only the state after the four steps.
 struct DeviceTableView {
     const uint8_t* base;   // start of the allocation
     int32_t m;
     int32_t k4_bytes;      // (m+1)*512
     int32_t d1_bytes;      // (m+1)*4 rounded up to 16
     int32_t stt_bytes;     // (m+1)*256
+    int32_t k4s_bytes;     // (m+1)*256
 };
 
 }  // namespace dnadfa
@@ -48,6 +51,7 @@ struct dfa_table {
     std::vector<uint8_t> d1;             // (m+1)*4, column = base_code
     std::vector<uint16_t> k4;            // (m+1)*256
     std::vector<uint8_t> stt;            // (m+1)*256, the paper's sparse ASCII STT
+    std::vector<uint8_t> k4s;            // (m+1)*256, state after four steps only
     int device;
     void* d_mem;
     size_t d_bytes;

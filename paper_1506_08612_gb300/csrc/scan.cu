@@ -38,6 +38,8 @@ namespace {
 
 constexpr int kLayoutK4 = 1;
 constexpr int kLayoutStt = 2;
+constexpr int kLayoutK4S = 3;     // four-step table of states only (u8), m >= kK4SMinM
+constexpr int kK4SMinM = 20;
 constexpr int kSlots = 16;                  // staged positions per thread per tile
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
@@ -53,7 +55,7 @@ struct ScanArgs {
     int64_t ntiles;
     const uint8_t* tab;   // device table allocation
     int32_t m;
-    int32_t k4_bytes, d1_bytes, stt_bytes;
+    int32_t k4_bytes, d1_bytes, stt_bytes, k4s_bytes;
     int32_t aligned;      // text is 16-byte aligned
     unsigned long long* count;
     int64_t* pos;
@@ -68,21 +70,33 @@ struct SmemTab {
     uint32_t k4;    // (m+1)*256 u16
     uint32_t d1;    // (m+1)*4 u8
     uint32_t stt;   // (m+1)*256 u8
+    uint32_t k4s;   // (m+1)*256 u8
     uint32_t m;
+    uint32_t sh;    // k4s: a group of four steps can accept only from a state with (q >> sh) != 0
+    uint32_t force; // k4s: 1 when m <= 4 (any state, even q0, may accept within four steps)
 };
 
-__device__ __forceinline__ uint32_t lds_u16(uint32_t addr)
-{
-    unsigned short v;
-    asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
-    return v;
-}
+// Dynamic shared memory of every kernel here.  Each kernel puts its layout's
+// main table (k4, k4s or stt) at offset 0, so a lookup is one load whose base
+// the compiler folds into the instruction.
+extern __shared__ __align__(1024) uint8_t g_smem[];
 
 __device__ __forceinline__ uint32_t lds_u8(uint32_t addr)
 {
-    unsigned short v;
-    asm("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(addr));
-    return v & 0xFFu;
+    uint32_t v;
+    asm("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// main-table lookups at offset 0 of dynamic shared memory
+__device__ __forceinline__ uint32_t tab16(uint32_t idx)
+{
+    return reinterpret_cast<const uint16_t*>(g_smem)[idx];
+}
+
+__device__ __forceinline__ uint32_t tab8(uint32_t idx)
+{
+    return g_smem[idx];
 }
 
 // ---------------------------------------------------------------- helpers
@@ -119,11 +133,11 @@ __device__ __forceinline__ uint32_t word_bad(uint32_t x)
 // (x & 0x06060606) holds the 2-bit codes at bits 8k+1; the multiply gathers
 // them, first byte lowest, into bits 24..31 without carries; byte_perm forms
 // the table index (state << 8) | code4.
-__device__ __forceinline__ uint32_t k4_next(uint32_t k4, uint32_t e, uint32_t x)
+__device__ __forceinline__ uint32_t k4_next(uint32_t /*k4 at offset 0*/, uint32_t e, uint32_t x)
 {
     uint32_t code = (x & 0x06060606u) * 0x00820820u;
     uint32_t idx = __byte_perm(code, e, 0x7743u);
-    return lds_u16(k4 + 2u * idx);
+    return tab16(idx);
 }
 
 // One automaton step on one raw byte (any byte value).
@@ -228,11 +242,47 @@ struct Walker {
         }
     }
 
+    // Four exact single steps on a word of four bases (no base test).
+    __device__ __forceinline__ void word_exact(uint32_t x, uint32_t r, uint32_t lim)
+    {
+#pragma unroll
+        for (uint32_t i = 0; i < 4; i++) {
+            e = lds_u8(T.d1 + e * 4u + ((x >> (8 * i + 1)) & 3u));
+            if (e == T.m && (!LIM || r + i < lim)) {
+                cnt++;
+                if (Sink::kRecord) sink.put(r + i);
+            }
+        }
+    }
+
+    // k4s fast path over n words of bases: one lookup per word, the states
+    // at the start of every group OR-ed; only a group starting at a state
+    // >= m - 4 can accept (the state grows by at most one per byte), so if
+    // the OR shows no such state nothing was accepted, else the words are
+    // walked again exactly from the saved state.
+    template <int N>
+    __device__ __forceinline__ void words_s(const uint32_t (&x)[N], uint32_t r, uint32_t lim)
+    {
+        const uint32_t e_in = e;
+        uint32_t orq = e | T.force;
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            const uint32_t code = (x[k] & 0x06060606u) * 0x00820820u;
+            e = tab8(__byte_perm(code, e, 0x7743u));
+            if (k + 1 < N) orq |= e;
+        }
+        if ((orq >> T.sh) != 0u) {
+            e = e_in;
+#pragma unroll
+            for (int k = 0; k < N; k++) word_exact(x[k], r + 4 * k, lim);
+        }
+    }
+
     __device__ __forceinline__ void word_stt(uint32_t x, uint32_t r, uint32_t lim)
     {
 #pragma unroll
         for (uint32_t i = 0; i < 4; i++) {
-            e = lds_u8(T.stt + __byte_perm(x, e, 0x7740u | i));
+            e = tab8(__byte_perm(x, e, 0x7740u | i));
             if (e == T.m && (!LIM || r + i < lim)) {
                 cnt++;
                 if (Sink::kRecord) sink.put(r + i);
@@ -250,7 +300,12 @@ struct Walker {
         for (int k = 0; k < 4; k++) {
             const uint32_t b = word_bad(w[k]);
             if (b == 0u) {
-                word_k4(w[k], r + 4 * k, lim);
+                if (LAYOUT == kLayoutK4S) {
+                    const uint32_t one[1] = {w[k]};
+                    words_s<1>(one, r + 4 * k, lim);
+                } else {
+                    word_k4(w[k], r + 4 * k, lim);
+                }
             } else if (((((b & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | b) & 0x80808080u) == 0x80808080u) {
                 e = 0u;                       // four non-bases: back to q0, nothing accepted
             } else {
@@ -265,7 +320,22 @@ struct Walker {
     // the common case of 64 bases.
     __device__ __forceinline__ void vec4(uint4 v0, uint4 v1, uint4 v2, uint4 v3, uint32_t r)
     {
-        if (LAYOUT == kLayoutK4) {
+        if (LAYOUT == kLayoutK4S) {
+            const uint32_t bad = word_bad(v0.x) | word_bad(v0.y) | word_bad(v0.z) | word_bad(v0.w) |
+                                 word_bad(v1.x) | word_bad(v1.y) | word_bad(v1.z) | word_bad(v1.w) |
+                                 word_bad(v2.x) | word_bad(v2.y) | word_bad(v2.z) | word_bad(v2.w) |
+                                 word_bad(v3.x) | word_bad(v3.y) | word_bad(v3.z) | word_bad(v3.w);
+            if (bad == 0u) {
+                const uint32_t x[16] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w,
+                                        v2.x, v2.y, v2.z, v2.w, v3.x, v3.y, v3.z, v3.w};
+                words_s<16>(x, r, 0);
+            } else {
+                slow_vec(v0, r, 0);
+                slow_vec(v1, r + 16, 0);
+                slow_vec(v2, r + 32, 0);
+                slow_vec(v3, r + 48, 0);
+            }
+        } else if (LAYOUT == kLayoutK4) {
             const uint32_t bad = word_bad(v0.x) | word_bad(v0.y) | word_bad(v0.z) | word_bad(v0.w) |
                                  word_bad(v1.x) | word_bad(v1.y) | word_bad(v1.z) | word_bad(v1.w) |
                                  word_bad(v2.x) | word_bad(v2.y) | word_bad(v2.z) | word_bad(v2.w) |
@@ -291,7 +361,14 @@ struct Walker {
 
     __device__ __forceinline__ void vec(uint4 v, uint32_t r, uint32_t lim)
     {
-        if (LAYOUT == kLayoutK4) {
+        if (LAYOUT == kLayoutK4S) {
+            if ((word_bad(v.x) | word_bad(v.y) | word_bad(v.z) | word_bad(v.w)) == 0u) {
+                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+                words_s<4>(x, r, lim);
+            } else {
+                slow_vec(v, r, lim);
+            }
+        } else if (LAYOUT == kLayoutK4) {
             uint32_t bad = word_bad(v.x) | word_bad(v.y) | word_bad(v.z) | word_bad(v.w);
             if (bad == 0u) {
                 word_k4(v.x, r, lim);
@@ -342,10 +419,10 @@ __device__ uint32_t walk_chunk(const ScanArgs& a, const SmemTab& T, int64_t s, i
     uint32_t q = 0, cnt = 0;
     for (int64_t j = s; j < hi; j++) {
         uint32_t c = a.text[j];
-        if (LAYOUT == kLayoutK4)
+        if (LAYOUT != kLayoutStt)
             q = byte_next(T.d1, q, c);
         else
-            q = lds_u8(T.stt + ((q << 8) | c));
+            q = tab8((q << 8) | c);
         if (q == m) {
             cnt++;
             if (Sink::kRecord) sink.put((uint32_t)(j - s));
@@ -359,8 +436,29 @@ __device__ __forceinline__ SmemTab load_tables(const ScanArgs& a, uint8_t* smem)
 {
     SmemTab T;
     T.m = (uint32_t)a.m;
+    // a group of four steps accepts only from a state q >= m - 4; every such q
+    // has a bit at position >= floor(log2(m - 4)), so the OR of the groups'
+    // start states shifted right by that much is non-zero whenever a group
+    // may accept (for m <= 4 every group may)
+    T.sh = a.m > 4 ? 31u - (uint32_t)__clz(a.m - 4) : 0u;
+    T.force = a.m <= 4 ? 1u : 0u;
+    T.k4s = 0;
     int bytes, src_off;
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem);
+    if (LAYOUT == kLayoutK4S) {
+        // [k4s][d1]: two source ranges
+        T.k4 = 0;
+        T.stt = 0;
+        T.k4s = base;
+        T.d1 = base + (uint32_t)a.k4s_bytes;
+        const uint4* s1 = reinterpret_cast<const uint4*>(a.tab + a.k4_bytes + a.d1_bytes + a.stt_bytes);
+        const uint4* s2 = reinterpret_cast<const uint4*>(a.tab + a.k4_bytes);
+        uint4* d = reinterpret_cast<uint4*>(smem);
+        for (int i = threadIdx.x; i < (a.k4s_bytes >> 4); i += blockDim.x) d[i] = s1[i];
+        d += a.k4s_bytes >> 4;
+        for (int i = threadIdx.x; i < (a.d1_bytes >> 4); i += blockDim.x) d[i] = s2[i];
+        return T;
+    }
     if (LAYOUT == kLayoutK4) {
         bytes = a.k4_bytes + a.d1_bytes;
         src_off = 0;
@@ -382,7 +480,8 @@ __device__ __forceinline__ SmemTab load_tables(const ScanArgs& a, uint8_t* smem)
 
 __device__ __forceinline__ int table_smem_bytes_dev(const ScanArgs& a, int layout)
 {
-    return layout == kLayoutK4 ? a.k4_bytes + a.d1_bytes : a.stt_bytes;
+    return layout == kLayoutK4 ? a.k4_bytes + a.d1_bytes
+                               : layout == kLayoutK4S ? a.k4s_bytes + a.d1_bytes : a.stt_bytes;
 }
 
 // ---------------------------------------------------------------- kernels
@@ -390,7 +489,7 @@ __device__ __forceinline__ int table_smem_bytes_dev(const ScanArgs& a, int layou
 template <int LAYOUT, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_count(const ScanArgs a)
 {
-    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* smem = g_smem;
     __shared__ unsigned long long s_warp[THREADS / 32];
     const SmemTab T = load_tables<LAYOUT>(a, smem);
     __syncthreads();
@@ -448,7 +547,7 @@ __device__ unsigned long long lookback(unsigned long long* work, int64_t tile, u
 template <int LAYOUT, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
 {
-    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* smem = g_smem;
     __shared__ uint32_t s_warp[THREADS / 32];
     __shared__ int64_t s_tile;
     __shared__ unsigned long long s_off;
@@ -573,6 +672,7 @@ struct TmaArgs {
     int32_t sps;          // body stages per tile (C / 64)
     int32_t table_bytes;  // shared bytes of the table, 128-aligned
     int32_t ahead;        // find: tiles the ticket warp may claim ahead (see above)
+    int32_t rings_off;    // byte offset of the TMA rings in dynamic shared memory
     // where a wait that gave up is reported: the find workspace's status
     // word (bit 1), or bit 63 of the count for a count without workspace
     unsigned long long* fail_word;
@@ -612,20 +712,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Non-blocking probe of an mbarrier phase.
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -815,6 +901,7 @@ __device__ __forceinline__ void count_stage(const SmemTab& T, uint32_t (&e)[kRPL
     }
 }
 
+
 // One tile's worth of a walker row's state, kept until its positions are
 // written (the row's bounds are recomputed from the tile id).
 struct PendingRow {
@@ -827,7 +914,7 @@ template <int LAYOUT, bool FIND, bool DENSE>
 __global__ void __launch_bounds__(kTmaThreads, 1)
     k_scan_tma(const __grid_constant__ CUtensorMap tmap, const TmaArgs p)
 {
-    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* smem = g_smem;
     __shared__ __align__(8) uint64_t s_full[kWalkWarps][kMaxStages];
     __shared__ __align__(8) uint64_t s_tready[kTicketRing];
     __shared__ __align__(8) uint64_t s_tfree[kTicketRing];
@@ -842,12 +929,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     __shared__ int s_abort;
 
     constexpr int KS = DENSE ? kTSlotsDense : kTSlots;
+    // the k4s walk only records in its rare exact replays: it walks with the
+    // recording sink directly, like a dense pattern
+    constexpr bool INLINE_REC = DENSE || LAYOUT == kLayoutK4S;
     const ScanArgs& a = p.a;
     const int nst = p.nst;
-    uint8_t* rings = smem;
-    uint8_t* tabmem = smem + (size_t)kWalkWarps * nst * kWarpStage;
-    const SmemTab T = load_tables<LAYOUT>(a, tabmem);
-    uint16_t* slots = reinterpret_cast<uint16_t*>(tabmem + p.table_bytes);
+    // [tables][position slots][rings], rings 1024-byte aligned for the TMA swizzle
+    const SmemTab T = load_tables<LAYOUT>(a, smem);
+    uint16_t* slots = reinterpret_cast<uint16_t*>(smem + p.table_bytes);
+    uint8_t* rings = smem + p.rings_off;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int w = 0; w < kWalkWarps; w++)
@@ -1041,7 +1131,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     v[i][2] = *reinterpret_cast<const uint4*>(rp + ((ob + i * 32 * kStageW) ^ 32u));
                     v[i][3] = *reinterpret_cast<const uint4*>(rp + ((ob + i * 32 * kStageW) ^ 48u));
                 }
-                if (FIND && DENSE) {
+                if (FIND && INLINE_REC) {
 #pragma unroll
                     for (int i = 0; i < kRPL; i++) {
                         if (!ok[i]) continue;
@@ -1080,7 +1170,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     if (!ok[i]) continue;
                     const uint8_t* q = rp + i * 32 * kStageW;
                     const uint4 h0 = *reinterpret_cast<const uint4*>(q + ob);
-                    if (FIND && DENSE) {
+                    if (FIND && INLINE_REC) {
                         Walker<LAYOUT, true, SlotSink> h{T, ss[i], e[i], cnt[i]};
                         h.vec(h0, (uint32_t)C, lim);
                         if (m > 17) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 16u)), (uint32_t)C + 16, lim);
@@ -1295,11 +1385,14 @@ constexpr int64_t kMinDefaultTile = 256 * 64;   // workspace sizing for cfg == N
 
 // Launch configuration for a scan of n bytes (n_avail readable).  The TMA
 // loader needs a 16-byte aligned text holding at least two full rows.
-int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int sms, Resolved* r)
+int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int sms, int m, Resolved* r)
 {
-    r->layout = cfg && cfg->layout ? cfg->layout : kLayoutK4;
+    // default layout: the four-step table of states only for long patterns
+    // (the TMA kernel's; see kK4SMinM), else the four-step table with counts
+    const bool user_layout = cfg && cfg->layout;
+    r->layout = user_layout ? cfg->layout : (m >= kK4SMinM ? kLayoutK4S : kLayoutK4);
     r->ctas_per_sm = cfg ? cfg->ctas_per_sm : 0;
-    if (r->layout != kLayoutK4 && r->layout != kLayoutStt) return DFA_EINVAL;
+    if (r->layout != kLayoutK4 && r->layout != kLayoutStt && r->layout != kLayoutK4S) return DFA_EINVAL;
     if (r->ctas_per_sm < 0 || r->ctas_per_sm > 32) return DFA_EINVAL;
     const int req_loader = cfg ? cfg->loader : 0;
     if (req_loader < 0 || req_loader > 2) return DFA_EINVAL;
@@ -1326,6 +1419,11 @@ int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int
             r->chunk = chunk;
             return DFA_OK;
         }
+    }
+    // the direct-load kernels have no k4s variant
+    if (r->layout == kLayoutK4S) {
+        if (user_layout && req_loader == 1) return DFA_EINVAL;
+        r->layout = kLayoutK4;
     }
     r->loader = 1;
     r->threads = cfg && cfg->threads ? cfg->threads : 256;
@@ -1370,7 +1468,8 @@ KernelFn pick_find(int layout, int threads)
 
 int table_smem(const dfa_table* t, int layout)
 {
-    return layout == kLayoutK4 ? t->view.k4_bytes + t->view.d1_bytes : t->view.stt_bytes;
+    return layout == kLayoutK4 ? t->view.k4_bytes + t->view.d1_bytes
+                               : layout == kLayoutK4S ? t->view.k4s_bytes + t->view.d1_bytes : t->view.stt_bytes;
 }
 
 typedef void (*TmaKernelFn)(const CUtensorMap, const TmaArgs);
@@ -1378,6 +1477,7 @@ typedef void (*TmaKernelFn)(const CUtensorMap, const TmaArgs);
 TmaKernelFn pick_tma(int layout, bool find, int m)
 {
     const bool dense = m <= kDenseMaxM;
+    if (layout == kLayoutK4S) return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
     if (layout == kLayoutK4) {
         if (!find) return k_scan_tma<kLayoutK4, false, false>;
         return dense ? k_scan_tma<kLayoutK4, true, true> : k_scan_tma<kLayoutK4, true, false>;
@@ -1432,13 +1532,14 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     cudaFuncAttributes fa;
     CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)fn));
     const int slot_bytes =
-        find ? kDefer * (t->m <= kDenseMaxM ? kTSlotsDense : kTSlots) * kRows * 2 : 0;
-    const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.table_bytes - slot_bytes;
+        find ? kDefer * (t->m <= kDenseMaxM && r.layout != kLayoutK4S ? kTSlotsDense : kTSlots) * kRows * 2 : 0;
+    p.rings_off = (p.table_bytes + slot_bytes + 1023) & ~1023;
+    const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.rings_off;
     const int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
     if (nst < 2) return DFA_EINVAL;
     p.nst = nst;
     p.ahead = std::min(3 + (nst - 1) / (p.sps + 1), kTicketRing);
-    const int smem = kWalkWarps * nst * kWarpStage + p.table_bytes + slot_bytes;
+    const int smem = p.rings_off + kWalkWarps * nst * kWarpStage;
     int occ = occupancy((const void*)fn, kTmaThreads, smem, dev, di->smem_optin);
     if (occ <= 0) return fail("TMA scan kernel does not fit on an SM (occupancy 0)");
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)di->sms);
@@ -1462,6 +1563,7 @@ void fill_args(ScanArgs* a, const uint8_t* text, int64_t n, int64_t n_own, const
     a->k4_bytes = t->view.k4_bytes;
     a->d1_bytes = t->view.d1_bytes;
     a->stt_bytes = t->view.stt_bytes;
+    a->k4s_bytes = t->view.k4s_bytes;
     a->aligned = ((uintptr_t)text & 15u) == 0;
 }
 
@@ -1481,7 +1583,7 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
     if (rc) return rc;
     if (dev != t->device) return DFA_EINVAL;
     Resolved r;
-    rc = resolve(cfg, n, n, ((uintptr_t)d_text & 15u) == 0, di->sms, &r);
+    rc = resolve(cfg, n, n, ((uintptr_t)d_text & 15u) == 0, di->sms, t->m, &r);
     if (rc) return rc;
     CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st));
     if (n < t->m) return DFA_OK;
@@ -1513,7 +1615,7 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     if (rc) return rc;
     if (dev != t->device) return DFA_EINVAL;
     Resolved r;
-    rc = resolve(cfg, n_own, n, ((uintptr_t)d_text & 15u) == 0, di->sms, &r);
+    rc = resolve(cfg, n_own, n, ((uintptr_t)d_text & 15u) == 0, di->sms, t->m, &r);
     if (rc) return rc;
     ScanArgs a;
     fill_args(&a, d_text, n, n_own, t, r);
@@ -1575,7 +1677,8 @@ int dfa_build(const char* pattern, int32_t m, dfa_table** out)
     t->view.k4_bytes = (m + 1) * 512;
     t->view.d1_bytes = ((m + 1) * 4 + 15) & ~15;
     t->view.stt_bytes = (m + 1) * 256;
-    t->d_bytes = (size_t)t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes;
+    t->view.k4s_bytes = (m + 1) * 256;
+    t->d_bytes = (size_t)t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes + t->view.k4s_bytes;
     if (cudaGetDevice(&t->device) != cudaSuccess || cudaMalloc(&t->d_mem, t->d_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete t;
@@ -1585,6 +1688,7 @@ int dfa_build(const char* pattern, int32_t m, dfa_table** out)
     memcpy(img.data(), t->k4.data(), (size_t)t->view.k4_bytes);
     memcpy(img.data() + t->view.k4_bytes, t->d1.data(), t->d1.size());
     memcpy(img.data() + t->view.k4_bytes + t->view.d1_bytes, t->stt.data(), t->stt.size());
+    memcpy(img.data() + t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes, t->k4s.data(), t->k4s.size());
     if (cudaMemcpy(t->d_mem, img.data(), t->d_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(t->d_mem);
         delete t;

@@ -27,6 +27,9 @@ CONFIGS = [
     dict(loader=2, layout=1, chunk=384),
     dict(loader=2, layout=2, chunk=192),
     dict(loader=2, layout=1, chunk=1280),
+    # four-step table of states only with exact replays (loader 2)
+    dict(loader=2, layout=3, chunk=128),
+    dict(loader=2, layout=3, chunk=1280),
 ]
 
 
@@ -97,7 +100,8 @@ def test_planted_long_patterns(gpu, cfg):
 
 @pytest.mark.parametrize("cfg,chunk", [(dict(loader=1, layout=1, threads=128, chunk=64), 64),
                                        (dict(loader=2, layout=1, chunk=128), 128),
-                                       (dict(loader=2, layout=2, chunk=64 * 3), 192)])
+                                       (dict(loader=2, layout=2, chunk=64 * 3), 192),
+                                       (dict(loader=2, layout=3, chunk=128), 128)])
 def test_border_plants(gpu, cfg, chunk):
     # occurrences planted at +-m around every chunk / tile border
     n = 256 * chunk * 6 + 77
@@ -137,7 +141,7 @@ def test_dense_matches_overflow_and_truncation(gpu):
     t = np.full(n, ord("A"), np.uint8)
     for cfg in (None, dict(loader=1, layout=1, threads=128, chunk=1024),
                 dict(loader=1, layout=2, threads=256, chunk=512), dict(loader=2, chunk=128),
-                dict(loader=2, layout=2, chunk=768)):
+                dict(loader=2, layout=2, chunk=768), dict(loader=2, layout=3, chunk=256)):
         for m in (1, 4, 64):
             _check(gpu, t, b"A" * m, cfg)
     # cap smaller than the count: exact count, first cap positions, ETRUNC
