@@ -177,6 +177,43 @@ int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int6
                   int64_t cap, uint64_t* h_count, void* d_stage, int64_t stage_bytes,
                   int64_t seg, void* stream);
 
+/*
+ * dfa_find for callers that must not allocate device memory.  The paper has
+ * no counterpart; this is a library service.  Some callers cannot allocate:
+ * code running in a process where another allocator already holds the
+ * device's memory (a framework's caching pool that reserved most of HBM, so
+ * a fresh cudaMalloc fails although the pool has room), code on a
+ * latency-bound stream (cudaMalloc and cudaFree can synchronise the whole
+ * device), or a plug-in that is handed only its input and output buffers.
+ * Such callers pass the text, positions and count buffers exactly as for
+ * dfa_find; the workspace is a fixed array inside the library's device
+ * image instead.
+ *
+ * Arguments, outputs and errors are those of dfa_find without d_work and
+ * work_bytes.  The array holds 65536 tile descriptors (512 KiB on every
+ * device that loads the library, until the process exits); a text that needs
+ * more tiles under `cfg` is rejected with DFA_EWORKSPACE before any GPU work,
+ * and dfa_last_error says so.
+ *
+ * Device-side outcome: there is no workspace to hand to dfa_find_status, so
+ * a bounded wait that gave up sets bit 63 of *d_count (DFA_COUNT_FAILED) and
+ * the count and positions are then invalid.  Truncation is count > cap, as
+ * for dfa_find.
+ *
+ * First call on each device: it resolves the array's address on the current
+ * device (cudaGetSymbolAddress), which may load the library's device code.
+ * Make that first call before any stream capture begins.
+ *
+ * Every call on a device shares the one array, which keeps the previous
+ * call's contents; each call clears the part it uses at its start, on
+ * `stream`.  Two calls that may overlap on the GPU (different streams with no
+ * ordering between them, or different host threads) race on the array and
+ * give wrong results: order them.  Asynchronous on `stream`; calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ */
+int dfa_find_noalloc(const uint8_t* d_text, int64_t n, const dfa_table* table, int64_t* d_pos,
+                     int64_t cap, uint64_t* d_count, const dfa_config* cfg, void* stream);
+
 /* Static text for a return code. */
 const char* dfa_strerror(int code);
 

@@ -11,6 +11,8 @@ device memory and the current CUDA stream.  The names follow the C ABI:
   start positions, single pass
 * ``dfa_find_status(workspace, count, cap)`` — device-side outcome
 * ``dfa_find_host(...)`` — host buffers in, host buffers out (copies inside)
+* ``dfa_find_noalloc(text, table, positions, count)`` — ``dfa_find`` with the
+  library's static device workspace, for callers that may not allocate
 
 plus ``find``/``count`` conveniences that allocate their outputs with torch.
 There is no CPU fallback: importing this package fails if the CUDA library
@@ -30,7 +32,7 @@ _lib = _native.lib
 
 __all__ = ["Table", "DfaError", "dfa_build", "dfa_free", "dfa_export_stt", "dfa_count",
            "dfa_find", "dfa_find_workspace_bytes", "dfa_find_status", "dfa_host_stage_bytes",
-           "dfa_find_host", "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
+           "dfa_find_host", "dfa_find_noalloc", "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
            "DFA_OK", "DFA_EINVAL", "DFA_ETRUNC", "DFA_ETIMEOUT", "DFA_ECUDA", "DFA_EWORKSPACE",
            "DFA_ENOMEM", "DFA_MAX_M"]
 
@@ -149,6 +151,21 @@ def dfa_find_status(workspace, count, cap: int, stream=None):
     rc = _lib.dfa_find_status(_ptr(workspace), _ptr(count), int(cap), ctypes.byref(h),
                               _stream(stream))
     return rc, int(h.value)
+
+
+def dfa_find_noalloc(text, table: Table, positions, count, cfg=None, stream=None) -> None:
+    """Enqueue dfa_find with the library's static device workspace: for
+    callers that may not allocate device memory.  A bounded wait that gave up
+    sets bit 63 of ``count``; calls that may overlap on the GPU race on the
+    shared workspace."""
+    cap = int(positions.numel()) if positions is not None else 0
+    rc = _lib.dfa_find_noalloc(_ptr(text), int(text.numel()), table.handle, _ptr(positions), cap,
+                               _ptr(count), _cfg(cfg), _stream(stream))
+    if rc != DFA_OK:
+        err = DfaError(rc, "dfa_find_noalloc")
+        if rc != DFA_ECUDA and _lib.dfa_last_error():
+            err.args = (f"{err.args[0]} [{_lib.dfa_last_error().decode(errors='replace')}]",)
+        raise err
 
 
 def dfa_host_stage_bytes(seg: int, cap: int) -> int:

@@ -37,6 +37,7 @@ def _declare(lib):
         "dfa_host_stage_bytes": ([i64, i64], i64),
         "dfa_find_host": ([vp, i64, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64), vp, i64, i64, vp],
                           ctypes.c_int),
+        "dfa_find_noalloc": ([vp, i64, vp, vp, i64, vp, cfgp, vp], ctypes.c_int),
         "dfa_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "dfa_version": ([], ctypes.c_char_p),
         "dfa_last_error": ([], ctypes.c_char_p),

@@ -1882,3 +1882,93 @@ const char* dfa_version(void) { return "dnadfa 0.1 (sm_103a)"; }
 const char* dfa_last_error(void) { return g_last_error; }
 
 }  // extern "C"
+
+// ================================================= find without an allocation
+//
+// dfa_find_noalloc runs dfa_find with its workspace (the ticket, the status
+// word and one look-back descriptor per tile) in a fixed array of this
+// library's device memory instead of memory the caller provides.  The paper
+// has no counterpart: it exists for callers that may not allocate device
+// memory at all (see include/dnadfa.h).
+
+namespace {
+
+// Tiles the static workspace can describe.  A tile is the text one CTA
+// takes per ticket (threads x chunk bytes of the resolved launch; 640 KiB by
+// default for multi-GB texts, so the default limit is about 40 GiB).
+constexpr int64_t kNoAllocTiles = 65536;
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+// The shared workspace: [0] ticket, [1] status, then one word per tile
+// (512 KiB + 16 bytes, held on every device that loads the library until the
+// process exits).  In host code this name is only a handle for
+// cudaGetSymbolAddress, never a device address.
+static __device__ __align__(256) unsigned long long g_noalloc_work[kWorkHeader + kNoAllocTiles];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices];   // device address of g_noalloc_work, per device
+
+// Set-up, once per device, with that device current: resolve the address of
+// g_noalloc_work on it.
+int noalloc_workspace(int dev, void** out)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "dfa_find_noalloc: device %d is beyond the %d devices it serves", dev,
+                 kNoAllocMaxDevices);
+        return DFA_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_work);
+        if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(g_noalloc_work)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return DFA_OK;
+}
+
+// Runs after the scan on the same stream: the status word is the caller's
+// only view of a bounded wait that gave up, so it is folded into bit 63 of
+// the count.
+__global__ void k_noalloc_status(const unsigned long long* work, unsigned long long* count)
+{
+    if (work[1]) atomicOr(count, 1ull << 63);
+}
+
+}  // namespace
+
+extern "C" int dfa_find_noalloc(const uint8_t* d_text, int64_t n, const dfa_table* table,
+                                int64_t* d_pos, int64_t cap, uint64_t* d_count,
+                                const dfa_config* cfg, void* stream)
+{
+    if (!table || !d_count || n < 0 || (n > 0 && !d_text) || cap < 0 || (cap > 0 && !d_pos))
+        return DFA_EINVAL;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail("dfa_find_noalloc: no current device");
+    void* work = nullptr;
+    int rc = noalloc_workspace(dev, &work);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // launch_find checks the tile count against the array before any GPU
+    // work and clears the header and descriptors this call uses.
+    rc = launch_find(d_text, n, n, table, d_pos, cap, d_count, nullptr, 0, work,
+                     (int64_t)sizeof(g_noalloc_work), cfg, st);
+    if (rc == DFA_EWORKSPACE) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "dfa_find_noalloc: a text of %lld bytes needs more than the %lld tiles its "
+                 "static workspace holds; use dfa_find with a caller workspace or a larger chunk",
+                 (long long)n, (long long)kNoAllocTiles);
+        return rc;
+    }
+    if (rc) return rc;
+    k_noalloc_status<<<1, 1, 0, st>>>(static_cast<const unsigned long long*>(work),
+                                      reinterpret_cast<unsigned long long*>(d_count));
+    CUDA_TRY(cudaGetLastError());
+    return DFA_OK;
+}
