@@ -816,6 +816,22 @@ __device__ unsigned long long lookback_warp(unsigned long long* work, int64_t ti
     return excl;
 }
 
+// A TMA walker row's staged end offsets: entry j at shared byte address
+// base + j * kRows * 2 (the tile's rows interleaved, so a warp's stores fall
+// in distinct banks).  n counts every accept put; n > CAP means the row
+// overflowed its slots and is walked again from global memory at flush.
+template <uint32_t CAP>
+struct RowSlots {
+    static constexpr bool kRecord = true;
+    uint32_t base;
+    uint32_t n;
+    __device__ __forceinline__ void put(uint32_t off)
+    {
+        if (n < CAP) asm volatile("st.shared.u16 [%0], %1;" ::"r"(base + n * (uint32_t)(kRows * 2)), "h"((uint16_t)off));
+        n++;
+    }
+};
+
 // Cold paths of the TMA walkers, kept out of line so that the hot loop's
 // register allocation does not pay for them.
 //   replay_stage: walk a 64-byte stage again from its start entry and record
@@ -823,29 +839,28 @@ __device__ unsigned long long lookback_warp(unsigned long long* work, int64_t ti
 //   replay_halo:  the same for the overlap stage, ends limited to lim;
 //   walk_cold:    a row walked from global memory (edge rows, overflow).
 template <int LAYOUT>
-__device__ __noinline__ uint2 replay_stage(SmemTab T, uint16_t* slots, uint32_t n, uint32_t over,
-                                           uint32_t e_in, const uint8_t* rp, uint32_t ob, uint32_t r)
+__device__ __noinline__ uint32_t replay_stage(SmemTab T, uint32_t slots, uint32_t n, uint32_t e_in,
+                                              const uint8_t* rp, uint32_t ob, uint32_t r)
 {
-    SlotSink ss{slots, (uint32_t)kRows, (uint32_t)kTSlots, n, over != 0u};
-    Walker<LAYOUT, false, SlotSink> rw{T, ss, e_in, 0u};
+    RowSlots<kTSlots> ss{slots, n};
+    Walker<LAYOUT, false, RowSlots<kTSlots>> rw{T, ss, e_in, 0u};
     rw.vec4(lds128_fresh(rp + ob), lds128_fresh(rp + (ob ^ 16u)), lds128_fresh(rp + (ob ^ 32u)),
             lds128_fresh(rp + (ob ^ 48u)), r);
-    return make_uint2(ss.n, ss.over ? 1u : 0u);
+    return ss.n;
 }
 
 template <int LAYOUT>
-__device__ __noinline__ uint2 replay_halo(SmemTab T, uint16_t* slots, uint32_t n, uint32_t over,
-                                          uint32_t e_in, const uint8_t* rp, uint32_t ob, uint32_t C,
-                                          uint32_t lim)
+__device__ __noinline__ uint32_t replay_halo(SmemTab T, uint32_t slots, uint32_t n, uint32_t e_in,
+                                             const uint8_t* rp, uint32_t ob, uint32_t C, uint32_t lim)
 {
-    SlotSink ss{slots, (uint32_t)kRows, (uint32_t)kTSlots, n, over != 0u};
-    Walker<LAYOUT, true, SlotSink> hr{T, ss, e_in, 0u};
+    RowSlots<kTSlots> ss{slots, n};
+    Walker<LAYOUT, true, RowSlots<kTSlots>> hr{T, ss, e_in, 0u};
     const uint32_t m = T.m;
     hr.vec(lds128_fresh(rp + ob), C, lim);
     if (m > 17) hr.vec(lds128_fresh(rp + (ob ^ 16u)), C + 16, lim);
     if (m > 33) hr.vec(lds128_fresh(rp + (ob ^ 32u)), C + 32, lim);
     if (m > 49) hr.vec(lds128_fresh(rp + (ob ^ 48u)), C + 48, lim);
-    return make_uint2(ss.n, ss.over ? 1u : 0u);
+    return ss.n;
 }
 
 template <int LAYOUT, class Sink>
@@ -902,13 +917,23 @@ __device__ __forceinline__ void count_stage(const SmemTab& T, uint32_t (&e)[kRPL
 }
 
 
-// One tile's worth of a walker row's state, kept until its positions are
-// written (the row's bounds are recomputed from the tile id).
-struct PendingRow {
-    uint32_t cnt, excl;
-    int32_t tile;
-    bool over;
-};
+// One tile's worth of a walker row's state, kept in one register until its
+// positions are written: the row's count (bits 0..12; at most a chunk of
+// 4096 bytes), its exclusive offset among the warp's rows (bits 13..29; at
+// most 31 x 4096) and the slot-overflow flag (bit 31).  The tile id comes
+// from the scheduler with the tile's offset.
+constexpr uint32_t kPendCntBits = 13;
+constexpr uint32_t kPendExclBits = 17;
+__device__ __forceinline__ uint32_t pend_pack(uint32_t cnt, uint32_t excl, bool over)
+{
+    return cnt | (excl << kPendCntBits) | (over ? 0x80000000u : 0u);
+}
+__device__ __forceinline__ uint32_t pend_cnt(uint32_t pr) { return pr & ((1u << kPendCntBits) - 1u); }
+__device__ __forceinline__ uint32_t pend_excl(uint32_t pr)
+{
+    return (pr >> kPendCntBits) & ((1u << kPendExclBits) - 1u);
+}
+__device__ __forceinline__ bool pend_over(uint32_t pr) { return (pr >> 31) != 0u; }
 
 template <int LAYOUT, bool FIND, bool DENSE>
 __global__ void __launch_bounds__(kTmaThreads, 1)
@@ -925,6 +950,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     __shared__ uint32_t s_wtot[kDefer][kWalkWarps];
     __shared__ uint32_t s_woff[kDefer][kWalkWarps];
     __shared__ unsigned long long s_tile_off[kDefer];
+    __shared__ int64_t s_tile_done[kDefer];       // the tile s_tile_off[b] belongs to
     __shared__ unsigned long long s_sum[kWalkWarps];
     __shared__ int s_abort;
 
@@ -937,6 +963,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     // [tables][position slots][rings], rings 1024-byte aligned for the TMA swizzle
     const SmemTab T = load_tables<LAYOUT>(a, smem);
     uint16_t* slots = reinterpret_cast<uint16_t*>(smem + p.table_bytes);
+    const uint32_t slots_sa = (uint32_t)__cvta_generic_to_shared(slots);
     uint8_t* rings = smem + p.rings_off;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -1002,6 +1029,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             const unsigned long long off = lookback_warp(a.work, tile, total, lane);
             if (lane == 0) {
                 s_tile_off[b] = base + off;
+                s_tile_done[b] = tile;
                 if (tile == a.ntiles - 1) *a.count = base + off + total;
             }
             __syncwarp();
@@ -1058,24 +1086,28 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 
     unsigned long long total = 0;
     // pend[d] holds tile k-1-d, for d = 0 .. kDefer-2
-    PendingRow pend[kDefer - 1][kRPL];
+    uint32_t pend[kDefer - 1][kRPL];
 #pragma unroll
     for (int d = 0; d < kDefer - 1; d++)
 #pragma unroll
-        for (int i = 0; i < kRPL; i++) pend[d][i] = PendingRow{0, 0, 0, false};
-    auto flush = [&](const PendingRow (&pr)[kRPL], int64_t kp) -> bool {
+        for (int i = 0; i < kRPL; i++) pend[d][i] = 0u;
+    auto flush = [&](const uint32_t (&pr)[kRPL], int64_t kp) -> bool {
         const int b = (int)((uint64_t)kp % kDefer);
         if (!warp_wait(&s_ready[b], (uint32_t)((uint64_t)kp / kDefer) & 1u, abort_flag, p)) return false;
 #pragma unroll
         for (int i = 0; i < kRPL; i++) {
-            if (pr[i].cnt == 0) continue;
-            const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + pr[i].excl);
-            const int64_t ps = ((int64_t)pr[i].tile * kRows + wrow0 + 32 * i) * C;
+            const uint32_t pc = pend_cnt(pr[i]);
+            if (pc == 0) continue;
+            const int64_t g0 = (int64_t)(s_tile_off[b] + s_woff[b][warp] + pend_excl(pr[i]));
+            const int64_t ps = (s_tile_done[b] * kRows + wrow0 + 32 * i) * C;
             const int64_t pe = min(ps + C, a.n_own);
             const int64_t start0 = a.pos_base + ps - (int64_t)(m - 1);
-            if (!pr[i].over) {
+            if (!pend_over(pr[i])) {
+                // a row that did not overflow recorded exactly pc <= KS ends;
+                // the bound keeps every read inside the slot array regardless
                 const uint16_t* sl = slots + (size_t)b * KS * kRows + wrow0 + 32 * i;
-                for (uint32_t j = 0; j < pr[i].cnt; j++) {
+                const uint32_t nrec = min(pc, (uint32_t)KS);
+                for (uint32_t j = 0; j < nrec; j++) {
                     const int64_t gi = g0 + j;
                     if (gi < a.cap) a.pos[gi] = start0 + sl[j * kRows];
                 }
@@ -1098,21 +1130,18 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         }
         if (tile < 0) break;
         const int kb = (int)((uint64_t)k % kDefer);
-        int64_t s0[kRPL], e0[kRPL];
-        bool has[kRPL], ok[kRPL];
+        bool ok[kRPL];
         uint32_t e[kRPL], cnt[kRPL];
-        SlotSink ss[kRPL];
+        RowSlots<KS> ss[kRPL];
 #pragma unroll
         for (int i = 0; i < kRPL; i++) {
+            // a full row whose successor row is complete too (its halo is the
+            // next row's first bytes); every other row is walked cold below
             const int64_t row = tile * kRows + wrow0 + 32 * i;
-            s0[i] = row * C;
-            has[i] = s0[i] < a.n_own;
-            e0[i] = has[i] ? min(s0[i] + C, a.n_own) : s0[i];
-            ok[i] = has[i] && e0[i] == s0[i] + C && row + 1 < p.nrows_full;
+            ok[i] = (row + 1) * C <= a.n_own && row + 1 < p.nrows_full;
             e[i] = 0;
             cnt[i] = 0;
-            ss[i] = SlotSink{slots + (size_t)kb * KS * kRows + wrow0 + 32 * i, (uint32_t)kRows, (uint32_t)KS,
-                             0u, false};
+            ss[i] = RowSlots<KS>{slots_sa + (uint32_t)(((uint32_t)kb * KS * kRows + wrow0 + 32 * i) * 2), 0u};
         }
         for (uint32_t s = 0; s < spt; s++) {
             if (!warp_wait(&full[c_slot], c_par, abort_flag, p)) {
@@ -1135,7 +1164,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 #pragma unroll
                     for (int i = 0; i < kRPL; i++) {
                         if (!ok[i]) continue;
-                        Walker<LAYOUT, false, SlotSink> wd{T, ss[i], e[i], cnt[i]};
+                        Walker<LAYOUT, false, RowSlots<KS>> wd{T, ss[i], e[i], cnt[i]};
                         wd.vec4(v[i][0], v[i][1], v[i][2], v[i][3], r);
                         e[i] = wd.e;
                         cnt[i] = wd.cnt;
@@ -1154,10 +1183,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                             if (ok[i] && cnt[i] != c_in[i]) {
                                 // a match in this stage: walk it again to record where
                                 // (the stage is re-read from its slot, released below)
-                                const uint2 st = replay_stage<LAYOUT>(T, ss[i].slots, ss[i].n, ss[i].over, e_in[i],
-                                                                      rp + i * 32 * kStageW, ob, r);
-                                ss[i].n = st.x;
-                                ss[i].over = st.y != 0u;
+                                ss[i].n = replay_stage<LAYOUT>(T, ss[i].base, ss[i].n, e_in[i],
+                                                               rp + i * 32 * kStageW, ob, r);
                             }
                         }
                     }
@@ -1171,7 +1198,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     const uint8_t* q = rp + i * 32 * kStageW;
                     const uint4 h0 = *reinterpret_cast<const uint4*>(q + ob);
                     if (FIND && INLINE_REC) {
-                        Walker<LAYOUT, true, SlotSink> h{T, ss[i], e[i], cnt[i]};
+                        Walker<LAYOUT, true, RowSlots<KS>> h{T, ss[i], e[i], cnt[i]};
                         h.vec(h0, (uint32_t)C, lim);
                         if (m > 17) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 16u)), (uint32_t)C + 16, lim);
                         if (m > 33) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 32u)), (uint32_t)C + 32, lim);
@@ -1185,10 +1212,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                         if (m > 33) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 32u)), (uint32_t)C + 32, lim);
                         if (m > 49) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 48u)), (uint32_t)C + 48, lim);
                         if (FIND && h.cnt != cnt[i]) {
-                            const uint2 st = replay_halo<LAYOUT>(T, ss[i].slots, ss[i].n, ss[i].over, e[i], q, ob,
-                                                                 (uint32_t)C, lim);
-                            ss[i].n = st.x;
-                            ss[i].over = st.y != 0u;
+                            ss[i].n = replay_halo<LAYOUT>(T, ss[i].base, ss[i].n, e[i], q, ob, (uint32_t)C, lim);
                         }
                         cnt[i] = h.cnt;
                     }
@@ -1208,16 +1232,17 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         if (aborted) break;
 #pragma unroll
         for (int i = 0; i < kRPL; i++) {
-            if (!has[i]) {
+            const int64_t s0 = (tile * kRows + wrow0 + 32 * i) * C;
+            const int64_t e0 = min(s0 + C, a.n_own);
+            if (s0 >= a.n_own) {
                 cnt[i] = 0;
             } else if (!ok[i]) {
                 ss[i].n = 0;
-                ss[i].over = false;
                 if (FIND)
-                    cnt[i] = walk_cold<LAYOUT>(a, T, s0[i], e0[i], &ss[i]);
+                    cnt[i] = walk_cold<LAYOUT>(a, T, s0, e0, &ss[i]);
                 else {
                     CountSink cs;
-                    cnt[i] = walk_cold<LAYOUT>(a, T, s0[i], e0[i], &cs);
+                    cnt[i] = walk_cold<LAYOUT>(a, T, s0, e0, &cs);
                 }
             }
         }
@@ -1257,7 +1282,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 #pragma unroll
                 for (int i = 0; i < kRPL; i++) pend[d][i] = pend[d - 1][i];
 #pragma unroll
-            for (int i = 0; i < kRPL; i++) pend[0][i] = PendingRow{cnt[i], excl[i], (int32_t)tile, ss[i].over};
+            for (int i = 0; i < kRPL; i++) pend[0][i] = pend_pack(cnt[i], excl[i], ss[i].n > (uint32_t)KS);
         }
         k++;
     }
