@@ -39,7 +39,12 @@ namespace {
 constexpr int kLayoutK4 = 1;
 constexpr int kLayoutStt = 2;
 constexpr int kLayoutK4S = 3;     // four-step table of states only (u8), m >= kK4SMinM
+constexpr int kLayoutK4F = 4;     // four-step states with accept flag (u8), kOptMinM <= m < kK4SMinM
 constexpr int kK4SMinM = 20;
+constexpr int kOptMinM = 8;       // default: layouts 3 and 4 (relaxed walk + exact replay) from here on
+// layout 4 keeps its flagged table at shared offset 0 and the u16 four-step
+// table of the exact replays at this fixed offset
+constexpr uint32_t kK4FTabOff = (uint32_t)K4F_ROWS * 256u;
 constexpr int kSlots = 16;                  // staged positions per thread per tile
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
@@ -55,7 +60,7 @@ struct ScanArgs {
     int64_t ntiles;
     const uint8_t* tab;   // device table allocation
     int32_t m;
-    int32_t k4_bytes, d1_bytes, stt_bytes, k4s_bytes;
+    int32_t k4_bytes, d1_bytes, stt_bytes, k4s_bytes, k4f_bytes;
     int32_t aligned;      // text is 16-byte aligned
     unsigned long long* count;
     int64_t* pos;
@@ -133,11 +138,13 @@ __device__ __forceinline__ uint32_t word_bad(uint32_t x)
 // (x & 0x06060606) holds the 2-bit codes at bits 8k+1; the multiply gathers
 // them, first byte lowest, into bits 24..31 without carries; byte_perm forms
 // the table index (state << 8) | code4.
-__device__ __forceinline__ uint32_t k4_next(uint32_t /*k4 at offset 0*/, uint32_t e, uint32_t x)
+// The u16 table sits at shared offset 0, or at kK4FTabOff in layout 4.
+template <int LAYOUT = kLayoutK4>
+__device__ __forceinline__ uint32_t k4_next(uint32_t /*fixed offset*/, uint32_t e, uint32_t x)
 {
     uint32_t code = (x & 0x06060606u) * 0x00820820u;
     uint32_t idx = __byte_perm(code, e, 0x7743u);
-    return tab16(idx);
+    return tab16(LAYOUT == kLayoutK4F ? idx + kK4FTabOff / 2u : idx);
 }
 
 // One automaton step on one raw byte (any byte value).
@@ -219,7 +226,7 @@ struct Walker {
 
     __device__ __forceinline__ void word_k4(uint32_t x, uint32_t r, uint32_t lim)
     {
-        e = k4_next(T.k4, e, x);
+        e = k4_next<LAYOUT>(T.k4, e, x);
         if (LIM) {
             uint32_t acc = ((e >> K4_ACC_SHIFT) & 0xFu) & lim_mask(r, lim);
             cnt += __popc(acc);
@@ -335,7 +342,7 @@ struct Walker {
                 slow_vec(v2, r + 32, 0);
                 slow_vec(v3, r + 48, 0);
             }
-        } else if (LAYOUT == kLayoutK4) {
+        } else if (LAYOUT == kLayoutK4 || LAYOUT == kLayoutK4F) {
             const uint32_t bad = word_bad(v0.x) | word_bad(v0.y) | word_bad(v0.z) | word_bad(v0.w) |
                                  word_bad(v1.x) | word_bad(v1.y) | word_bad(v1.z) | word_bad(v1.w) |
                                  word_bad(v2.x) | word_bad(v2.y) | word_bad(v2.z) | word_bad(v2.w) |
@@ -368,7 +375,7 @@ struct Walker {
             } else {
                 slow_vec(v, r, lim);
             }
-        } else if (LAYOUT == kLayoutK4) {
+        } else if (LAYOUT == kLayoutK4 || LAYOUT == kLayoutK4F) {
             uint32_t bad = word_bad(v.x) | word_bad(v.y) | word_bad(v.z) | word_bad(v.w);
             if (bad == 0u) {
                 word_k4(v.x, r, lim);
@@ -459,6 +466,20 @@ __device__ __forceinline__ SmemTab load_tables(const ScanArgs& a, uint8_t* smem)
         for (int i = threadIdx.x; i < (a.d1_bytes >> 4); i += blockDim.x) d[i] = s2[i];
         return T;
     }
+    if (LAYOUT == kLayoutK4F) {
+        // [k4f][k4 at kK4FTabOff][d1]
+        T.k4 = base + kK4FTabOff;
+        T.d1 = base + kK4FTabOff + (uint32_t)a.k4_bytes;
+        T.stt = 0;
+        const uint4* s1 = reinterpret_cast<const uint4*>(a.tab + a.k4_bytes + a.d1_bytes + a.stt_bytes +
+                                                         a.k4s_bytes);
+        const uint4* s2 = reinterpret_cast<const uint4*>(a.tab);
+        uint4* d = reinterpret_cast<uint4*>(smem);
+        for (int i = threadIdx.x; i < (a.k4f_bytes >> 4); i += blockDim.x) d[i] = s1[i];
+        d += kK4FTabOff >> 4;
+        for (int i = threadIdx.x; i < ((a.k4_bytes + a.d1_bytes) >> 4); i += blockDim.x) d[i] = s2[i];
+        return T;
+    }
     if (LAYOUT == kLayoutK4) {
         bytes = a.k4_bytes + a.d1_bytes;
         src_off = 0;
@@ -480,8 +501,10 @@ __device__ __forceinline__ SmemTab load_tables(const ScanArgs& a, uint8_t* smem)
 
 __device__ __forceinline__ int table_smem_bytes_dev(const ScanArgs& a, int layout)
 {
-    return layout == kLayoutK4 ? a.k4_bytes + a.d1_bytes
-                               : layout == kLayoutK4S ? a.k4s_bytes + a.d1_bytes : a.stt_bytes;
+    return layout == kLayoutK4    ? a.k4_bytes + a.d1_bytes
+           : layout == kLayoutK4S ? a.k4s_bytes + a.d1_bytes
+           : layout == kLayoutK4F ? (int)kK4FTabOff + a.k4_bytes + a.d1_bytes
+                                  : a.stt_bytes;
 }
 
 // ---------------------------------------------------------------- kernels
@@ -869,6 +892,107 @@ __device__ __noinline__ uint32_t walk_cold(const ScanArgs a, SmemTab T, int64_t 
     return walk_chunk<LAYOUT>(a, T, s, e, *sink);
 }
 
+// Relaxed walk of layouts 3 and 4 (patterns of kOptMinM and more).  The
+// text is read through the 2-bit codes alone, i.e. every byte that is not a
+// base is taken as the base with the same code, and no byte is tested.
+// Against the exact walk (a non-base resets to q0) this relaxed walk is
+// never behind: its state is the longest suffix of the relaxed text that is
+// a prefix of P, the exact state the longest such suffix holding no
+// non-base, which is also a suffix of the relaxed text.  So every exact
+// accept is a relaxed accept, and a stage whose relaxed walk shows none has
+// none.  A stage that may hold one is walked again exactly (replay_exact).
+//   layout 4: entries carry a flag for "one of the four steps accepted";
+//   layout 3: states only; a group of four steps can accept only from a
+//             state q >= m - 4, i.e. with (q >> T.sh) != 0 (force for m <= 4).
+// Returns non-zero when the words may hold an accept.
+template <int LAYOUT, int N>
+__device__ __forceinline__ uint32_t relaxed_words(const SmemTab& T, uint32_t& e, const uint32_t (&x)[N])
+{
+    uint32_t orq = LAYOUT == kLayoutK4S ? e : 0u;
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+        const uint32_t code = (x[k] & 0x06060606u) * 0x00820820u;
+        e = tab8(__byte_perm(code, e, 0x7743u));
+        if (LAYOUT == kLayoutK4F || k + 1 < N) orq |= e;
+    }
+    return LAYOUT == kLayoutK4F ? (orq & K4F_FLAG) : ((orq >> T.sh) | T.force);
+}
+
+// Shared-memory table view of layouts 3 and 4 (as load_tables lays them
+// out), rebuilt from m alone.
+template <int LAYOUT>
+__device__ __forceinline__ SmemTab opt_tab(uint32_t m)
+{
+    SmemTab T;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(g_smem);
+    T.m = m;
+    T.sh = m > 4 ? 31u - (uint32_t)__clz(m - 4) : 0u;
+    T.force = m <= 4 ? 1u : 0u;
+    T.stt = 0;
+    if (LAYOUT == kLayoutK4F) {
+        T.k4 = base + kK4FTabOff;
+        T.k4s = 0;
+        T.d1 = base + kK4FTabOff + (m + 1) * 512u;
+    } else {
+        T.k4 = 0;
+        T.k4s = base;
+        T.d1 = base + (m + 1) * 256u;
+    }
+    return T;
+}
+
+__device__ __forceinline__ uint4 lds128_at(uint32_t addr)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+// Exact walk of one stage of a row (64 bytes at row offset r, or the
+// overlap stage with ends limited to lim) after a relaxed walk flagged it.
+// The exact state at the stage start depends on at most the m <= 64 bytes
+// before it (Algorithm 1's overlap argument), so the walk starts from q0 on
+// the previous 64 bytes of the row, read again from global memory at g, or
+// at the row start (g == nullptr).  The stage itself is read from its ring
+// slot (shared address rp, the lane's swizzled offset ob).  With REC the
+// accepts go to the row's slots (base, n).  Returns (count, n).
+template <int LAYOUT, bool LIM, bool REC>
+__device__ __noinline__ uint2 replay_exact(uint32_t m, const uint4* g, uint32_t rp, uint32_t ob, uint32_t r,
+                                           uint32_t lim, uint32_t slot_base, uint32_t slot_n)
+{
+    const SmemTab T = opt_tab<LAYOUT>(m);
+    uint32_t e0 = 0u;
+    if (g) {
+        CountSink cs;
+        Walker<LAYOUT, false, CountSink> w{T, cs, 0u, 0u};
+        w.vec4(ldg16(g), ldg16(g + 1), ldg16(g + 2), ldg16(g + 3), 0u);
+        e0 = w.e;
+    }
+    using Sink = typename std::conditional<REC, RowSlots<kTSlots>, CountSink>::type;
+    Sink sink{};
+    if (REC) {
+        reinterpret_cast<RowSlots<kTSlots>*>(&sink)->base = slot_base;
+        reinterpret_cast<RowSlots<kTSlots>*>(&sink)->n = slot_n;
+    }
+    uint32_t cnt;
+    if (!LIM) {
+        Walker<LAYOUT, false, Sink> w{T, sink, e0, 0u};
+        w.vec4(lds128_at(rp + ob), lds128_at(rp + (ob ^ 16u)), lds128_at(rp + (ob ^ 32u)),
+               lds128_at(rp + (ob ^ 48u)), r);
+        cnt = w.cnt;
+    } else {
+        Walker<LAYOUT, true, Sink> h{T, sink, e0, 0u};
+        h.vec(lds128_at(rp + ob), r, lim);
+        if (m > 17) h.vec(lds128_at(rp + (ob ^ 16u)), r + 16, lim);
+        if (m > 33) h.vec(lds128_at(rp + (ob ^ 32u)), r + 32, lim);
+        if (m > 49) h.vec(lds128_at(rp + (ob ^ 48u)), r + 48, lim);
+        cnt = h.cnt;
+    }
+    return make_uint2(cnt, REC ? reinterpret_cast<RowSlots<kTSlots>*>(&sink)->n : 0u);
+}
+
 // The common case of a stage: kRPL rows of 64 bytes each, counted only.
 // The rows' automaton chains are advanced word by word in turn so that their
 // table lookups overlap; a stage holding any non-base byte takes the
@@ -955,9 +1079,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     __shared__ int s_abort;
 
     constexpr int KS = DENSE ? kTSlotsDense : kTSlots;
-    // the k4s walk only records in its rare exact replays: it walks with the
-    // recording sink directly, like a dense pattern
-    constexpr bool INLINE_REC = DENSE || LAYOUT == kLayoutK4S;
+    // layouts 3 and 4: relaxed walk, exact replay of the rare flagged stages;
+    // dense patterns: exact walk recording every accept inline
+    constexpr bool OPT = !DENSE && (LAYOUT == kLayoutK4S || LAYOUT == kLayoutK4F);
+    constexpr bool INLINE_REC = DENSE;
     const ScanArgs& a = p.a;
     const int nst = p.nst;
     // [tables][position slots][rings], rings 1024-byte aligned for the TMA swizzle
@@ -1160,7 +1285,26 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     v[i][2] = *reinterpret_cast<const uint4*>(rp + ((ob + i * 32 * kStageW) ^ 32u));
                     v[i][3] = *reinterpret_cast<const uint4*>(rp + ((ob + i * 32 * kStageW) ^ 48u));
                 }
-                if (FIND && INLINE_REC) {
+                if (OPT) {
+#pragma unroll
+                    for (int i = 0; i < kRPL; i++) {
+                        const uint32_t x[16] = {v[i][0].x, v[i][0].y, v[i][0].z, v[i][0].w,
+                                                v[i][1].x, v[i][1].y, v[i][1].z, v[i][1].w,
+                                                v[i][2].x, v[i][2].y, v[i][2].z, v[i][2].w,
+                                                v[i][3].x, v[i][3].y, v[i][3].z, v[i][3].w};
+                        const uint32_t flag = relaxed_words<LAYOUT, 16>(T, e[i], x);
+                        if (flag != 0u && ok[i]) {
+                            const uint4* g =
+                                s ? reinterpret_cast<const uint4*>(a.text + (tile * kRows + wrow0 + 32 * i) * C + r -
+                                                                   kStageW)
+                                  : nullptr;
+                            const uint2 rc = replay_exact<LAYOUT, false, FIND>(
+                                m, g, smem_u32(rp + i * 32 * kStageW), ob, r, 0u, ss[i].base, ss[i].n);
+                            cnt[i] += rc.x;
+                            if (FIND) ss[i].n = rc.y;
+                        }
+                    }
+                } else if (FIND && INLINE_REC) {
 #pragma unroll
                     for (int i = 0; i < kRPL; i++) {
                         if (!ok[i]) continue;
@@ -1197,7 +1341,26 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     if (!ok[i]) continue;
                     const uint8_t* q = rp + i * 32 * kStageW;
                     const uint4 h0 = *reinterpret_cast<const uint4*>(q + ob);
-                    if (FIND && INLINE_REC) {
+                    if (OPT) {
+                        const uint32_t x0[4] = {h0.x, h0.y, h0.z, h0.w};
+                        uint32_t flag = relaxed_words<LAYOUT, 4>(T, e[i], x0);
+#pragma unroll
+                        for (uint32_t j = 1; j < 4; j++) {
+                            if (m > 16 * j + 1) {
+                                const uint4 hj = *reinterpret_cast<const uint4*>(q + (ob ^ (j << 4)));
+                                const uint32_t xj[4] = {hj.x, hj.y, hj.z, hj.w};
+                                flag |= relaxed_words<LAYOUT, 4>(T, e[i], xj);
+                            }
+                        }
+                        if (flag != 0u) {
+                            const uint4* g = reinterpret_cast<const uint4*>(
+                                a.text + (tile * kRows + wrow0 + 32 * i) * C + C - kStageW);
+                            const uint2 rc = replay_exact<LAYOUT, true, FIND>(m, g, smem_u32(q), ob, (uint32_t)C, lim,
+                                                                            ss[i].base, ss[i].n);
+                            cnt[i] += rc.x;
+                            if (FIND) ss[i].n = rc.y;
+                        }
+                    } else if (FIND && INLINE_REC) {
                         Walker<LAYOUT, true, RowSlots<KS>> h{T, ss[i], e[i], cnt[i]};
                         h.vec(h0, (uint32_t)C, lim);
                         if (m > 17) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 16u)), (uint32_t)C + 16, lim);
@@ -1412,12 +1575,17 @@ constexpr int64_t kMinDefaultTile = 256 * 64;   // workspace sizing for cfg == N
 // loader needs a 16-byte aligned text holding at least two full rows.
 int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int sms, int m, Resolved* r)
 {
-    // default layout: the four-step table of states only for long patterns
-    // (the TMA kernel's; see kK4SMinM), else the four-step table with counts
+    // default layout (the TMA kernel's): short patterns walk the four-step
+    // table exactly; from kOptMinM on the relaxed walk takes the flagged
+    // four-step table, and from kK4SMinM the table of states only
     const bool user_layout = cfg && cfg->layout;
-    r->layout = user_layout ? cfg->layout : (m >= kK4SMinM ? kLayoutK4S : kLayoutK4);
+    r->layout = user_layout ? cfg->layout
+                            : (m >= kK4SMinM ? kLayoutK4S : m >= kOptMinM ? kLayoutK4F : kLayoutK4);
     r->ctas_per_sm = cfg ? cfg->ctas_per_sm : 0;
-    if (r->layout != kLayoutK4 && r->layout != kLayoutStt && r->layout != kLayoutK4S) return DFA_EINVAL;
+    if (r->layout != kLayoutK4 && r->layout != kLayoutStt && r->layout != kLayoutK4S && r->layout != kLayoutK4F)
+        return DFA_EINVAL;
+    // the flagged table has room for states up to K4F_MAX_M only
+    if (r->layout == kLayoutK4F && m > K4F_MAX_M) r->layout = kLayoutK4S;
     if (r->ctas_per_sm < 0 || r->ctas_per_sm > 32) return DFA_EINVAL;
     const int req_loader = cfg ? cfg->loader : 0;
     if (req_loader < 0 || req_loader > 2) return DFA_EINVAL;
@@ -1445,8 +1613,8 @@ int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int
             return DFA_OK;
         }
     }
-    // the direct-load kernels have no k4s variant
-    if (r->layout == kLayoutK4S) {
+    // the direct-load kernels have no k4s or k4f variant
+    if (r->layout == kLayoutK4S || r->layout == kLayoutK4F) {
         if (user_layout && req_loader == 1) return DFA_EINVAL;
         r->layout = kLayoutK4;
     }
@@ -1493,16 +1661,25 @@ KernelFn pick_find(int layout, int threads)
 
 int table_smem(const dfa_table* t, int layout)
 {
-    return layout == kLayoutK4 ? t->view.k4_bytes + t->view.d1_bytes
-                               : layout == kLayoutK4S ? t->view.k4s_bytes + t->view.d1_bytes : t->view.stt_bytes;
+    return layout == kLayoutK4    ? t->view.k4_bytes + t->view.d1_bytes
+           : layout == kLayoutK4S ? t->view.k4s_bytes + t->view.d1_bytes
+           : layout == kLayoutK4F ? (int)kK4FTabOff + t->view.k4_bytes + t->view.d1_bytes
+                                  : t->view.stt_bytes;
 }
 
 typedef void (*TmaKernelFn)(const CUtensorMap, const TmaArgs);
 
+// Finds of patterns this short record every accept inline (layouts 1, 2).
+bool tma_dense(int layout, int m)
+{
+    return m <= kDenseMaxM && (layout == kLayoutK4 || layout == kLayoutStt);
+}
+
 TmaKernelFn pick_tma(int layout, bool find, int m)
 {
-    const bool dense = m <= kDenseMaxM;
+    const bool dense = tma_dense(layout, m);
     if (layout == kLayoutK4S) return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
+    if (layout == kLayoutK4F) return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
     if (layout == kLayoutK4) {
         if (!find) return k_scan_tma<kLayoutK4, false, false>;
         return dense ? k_scan_tma<kLayoutK4, true, true> : k_scan_tma<kLayoutK4, true, false>;
@@ -1557,7 +1734,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     cudaFuncAttributes fa;
     CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)fn));
     const int slot_bytes =
-        find ? kDefer * (t->m <= kDenseMaxM && r.layout != kLayoutK4S ? kTSlotsDense : kTSlots) * kRows * 2 : 0;
+        find ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2 : 0;
     p.rings_off = (p.table_bytes + slot_bytes + 1023) & ~1023;
     const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.rings_off;
     const int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
@@ -1589,6 +1766,7 @@ void fill_args(ScanArgs* a, const uint8_t* text, int64_t n, int64_t n_own, const
     a->d1_bytes = t->view.d1_bytes;
     a->stt_bytes = t->view.stt_bytes;
     a->k4s_bytes = t->view.k4s_bytes;
+    a->k4f_bytes = t->view.k4f_bytes;
     a->aligned = ((uintptr_t)text & 15u) == 0;
 }
 
@@ -1703,7 +1881,9 @@ int dfa_build(const char* pattern, int32_t m, dfa_table** out)
     t->view.d1_bytes = ((m + 1) * 4 + 15) & ~15;
     t->view.stt_bytes = (m + 1) * 256;
     t->view.k4s_bytes = (m + 1) * 256;
-    t->d_bytes = (size_t)t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes + t->view.k4s_bytes;
+    t->view.k4f_bytes = (int32_t)t->k4f.size();
+    t->d_bytes = (size_t)t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes + t->view.k4s_bytes +
+                 t->view.k4f_bytes;
     if (cudaGetDevice(&t->device) != cudaSuccess || cudaMalloc(&t->d_mem, t->d_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete t;
@@ -1714,6 +1894,9 @@ int dfa_build(const char* pattern, int32_t m, dfa_table** out)
     memcpy(img.data() + t->view.k4_bytes, t->d1.data(), t->d1.size());
     memcpy(img.data() + t->view.k4_bytes + t->view.d1_bytes, t->stt.data(), t->stt.size());
     memcpy(img.data() + t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes, t->k4s.data(), t->k4s.size());
+    if (!t->k4f.empty())
+        memcpy(img.data() + t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes + t->view.k4s_bytes,
+               t->k4f.data(), t->k4f.size());
     if (cudaMemcpy(t->d_mem, img.data(), t->d_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(t->d_mem);
         delete t;

@@ -27,9 +27,12 @@ CONFIGS = [
     dict(loader=2, layout=1, chunk=384),
     dict(loader=2, layout=2, chunk=192),
     dict(loader=2, layout=1, chunk=1280),
-    # four-step table of states only with exact replays (loader 2)
+    # relaxed walks with exact replays (loader 2): states only (layout 3),
+    # states with accept flags (layout 4; layout 3 beyond m = 31)
     dict(loader=2, layout=3, chunk=128),
     dict(loader=2, layout=3, chunk=1280),
+    dict(loader=2, layout=4, chunk=128),
+    dict(loader=2, layout=4, chunk=1280),
 ]
 
 
@@ -101,7 +104,8 @@ def test_planted_long_patterns(gpu, cfg):
 @pytest.mark.parametrize("cfg,chunk", [(dict(loader=1, layout=1, threads=128, chunk=64), 64),
                                        (dict(loader=2, layout=1, chunk=128), 128),
                                        (dict(loader=2, layout=2, chunk=64 * 3), 192),
-                                       (dict(loader=2, layout=3, chunk=128), 128)])
+                                       (dict(loader=2, layout=3, chunk=128), 128),
+                                       (dict(loader=2, layout=4, chunk=128), 128)])
 def test_border_plants(gpu, cfg, chunk):
     # occurrences planted at +-m around every chunk / tile border
     n = 256 * chunk * 6 + 77
@@ -218,3 +222,51 @@ def test_streams_and_concurrency(gpu):
         rc, c = gpu.dfa_find_status(ws, cnt, pos.numel(), stream=s)
         assert rc == gpu.DFA_OK and c == wc
         assert np.array_equal(pos[:c].cpu().numpy(), wp)
+
+
+def _same_code_nonbases(code):
+    """Bytes that are not bases but share a base's 2-bit code (c >> 1) & 3."""
+    return [c for c in range(256) if (c >> 1) & 3 == code and c not in b"ACGTacgt"]
+
+
+@pytest.mark.parametrize("cfg", [None, dict(loader=2, layout=3, chunk=128), dict(loader=2, layout=4, chunk=256),
+                                 dict(loader=2, layout=1, chunk=128)])
+def test_relaxed_walk_decoys(gpu, cfg):
+    # copies of P with one byte swapped for a non-base of the same code: a walk
+    # that reads codes only sees P there, the exact walk must not; placed
+    # across every stage (64 B) and row border, plus true copies beside them
+    chunk = 256 if cfg is None else cfg["chunk"]
+    n = 512 * chunk * 3 + 4099
+    for m in (8, 12, 19, 20, 31, 33, 64):
+        t = synth.genome_text(n, 40 + m, n_gap_mean=0)
+        pat = synth.pattern(m, 900 + m)
+        codes = [(c >> 1) & 3 for c in pat]
+        rnd = synth.uniform_ints(4 * (n // 64), 1 << 30, 70 + m)
+        k = 0
+        step = 64 * ((3 * m + 3 + 63) // 64)       # decoy and true copy never overwrite the next ones
+        for b in range(64, n - 3 * m - 3, step):
+            st = b - int(rnd[k] % (m + 1)) if b >= m + 1 else b
+            k += 1
+            if st < 0 or st + m > n:
+                continue
+            dec = bytearray(pat)
+            j = int(rnd[k] % m); k += 1
+            alts = _same_code_nonbases(codes[j])
+            dec[j] = alts[int(rnd[k] % len(alts))]; k += 1
+            if rnd[k] & 1:
+                dec = bytearray(bytes(dec).lower())
+            k += 1
+            t[st:st + m] = np.frombuffer(bytes(dec), np.uint8)
+            if (b // step) % 5 == 0:
+                t[st + m + 3:st + 2 * m + 3] = np.frombuffer(pat, np.uint8)
+        assert _check(gpu, t, pat, cfg) > 0
+
+
+def test_relaxed_walk_nonbase_runs(gpu):
+    # runs of N read as runs of G by codes alone: a pattern of G's makes the
+    # relaxed walk flag every run, the exact walk counts nothing inside them
+    n = 2_000_003
+    t = synth.genome_text(n, 77, n_gap_mean=3_000, n_run_mean=500)
+    for pat in (b"GGGGGGGG", b"G" * 20, b"G" * 40, b"ACGGGGGGGGGT"):
+        for cfg in (None, dict(loader=2, layout=4, chunk=128), dict(loader=2, layout=3, chunk=1280)):
+            _check(gpu, t, pat, cfg)
