@@ -366,6 +366,45 @@ struct Walker {
         }
     }
 
+    // vec4 for a recording K4 walk of a dense pattern: the accept masks of the
+    // 16 words are gathered into a 64-bit map of end offsets (bit j = end
+    // r + j) without branches, then counted and handed to the sink once.
+    __device__ __forceinline__ void vec4_map(uint4 v0, uint4 v1, uint4 v2, uint4 v3, uint32_t r)
+    {
+        const uint32_t x[16] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w,
+                                v2.x, v2.y, v2.z, v2.w, v3.x, v3.y, v3.z, v3.w};
+        uint32_t bad = 0u;
+#pragma unroll
+        for (int k = 0; k < 16; k++) bad |= word_bad(x[k]);
+        if (bad != 0u) {
+            slow_vec(v0, r, 0);
+            slow_vec(v1, r + 16, 0);
+            slow_vec(v2, r + 32, 0);
+            slow_vec(v3, r + 48, 0);
+            return;
+        }
+        uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            e = k4_next<LAYOUT>(T.k4, e, x[k]);
+            const uint32_t acc = e & (0xFu << K4_ACC_SHIFT);      // bits 8..11
+            const int sh = 4 * (k & 7) - (int)K4_ACC_SHIFT;       // to bits 4k..4k+3 of its half
+            const uint32_t a = sh >= 0 ? acc << (sh & 31) : acc >> ((-sh) & 31);
+            if (k < 8) lo |= a; else hi |= a;
+        }
+        cnt += __popc(lo) + __popc(hi);
+        if (Sink::kRecord) {
+            while (lo) {
+                sink.put(r + (uint32_t)(__ffs(lo) - 1));
+                lo &= lo - 1u;
+            }
+            while (hi) {
+                sink.put(r + 32u + (uint32_t)(__ffs(hi) - 1));
+                hi &= hi - 1u;
+            }
+        }
+    }
+
     __device__ __forceinline__ void vec(uint4 v, uint32_t r, uint32_t lim)
     {
         if (LAYOUT == kLayoutK4S) {
@@ -404,7 +443,7 @@ __device__ uint32_t walk_chunk(const ScanArgs& a, const SmemTab& T, int64_t s, i
     const int64_t len = e - s;
     const uint32_t lim = (uint32_t)len + m - 1;               // end offsets must be < lim
     const uint32_t h16 = (m - 1 + 15) & ~15u;                 // halo rounded to vectors
-    if (a.aligned && len == a.chunk && s + len + h16 <= a.n) {
+    if (a.aligned && len > 0 && ((s | len) & 15) == 0 && s + len + h16 <= a.n) {
         const uint4* p = reinterpret_cast<const uint4*>(a.text + s);
         const int nv = (int)(len >> 4);
         Walker<LAYOUT, false, Sink> w{T, sink, 0u, 0u};
@@ -438,10 +477,13 @@ __device__ uint32_t walk_chunk(const ScanArgs& a, const SmemTab& T, int64_t s, i
     return cnt;
 }
 
+// Where load_tables puts each table of a layout (shared addresses), from
+// the launch arguments alone.
 template <int LAYOUT>
-__device__ __forceinline__ SmemTab load_tables(const ScanArgs& a, uint8_t* smem)
+__device__ __forceinline__ SmemTab tab_view(const ScanArgs& a)
 {
     SmemTab T;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(g_smem);
     T.m = (uint32_t)a.m;
     // a group of four steps accepts only from a state q >= m - 4; every such q
     // has a bit at position >= floor(log2(m - 4)), so the OR of the groups'
@@ -449,54 +491,57 @@ __device__ __forceinline__ SmemTab load_tables(const ScanArgs& a, uint8_t* smem)
     // may accept (for m <= 4 every group may)
     T.sh = a.m > 4 ? 31u - (uint32_t)__clz(a.m - 4) : 0u;
     T.force = a.m <= 4 ? 1u : 0u;
+    T.k4 = 0;
+    T.d1 = 0;
+    T.stt = 0;
     T.k4s = 0;
-    int bytes, src_off;
-    const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem);
-    if (LAYOUT == kLayoutK4S) {
-        // [k4s][d1]: two source ranges
-        T.k4 = 0;
-        T.stt = 0;
+    if (LAYOUT == kLayoutK4S) {            // [k4s][d1]
         T.k4s = base;
         T.d1 = base + (uint32_t)a.k4s_bytes;
-        const uint4* s1 = reinterpret_cast<const uint4*>(a.tab + a.k4_bytes + a.d1_bytes + a.stt_bytes);
-        const uint4* s2 = reinterpret_cast<const uint4*>(a.tab + a.k4_bytes);
-        uint4* d = reinterpret_cast<uint4*>(smem);
-        for (int i = threadIdx.x; i < (a.k4s_bytes >> 4); i += blockDim.x) d[i] = s1[i];
-        d += a.k4s_bytes >> 4;
-        for (int i = threadIdx.x; i < (a.d1_bytes >> 4); i += blockDim.x) d[i] = s2[i];
-        return T;
-    }
-    if (LAYOUT == kLayoutK4F) {
-        // [k4f][k4 at kK4FTabOff][d1]
+    } else if (LAYOUT == kLayoutK4F) {     // [k4f][k4 at kK4FTabOff][d1]
         T.k4 = base + kK4FTabOff;
         T.d1 = base + kK4FTabOff + (uint32_t)a.k4_bytes;
-        T.stt = 0;
-        const uint4* s1 = reinterpret_cast<const uint4*>(a.tab + a.k4_bytes + a.d1_bytes + a.stt_bytes +
-                                                         a.k4s_bytes);
-        const uint4* s2 = reinterpret_cast<const uint4*>(a.tab);
-        uint4* d = reinterpret_cast<uint4*>(smem);
-        for (int i = threadIdx.x; i < (a.k4f_bytes >> 4); i += blockDim.x) d[i] = s1[i];
-        d += kK4FTabOff >> 4;
-        for (int i = threadIdx.x; i < ((a.k4_bytes + a.d1_bytes) >> 4); i += blockDim.x) d[i] = s2[i];
-        return T;
-    }
-    if (LAYOUT == kLayoutK4) {
-        bytes = a.k4_bytes + a.d1_bytes;
-        src_off = 0;
+    } else if (LAYOUT == kLayoutK4) {      // [k4][d1]
         T.k4 = base;
         T.d1 = base + (uint32_t)a.k4_bytes;
-        T.stt = 0;
-    } else {
-        bytes = a.stt_bytes;
-        src_off = a.k4_bytes + a.d1_bytes;
-        T.k4 = 0;
-        T.d1 = 0;
+    } else {                               // [stt]
         T.stt = base;
     }
-    const uint4* src = reinterpret_cast<const uint4*>(a.tab + src_off);
-    uint4* dst = reinterpret_cast<uint4*>(smem);
-    for (int i = threadIdx.x; i < (bytes >> 4); i += blockDim.x) dst[i] = src[i];
     return T;
+}
+
+// Copy the layout's tables from global memory to shared offset 0 (every
+// thread of the CTA takes part; the caller synchronises).
+template <int LAYOUT>
+__device__ __forceinline__ void load_tables(const ScanArgs& a, uint8_t* smem)
+{
+    // (destination offset, source offset, bytes) of up to two ranges
+    int d0 = 0, s0, n0, d1 = 0, s1 = 0, n1 = 0;
+    if (LAYOUT == kLayoutK4S) {
+        s0 = a.k4_bytes + a.d1_bytes + a.stt_bytes;
+        n0 = a.k4s_bytes;
+        d1 = a.k4s_bytes;
+        s1 = a.k4_bytes;
+        n1 = a.d1_bytes;
+    } else if (LAYOUT == kLayoutK4F) {
+        s0 = a.k4_bytes + a.d1_bytes + a.stt_bytes + a.k4s_bytes;
+        n0 = a.k4f_bytes;
+        d1 = (int)kK4FTabOff;
+        s1 = 0;
+        n1 = a.k4_bytes + a.d1_bytes;
+    } else if (LAYOUT == kLayoutK4) {
+        s0 = 0;
+        n0 = a.k4_bytes + a.d1_bytes;
+    } else {
+        s0 = a.k4_bytes + a.d1_bytes;
+        n0 = a.stt_bytes;
+    }
+    const uint4* src0 = reinterpret_cast<const uint4*>(a.tab + s0);
+    uint4* dst0 = reinterpret_cast<uint4*>(smem + d0);
+    for (int i = threadIdx.x; i < (n0 >> 4); i += blockDim.x) dst0[i] = src0[i];
+    const uint4* src1 = reinterpret_cast<const uint4*>(a.tab + s1);
+    uint4* dst1 = reinterpret_cast<uint4*>(smem + d1);
+    for (int i = threadIdx.x; i < (n1 >> 4); i += blockDim.x) dst1[i] = src1[i];
 }
 
 __device__ __forceinline__ int table_smem_bytes_dev(const ScanArgs& a, int layout)
@@ -514,7 +559,8 @@ __global__ void __launch_bounds__(THREADS) k_count(const ScanArgs a)
 {
     uint8_t* smem = g_smem;
     __shared__ unsigned long long s_warp[THREADS / 32];
-    const SmemTab T = load_tables<LAYOUT>(a, smem);
+    load_tables<LAYOUT>(a, smem);
+    const SmemTab T = tab_view<LAYOUT>(a);
     __syncthreads();
     const int64_t tb = (int64_t)THREADS * a.chunk;
     unsigned long long total = 0;
@@ -574,7 +620,8 @@ __global__ void __launch_bounds__(THREADS) k_find(const ScanArgs a)
     __shared__ uint32_t s_warp[THREADS / 32];
     __shared__ int64_t s_tile;
     __shared__ unsigned long long s_off;
-    const SmemTab T = load_tables<LAYOUT>(a, smem);
+    load_tables<LAYOUT>(a, smem);
+    const SmemTab T = tab_view<LAYOUT>(a);
     uint16_t* slots = reinterpret_cast<uint16_t*>(smem + ((table_smem_bytes_dev(a, LAYOUT) + 15) & ~15));
     const unsigned long long base = a.base_in ? *a.base_in : 0ull;
     const int64_t tb = (int64_t)THREADS * a.chunk;
@@ -700,6 +747,10 @@ struct TmaArgs {
     // word (bit 1), or bit 63 of the count for a count without workspace
     unsigned long long* fail_word;
     unsigned long long fail_bit;
+    // count mode, first pass of a two-pass find: every row's count (u16) and
+    // every tile's total (added up) go here; null otherwise
+    uint16_t* rows;
+    unsigned long long* tile_sum;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -887,9 +938,10 @@ __device__ __noinline__ uint32_t replay_halo(SmemTab T, uint32_t slots, uint32_t
 }
 
 template <int LAYOUT, class Sink>
-__device__ __noinline__ uint32_t walk_cold(const ScanArgs a, SmemTab T, int64_t s, int64_t e, Sink* sink)
+__device__ __noinline__ uint32_t walk_cold(const ScanArgs* a, int64_t s, int64_t e, Sink* sink)
 {
-    return walk_chunk<LAYOUT>(a, T, s, e, *sink);
+    const SmemTab T = tab_view<LAYOUT>(*a);
+    return walk_chunk<LAYOUT>(*a, T, s, e, *sink);
 }
 
 // Relaxed walk of layouts 3 and 4 (patterns of kOptMinM and more).  The
@@ -1061,7 +1113,7 @@ __device__ __forceinline__ bool pend_over(uint32_t pr) { return (pr >> 31) != 0u
 
 template <int LAYOUT, bool FIND, bool DENSE>
 __global__ void __launch_bounds__(kTmaThreads, 1)
-    k_scan_tma(const __grid_constant__ CUtensorMap tmap, const TmaArgs p)
+    k_scan_tma(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TmaArgs p)
 {
     uint8_t* smem = g_smem;
     __shared__ __align__(8) uint64_t s_full[kWalkWarps][kMaxStages];
@@ -1086,7 +1138,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     const ScanArgs& a = p.a;
     const int nst = p.nst;
     // [tables][position slots][rings], rings 1024-byte aligned for the TMA swizzle
-    const SmemTab T = load_tables<LAYOUT>(a, smem);
+    load_tables<LAYOUT>(a, smem);
+    const SmemTab T = tab_view<LAYOUT>(a);
     uint16_t* slots = reinterpret_cast<uint16_t*>(smem + p.table_bytes);
     const uint32_t slots_sa = (uint32_t)__cvta_generic_to_shared(slots);
     uint8_t* rings = smem + p.rings_off;
@@ -1238,7 +1291,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 }
             } else if (g0 < a.cap) {
                 GlobalSink gs{a.pos, a.cap, g0, start0};
-                walk_cold<LAYOUT>(a, T, ps, pe, &gs);
+                walk_cold<LAYOUT>(&a, ps, pe, &gs);
             }
         }
         return true;
@@ -1309,7 +1362,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     for (int i = 0; i < kRPL; i++) {
                         if (!ok[i]) continue;
                         Walker<LAYOUT, false, RowSlots<KS>> wd{T, ss[i], e[i], cnt[i]};
-                        wd.vec4(v[i][0], v[i][1], v[i][2], v[i][3], r);
+                        if (LAYOUT == kLayoutK4)
+                            wd.vec4_map(v[i][0], v[i][1], v[i][2], v[i][3], r);
+                        else
+                            wd.vec4(v[i][0], v[i][1], v[i][2], v[i][3], r);
                         e[i] = wd.e;
                         cnt[i] = wd.cnt;
                     }
@@ -1402,10 +1458,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             } else if (!ok[i]) {
                 ss[i].n = 0;
                 if (FIND)
-                    cnt[i] = walk_cold<LAYOUT>(a, T, s0, e0, &ss[i]);
+                    cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &ss[i]);
                 else {
                     CountSink cs;
-                    cnt[i] = walk_cold<LAYOUT>(a, T, s0, e0, &cs);
+                    cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &cs);
                 }
             }
         }
@@ -1415,6 +1471,17 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         if (!FIND) {
 #pragma unroll
             for (int i = 0; i < kRPL; i++) total += cnt[i];
+            if (p.rows) {
+                uint32_t ws = 0;
+#pragma unroll
+                for (int i = 0; i < kRPL; i++) {
+                    p.rows[tile * kRows + wrow0 + 32 * i] = (uint16_t)cnt[i];
+                    ws += cnt[i];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+                if (lane == 0 && ws) atomicAdd(p.tile_sum + tile, (unsigned long long)ws);
+            }
         } else {
             // exclusive offsets of this lane's rows among the warp's rows
             // (row i of every lane, then row i+1 of every lane)
@@ -1482,6 +1549,134 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 #pragma unroll
     for (int d = kDefer - 2; d >= 0; d--)
         if (k >= d + 1 && !flush(pend[d], k - 1 - d)) return;
+}
+
+// ------------------------------------------------ two-pass find, passes 2, 3
+//
+// For the relaxed-walk layouts a find is: the count kernel writing every
+// row's count and every tile's total (pass 1), an exclusive scan of the tile
+// totals (pass 2), and an exact walk of just the rows that hold an accept,
+// each writing its positions at its own offset (pass 3).  Sparse patterns
+// have few such rows, so the find costs little more than the count.
+
+// Pass 2 (one CTA of 1024 threads): tile_sum[t] becomes the global index of
+// tile t's first position (base included); *count becomes base + total.
+__global__ void __launch_bounds__(1024)
+    k_tile_offsets(unsigned long long* tile_sum, int64_t ntiles, const unsigned long long* base_in,
+                   unsigned long long* count)
+{
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = base_in ? *base_in : 0ull;
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < ntiles; t0 += 1024) {
+        const int64_t t = t0 + threadIdx.x;
+        const unsigned long long v = t < ntiles ? tile_sum[t] : 0ull;
+        unsigned long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;                  // inclusive over warps
+        }
+        __syncthreads();
+        const unsigned long long carry = s_carry;
+        const unsigned long long excl = carry + (warp ? s_warp[warp - 1] : 0ull) + x - v;
+        if (t < ntiles) tile_sum[t] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = s_carry;
+}
+
+// Pass 3: a CTA per tile holding accepts; its rows with a non-zero count are
+// listed with their offsets, and each is walked again exactly by one warp:
+// lane l takes the l-th 16-byte-aligned slice of the row plus the m-1 byte
+// overlap (Algorithm 1 within the row), counts, and after a warp scan walks
+// its slice once more writing the positions.
+__device__ __noinline__ void rewalk_row(const ScanArgs* a, int64_t row, unsigned long long first, int lane)
+{
+    const SmemTab T = tab_view<kLayoutK4>(*a);
+    const int64_t C = a->chunk;
+    const int64_t s = row * C;
+    const int64_t e = min(s + C, a->n_own);
+    const int64_t span = ((C + 32 * 16 - 1) / (32 * 16)) * 16;       // 16-byte multiple
+    const int64_t sl = min(s + lane * span, e);
+    const int64_t el = min(sl + span, e);
+    CountSink cs;
+    const uint32_t c = sl < el ? walk_chunk<kLayoutK4>(*a, T, sl, el, cs) : 0u;
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (c) {
+        GlobalSink gs{a->pos, a->cap, (int64_t)(first + x - c), a->pos_base + sl - (int64_t)(a->m - 1)};
+        walk_chunk<kLayoutK4>(*a, T, sl, el, gs);
+    }
+}
+
+__global__ void __launch_bounds__(kRows)
+    k_rewalk(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off)
+{
+    __shared__ uint32_t s_warp[kRows / 32];
+    __shared__ uint32_t s_row[kRows];      // rows of the tile with accepts ...
+    __shared__ uint32_t s_first[kRows];    // ... and their first index within the tile
+    load_tables<kLayoutK4>(a, g_smem);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long end_all = *a.count;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const unsigned long long off = tile_off[tile];
+        const unsigned long long nxt = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
+        if (nxt == off) continue;
+        const uint32_t rc = rows[tile * kRows + threadIdx.x];
+        // warp scans of the counts (offsets) and of the non-zero flags (list slots)
+        uint32_t x = rc, f = rc ? 1u : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t z = __shfl_up_sync(0xffffffffu, f, o);
+            if (lane >= o) {
+                x += y;
+                f += z;
+            }
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; w++) before += s_warp[w];
+        __syncthreads();
+        if (lane == 31) s_warp[warp] = f;
+        __syncthreads();
+        uint32_t fbefore = 0, nz = 0;
+        for (int w = 0; w < kRows / 32; w++) {
+            if (w < warp) fbefore += s_warp[w];
+            nz += s_warp[w];
+        }
+        if (rc) {
+            const uint32_t slot = fbefore + f - 1u;
+            s_row[slot] = threadIdx.x;
+            s_first[slot] = before + x - rc;
+        }
+        __syncthreads();
+        for (uint32_t j = (uint32_t)warp; j < nz; j += kRows / 32)
+            rewalk_row(&a, tile * kRows + s_row[j], off + s_first[j], lane);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -1708,7 +1903,8 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
 
 // Launch the TMA-staged kernel for the filled-in arguments `a`.
 int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
-               const DeviceInfo* di, cudaStream_t st)
+               const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr,
+               unsigned long long* tile_sum = nullptr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
     int rc = tensor_map_encoder(&encode);
@@ -1719,8 +1915,12 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.nrows_full = a.n / C;
     p.sps = (int32_t)(C / kStageW);
     p.table_bytes = (table_smem(t, r.layout) + 127) & ~127;
-    p.fail_word = find ? a.work + 1 : a.count;
-    p.fail_bit = find ? 2ull : (1ull << 63);
+    // a wait that gave up: the find workspace's status word (also for the
+    // count pass of a two-pass find), else bit 63 of the count
+    p.fail_word = find || rows ? a.work + 1 : a.count;
+    p.fail_bit = find || rows ? 2ull : (1ull << 63);
+    p.rows = rows;
+    p.tile_sum = tile_sum;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
@@ -1807,6 +2007,36 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
 
 int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
 
+// Two-pass find: [header][one word per tile][one u16 per row of every tile].
+int64_t work_bytes_two_pass(int64_t ntiles) { return work_bytes_for(ntiles) + ntiles * kRows * 2; }
+
+bool two_pass_layout(const Resolved& r)
+{
+    return r.loader == 2 && (r.layout == kLayoutK4F || r.layout == kLayoutK4S);
+}
+
+// Passes 1-3 of the two-pass find (see k_tile_offsets); the header and tile
+// words of the workspace are already zero.
+int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, int dev, const DeviceInfo* di,
+                    cudaStream_t st)
+{
+    unsigned long long* tile_sum = a.work + kWorkHeader;
+    uint16_t* rows = reinterpret_cast<uint16_t*>(tile_sum + a.ntiles);
+    ScanArgs a1 = a;
+    a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
+    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, tile_sum);
+    if (rc) return rc;
+    k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
+    CUDA_TRY(cudaGetLastError());
+    const int smem = table_smem(t, kLayoutK4);
+    int occ = occupancy((const void*)k_rewalk, kRows, smem, dev, di->smem_optin);
+    if (occ <= 0) return fail("re-walk kernel does not fit on an SM (occupancy 0)");
+    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
+    k_rewalk<<<(unsigned)grid, kRows, smem, st>>>(a, rows, tile_sum);
+    CUDA_TRY(cudaGetLastError());
+    return DFA_OK;
+}
+
 // Shared by dfa_find and the segmented host path.
 int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table* t, int64_t* d_pos,
                 int64_t cap, uint64_t* d_count, const uint64_t* d_base, int64_t pos_base, void* d_work,
@@ -1838,6 +2068,8 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     a.pos_base = pos_base;
     a.base_in = reinterpret_cast<const unsigned long long*>(d_base);
     a.work = static_cast<unsigned long long*>(d_work);
+    if (two_pass_layout(r) && work_bytes >= work_bytes_two_pass(a.ntiles))
+        return launch_two_pass(r, a, t, dev, di, st);
     if (r.loader == 2) return launch_tma(r, a, t, true, dev, di, st);
     KernelFn fn = pick_find(r.layout, r.threads);
     const int smem = ((table_smem(t, r.layout) + 15) & ~15) + kSlots * r.threads * 2;
@@ -1946,7 +2178,24 @@ int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg)
     } else {
         tb = kMinDefaultTile;
     }
-    return work_bytes_for((n + tb - 1) / tb);
+    const int64_t single = work_bytes_for((n + tb - 1) / tb);
+    // room for the two-pass find of the TMA kernel as well: its tiles are
+    // kRows rows of the chunk resolve picks on the current device
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        const DeviceInfo* di = device_info(dev);
+        if (di) sms = di->sms;
+    }
+    if (sms <= 0) {
+        (void)cudaGetLastError();
+        sms = 152;
+    }
+    Resolved r;
+    if (resolve(cfg, n, n, true, sms, kOptMinM, &r) == DFA_OK && r.loader == 2) {
+        const int64_t tile_bytes = (int64_t)kRows * r.chunk;
+        return std::max(single, work_bytes_two_pass((n + tile_bytes - 1) / tile_bytes));
+    }
+    return single;
 }
 
 int dfa_find(const uint8_t* d_text, int64_t n, const dfa_table* table, int64_t* d_pos, int64_t cap,

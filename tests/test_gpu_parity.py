@@ -270,3 +270,31 @@ def test_relaxed_walk_nonbase_runs(gpu):
     for pat in (b"GGGGGGGG", b"G" * 20, b"G" * 40, b"ACGGGGGGGGGT"):
         for cfg in (None, dict(loader=2, layout=4, chunk=128), dict(loader=2, layout=3, chunk=1280)):
             _check(gpu, t, pat, cfg)
+
+
+@pytest.mark.parametrize("layout", [3, 4])
+def test_single_pass_find_with_small_workspace(gpu, layout):
+    # a workspace with room for the tile words only (no per-row counts) takes
+    # the single-pass find; both forms must give the same exact result
+    import torch
+    n = 3_000_017
+    t = synth.genome_text(n, 31)
+    td = _dev(gpu, t)
+    cfg = dict(loader=2, layout=layout, chunk=128)
+    ntiles = -(-n // (512 * 128))
+    for m in (8, 13, 24, 31):
+        pat = synth.pattern(m, 300 + m)
+        pos_idx = synth.uniform_ints(300, n - m, 5 + m)
+        synth.plant(t, pat, np.unique(pos_idx // m * m))
+        td = _dev(gpu, t)
+        want_c, want_p = oracle.find_brute(t, pat)
+        tab = gpu.dfa_build(pat)
+        for ws_bytes in (8 * (2 + ntiles), gpu.dfa_find_workspace_bytes(n, cfg)):
+            cap = want_c + 5
+            pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+            gpu.dfa_find(td, tab, pos, cnt, ws, cfg=cfg)
+            rc, c = gpu.dfa_find_status(ws, cnt, cap)
+            assert rc == gpu.DFA_OK and c == want_c, (m, ws_bytes, c, want_c)
+            assert np.array_equal(pos[:c].cpu().numpy(), want_p)
