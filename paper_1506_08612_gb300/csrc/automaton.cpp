@@ -62,18 +62,16 @@ int build_host_tables(dfa_table* t)
 
     // four-step states with an accept flag, for the relaxed walk: the row of
     // an entry is the entry itself, so flagged rows repeat the plain ones
+    const int F = k4f_flag(m);
     std::vector<uint8_t>& k4f = t->k4f;
-    k4f.clear();
-    if (m <= K4F_MAX_M) {
-        k4f.assign((size_t)K4F_ROWS * 256, 0);
-        for (int q = 0; q < S; q++)
-            for (int code4 = 0; code4 < 256; code4++) {
-                uint16_t v = k4[(size_t)q * 256 + code4];
-                uint8_t f = (uint8_t)((v & 0xFFu) | (((v >> K4_ACC_SHIFT) & 0xFu) ? K4F_FLAG : 0u));
-                k4f[(size_t)q * 256 + code4] = f;
-                k4f[(size_t)(q | K4F_FLAG) * 256 + code4] = f;
-            }
-    }
+    k4f.assign((size_t)(F + S) * 256, 0);
+    for (int q = 0; q < S; q++)
+        for (int code4 = 0; code4 < 256; code4++) {
+            uint16_t v = k4[(size_t)q * 256 + code4];
+            uint8_t f = (uint8_t)((v & 0xFFu) + (((v >> K4_ACC_SHIFT) & 0xFu) ? F : 0));
+            k4f[(size_t)q * 256 + code4] = f;
+            k4f[(size_t)(q | F) * 256 + code4] = f;
+        }
 
     // the paper's sparse ASCII STT: columns are raw byte values; only the
     // eight base columns hold transitions, every other column holds q0

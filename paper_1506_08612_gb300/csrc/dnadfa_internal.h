@@ -30,18 +30,21 @@ inline bool code_valid(uint32_t c)
 constexpr uint32_t K4_ACC_SHIFT = 8;
 constexpr uint32_t K4_CNT_SHIFT = 12;
 
-// Four-step table with accept flags (u8, patterns with m <= K4F_MAX_M): row q
-// (and its copy, row q | K4F_FLAG) holds, per code4, the state after the
-// four steps with K4F_FLAG set if one of the four steps reached state m.
+// Four-step table with accept flags (u8): with F the smallest power of two
+// above m, row q (and its copy, row q | F) holds, per code4, the state after
+// the four steps with F added if one of the four steps reached state m.
 // Rows are indexed by the previous entry as is, flag included, so the walk
-// needs no masking; K4F_ROWS rows in all.
-constexpr uint32_t K4F_FLAG = 0x20;
-constexpr int K4F_MAX_M = 31;
-constexpr int K4F_ROWS = 64;
+// needs no masking; rows 0..m and F..F+m are used, F+m+1 rows in all.
+inline int k4f_flag(int m)
+{
+    int f = 1;
+    while (f <= m) f <<= 1;
+    return f;
+}
 
 // Device copy layout, one allocation, every part 16-byte aligned:
 //   [k4: (m+1)*256 u16][d1: (m+1)*4 u8, padded to 16][stt: (m+1)*256 u8]
-//   [k4s: (m+1)*256 u8][k4f: K4F_ROWS*256 u8, only when m <= K4F_MAX_M]
+//   [k4s: (m+1)*256 u8][k4f: (k4f_flag(m)+m+1)*256 u8]
 // k4s is the four-step table holding only the state after the four steps.
 struct DeviceTableView {
     const uint8_t* base;   // start of the allocation
@@ -50,7 +53,7 @@ struct DeviceTableView {
     int32_t d1_bytes;      // (m+1)*4 rounded up to 16
     int32_t stt_bytes;     // (m+1)*256
     int32_t k4s_bytes;     // (m+1)*256
-    int32_t k4f_bytes;     // K4F_ROWS*256, or 0 when m > K4F_MAX_M
+    int32_t k4f_bytes;     // (k4f_flag(m)+m+1)*256
 };
 
 }  // namespace dnadfa
@@ -62,7 +65,7 @@ struct dfa_table {
     std::vector<uint16_t> k4;            // (m+1)*256
     std::vector<uint8_t> stt;            // (m+1)*256, the paper's sparse ASCII STT
     std::vector<uint8_t> k4s;            // (m+1)*256, state after four steps only
-    std::vector<uint8_t> k4f;            // K4F_ROWS*256 (m <= K4F_MAX_M), states + accept flag
+    std::vector<uint8_t> k4f;            // (k4f_flag(m)+m+1)*256, states + accept flag
     int device;
     void* d_mem;
     size_t d_bytes;

@@ -38,13 +38,9 @@ namespace {
 
 constexpr int kLayoutK4 = 1;
 constexpr int kLayoutStt = 2;
-constexpr int kLayoutK4S = 3;     // four-step table of states only (u8), m >= kK4SMinM
-constexpr int kLayoutK4F = 4;     // four-step states with accept flag (u8), kOptMinM <= m < kK4SMinM
-constexpr int kK4SMinM = 20;
-constexpr int kOptMinM = 8;       // default: layouts 3 and 4 (relaxed walk + exact replay) from here on
-// layout 4 keeps its flagged table at shared offset 0 and the u16 four-step
-// table of the exact replays at this fixed offset
-constexpr uint32_t kK4FTabOff = (uint32_t)K4F_ROWS * 256u;
+constexpr int kLayoutK4S = 3;     // four-step table of states only (u8)
+constexpr int kLayoutK4F = 4;     // four-step states with accept flag (u8), m >= kOptMinM
+constexpr int kOptMinM = 8;       // default: layout 4 (relaxed walk + exact replay) from here on
 constexpr int kSlots = 16;                  // staged positions per thread per tile
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
@@ -79,6 +75,7 @@ struct SmemTab {
     uint32_t m;
     uint32_t sh;    // k4s: a group of four steps can accept only from a state with (q >> sh) != 0
     uint32_t force; // k4s: 1 when m <= 4 (any state, even q0, may accept within four steps)
+    uint32_t fl;    // k4f: the accept flag (smallest power of two above m)
 };
 
 // Dynamic shared memory of every kernel here.  Each kernel puts its layout's
@@ -138,13 +135,19 @@ __device__ __forceinline__ uint32_t word_bad(uint32_t x)
 // (x & 0x06060606) holds the 2-bit codes at bits 8k+1; the multiply gathers
 // them, first byte lowest, into bits 24..31 without carries; byte_perm forms
 // the table index (state << 8) | code4.
-// The u16 table sits at shared offset 0, or at kK4FTabOff in layout 4.
+// The u16 table sits at shared offset 0, or at shared address k4 in layout 4
+// (behind its flagged table, used there by the exact replays only).
 template <int LAYOUT = kLayoutK4>
-__device__ __forceinline__ uint32_t k4_next(uint32_t /*fixed offset*/, uint32_t e, uint32_t x)
+__device__ __forceinline__ uint32_t k4_next(uint32_t k4, uint32_t e, uint32_t x)
 {
     uint32_t code = (x & 0x06060606u) * 0x00820820u;
     uint32_t idx = __byte_perm(code, e, 0x7743u);
-    return tab16(LAYOUT == kLayoutK4F ? idx + kK4FTabOff / 2u : idx);
+    if (LAYOUT == kLayoutK4F) {
+        uint32_t v;
+        asm("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(k4 + idx * 2u));
+        return v;
+    }
+    return tab16(idx);
 }
 
 // One automaton step on one raw byte (any byte value).
@@ -491,6 +494,7 @@ __device__ __forceinline__ SmemTab tab_view(const ScanArgs& a)
     // may accept (for m <= 4 every group may)
     T.sh = a.m > 4 ? 31u - (uint32_t)__clz(a.m - 4) : 0u;
     T.force = a.m <= 4 ? 1u : 0u;
+    T.fl = (uint32_t)(a.k4f_bytes >> 8) - (uint32_t)a.m - 1u;
     T.k4 = 0;
     T.d1 = 0;
     T.stt = 0;
@@ -498,9 +502,9 @@ __device__ __forceinline__ SmemTab tab_view(const ScanArgs& a)
     if (LAYOUT == kLayoutK4S) {            // [k4s][d1]
         T.k4s = base;
         T.d1 = base + (uint32_t)a.k4s_bytes;
-    } else if (LAYOUT == kLayoutK4F) {     // [k4f][k4 at kK4FTabOff][d1]
-        T.k4 = base + kK4FTabOff;
-        T.d1 = base + kK4FTabOff + (uint32_t)a.k4_bytes;
+    } else if (LAYOUT == kLayoutK4F) {     // [k4f][k4][d1]
+        T.k4 = base + (uint32_t)a.k4f_bytes;
+        T.d1 = T.k4 + (uint32_t)a.k4_bytes;
     } else if (LAYOUT == kLayoutK4) {      // [k4][d1]
         T.k4 = base;
         T.d1 = base + (uint32_t)a.k4_bytes;
@@ -526,7 +530,7 @@ __device__ __forceinline__ void load_tables(const ScanArgs& a, uint8_t* smem)
     } else if (LAYOUT == kLayoutK4F) {
         s0 = a.k4_bytes + a.d1_bytes + a.stt_bytes + a.k4s_bytes;
         n0 = a.k4f_bytes;
-        d1 = (int)kK4FTabOff;
+        d1 = a.k4f_bytes;
         s1 = 0;
         n1 = a.k4_bytes + a.d1_bytes;
     } else if (LAYOUT == kLayoutK4) {
@@ -548,7 +552,7 @@ __device__ __forceinline__ int table_smem_bytes_dev(const ScanArgs& a, int layou
 {
     return layout == kLayoutK4    ? a.k4_bytes + a.d1_bytes
            : layout == kLayoutK4S ? a.k4s_bytes + a.d1_bytes
-           : layout == kLayoutK4F ? (int)kK4FTabOff + a.k4_bytes + a.d1_bytes
+           : layout == kLayoutK4F ? a.k4f_bytes + a.k4_bytes + a.d1_bytes
                                   : a.stt_bytes;
 }
 
@@ -957,90 +961,76 @@ __device__ __noinline__ uint32_t walk_cold(const ScanArgs* a, int64_t s, int64_t
 //   layout 3: states only; a group of four steps can accept only from a
 //             state q >= m - 4, i.e. with (q >> T.sh) != 0 (force for m <= 4).
 // Returns non-zero when the words may hold an accept.
+// tmask: layout 4: the flag; layout 3: the bits of the states >= 2^sh (all
+// bits, with orq forced non-zero, when m <= 4).
 template <int LAYOUT, int N>
-__device__ __forceinline__ uint32_t relaxed_words(const SmemTab& T, uint32_t& e, const uint32_t (&x)[N])
+__device__ __forceinline__ uint32_t relaxed_words(uint32_t tmask, uint32_t& e, const uint32_t (&x)[N])
 {
-    uint32_t orq = LAYOUT == kLayoutK4S ? e : 0u;
+    uint32_t orq = LAYOUT == kLayoutK4S ? (e | (tmask == ~0u ? 1u : 0u)) : 0u;
 #pragma unroll
     for (int k = 0; k < N; k++) {
         const uint32_t code = (x[k] & 0x06060606u) * 0x00820820u;
         e = tab8(__byte_perm(code, e, 0x7743u));
         if (LAYOUT == kLayoutK4F || k + 1 < N) orq |= e;
     }
-    return LAYOUT == kLayoutK4F ? (orq & K4F_FLAG) : ((orq >> T.sh) | T.force);
+    return orq & tmask;
 }
 
-// Shared-memory table view of layouts 3 and 4 (as load_tables lays them
-// out), rebuilt from m alone.
 template <int LAYOUT>
-__device__ __forceinline__ SmemTab opt_tab(uint32_t m)
+__device__ __forceinline__ uint32_t relaxed_mask(uint32_t m)
 {
-    SmemTab T;
-    const uint32_t base = (uint32_t)__cvta_generic_to_shared(g_smem);
-    T.m = m;
-    T.sh = m > 4 ? 31u - (uint32_t)__clz(m - 4) : 0u;
-    T.force = m <= 4 ? 1u : 0u;
-    T.stt = 0;
-    if (LAYOUT == kLayoutK4F) {
-        T.k4 = base + kK4FTabOff;
-        T.k4s = 0;
-        T.d1 = base + kK4FTabOff + (m + 1) * 512u;
-    } else {
-        T.k4 = 0;
-        T.k4s = base;
-        T.d1 = base + (m + 1) * 256u;
-    }
-    return T;
+    if (LAYOUT == kLayoutK4F) return 1u << (32 - __clz(m));
+    if (m <= 4) return ~0u;
+    return ~((1u << (31u - (uint32_t)__clz(m - 4))) - 1u);
 }
 
-__device__ __forceinline__ uint4 lds128_at(uint32_t addr)
+// Exact walk, at the end of a tile, of the stages of one row (starting at
+// text offset rs) that its relaxed walk flagged: bit s of mask for body
+// stage s (64 bytes at rs + 64 s), bit sps for the overlap stage (ends
+// limited to C + m - 1).  The exact state at a stage start depends on at
+// most the m <= 64 bytes before it (Algorithm 1's overlap argument), so each
+// stage is walked from q0 at the previous 64 bytes of the row (from the row
+// start for stage 0).  Every byte is read again from global memory, where
+// the tile was just streamed from.  With REC the accepts go to the row's
+// slots (base, n), in ascending order.  Returns (count, n).
+template <int LAYOUT, bool REC>
+__device__ __noinline__ uint2 replay_row(const ScanArgs* a, int64_t rs, uint32_t sps, uint64_t mask,
+                                         uint32_t slot_base, uint32_t slot_n)
 {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "r"(addr));
-    return v;
-}
-
-// Exact walk of one stage of a row (64 bytes at row offset r, or the
-// overlap stage with ends limited to lim) after a relaxed walk flagged it.
-// The exact state at the stage start depends on at most the m <= 64 bytes
-// before it (Algorithm 1's overlap argument), so the walk starts from q0 on
-// the previous 64 bytes of the row, read again from global memory at g, or
-// at the row start (g == nullptr).  The stage itself is read from its ring
-// slot (shared address rp, the lane's swizzled offset ob).  With REC the
-// accepts go to the row's slots (base, n).  Returns (count, n).
-template <int LAYOUT, bool LIM, bool REC>
-__device__ __noinline__ uint2 replay_exact(uint32_t m, const uint4* g, uint32_t rp, uint32_t ob, uint32_t r,
-                                           uint32_t lim, uint32_t slot_base, uint32_t slot_n)
-{
-    const SmemTab T = opt_tab<LAYOUT>(m);
-    uint32_t e0 = 0u;
-    if (g) {
-        CountSink cs;
-        Walker<LAYOUT, false, CountSink> w{T, cs, 0u, 0u};
-        w.vec4(ldg16(g), ldg16(g + 1), ldg16(g + 2), ldg16(g + 3), 0u);
-        e0 = w.e;
-    }
+    const SmemTab T = tab_view<LAYOUT>(*a);
+    const uint32_t m = (uint32_t)a->m;
+    const uint32_t C = sps * kStageW;
     using Sink = typename std::conditional<REC, RowSlots<kTSlots>, CountSink>::type;
     Sink sink{};
     if (REC) {
         reinterpret_cast<RowSlots<kTSlots>*>(&sink)->base = slot_base;
         reinterpret_cast<RowSlots<kTSlots>*>(&sink)->n = slot_n;
     }
-    uint32_t cnt;
-    if (!LIM) {
-        Walker<LAYOUT, false, Sink> w{T, sink, e0, 0u};
-        w.vec4(lds128_at(rp + ob), lds128_at(rp + (ob ^ 16u)), lds128_at(rp + (ob ^ 32u)),
-               lds128_at(rp + (ob ^ 48u)), r);
-        cnt = w.cnt;
-    } else {
-        Walker<LAYOUT, true, Sink> h{T, sink, e0, 0u};
-        h.vec(lds128_at(rp + ob), r, lim);
-        if (m > 17) h.vec(lds128_at(rp + (ob ^ 16u)), r + 16, lim);
-        if (m > 33) h.vec(lds128_at(rp + (ob ^ 32u)), r + 32, lim);
-        if (m > 49) h.vec(lds128_at(rp + (ob ^ 48u)), r + 48, lim);
-        cnt = h.cnt;
+    uint32_t cnt = 0;
+    while (mask) {
+        const uint32_t s = (uint32_t)__ffsll((long long)mask) - 1u;
+        mask &= mask - 1ull;
+        const uint4* g = reinterpret_cast<const uint4*>(a->text + rs + (int64_t)s * kStageW);
+        uint32_t e0 = 0u;
+        if (s) {
+            CountSink cs;
+            Walker<LAYOUT, false, CountSink> w{T, cs, 0u, 0u};
+            w.vec4(ldg16(g - 4), ldg16(g - 3), ldg16(g - 2), ldg16(g - 1), 0u);
+            e0 = w.e;
+        }
+        if (s < sps) {
+            Walker<LAYOUT, false, Sink> w{T, sink, e0, 0u};
+            w.vec4(ldg16(g), ldg16(g + 1), ldg16(g + 2), ldg16(g + 3), s * kStageW);
+            cnt += w.cnt;
+        } else {
+            const uint32_t lim = C + m - 1;
+            Walker<LAYOUT, true, Sink> h{T, sink, e0, 0u};
+            h.vec(ldg16(g), C, lim);
+            if (m > 17) h.vec(ldg16(g + 1), C + 16, lim);
+            if (m > 33) h.vec(ldg16(g + 2), C + 32, lim);
+            if (m > 49) h.vec(ldg16(g + 3), C + 48, lim);
+            cnt += h.cnt;
+        }
     }
     return make_uint2(cnt, REC ? reinterpret_cast<RowSlots<kTSlots>*>(&sink)->n : 0u);
 }
@@ -1216,7 +1206,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
 
     // ---------------------------------------------------------- walkers
-    const uint32_t m = T.m;
+    const uint32_t m = (uint32_t)a.m;
     uint8_t* ring = rings + (size_t)warp * nst * kWarpStage;
     uint64_t* full = s_full[warp];
     // row i of this lane is box row 32i + lane; its 16-byte piece j sits at
@@ -1225,16 +1215,18 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     const uint32_t wrow0 = (uint32_t)warp * kWarpRows + lane;    // row 0 of this lane in the tile
     bool aborted = false;
 
-    auto tile_id = [&](int64_t kk, int64_t* out) -> bool {
-        const int slot = (int)((uint64_t)kk % kTicketRing);
-        if (!warp_wait(&s_tready[slot], (uint32_t)((uint64_t)kk / kTicketRing) & 1u, abort_flag, p)) return false;
-        *out = s_tiles[slot];
+    // tile ids and per-CTA tile counts fit 32 bits (a tile is at least 64 KiB)
+    auto tile_id = [&](uint32_t kk, int32_t* out) -> bool {
+        const uint32_t slot = kk % kTicketRing;
+        if (!warp_wait(&s_tready[slot], (kk / kTicketRing) & 1u, abort_flag, p)) return false;
+        *out = (int32_t)s_tiles[slot];
         return true;
     };
     // refill cursor: the next stage of this warp's rows to load, kept as
     // (tile index, stage within the tile, ring slot) without divisions; the
     // warp's lane 0 loads a slot again as soon as the warp has read it
-    int64_t i_k = 0, i_tile = 0;
+    uint32_t i_k = 0;
+    int32_t i_tile = 0;
     uint32_t i_s = 0, i_slot = 0, n_issued = 0, n_consumed = 0;
     bool i_done = false;
     auto issue_next = [&]() -> bool {
@@ -1249,7 +1241,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         if (lane == 0) {
             mbar_arrive_expect_tx(&full[i_slot], kWarpStage);
             const int32_t x = i_s < sps ? (int32_t)(i_s * kStageW) : 0;
-            const int32_t y = (int32_t)(i_tile * kRows + warp * kWarpRows) + (i_s < sps ? 0 : 1);
+            const int32_t y = i_tile * kRows + warp * kWarpRows + (i_s < sps ? 0 : 1);
             tma_load_2d(ring + (size_t)i_slot * kWarpStage, &tmap, x, y, &full[i_slot]);
         }
         n_issued++;
@@ -1298,27 +1290,29 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     };
 
     uint32_t c_slot = 0, c_par = 0;               // consume cursor
-    int64_t k = 0;
+    uint32_t k = 0;
     while (!aborted) {
-        const int tslot = (int)((uint64_t)k % kTicketRing);
-        int64_t tile;
+        const int tslot = (int)(k % kTicketRing);
+        int32_t tile;
         if (!tile_id(k, &tile)) {
             aborted = true;
             break;
         }
         if (tile < 0) break;
-        const int kb = (int)((uint64_t)k % kDefer);
+        const int kb = (int)(k % kDefer);
         bool ok[kRPL];
         uint32_t e[kRPL], cnt[kRPL];
+        uint64_t fmask[kRPL];                     // relaxed walks: stages to replay exactly
         RowSlots<KS> ss[kRPL];
 #pragma unroll
         for (int i = 0; i < kRPL; i++) {
             // a full row whose successor row is complete too (its halo is the
             // next row's first bytes); every other row is walked cold below
-            const int64_t row = tile * kRows + wrow0 + 32 * i;
+            const int64_t row = (int64_t)tile * kRows + wrow0 + 32 * i;
             ok[i] = (row + 1) * C <= a.n_own && row + 1 < p.nrows_full;
             e[i] = 0;
             cnt[i] = 0;
+            fmask[i] = 0;
             ss[i] = RowSlots<KS>{slots_sa + (uint32_t)(((uint32_t)kb * KS * kRows + wrow0 + 32 * i) * 2), 0u};
         }
         for (uint32_t s = 0; s < spt; s++) {
@@ -1345,17 +1339,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                                                 v[i][1].x, v[i][1].y, v[i][1].z, v[i][1].w,
                                                 v[i][2].x, v[i][2].y, v[i][2].z, v[i][2].w,
                                                 v[i][3].x, v[i][3].y, v[i][3].z, v[i][3].w};
-                        const uint32_t flag = relaxed_words<LAYOUT, 16>(T, e[i], x);
-                        if (flag != 0u && ok[i]) {
-                            const uint4* g =
-                                s ? reinterpret_cast<const uint4*>(a.text + (tile * kRows + wrow0 + 32 * i) * C + r -
-                                                                   kStageW)
-                                  : nullptr;
-                            const uint2 rc = replay_exact<LAYOUT, false, FIND>(
-                                m, g, smem_u32(rp + i * 32 * kStageW), ob, r, 0u, ss[i].base, ss[i].n);
-                            cnt[i] += rc.x;
-                            if (FIND) ss[i].n = rc.y;
-                        }
+                        const uint32_t flag = relaxed_words<LAYOUT, 16>(relaxed_mask<LAYOUT>(m), e[i], x);
+                        fmask[i] |= (uint64_t)(flag != 0u) << s;
                     }
                 } else if (FIND && INLINE_REC) {
 #pragma unroll
@@ -1399,23 +1384,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     const uint4 h0 = *reinterpret_cast<const uint4*>(q + ob);
                     if (OPT) {
                         const uint32_t x0[4] = {h0.x, h0.y, h0.z, h0.w};
-                        uint32_t flag = relaxed_words<LAYOUT, 4>(T, e[i], x0);
+                        uint32_t flag = relaxed_words<LAYOUT, 4>(relaxed_mask<LAYOUT>(m), e[i], x0);
 #pragma unroll
                         for (uint32_t j = 1; j < 4; j++) {
                             if (m > 16 * j + 1) {
                                 const uint4 hj = *reinterpret_cast<const uint4*>(q + (ob ^ (j << 4)));
                                 const uint32_t xj[4] = {hj.x, hj.y, hj.z, hj.w};
-                                flag |= relaxed_words<LAYOUT, 4>(T, e[i], xj);
+                                flag |= relaxed_words<LAYOUT, 4>(relaxed_mask<LAYOUT>(m), e[i], xj);
                             }
                         }
-                        if (flag != 0u) {
-                            const uint4* g = reinterpret_cast<const uint4*>(
-                                a.text + (tile * kRows + wrow0 + 32 * i) * C + C - kStageW);
-                            const uint2 rc = replay_exact<LAYOUT, true, FIND>(m, g, smem_u32(q), ob, (uint32_t)C, lim,
-                                                                            ss[i].base, ss[i].n);
-                            cnt[i] += rc.x;
-                            if (FIND) ss[i].n = rc.y;
-                        }
+                        fmask[i] |= (uint64_t)(flag != 0u) << s;
                     } else if (FIND && INLINE_REC) {
                         Walker<LAYOUT, true, RowSlots<KS>> h{T, ss[i], e[i], cnt[i]};
                         h.vec(h0, (uint32_t)C, lim);
@@ -1451,7 +1429,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         if (aborted) break;
 #pragma unroll
         for (int i = 0; i < kRPL; i++) {
-            const int64_t s0 = (tile * kRows + wrow0 + 32 * i) * C;
+            const int64_t s0 = ((int64_t)tile * kRows + wrow0 + 32 * i) * C;
             const int64_t e0 = min(s0 + C, a.n_own);
             if (s0 >= a.n_own) {
                 cnt[i] = 0;
@@ -1463,6 +1441,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     CountSink cs;
                     cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &cs);
                 }
+            } else if (OPT && fmask[i] != 0ull) {
+                const uint2 rc = replay_row<LAYOUT, FIND>(&a, s0, sps, fmask[i], ss[i].base, ss[i].n);
+                cnt[i] += rc.x;
+                if (FIND) ss[i].n = rc.y;
             }
         }
         __syncwarp();
@@ -1475,7 +1457,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 uint32_t ws = 0;
 #pragma unroll
                 for (int i = 0; i < kRPL; i++) {
-                    p.rows[tile * kRows + wrow0 + 32 * i] = (uint16_t)cnt[i];
+                    p.rows[(int64_t)tile * kRows + wrow0 + 32 * i] = (uint16_t)cnt[i];
                     ws += cnt[i];
                 }
 #pragma unroll
@@ -1772,21 +1754,19 @@ int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int
 {
     // default layout (the TMA kernel's): short patterns walk the four-step
     // table exactly; from kOptMinM on the relaxed walk takes the flagged
-    // four-step table, and from kK4SMinM the table of states only
+    // four-step table
     const bool user_layout = cfg && cfg->layout;
     r->layout = user_layout ? cfg->layout
-                            : (m >= kK4SMinM ? kLayoutK4S : m >= kOptMinM ? kLayoutK4F : kLayoutK4);
+                            : (m >= kOptMinM ? kLayoutK4F : kLayoutK4);
     r->ctas_per_sm = cfg ? cfg->ctas_per_sm : 0;
     if (r->layout != kLayoutK4 && r->layout != kLayoutStt && r->layout != kLayoutK4S && r->layout != kLayoutK4F)
         return DFA_EINVAL;
-    // the flagged table has room for states up to K4F_MAX_M only
-    if (r->layout == kLayoutK4F && m > K4F_MAX_M) r->layout = kLayoutK4S;
     if (r->ctas_per_sm < 0 || r->ctas_per_sm > 32) return DFA_EINVAL;
     const int req_loader = cfg ? cfg->loader : 0;
     if (req_loader < 0 || req_loader > 2) return DFA_EINVAL;
     if (sms <= 0) sms = 152;
     const bool tma_chunk = !(cfg && cfg->chunk) ||
-                           (cfg->chunk % kStageW == 0 && cfg->chunk >= 2 * kStageW && cfg->chunk <= kStageW * 64);
+                           (cfg->chunk % kStageW == 0 && cfg->chunk >= 2 * kStageW && cfg->chunk <= kStageW * 63);
     if (req_loader == 2 && !tma_chunk) return DFA_EINVAL;
     if (req_loader == 2 || (req_loader == 0 && tma_chunk)) {
         // TMA-staged tiles of 256 rows x chunk bytes, chunk a multiple of 80
@@ -1858,7 +1838,7 @@ int table_smem(const dfa_table* t, int layout)
 {
     return layout == kLayoutK4    ? t->view.k4_bytes + t->view.d1_bytes
            : layout == kLayoutK4S ? t->view.k4s_bytes + t->view.d1_bytes
-           : layout == kLayoutK4F ? (int)kK4FTabOff + t->view.k4_bytes + t->view.d1_bytes
+           : layout == kLayoutK4F ? t->view.k4f_bytes + t->view.k4_bytes + t->view.d1_bytes
                                   : t->view.stt_bytes;
 }
 
