@@ -1102,7 +1102,10 @@ __device__ __forceinline__ uint32_t pend_excl(uint32_t pr)
 __device__ __forceinline__ bool pend_over(uint32_t pr) { return (pr >> 31) != 0u; }
 
 template <int LAYOUT, bool FIND, bool DENSE>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+// A count has static tiles and no offsets to resolve: its CTA is the 16
+// walker warps alone (128 registers a thread); a find adds the ticket and
+// scheduler warps (96 registers a thread).
+__global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
     k_scan_tma(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TmaArgs p)
 {
     uint8_t* smem = g_smem;
@@ -1154,7 +1157,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     const uint32_t spt = sps + 1;                 // stages per tile, halo included
     const int64_t C = a.chunk;
 
-    if (warp == kProducerWarp) {
+    if (FIND && warp == kProducerWarp) {
         // ------------------------------------------------------ tickets
         if (lane != 0) return;
         const int64_t ahead = FIND ? (int64_t)p.ahead : (int64_t)kTicketRing;
@@ -1176,7 +1179,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         }
     }
 
-    if (warp == kSchedulerWarp) {
+    if (FIND && warp == kSchedulerWarp) {
         // ------------------------------------------------------ scheduler
         if (!FIND) return;
         const unsigned long long base = a.base_in ? *a.base_in : 0ull;
@@ -1217,6 +1220,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 
     // tile ids and per-CTA tile counts fit 32 bits (a tile is at least 64 KiB)
     auto tile_id = [&](uint32_t kk, int32_t* out) -> bool {
+        if (!FIND) {                              // count: static tiles
+            const int64_t t = (int64_t)blockIdx.x + (int64_t)kk * gridDim.x;
+            *out = t < a.ntiles ? (int32_t)t : -1;
+            return true;
+        }
         const uint32_t slot = kk % kTicketRing;
         if (!warp_wait(&s_tready[slot], (kk / kTicketRing) & 1u, abort_flag, p)) return false;
         *out = (int32_t)s_tiles[slot];
@@ -1448,7 +1456,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&s_tfree[tslot]);
+        if (FIND && lane == 0) mbar_arrive(&s_tfree[tslot]);
 
         if (!FIND) {
 #pragma unroll
@@ -1922,10 +1930,11 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.nst = nst;
     p.ahead = std::min(3 + (nst - 1) / (p.sps + 1), kTicketRing);
     const int smem = p.rings_off + kWalkWarps * nst * kWarpStage;
-    int occ = occupancy((const void*)fn, kTmaThreads, smem, dev, di->smem_optin);
+    const int threads = find ? kTmaThreads : kWalkThreads;
+    int occ = occupancy((const void*)fn, threads, smem, dev, di->smem_optin);
     if (occ <= 0) return fail("TMA scan kernel does not fit on an SM (occupancy 0)");
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)di->sms);
-    fn<<<(unsigned)grid, kTmaThreads, smem, st>>>(map, p);
+    fn<<<(unsigned)grid, threads, smem, st>>>(map, p);
     CUDA_TRY(cudaGetLastError());
     return DFA_OK;
 }
