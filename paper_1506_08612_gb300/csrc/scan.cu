@@ -1423,6 +1423,11 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                     }
                 }
             }
+            // The slot is reloaded only after the walk: every lane's walk has
+            // consumed each word it read from the slot, so its shared loads
+            // are complete before the warp syncs and lane 0 starts the TMA
+            // that overwrites them.  (Reloading right after the loads, before
+            // the walk, raced with them in the dense find.)
             __syncwarp();
             n_consumed++;
             if (++c_slot == (uint32_t)nst) {

@@ -298,3 +298,33 @@ def test_single_pass_find_with_small_workspace(gpu, layout):
             rc, c = gpu.dfa_find_status(ws, cnt, cap)
             assert rc == gpu.DFA_OK and c == want_c, (m, ws_bytes, c, want_c)
             assert np.array_equal(pos[:c].cpu().numpy(), want_p)
+
+
+def test_repeated_launches_identical(gpu):
+    # the same find many times on a text larger than L2: every result equal
+    # (a race between a ring slot's reload and its readers would show here)
+    import torch
+    n = 400_000_000
+    t = synth.genome_text(n, 2)
+    td = _dev(gpu, t)
+    for m, seed in ((4, 3), (8, 4), (16, 5)):
+        pat = synth.pattern(m, seed)
+        want_c = oracle.count_brute(t, pat)
+        tab = gpu.dfa_build(pat)
+        cap = want_c + 16
+        pos = torch.empty(cap, dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ws = torch.empty(gpu.dfa_find_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        ref = None
+        for _ in range(12):
+            gpu.dfa_find(td, tab, pos, cnt, ws)
+            rc, c = gpu.dfa_find_status(ws, cnt, cap)
+            assert rc == gpu.DFA_OK and c == want_c, (m, c, want_c)
+            cur = pos[:c].clone()
+            if ref is None:
+                ref = cur
+            else:
+                assert torch.equal(cur, ref), m
+            out = torch.zeros(1, dtype=torch.int64, device="cuda")
+            gpu.dfa_count(td, tab, out)
+            assert int(out.item()) == want_c
