@@ -328,3 +328,29 @@ def test_repeated_launches_identical(gpu):
             out = torch.zeros(1, dtype=torch.int64, device="cuda")
             gpu.dfa_count(td, tab, out)
             assert int(out.item()) == want_c
+
+
+def test_sharded_find_with_library_engine(gpu):
+    # the multi-process decomposition run rank by rank on one GPU (no rank
+    # waits on another): each slice scanned by the library, results merged
+    from paper_1506_08612_gb300 import shard
+    n = 3_000_001
+    t = synth.genome_text(n, 17)
+    td = _dev(gpu, t)
+    for m, pseed in ((4, 1), (9, 2), (40, 3)):
+        pat = synth.pattern(m, pseed)
+        t2 = t.copy()
+        synth.plant(t2, pat, np.arange(0, n - m, 99_991))
+        td = _dev(gpu, t2)
+
+        def engine(sl, n_own):
+            c, p = gpu.find(sl, pat)
+            p = p.cpu().numpy()
+            keep = p < n_own
+            return int(keep.sum()), p[keep]
+
+        want_c, want_p = oracle.find_brute(t2, pat)
+        for world in (2, 3, 7):
+            parts = [shard.local_find(td, m, world, r, engine) for r in range(world)]
+            c, p = shard.merge([x[0] for x in parts], [x[1] for x in parts])
+            assert c == want_c and np.array_equal(p, want_p), (m, world)
