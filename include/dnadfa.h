@@ -214,6 +214,56 @@ int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int6
 int dfa_find_noalloc(const uint8_t* d_text, int64_t n, const dfa_table* table, int64_t* d_pos,
                      int64_t cap, uint64_t* d_count, const dfa_config* cfg, void* stream);
 
+/* ------------------------------------------------------------------
+ * Many patterns at once: the multi-pattern failure-less automaton of
+ * Sec. III-B (one automaton for a set of patterns, failure transitions
+ * folded into the table, one lookup per character) and a batched count
+ * over many sequences in one launch.
+ * ------------------------------------------------------------------ */
+typedef struct dfa_multi dfa_multi;
+
+/*
+ * Build the automaton of npat patterns (patterns[i]: lengths[i] bytes of
+ * ACGTacgt, 1..DFA_MAX_M; case-insensitive; duplicates allowed and counted
+ * separately).  At most 8192 patterns and 16384 automaton states (the trie
+ * of the patterns).  Copies the tables to the current device.
+ * Errors: DFA_EINVAL (bad pattern, too many states: see dfa_last_error),
+ * DFA_ENOMEM, DFA_ECUDA.
+ */
+int dfa_multi_build(const char* const* patterns, const int32_t* lengths, int32_t npat,
+                    dfa_multi** out);
+void dfa_multi_free(dfa_multi* table);
+
+/* Number of automaton states (trie states, root 0, breadth-first order). */
+int32_t dfa_multi_states(const dfa_multi* table);
+
+/*
+ * Host copy of the automaton for checking: h_next[q*4 + a] = delta(q, a)
+ * with a the 2-bit code ((c >> 1) & 3: A 0, C 1, T 2, G 3), h_nout[q] = the
+ * number of patterns that end in state q (own and via failure links).
+ * Either pointer may be NULL.  cap_states >= dfa_multi_states.
+ */
+int dfa_multi_export(const dfa_multi* table, int32_t* h_next, int32_t* h_nout, int64_t cap_states);
+
+/* Shared memory one CTA of dfa_multi_count needs for this automaton. */
+int64_t dfa_multi_smem_bytes(const dfa_multi* table);
+
+/*
+ * Count every occurrence (overlaps included) of every pattern in every
+ * sequence, in one launch.  d_texts: HOST array of nseq (1..64) DEVICE
+ * pointers, lengths: HOST array of their byte counts.  d_counts: device
+ * uint64[nseq * npat], row-major by sequence, overwritten.  Occurrences are
+ * owned by the chunk holding their start (Algorithm 1 with patterns of
+ * several lengths: each chunk reads m_max - 1 bytes past its end).
+ *   cfg: threads (128, 256 or 512 per CTA) and chunk (bytes per thread per
+ *        tile, multiple of 16); other fields ignored; NULL = 256 x 1024.
+ * Asynchronous on `stream`; allocates nothing (capturable in a CUDA graph).
+ * Errors: DFA_EINVAL, DFA_ECUDA.
+ */
+int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32_t nseq,
+                    const dfa_multi* table, uint64_t* d_counts, const dfa_config* cfg,
+                    void* stream);
+
 /* Static text for a return code. */
 const char* dfa_strerror(int code);
 

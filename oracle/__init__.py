@@ -220,3 +220,14 @@ def valid_windows(text, k: int) -> int:
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def multi_count(texts, patterns) -> np.ndarray:
+    """Counts of every pattern (overlaps included) in every text, by the
+    definition (Sec. II-A, one brute-force window compare per pattern):
+    uint64[len(texts), len(patterns)]."""
+    out = np.zeros((len(texts), len(patterns)), dtype=np.uint64)
+    for i, t in enumerate(texts):
+        for j, p in enumerate(patterns):
+            out[i, j] = count_brute(t, p)
+    return out

@@ -11,6 +11,8 @@ device memory and the current CUDA stream.  The names follow the C ABI:
   start positions, single pass
 * ``dfa_find_status(workspace, count, cap)`` — device-side outcome
 * ``dfa_find_host(...)`` — host buffers in, host buffers out (copies inside)
+* ``MultiTable(patterns)`` / ``dfa_multi_count(texts, table, counts)`` — the
+  multi-pattern automaton and one batched count over many sequences
 * ``dfa_find_noalloc(text, table, positions, count)`` — ``dfa_find`` with the
   library's static device workspace, for callers that may not allocate
 
@@ -32,7 +34,8 @@ _lib = _native.lib
 
 __all__ = ["Table", "DfaError", "dfa_build", "dfa_free", "dfa_export_stt", "dfa_count",
            "dfa_find", "dfa_find_workspace_bytes", "dfa_find_status", "dfa_host_stage_bytes",
-           "dfa_find_host", "dfa_find_noalloc", "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
+           "dfa_find_host", "dfa_find_noalloc", "MultiTable", "dfa_multi_count", "multi_count",
+           "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
            "DFA_OK", "DFA_EINVAL", "DFA_ETRUNC", "DFA_ETIMEOUT", "DFA_ECUDA", "DFA_EWORKSPACE",
            "DFA_ENOMEM", "DFA_MAX_M"]
 
@@ -185,6 +188,78 @@ def dfa_find_host(h_text, table: Table, h_positions, stage, seg: int, stream=Non
     if rc not in (DFA_OK, DFA_ETRUNC):
         raise DfaError(rc, "dfa_find_host")
     return rc, int(h.value)
+
+
+# ------------------------------------------------------- many patterns
+
+class MultiTable:
+    """Owns a dfa_multi (multi-pattern automaton); frees it on close/del."""
+
+    def __init__(self, patterns):
+        pats = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
+        self.patterns = pats
+        arr = (ctypes.c_char_p * len(pats))(*pats)
+        lens = (ctypes.c_int32 * len(pats))(*[len(p) for p in pats])
+        h = ctypes.c_void_p()
+        rc = _lib.dfa_multi_build(arr, lens, len(pats), ctypes.byref(h))
+        if rc != DFA_OK:
+            msg = _lib.dfa_last_error().decode(errors="replace")
+            raise DfaError(rc, f"dfa_multi_build [{msg}]")
+        self._h = h
+        self.npat = len(pats)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise ValueError("multi table already freed")
+        return self._h
+
+    def states(self) -> int:
+        return int(_lib.dfa_multi_states(self.handle))
+
+    def export(self):
+        """(next[states, 4] over codes A0 C1 T2 G3, outputs[states])."""
+        ns = self.states()
+        nxt = np.zeros(ns * 4, dtype=np.int32)
+        nout = np.zeros(ns, dtype=np.int32)
+        _check(_lib.dfa_multi_export(self.handle, nxt.ctypes.data_as(ctypes.c_void_p),
+                                     nout.ctypes.data_as(ctypes.c_void_p), ns), "dfa_multi_export")
+        return nxt.reshape(ns, 4), nout
+
+    def smem_bytes(self) -> int:
+        return int(_lib.dfa_multi_smem_bytes(self.handle))
+
+    def free(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.dfa_multi_free(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dfa_multi_count(texts, table: MultiTable, counts, cfg=None, stream=None) -> None:
+    """Enqueue per-(sequence, pattern) counts of every pattern in every text
+    (device uint8 tensors) into ``counts`` (device int64 tensor of
+    len(texts) * npat, row-major by sequence)."""
+    ns = len(texts)
+    ptrs = (ctypes.c_void_p * ns)(*[t.data_ptr() if t.numel() else 0 for t in texts])
+    lens = (ctypes.c_int64 * ns)(*[int(t.numel()) for t in texts])
+    _check(_lib.dfa_multi_count(ptrs, lens, ns, table.handle, _ptr(counts), _cfg(cfg),
+                                _stream(stream)), "dfa_multi_count")
+
+
+def multi_count(texts, patterns, cfg=None) -> np.ndarray:
+    """Synchronous batched count: returns uint64[len(texts), len(patterns)]."""
+    import torch
+    t = patterns if isinstance(patterns, MultiTable) else MultiTable(patterns)
+    dev = texts[0].device
+    out = torch.zeros(len(texts) * t.npat, dtype=torch.int64, device=dev)
+    dfa_multi_count(texts, t, out, cfg=cfg)
+    return out.cpu().numpy().astype(np.uint64).reshape(len(texts), t.npat)
 
 
 # ----------------------------------------------------------- conveniences

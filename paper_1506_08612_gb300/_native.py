@@ -38,6 +38,13 @@ def _declare(lib):
         "dfa_find_host": ([vp, i64, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64), vp, i64, i64, vp],
                           ctypes.c_int),
         "dfa_find_noalloc": ([vp, i64, vp, vp, i64, vp, cfgp, vp], ctypes.c_int),
+        "dfa_multi_build": ([ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32), i32, ctypes.POINTER(vp)],
+                            ctypes.c_int),
+        "dfa_multi_free": ([vp], None),
+        "dfa_multi_states": ([vp], i32),
+        "dfa_multi_export": ([vp, vp, vp, i64], ctypes.c_int),
+        "dfa_multi_smem_bytes": ([vp], i64),
+        "dfa_multi_count": ([ctypes.POINTER(vp), ctypes.POINTER(i64), i32, vp, vp, cfgp, vp], ctypes.c_int),
         "dfa_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "dfa_version": ([], ctypes.c_char_p),
         "dfa_last_error": ([], ctypes.c_char_p),

@@ -75,4 +75,7 @@ struct dfa_table {
 namespace dnadfa {
 // Fill d1, k4, stt, k4s and k4f of t from t->pattern / t->m.  Returns DFA_OK or DFA_EINVAL.
 int build_host_tables(dfa_table* t);
+
+// Record the text of a failure for dfa_last_error (thread-local); returns code.
+int set_last_error(int code, const char* msg);
 }  // namespace dnadfa

@@ -2078,6 +2078,14 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
 
 }  // namespace
 
+namespace dnadfa {
+int set_last_error(int code, const char* msg)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+    return code;
+}
+}  // namespace dnadfa
+
 // ==================================================================== C ABI
 
 extern "C" {

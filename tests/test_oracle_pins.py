@@ -396,3 +396,19 @@ def test_planted_long_patterns_found():
         c, p = oracle.find_brute(t, pat)
         assert set(pos.tolist()) <= set(p.tolist())
         assert c == oracle.dfa_scan(t, oracle.dfa_delta(pat), m)[0]
+
+
+def test_multi_count_equals_census_and_definition():
+    # two separately written oracle routines agree: the per-pattern brute
+    # force over all 4^k k-mers (lexicographic) and the census by codes
+    import itertools
+    t = synth.genome_text(60_000, 4, mask_mean=30, n_gap_mean=3000, n_run_mean=100)
+    k = 4
+    pats = ["".join(s) for s in itertools.product("ACGT", repeat=k)]
+    mc = oracle.multi_count([t], pats)[0]
+    assert np.array_equal(mc, oracle.kmer_census(t, k))
+    assert int(mc.sum()) == oracle.valid_windows(t, k)
+    # empty text, and a text per pattern set with nested patterns
+    assert oracle.multi_count([np.zeros(0, np.uint8)], ["A"]).tolist() == [[0]]
+    aa = np.frombuffer(b"AAAAAA", np.uint8).copy()
+    assert oracle.multi_count([aa], ["A", "AA", "AAAA"]).tolist() == [[6, 5, 3]]
