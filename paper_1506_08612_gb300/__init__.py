@@ -207,6 +207,7 @@ class MultiTable:
             raise DfaError(rc, f"dfa_multi_build [{msg}]")
         self._h = h
         self.npat = len(pats)
+        self.mmax = max(len(p) for p in pats)
 
     @property
     def handle(self) -> ctypes.c_void_p:
@@ -300,3 +301,8 @@ def find(text, pattern, cap: int | None = None, cfg=None):
             cap = c
             continue
         raise DfaError(rc, "dfa_find")
+
+
+from .batched import BatchedCount  # noqa: E402  (needs the names above)
+
+__all__ += ["BatchedCount"]

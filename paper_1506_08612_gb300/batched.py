@@ -1,0 +1,118 @@
+"""Many patterns over many sequences in one persistent, graph-captured launch.
+
+The paper scans one genome per program run.  Here a batch of patterns of
+uneven length over sequences of uneven size is counted in one persistent
+kernel launch per automaton: the patterns become one failure-less
+multi-pattern automaton (Sec. III-B), each CTA takes tiles of (sequence,
+offset) in turn, and every thread walks its chunk plus the m_max - 1 byte
+overlap of Algorithm 1.  The launch is captured once in a CUDA graph and
+replayed, so a repeated batch costs one graph launch on the host.
+
+Pattern sets whose automaton would exceed the kernel's limits (8192 patterns,
+16384 states) are split into groups, one automaton and one launch each,
+all inside the same graph; more than 64 sequences are split the same way.
+The chunk length and threads per CTA come from the autotuner unless given.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import MultiTable, autotune, dfa_multi_count
+
+MAX_SEQ_PER_LAUNCH = 64
+MAX_PAT_PER_TABLE = 8192
+MAX_STATES = 16383
+
+
+def group_patterns(patterns, max_states: int = MAX_STATES, max_pat: int = MAX_PAT_PER_TABLE):
+    """Split pattern indices into consecutive groups whose trie surely fits:
+    the trie of a group has at most 1 + the sum of its pattern lengths
+    states."""
+    groups, cur, states = [], [], 1
+    for i, p in enumerate(patterns):
+        m = len(p)
+        if cur and (states + m > max_states or len(cur) >= max_pat):
+            groups.append(cur)
+            cur, states = [], 1
+        cur.append(i)
+        states += m
+    if cur:
+        groups.append(cur)
+    return groups
+
+
+class BatchedCount:
+    """Counts of every pattern in every sequence (overlaps included).
+
+    texts: device uint8 tensors (kept referenced; their contents may change
+    between runs, their storage may not).  patterns: bytes/str.  cfg:
+    "auto" (autotuner), None (library default) or a dfa_config dict.
+    ``run()`` enqueues the whole batch on ``stream`` (one graph replay when
+    captured); ``result()`` waits and returns uint64[nseq, npat].
+    """
+
+    def __init__(self, texts, patterns, cfg="auto", stream=None, capture: bool = True):
+        import torch
+
+        if not texts:
+            raise ValueError("no sequences")
+        self.texts = list(texts)
+        self.device = self.texts[0].device
+        self.patterns = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
+        if not self.patterns:
+            raise ValueError("no patterns")
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.groups = group_patterns(self.patterns)
+        self.tables = [MultiTable([self.patterns[i] for i in g]) for g in self.groups]
+        self.seq_groups = [list(range(i, min(i + MAX_SEQ_PER_LAUNCH, len(self.texts))))
+                           for i in range(0, len(self.texts), MAX_SEQ_PER_LAUNCH)]
+        self.out = [[torch.zeros(len(sg) * t.npat, dtype=torch.int64, device=self.device)
+                     for t in self.tables] for sg in self.seq_groups]
+        if cfg == "auto":
+            with torch.cuda.stream(self.stream):
+                self.cfgs = [autotune.tune_multi(self.texts, t, stream=self.stream)
+                             for t in self.tables]
+        else:
+            self.cfgs = [cfg] * len(self.tables)
+        self.launches = len(self.tables) * len(self.seq_groups)
+        self.graph = None
+        # first run eagerly: loads the kernel and sets its shared-memory limit
+        # outside any capture
+        self._enqueue()
+        self.stream.synchronize()
+        if capture:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=self.stream):
+                self._enqueue()
+            self.graph = g
+
+    def _enqueue(self):
+        for si, sg in enumerate(self.seq_groups):
+            seqs = [self.texts[i] for i in sg]
+            for ti, t in enumerate(self.tables):
+                dfa_multi_count(seqs, t, self.out[si][ti], cfg=self.cfgs[ti], stream=self.stream)
+
+    def run(self):
+        """Enqueue the batch (asynchronous)."""
+        import torch
+        if self.graph is not None:
+            with torch.cuda.stream(self.stream):
+                self.graph.replay()
+        else:
+            self._enqueue()
+
+    def result(self) -> np.ndarray:
+        """Wait for the last run and return uint64[nseq, npat]."""
+        self.stream.synchronize()
+        res = np.zeros((len(self.texts), len(self.patterns)), dtype=np.uint64)
+        for si, sg in enumerate(self.seq_groups):
+            for ti, g in enumerate(self.groups):
+                block = self.out[si][ti].cpu().numpy().astype(np.uint64).reshape(len(sg), len(g))
+                res[np.ix_(sg, g)] = block
+        return res
+
+    def close(self):
+        self.graph = None
+        for t in self.tables:
+            t.free()
+        self.tables = []

@@ -1,0 +1,94 @@
+"""Parity at the workloads' full sizes, in the launch configurations the
+benchmark times (library defaults for one pattern, the autotuned batched
+launch for many).
+
+* Genome-scale single pattern: the 3.2e9-byte genome-like text (seed 2) and
+  the five patterns m = 4, 8, 16, 32, 64 (seeds 3..7): counts and every
+  position against the oracle's window compare, which finishes in seconds
+  per pattern at this size.
+* Batched: the six sequences (0.2 .. 3.2 GB, seeds 10..15) x 256 patterns of
+  length uniform in [4, 64] (seed 16) in one graph-captured launch; one
+  (sequence, pattern) pair per sequence, plus every pattern on the smallest
+  sequence, checked one by one against the oracle.
+* 6-mer census: 1e9 bytes (seed 20), all 4096 6-mers in one batched launch,
+  against the oracle's census and the invariant sum = valid windows.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GENOME_N = 3_200_000_000
+BATCH_SIZES = (200_000_000, 1_000_000_000, 2_400_000_000, 2_400_000_000, 2_700_000_000,
+               3_200_000_000)
+
+
+@pytest.fixture(autouse=True)
+def _tune_cache(tmp_path, monkeypatch):
+    from paper_1506_08612_gb300 import autotune
+    monkeypatch.setenv("DNADFA_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.delenv("DNADFA_CONFIG", raising=False)
+    autotune.reset_memory_cache()
+    yield
+    autotune.reset_memory_cache()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(a).cuda()
+
+
+def test_genome_scale_single_pattern_all_positions(gpu):
+    import torch
+    text = synth.genome_text(GENOME_N, 2)
+    td = _dev(text)
+    for m, seed in zip((4, 8, 16, 32, 64), (3, 4, 5, 6, 7)):
+        pat = synth.pattern(m, seed)
+        want_c, want_p = oracle.find_brute(text, pat)
+        c, pos = gpu.find(td, pat)
+        assert c == want_c, (m, c, want_c)
+        assert np.array_equal(pos.cpu().numpy(), want_p), m
+        del pos
+    del td
+    torch.cuda.empty_cache()
+
+
+def test_batched_six_sequences_sampled(gpu):
+    import torch
+    lens = synth.uniform_ints(256, 61, 16) + 4
+    pats = [synth.pattern(int(m), 16 * 100_000 + i) for i, m in enumerate(lens)]
+    texts, devs = [], []
+    for i, n in enumerate(BATCH_SIZES):
+        t = synth.genome_text(n, 10 + i)
+        texts.append(t)
+        devs.append(_dev(t))
+    b = gpu.BatchedCount(devs, pats, cfg="auto")
+    b.run()
+    got = b.result()
+    # the smallest sequence: every pattern
+    want0 = np.array([oracle.count_brute(texts[0], p) for p in pats], dtype=np.uint64)
+    assert np.array_equal(got[0], want0)
+    # one pair per sequence, the shortest patterns first (non-zero counts)
+    order = np.argsort(lens, kind="stable")
+    for i in range(1, len(texts)):
+        j = int(order[i])
+        assert int(got[i, j]) == oracle.count_brute(texts[i], pats[j]), (i, j)
+    assert (got[:, order[:6]] > 0).all()
+    b.close()
+    del devs
+    torch.cuda.empty_cache()
+
+
+def test_kmer_census_1GB(gpu):
+    import itertools
+    text = synth.genome_text(1_000_000_000, 20)
+    pats = ["".join(s) for s in itertools.product("ACGT", repeat=6)]
+    b = gpu.BatchedCount([_dev(text)], pats, cfg="auto")
+    b.run()
+    got = b.result()[0]
+    want = oracle.kmer_census(text, 6)
+    assert np.array_equal(got, want)
+    assert int(got.sum()) == oracle.valid_windows(text, 6)
