@@ -75,8 +75,31 @@ typedef struct dfa_table dfa_table;
  */
 int dfa_build(const char* pattern, int32_t m, dfa_table** out);
 
-/* Release a table (host and device memory).  NULL is ignored.  The caller
- * must make sure no enqueued call still uses it. */
+/* Bytes of device memory the tables of one pattern of length m occupy (every
+ * layout of the automaton of Sec. III-B), for dfa_build_into; -1 if m is out
+ * of range. */
+int64_t dfa_table_bytes(int32_t m);
+
+/*
+ * dfa_build without a device allocation, for callers that manage device
+ * memory themselves (a serving loop with its own arena; cudaMalloc and
+ * cudaFree may synchronise the device and stall work in flight).
+ *   d_mem / bytes: caller-owned device memory on the current device, 16-byte
+ *            aligned, at least dfa_table_bytes(m) bytes; it must stay valid
+ *            until the last call that uses the table has completed.
+ *   stream:  the copy of the tables into d_mem is enqueued on this stream;
+ *            calls that use the table must be ordered after it (the same
+ *            stream, or an event).
+ * The table behaves like one from dfa_build; dfa_free releases its host
+ * memory only.  Errors: DFA_EINVAL (as dfa_build, or d_mem NULL, unaligned
+ * or too small), DFA_ENOMEM, DFA_ECUDA.
+ */
+int dfa_build_into(const char* pattern, int32_t m, void* d_mem, int64_t bytes, void* stream,
+                   dfa_table** out);
+
+/* Release a table (host and device memory; for a table from dfa_build_into,
+ * host memory only).  NULL is ignored.  The caller must make sure no enqueued
+ * call still uses it. */
 void dfa_free(dfa_table* table);
 
 /* Pattern length m of a table, or -1 for NULL. */
@@ -232,6 +255,25 @@ typedef struct dfa_multi dfa_multi;
  */
 int dfa_multi_build(const char* const* patterns, const int32_t* lengths, int32_t npat,
                     dfa_multi** out);
+
+/*
+ * The same automaton built on the host only, with no device copy yet (for
+ * callers that manage device memory themselves, as for dfa_build_into).
+ * dfa_multi_image_bytes gives the size of its device image (-1 for NULL);
+ * dfa_multi_attach enqueues, on `stream`, the copy of the image into
+ * caller-owned device memory d_mem (current device, 16-byte aligned, at least
+ * that many bytes, valid until the last use of the table) and makes the
+ * table usable by dfa_multi_count on calls ordered after the copy.  A table
+ * can be attached once.  Errors: as dfa_multi_build; DFA_EINVAL for an
+ * attached table, a NULL, unaligned or too small d_mem.
+ */
+int dfa_multi_build_host(const char* const* patterns, const int32_t* lengths, int32_t npat,
+                         dfa_multi** out);
+int64_t dfa_multi_image_bytes(const dfa_multi* table);
+int dfa_multi_attach(dfa_multi* table, void* d_mem, int64_t bytes, void* stream);
+
+/* Release an automaton (its device copy too, unless the caller attached it
+ * to its own memory).  NULL is ignored. */
 void dfa_multi_free(dfa_multi* table);
 
 /* Number of automaton states (trie states, root 0, breadth-first order). */

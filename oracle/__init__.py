@@ -222,12 +222,17 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
-def multi_count(texts, patterns) -> np.ndarray:
+def multi_count(texts, patterns, threads: int | None = None) -> np.ndarray:
     """Counts of every pattern (overlaps included) in every text, by the
     definition (Sec. II-A, one brute-force window compare per pattern):
-    uint64[len(texts), len(patterns)]."""
+    uint64[len(texts), len(patterns)].  The independent (text, pattern)
+    compares run on ``threads`` host threads (default: all cores); each is
+    the same single-threaded C loop."""
+    from concurrent.futures import ThreadPoolExecutor
     out = np.zeros((len(texts), len(patterns)), dtype=np.uint64)
-    for i, t in enumerate(texts):
-        for j, p in enumerate(patterns):
-            out[i, j] = count_brute(t, p)
+    ts = [_bytes(t) for t in texts]
+    jobs = [(i, j) for i in range(len(ts)) for j in range(len(patterns))]
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+        for (i, j), c in zip(jobs, ex.map(lambda ij: count_brute(ts[ij[0]], patterns[ij[1]]), jobs)):
+            out[i, j] = c
     return out

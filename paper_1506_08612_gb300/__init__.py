@@ -33,7 +33,7 @@ from ._native import (DFA_COUNT_FAILED, DFA_ECUDA, DFA_EINVAL, DFA_ENOMEM, DFA_E
 _lib = _native.lib
 
 __all__ = ["Table", "DfaError", "dfa_build", "dfa_free", "dfa_export_stt", "dfa_count",
-           "dfa_find", "dfa_find_workspace_bytes", "dfa_find_status", "dfa_host_stage_bytes",
+           "dfa_find", "dfa_find_workspace_bytes", "dfa_table_bytes", "dfa_find_status", "dfa_host_stage_bytes",
            "dfa_find_host", "dfa_find_noalloc", "MultiTable", "dfa_multi_count", "multi_count",
            "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
            "DFA_OK", "DFA_EINVAL", "DFA_ETRUNC", "DFA_ETIMEOUT", "DFA_ECUDA", "DFA_EWORKSPACE",
@@ -83,13 +83,23 @@ def _ptr(t) -> ctypes.c_void_p:
 class Table:
     """Automaton of one pattern (library-owned host + device tables)."""
 
-    def __init__(self, pattern):
+    def __init__(self, pattern, into=None, stream=None):
+        """``into``: optional device uint8 tensor of at least
+        ``dfa_table_bytes(m)`` bytes that receives the tables (dfa_build_into,
+        copy enqueued on ``stream``); the caller keeps it alive while the
+        table is in use."""
         if isinstance(pattern, str):
             pattern = pattern.encode("ascii")
         pattern = bytes(pattern)
         h = ctypes.c_void_p()
-        _check(_lib.dfa_build(pattern, len(pattern), ctypes.byref(h)), "dfa_build")
+        if into is None:
+            _check(_lib.dfa_build(pattern, len(pattern), ctypes.byref(h)), "dfa_build")
+        else:
+            _check(_lib.dfa_build_into(pattern, len(pattern), _ptr(into),
+                                       int(into.numel() * into.element_size()), _stream(stream),
+                                       ctypes.byref(h)), "dfa_build_into")
         self._h = h
+        self._into = into
         self.pattern = pattern.upper()
         self.m = len(pattern)
 
@@ -117,6 +127,10 @@ def dfa_build(pattern) -> Table:
 
 def dfa_free(table: Table) -> None:
     table.free()
+
+
+def dfa_table_bytes(m: int) -> int:
+    return int(_lib.dfa_table_bytes(int(m)))
 
 
 def dfa_export_stt(table: Table) -> np.ndarray:
@@ -195,17 +209,21 @@ def dfa_find_host(h_text, table: Table, h_positions, stage, seg: int, stream=Non
 class MultiTable:
     """Owns a dfa_multi (multi-pattern automaton); frees it on close/del."""
 
-    def __init__(self, patterns):
+    def __init__(self, patterns, device: bool = True):
+        """device=False builds the host automaton only (dfa_multi_build_host);
+        ``attach`` then copies it into caller-owned device memory."""
         pats = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
         self.patterns = pats
         arr = (ctypes.c_char_p * len(pats))(*pats)
         lens = (ctypes.c_int32 * len(pats))(*[len(p) for p in pats])
         h = ctypes.c_void_p()
-        rc = _lib.dfa_multi_build(arr, lens, len(pats), ctypes.byref(h))
+        fn = _lib.dfa_multi_build if device else _lib.dfa_multi_build_host
+        rc = fn(arr, lens, len(pats), ctypes.byref(h))
         if rc != DFA_OK:
             msg = _lib.dfa_last_error().decode(errors="replace")
-            raise DfaError(rc, f"dfa_multi_build [{msg}]")
+            raise DfaError(rc, f"{fn.__name__} [{msg}]")
         self._h = h
+        self._into = None
         self.npat = len(pats)
         self.mmax = max(len(p) for p in pats)
 
@@ -229,6 +247,16 @@ class MultiTable:
 
     def smem_bytes(self) -> int:
         return int(_lib.dfa_multi_smem_bytes(self.handle))
+
+    def image_bytes(self) -> int:
+        return int(_lib.dfa_multi_image_bytes(self.handle))
+
+    def attach(self, into, stream=None) -> None:
+        """Copy the automaton into ``into`` (device uint8 tensor of at least
+        image_bytes(), kept alive by the caller) on ``stream``."""
+        _check(_lib.dfa_multi_attach(self.handle, _ptr(into), int(into.numel() * into.element_size()),
+                                     _stream(stream)), "dfa_multi_attach")
+        self._into = into
 
     def free(self):
         if getattr(self, "_h", None) is not None:

@@ -28,6 +28,8 @@ def _declare(lib):
     sig = {
         "dfa_build": ([ctypes.c_char_p, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "dfa_free": ([vp], None),
+        "dfa_table_bytes": ([i32], i64),
+        "dfa_build_into": ([ctypes.c_char_p, i32, vp, i64, vp, ctypes.POINTER(vp)], ctypes.c_int),
         "dfa_pattern_length": ([vp], i32),
         "dfa_export_stt": ([vp, vp, i64], ctypes.c_int),
         "dfa_count": ([vp, i64, vp, vp, cfgp, vp], ctypes.c_int),
@@ -41,6 +43,10 @@ def _declare(lib):
         "dfa_multi_build": ([ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32), i32, ctypes.POINTER(vp)],
                             ctypes.c_int),
         "dfa_multi_free": ([vp], None),
+        "dfa_multi_build_host": ([ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32), i32,
+                                  ctypes.POINTER(vp)], ctypes.c_int),
+        "dfa_multi_image_bytes": ([vp], i64),
+        "dfa_multi_attach": ([vp, vp, i64, vp], ctypes.c_int),
         "dfa_multi_states": ([vp], i32),
         "dfa_multi_export": ([vp, vp, vp, i64], ctypes.c_int),
         "dfa_multi_smem_bytes": ([vp], i64),

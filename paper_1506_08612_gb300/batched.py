@@ -24,18 +24,32 @@ MAX_PAT_PER_TABLE = 8192
 MAX_STATES = 16383
 
 
+def new_prefixes(prefixes: set, pattern) -> list:
+    """Prefixes of ``pattern`` (case folded) not yet in ``prefixes``: the
+    trie states it would add to an automaton holding those prefixes."""
+    p = (pattern.encode() if isinstance(pattern, str) else bytes(pattern)).upper()
+    out = []
+    for k in range(len(p), 0, -1):
+        q = p[:k]
+        if q in prefixes:
+            break
+        out.append(q)
+    return out
+
+
 def group_patterns(patterns, max_states: int = MAX_STATES, max_pat: int = MAX_PAT_PER_TABLE):
-    """Split pattern indices into consecutive groups whose trie surely fits:
-    the trie of a group has at most 1 + the sum of its pattern lengths
-    states."""
-    groups, cur, states = [], [], 1
+    """Split pattern indices into consecutive groups whose automaton fits:
+    a group's trie has one state per distinct prefix (the empty one
+    included), counted exactly as patterns are added."""
+    groups, cur, seen = [], [], {b""}
     for i, p in enumerate(patterns):
-        m = len(p)
-        if cur and (states + m > max_states or len(cur) >= max_pat):
+        add = new_prefixes(seen, p)
+        if cur and (len(seen) + len(add) > max_states or len(cur) >= max_pat):
             groups.append(cur)
-            cur, states = [], 1
+            cur, seen = [], {b""}
+            add = new_prefixes(seen, p)
         cur.append(i)
-        states += m
+        seen.update(add)
     if cur:
         groups.append(cur)
     return groups

@@ -70,6 +70,8 @@ struct dfa_table {
     void* d_mem;
     size_t d_bytes;
     dnadfa::DeviceTableView view;
+    bool owns_mem = true;                // false: d_mem is the caller's (dfa_build_into)
+    std::vector<uint8_t> img;            // device image kept for dfa_build_into's async copy
 };
 
 namespace dnadfa {

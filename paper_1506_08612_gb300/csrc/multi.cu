@@ -40,7 +40,9 @@ struct dfa_multi {
     std::vector<uint16_t> out_ids;      // concatenated output lists
     int device = 0;
     void* d_mem = nullptr;
-    int32_t delta_bytes = 0, off_bytes = 0, ids_bytes = 0, mlen_bytes = 0;
+    int32_t delta_bytes = 0, out1_bytes = 0, off_bytes = 0, ids_bytes = 0, mlen_bytes = 0;
+    bool owns_mem = true;               // false: d_mem is the caller's (dfa_multi_attach)
+    std::vector<uint8_t> img;           // device image, kept until the table is freed
 };
 
 namespace {
@@ -51,13 +53,18 @@ constexpr int kMultiMaxPat = 8192;       // per-CTA counters: 32 KiB
 
 int round16(int64_t b) { return (int)((b + 15) & ~(int64_t)15); }
 
+constexpr uint32_t kMany = 0xFFFFu;      // out1 entry of a state with 0 or >= 2 outputs
+
 struct MultiArgs {
     const uint8_t* text[kMultiMaxSeq];
     int64_t n[kMultiMaxSeq];
     int64_t tile0[kMultiMaxSeq + 1];     // first tile of each sequence; tile0[nseq] = all tiles
     int32_t nseq, npat, mmax, chunk;
-    int32_t delta_bytes, off_bytes, ids_bytes, mlen_bytes;
-    const uint8_t* tab;
+    int32_t delta_bytes, out1_bytes;     // the parts copied to shared memory
+    const uint8_t* tab;                  // device image: [delta][out1][off][ids][mlen]
+    const uint32_t* off;
+    const uint16_t* ids;
+    const uint8_t* mlen;
     unsigned long long* counts;         // [nseq][npat]
 };
 
@@ -70,7 +77,7 @@ __device__ __forceinline__ uint4 ldg16m(const uint4* p)
     return v;
 }
 
-// Zero iff all four bytes of x are bases (A C G T a c g t).
+// Per byte of x: zero iff the byte is a base (A C G T a c g t).
 __device__ __forceinline__ uint32_t word_bad_m(uint32_t x)
 {
     uint32_t t = (x >> 2) & ~(x >> 1) & 0x01010101u;
@@ -78,85 +85,100 @@ __device__ __forceinline__ uint32_t word_bad_m(uint32_t x)
 }
 
 struct MultiTab {
-    const uint16_t* delta;
-    const uint32_t* off;
-    const uint16_t* ids;
-    const uint8_t* mlen;
-    uint32_t* hist;
+    const uint16_t* delta;   // shared: 4 * state + code -> 4 * next | (out(next) not empty)
+    const uint16_t* out1;    // shared: the one pattern a state outputs, or kMany
+    uint32_t* hist;          // shared: per-pattern counts of this CTA
+    const MultiArgs* args;   // the launch's arguments (output lists in global memory)
 };
 
-// One row: owned starts [0, own) relative to its first byte, bytes
-// [0, len) walked.
-struct RowWalk {
-    const MultiTab& M;
-    uint32_t ent;     // last entry: 4 * state | output flag
-    uint32_t own;
+// Outputs of state st at end offset j, one by one from the list
+// (ids[off[st] .. off[st+1])), each kept iff its start j - m_p + 1 lies
+// below own (the chunk's owned starts).
+__device__ __noinline__ void emit_list(const MultiArgs* a, uint32_t* hist, uint32_t st, uint32_t j, uint32_t own)
+{
+    const uint32_t* off = a->off;
+    const uint32_t k1 = __ldg(off + st + 1);
+    for (uint32_t k = __ldg(off + st); k < k1; k++) {
+        const uint32_t p = __ldg(a->ids + k);
+        if (j + 1u < own + __ldg(a->mlen + p)) atomicAdd(hist + p, 1u);
+    }
+}
 
-    __device__ __forceinline__ void outputs(uint32_t j)
-    {
-        const uint32_t st = ent >> 2;
-        const uint32_t k1 = M.off[st + 1];
-        for (uint32_t k = M.off[st]; k < k1; k++) {
-            const uint32_t p = M.ids[k];
-            if (j + 1u < own + M.mlen[p]) atomicAdd(&M.hist[p], 1u);
-        }
+// Entry e has its output flag set: count the patterns ending at j.  A state
+// with one output inside the owned part (every start there is owned) takes
+// the shared-memory fast path.
+__device__ __forceinline__ void emit(const MultiTab& M, uint32_t e, uint32_t j, uint32_t own)
+{
+    const uint32_t st = e >> 2;
+    const uint32_t p = M.out1[st];
+    if (p != kMany && j < own)
+        atomicAdd(M.hist + p, 1u);
+    else
+        emit_list(M.args, M.hist, st, j, own);
+}
+
+// Four bases of a word w, byte k ending at offset j + k: four dependent
+// lookups, one test of the output flags.
+__device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
+{
+    const uint32_t c = (w >> 1) & 0x03030303u;
+    const uint32_t e0 = M.delta[(ent & ~3u) | (c & 3u)];
+    const uint32_t e1 = M.delta[(e0 & ~3u) | ((c >> 8) & 3u)];
+    const uint32_t e2 = M.delta[(e1 & ~3u) | ((c >> 16) & 3u)];
+    const uint32_t e3 = M.delta[(e2 & ~3u) | (c >> 24)];
+    ent = e3;
+    if ((e0 | e1 | e2 | e3) & 1u) {
+        if (e0 & 1u) emit(M, e0, j, own);
+        if (e1 & 1u) emit(M, e1, j + 1, own);
+        if (e2 & 1u) emit(M, e2, j + 2, own);
+        if (e3 & 1u) emit(M, e3, j + 3, own);
     }
-    __device__ __forceinline__ void step(uint32_t code, uint32_t j)
-    {
-        ent = M.delta[(ent & ~3u) | code];
-        if (ent & 1u) outputs(j);
-    }
-    // four bases of a word, byte k at end offset j + k
-    __device__ __forceinline__ void word_fast(uint32_t w, uint32_t j)
-    {
-        const uint32_t c = (w >> 1) & 0x03030303u;
-        step(__byte_perm(c, 0u, 0x4440u), j);
-        step(__byte_perm(c, 0u, 0x4441u), j + 1);
-        step(__byte_perm(c, 0u, 0x4442u), j + 2);
-        step(__byte_perm(c, 0u, 0x4443u), j + 3);
-    }
-    __device__ __forceinline__ void byte(uint32_t c, uint32_t j)
-    {
-        const uint32_t t = (c >> 2) & ~(c >> 1) & 1u;
-        if (((c ^ (t * 0x11u)) & 0xD9u) == 0x41u)
-            step((c >> 1) & 3u, j);
-        else
-            ent = 0u;
-    }
-    __device__ __forceinline__ void word(uint32_t w, uint32_t j)
-    {
-        if (word_bad_m(w) == 0u) {
-            word_fast(w, j);
+}
+
+// A word holding bases and non-bases: byte by byte, every non-base resets
+// the walk to q0 (Sec. III-B: columns outside the alphabet lead to q0).
+__device__ __noinline__ uint32_t word_mixed(const MultiTab M, uint32_t ent, uint32_t w, uint32_t j, uint32_t own)
+{
+    for (int k = 0; k < 4; k++) {
+        const uint32_t b = (w >> (8 * k)) & 0xFFu;
+        const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
+        if (((b ^ (t * 0x11u)) & 0xD9u) == 0x41u) {
+            ent = M.delta[(ent & ~3u) | ((b >> 1) & 3u)];
+            if (ent & 1u) emit(M, ent, j + k, own);
         } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++) byte((w >> (8 * k)) & 0xFFu, j + k);
+            ent = 0u;
         }
     }
-    __device__ __forceinline__ void vec(uint4 v, uint32_t j)
-    {
-        word(v.x, j);
-        word(v.y, j + 4);
-        word(v.z, j + 8);
-        word(v.w, j + 12);
+    return ent;
+}
+
+__device__ __forceinline__ void word_any(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
+{
+    const uint32_t bad = word_bad_m(w);
+    if (bad == 0u) {
+        word_bases(M, ent, w, j, own);
+    } else if (((bad - 0x01010101u) & ~bad & 0x80808080u) == 0u) {
+        ent = 0u;                                   // four non-bases (an N block)
+    } else {
+        ent = word_mixed(M, ent, w, j, own);
     }
-};
+}
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_multi_count(const __grid_constant__ MultiArgs a)
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const __grid_constant__ MultiArgs a)
 {
     extern __shared__ __align__(16) uint8_t msm[];
-    const int tab_bytes = a.delta_bytes + a.off_bytes + a.ids_bytes + a.mlen_bytes;
     {
+        const int bytes = a.delta_bytes + a.out1_bytes;
         const uint4* src = reinterpret_cast<const uint4*>(a.tab);
         uint4* dst = reinterpret_cast<uint4*>(msm);
-        for (int i = threadIdx.x; i < (tab_bytes >> 4); i += THREADS) dst[i] = src[i];
+        for (int i = threadIdx.x; i < (bytes >> 4); i += THREADS) dst[i] = src[i];
     }
     MultiTab M;
     M.delta = reinterpret_cast<const uint16_t*>(msm);
-    M.off = reinterpret_cast<const uint32_t*>(msm + a.delta_bytes);
-    M.ids = reinterpret_cast<const uint16_t*>(msm + a.delta_bytes + a.off_bytes);
-    M.mlen = msm + a.delta_bytes + a.off_bytes + a.ids_bytes;
-    M.hist = reinterpret_cast<uint32_t*>(msm + tab_bytes);
+    M.out1 = reinterpret_cast<const uint16_t*>(msm + a.delta_bytes);
+    M.hist = reinterpret_cast<uint32_t*>(msm + a.delta_bytes + a.out1_bytes);
+    M.args = &a;
     for (int p = threadIdx.x; p < a.npat; p += THREADS) M.hist[p] = 0u;
     __syncthreads();
 
@@ -189,29 +211,41 @@ __global__ void __launch_bounds__(THREADS) k_multi_count(const __grid_constant__
         if (s >= n) continue;
         const int64_t e = min(s + C, n);
         const int64_t hi = min(e + (int64_t)a.mmax - 1, n);
-        RowWalk w{M, 0u, (uint32_t)(e - s)};
+        const uint32_t own = (uint32_t)(e - s);
         const uint32_t len = (uint32_t)(hi - s);
+        uint32_t ent = 0u;
         uint32_t done = 0;
         if ((((uintptr_t)text) & 15u) == 0 && len >= 16) {
-            // 16-byte vectors, four loads in flight
+            // 16-byte vectors, two in flight ahead of the one walked
             const uint4* p = reinterpret_cast<const uint4*>(text + s);
             const uint32_t nv = len >> 4;
-            uint4 b0 = ldg16m(p), b1 = nv > 1 ? ldg16m(p + 1) : b0, b2 = nv > 2 ? ldg16m(p + 2) : b0,
-                  b3 = nv > 3 ? ldg16m(p + 3) : b0;
-            for (uint32_t g = 0; g < nv; g += 4) {
-                const uint4 c0 = b0, c1 = b1, c2 = b2, c3 = b3;
-                if (g + 4 < nv) b0 = ldg16m(p + g + 4);
-                if (g + 5 < nv) b1 = ldg16m(p + g + 5);
-                if (g + 6 < nv) b2 = ldg16m(p + g + 6);
-                if (g + 7 < nv) b3 = ldg16m(p + g + 7);
-                w.vec(c0, 16 * g);
-                if (g + 1 < nv) w.vec(c1, 16 * (g + 1));
-                if (g + 2 < nv) w.vec(c2, 16 * (g + 2));
-                if (g + 3 < nv) w.vec(c3, 16 * (g + 3));
+            uint4 b0 = ldg16m(p);
+            uint4 b1 = nv > 1 ? ldg16m(p + 1) : b0;
+            uint4 b2 = nv > 2 ? ldg16m(p + 2) : b0;
+#pragma unroll 1
+            for (uint32_t g = 0; g < nv; g++) {
+                const uint4 v = b0;
+                b0 = b1;
+                b1 = b2;
+                if (g + 3 < nv) b2 = ldg16m(p + g + 3);
+                const uint32_t j = 16u * g;
+                word_any(M, ent, v.x, j, own);
+                word_any(M, ent, v.y, j + 4, own);
+                word_any(M, ent, v.z, j + 8, own);
+                word_any(M, ent, v.w, j + 12, own);
             }
             done = nv << 4;
         }
-        for (uint32_t j = done; j < len; j++) w.byte(text[s + j], j);
+        for (uint32_t j = done; j < len; j++) {
+            const uint32_t b = text[s + j];
+            const uint32_t tt = (b >> 2) & ~(b >> 1) & 1u;
+            if (((b ^ (tt * 0x11u)) & 0xD9u) == 0x41u) {
+                ent = M.delta[(ent & ~3u) | ((b >> 1) & 3u)];
+                if (ent & 1u) emit(M, ent, j, own);
+            } else {
+                ent = 0u;
+            }
+        }
     }
     if (cur >= 0) flush(cur);
 }
@@ -236,7 +270,7 @@ int multi_fail(const char* what, cudaError_t err)
 
 extern "C" {
 
-int dfa_multi_build(const char* const* patterns, const int32_t* lengths, int32_t npat, dfa_multi** out)
+int dfa_multi_build_host(const char* const* patterns, const int32_t* lengths, int32_t npat, dfa_multi** out)
 {
     if (!patterns || !lengths || !out || npat < 1 || npat > kMultiMaxPat) return DFA_EINVAL;
     *out = nullptr;
@@ -306,23 +340,47 @@ int dfa_multi_build(const char* const* patterns, const int32_t* lengths, int32_t
         t->out_ids.insert(t->out_ids.end(), outs[u].begin(), outs[u].end());
     }
     // device image: [delta][out_off][out_ids][mlen], 16-byte aligned parts
+    // out1[q]: the pattern of a state with exactly one output, else kMany
+    std::vector<uint16_t> out1(S, (uint16_t)kMany);
+    for (int i = 0; i < S; i++)
+        if (t->out_off[i + 1] - t->out_off[i] == 1) out1[i] = t->out_ids[t->out_off[i]];
     t->delta_bytes = round16((int64_t)S * 4 * 2);
+    t->out1_bytes = round16((int64_t)S * 2);
     t->off_bytes = round16((int64_t)(S + 1) * 4);
     t->ids_bytes = round16((int64_t)std::max<size_t>(t->out_ids.size(), 1) * 2);
     t->mlen_bytes = round16(npat);
-    const size_t bytes = (size_t)t->delta_bytes + t->off_bytes + t->ids_bytes + t->mlen_bytes;
-    std::vector<uint8_t> img(bytes, 0);
-    memcpy(img.data(), t->delta.data(), t->delta.size() * 2);
-    memcpy(img.data() + t->delta_bytes, t->out_off.data(), t->out_off.size() * 4);
-    if (!t->out_ids.empty())
-        memcpy(img.data() + t->delta_bytes + t->off_bytes, t->out_ids.data(), t->out_ids.size() * 2);
-    memcpy(img.data() + t->delta_bytes + t->off_bytes + t->ids_bytes, t->mlen.data(), npat);
+    const size_t bytes = (size_t)t->delta_bytes + t->out1_bytes + t->off_bytes + t->ids_bytes + t->mlen_bytes;
+    std::vector<uint8_t>& img = t->img;
+    img.assign(bytes, 0);
+    uint8_t* q = img.data();
+    memcpy(q, t->delta.data(), t->delta.size() * 2);
+    q += t->delta_bytes;
+    memcpy(q, out1.data(), out1.size() * 2);
+    q += t->out1_bytes;
+    memcpy(q, t->out_off.data(), t->out_off.size() * 4);
+    q += t->off_bytes;
+    if (!t->out_ids.empty()) memcpy(q, t->out_ids.data(), t->out_ids.size() * 2);
+    q += t->ids_bytes;
+    memcpy(q, t->mlen.data(), npat);
+    t->owns_mem = false;
+    *out = t;
+    return DFA_OK;
+}
+
+int dfa_multi_build(const char* const* patterns, const int32_t* lengths, int32_t npat, dfa_multi** out)
+{
+    if (!out) return DFA_EINVAL;
+    dfa_multi* t = nullptr;
+    int rc = dfa_multi_build_host(patterns, lengths, npat, &t);
+    if (rc) return rc;
+    const size_t bytes = t->img.size();
     cudaError_t err;
     if ((err = cudaGetDevice(&t->device)) != cudaSuccess || (err = cudaMalloc(&t->d_mem, bytes)) != cudaSuccess) {
         delete t;
         return multi_fail("dfa_multi_build", err);
     }
-    if ((err = cudaMemcpy(t->d_mem, img.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    t->owns_mem = true;
+    if ((err = cudaMemcpy(t->d_mem, t->img.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
         cudaFree(t->d_mem);
         delete t;
         return multi_fail("dfa_multi_build", err);
@@ -331,10 +389,27 @@ int dfa_multi_build(const char* const* patterns, const int32_t* lengths, int32_t
     return DFA_OK;
 }
 
+int64_t dfa_multi_image_bytes(const dfa_multi* t) { return t ? (int64_t)t->img.size() : -1; }
+
+int dfa_multi_attach(dfa_multi* t, void* d_mem, int64_t bytes, void* stream)
+{
+    if (!t || t->d_mem || !d_mem || (reinterpret_cast<uintptr_t>(d_mem) & 15u) ||
+        bytes < (int64_t)t->img.size())
+        return DFA_EINVAL;
+    cudaError_t err;
+    if ((err = cudaGetDevice(&t->device)) != cudaSuccess ||
+        (err = cudaMemcpyAsync(d_mem, t->img.data(), t->img.size(), cudaMemcpyHostToDevice,
+                               static_cast<cudaStream_t>(stream))) != cudaSuccess)
+        return multi_fail("dfa_multi_attach", err);
+    t->d_mem = d_mem;
+    t->owns_mem = false;
+    return DFA_OK;
+}
+
 void dfa_multi_free(dfa_multi* t)
 {
     if (!t) return;
-    if (t->d_mem) cudaFree(t->d_mem);
+    if (t->d_mem && t->owns_mem) cudaFree(t->d_mem);
     delete t;
 }
 
@@ -354,13 +429,14 @@ int dfa_multi_export(const dfa_multi* t, int32_t* h_next, int32_t* h_nout, int64
 int64_t dfa_multi_smem_bytes(const dfa_multi* t)
 {
     if (!t) return -1;
-    return (int64_t)t->delta_bytes + t->off_bytes + t->ids_bytes + t->mlen_bytes + (int64_t)t->npat * 4;
+    return (int64_t)t->delta_bytes + t->out1_bytes + (int64_t)t->npat * 4;
 }
 
 int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32_t nseq, const dfa_multi* t,
                     uint64_t* d_counts, const dfa_config* cfg, void* stream)
 {
     if (!t || !d_counts || !d_texts || !lengths || nseq < 1 || nseq > kMultiMaxSeq) return DFA_EINVAL;
+    if (!t->d_mem) return set_last_error(DFA_EINVAL, "dfa_multi_count: the automaton has no device copy (dfa_multi_attach)");
     const int threads = cfg && cfg->threads ? cfg->threads : 256;
     const int chunk = cfg && cfg->chunk ? cfg->chunk : 1024;
     if (threads != 128 && threads != 256 && threads != 512) return DFA_EINVAL;
@@ -385,10 +461,11 @@ int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32
     a.mmax = t->mmax;
     a.chunk = chunk;
     a.delta_bytes = t->delta_bytes;
-    a.off_bytes = t->off_bytes;
-    a.ids_bytes = t->ids_bytes;
-    a.mlen_bytes = t->mlen_bytes;
+    a.out1_bytes = t->out1_bytes;
     a.tab = static_cast<const uint8_t*>(t->d_mem);
+    a.off = reinterpret_cast<const uint32_t*>(a.tab + t->delta_bytes + t->out1_bytes);
+    a.ids = reinterpret_cast<const uint16_t*>(a.tab + t->delta_bytes + t->out1_bytes + t->off_bytes);
+    a.mlen = a.tab + t->delta_bytes + t->out1_bytes + t->off_bytes + t->ids_bytes;
     a.counts = reinterpret_cast<unsigned long long*>(d_counts);
     if ((err = cudaMemsetAsync(d_counts, 0, (size_t)nseq * t->npat * 8, st)) != cudaSuccess)
         return multi_fail("dfa_multi_count", err);

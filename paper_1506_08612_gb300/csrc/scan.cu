@@ -2088,9 +2088,11 @@ int set_last_error(int code, const char* msg)
 
 // ==================================================================== C ABI
 
-extern "C" {
+namespace {
 
-int dfa_build(const char* pattern, int32_t m, dfa_table** out)
+// Host part of dfa_build / dfa_build_into: validated pattern, host tables,
+// sizes of the device image and the image itself in t->img.
+int make_table(const char* pattern, int32_t m, dfa_table** out)
 {
     if (!pattern || !out || m < 1 || m > DFA_MAX_M) return DFA_EINVAL;
     *out = nullptr;
@@ -2118,12 +2120,8 @@ int dfa_build(const char* pattern, int32_t m, dfa_table** out)
     t->view.k4f_bytes = (int32_t)t->k4f.size();
     t->d_bytes = (size_t)t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes + t->view.k4s_bytes +
                  t->view.k4f_bytes;
-    if (cudaGetDevice(&t->device) != cudaSuccess || cudaMalloc(&t->d_mem, t->d_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        delete t;
-        return DFA_ECUDA;
-    }
-    std::vector<uint8_t> img(t->d_bytes, 0);
+    std::vector<uint8_t>& img = t->img;
+    img.assign(t->d_bytes, 0);
     memcpy(img.data(), t->k4.data(), (size_t)t->view.k4_bytes);
     memcpy(img.data() + t->view.k4_bytes, t->d1.data(), t->d1.size());
     memcpy(img.data() + t->view.k4_bytes + t->view.d1_bytes, t->stt.data(), t->stt.size());
@@ -2131,12 +2129,61 @@ int dfa_build(const char* pattern, int32_t m, dfa_table** out)
     if (!t->k4f.empty())
         memcpy(img.data() + t->view.k4_bytes + t->view.d1_bytes + t->view.stt_bytes + t->view.k4s_bytes,
                t->k4f.data(), t->k4f.size());
-    if (cudaMemcpy(t->d_mem, img.data(), t->d_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    *out = t;
+    return DFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfa_build(const char* pattern, int32_t m, dfa_table** out)
+{
+    dfa_table* t = nullptr;
+    int rc = make_table(pattern, m, &t);
+    if (rc) return rc;
+    if (cudaGetDevice(&t->device) != cudaSuccess || cudaMalloc(&t->d_mem, t->d_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete t;
+        return DFA_ECUDA;
+    }
+    if (cudaMemcpy(t->d_mem, t->img.data(), t->d_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(t->d_mem);
         delete t;
         return DFA_ECUDA;
     }
+    std::vector<uint8_t>().swap(t->img);
     t->view.base = static_cast<const uint8_t*>(t->d_mem);
+    *out = t;
+    return DFA_OK;
+}
+
+int64_t dfa_table_bytes(int32_t m)
+{
+    if (m < 1 || m > DFA_MAX_M) return -1;
+    return (int64_t)(m + 1) * 512 + (((m + 1) * 4 + 15) & ~15) + (int64_t)(m + 1) * 256 * 2 +
+           (int64_t)(k4f_flag(m) + m + 1) * 256;
+}
+
+int dfa_build_into(const char* pattern, int32_t m, void* d_mem, int64_t bytes, void* stream, dfa_table** out)
+{
+    if (!out) return DFA_EINVAL;
+    *out = nullptr;
+    if (!d_mem || (reinterpret_cast<uintptr_t>(d_mem) & 15u) || bytes < dfa_table_bytes(m))
+        return DFA_EINVAL;
+    dfa_table* t = nullptr;
+    int rc = make_table(pattern, m, &t);
+    if (rc) return rc;
+    cudaError_t err;
+    if ((err = cudaGetDevice(&t->device)) != cudaSuccess ||
+        (err = cudaMemcpyAsync(d_mem, t->img.data(), t->d_bytes, cudaMemcpyHostToDevice,
+                               static_cast<cudaStream_t>(stream))) != cudaSuccess) {
+        delete t;
+        return cuda_fail(err, "dfa_build_into");
+    }
+    t->d_mem = d_mem;
+    t->owns_mem = false;
+    t->view.base = static_cast<const uint8_t*>(d_mem);
     *out = t;
     return DFA_OK;
 }
@@ -2144,7 +2191,7 @@ int dfa_build(const char* pattern, int32_t m, dfa_table** out)
 void dfa_free(dfa_table* table)
 {
     if (!table) return;
-    if (table->d_mem) {
+    if (table->d_mem && table->owns_mem) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (cur != table->device) cudaSetDevice(table->device);

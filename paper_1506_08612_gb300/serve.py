@@ -1,0 +1,462 @@
+"""Serving loop: genomes resident in HBM, pattern queries arriving over time.
+
+The paper scans one genome per program run and advises keeping the data on
+the coprocessor (Sec. II-B).  A server keeps every sequence resident on the
+GPU and answers queries {sequence, patterns, mode} as they arrive:
+
+* **Continuous batching.**  Each scheduler iteration takes the arrivals,
+  polls the work in flight (CUDA events, never a blocking wait) and, while
+  a stream slot is free, forms a batch from the waiting queries of one
+  sequence (the oldest query's sequence, then every other waiting query on
+  it, up to ``max_batch_patterns`` distinct patterns).  Batches on different
+  slots run on different CUDA streams, so new work overlaps with work
+  already on the device.
+* **Count stage.**  The batch's distinct patterns become one multi-pattern
+  failure-less automaton (Sec. III-B) and one persistent launch counts them
+  all over the sequence.  Count-mode queries are answered from it.
+* **Admission by position memory.**  A positions-mode query needs 8 bytes
+  per occurrence.  After the count stage those sizes are exact; the batch's
+  positions are admitted when they fit in the position arena (a fixed
+  device buffer, first-fit), in arrival order, and wait otherwise.  A request
+  larger than the whole arena fails with an error instead of waiting forever.
+* **Find stage.**  Each distinct positions pattern is located with the
+  single-pattern find (sorted start positions, exact count as capacity) into
+  the admitted region, and the region is copied back in one transfer.
+
+The GPU work sits behind an engine interface (``GpuEngine``) so the
+scheduler's policy can run against a stand-in engine on the CPU.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .batched import MAX_STATES, new_prefixes
+
+
+# ------------------------------------------------------------------ queries
+
+@dataclass
+class Query:
+    seq: int
+    patterns: list
+    mode: str = "count"                  # "count" | "positions"
+    t_arrive: float = 0.0                # perf_counter seconds
+    qid: int = -1
+    t_done: float = 0.0
+    counts: np.ndarray | None = None     # uint64[len(patterns)]
+    positions: list | None = None        # per pattern, sorted int64 start positions
+    error: str | None = None
+    batch: int = -1                      # id of the batch that served it
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrive
+
+
+def _key(p) -> bytes:
+    b = p.encode() if isinstance(p, str) else bytes(p)
+    return b.upper()
+
+
+# ------------------------------------------------------------------ arena
+
+class Arena:
+    """First-fit allocator over [0, size) with coalescing of free blocks.
+    Offsets and sizes are multiples of ``align`` bytes."""
+
+    def __init__(self, size: int, align: int = 256):
+        self.size = int(size) // align * align
+        self.align = align
+        self.free = [(0, self.size)]          # sorted (offset, length)
+        self.used = 0
+
+    def alloc(self, nbytes: int):
+        n = max(self.align, (int(nbytes) + self.align - 1) // self.align * self.align)
+        for i, (off, ln) in enumerate(self.free):
+            if ln >= n:
+                if ln == n:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (off + n, ln - n)
+                self.used += n
+                return off, n
+        return None
+
+    def release(self, off: int, n: int) -> None:
+        self.used -= n
+        fl = self.free
+        lo, hi = 0, len(fl)
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if fl[mid][0] < off:
+                lo = mid + 1
+            else:
+                hi = mid
+        fl.insert(lo, (off, n))
+        # coalesce with the next, then the previous block
+        if lo + 1 < len(fl) and fl[lo][0] + fl[lo][1] == fl[lo + 1][0]:
+            fl[lo] = (fl[lo][0], fl[lo][1] + fl[lo + 1][1])
+            fl.pop(lo + 1)
+        if lo > 0 and fl[lo - 1][0] + fl[lo - 1][1] == fl[lo][0]:
+            fl[lo - 1] = (fl[lo - 1][0], fl[lo - 1][1] + fl[lo][1])
+            fl.pop(lo)
+
+
+# ------------------------------------------------------------------ batches
+
+@dataclass
+class Batch:
+    bid: int
+    seq: int
+    queries: list
+    patterns: list                        # distinct upper-case patterns
+    index: dict                           # pattern -> column
+    state: str = "count"                  # count -> (wait_mem -> find) -> done
+    job: object = None
+    counts: np.ndarray | None = None
+    find_patterns: list = field(default_factory=list)
+    region: tuple | None = None           # (offset, bytes) in the position arena
+
+
+class GpuEngine:
+    """The device side of the server: resident sequences, stream slots, the
+    position arena, and the two stages as non-blocking jobs."""
+
+    def __init__(self, sequences, slots: int = 4, arena_bytes: int = 8 << 30,
+                 table_bytes: int = 64 << 20, device=None, plain: bool = False):
+        """plain=True counts with one single-pattern launch per pattern
+        instead of the multi-pattern automaton (the unbatched form, for
+        comparison)."""
+        import torch
+
+        import paper_1506_08612_gb300 as dd
+        self.dd = dd
+        self.torch = torch
+        self.seqs = list(sequences)
+        self.device = device or self.seqs[0].device
+        self.nslots = slots
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
+        nmax = max(int(s.numel()) for s in self.seqs)
+        self.ws = [torch.empty(dd.dfa_find_workspace_bytes(nmax), dtype=torch.uint8, device=self.device)
+                   for _ in range(slots)]
+        self.tab = [torch.empty(table_bytes, dtype=torch.uint8, device=self.device) for _ in range(slots)]
+        self.arena_bytes = int(arena_bytes)
+        self.arena = torch.empty(self.arena_bytes // 8, dtype=torch.int64, device=self.device)
+        self.plain = plain
+
+    # -- count stage: one multi-pattern launch over the batch's sequence
+    def launch_count(self, slot: int, seq: int, patterns):
+        dd, torch = self.dd, self.torch
+        st = self.streams[slot]
+        if self.plain:
+            return self._launch_count_plain(slot, seq, patterns)
+        mt = dd.MultiTable(patterns, device=False)
+        need = mt.image_bytes()
+        if need > self.tab[slot].numel():
+            self.tab[slot] = torch.empty(need, dtype=torch.uint8, device=self.device)
+        with torch.cuda.stream(st):
+            mt.attach(self.tab[slot], stream=st)
+            out = torch.empty(len(patterns), dtype=torch.int64, device=self.device)
+            dd.dfa_multi_count([self.seqs[seq]], mt, out, stream=st)
+            host = torch.empty(len(patterns), dtype=torch.int64, pin_memory=True)
+            host.copy_(out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return {"ev": ev, "host": host, "keep": (mt, out)}
+
+    def _launch_count_plain(self, slot, seq, patterns):
+        dd, torch = self.dd, self.torch
+        st = self.streams[slot]
+        need = sum((dd.dfa_table_bytes(len(p)) + 255) // 256 * 256 for p in patterns)
+        if need > self.tab[slot].numel():
+            self.tab[slot] = torch.empty(need, dtype=torch.uint8, device=self.device)
+        tabs = []
+        with torch.cuda.stream(st):
+            out = torch.empty(len(patterns), dtype=torch.int64, device=self.device)
+            toff = 0
+            for i, p in enumerate(patterns):
+                tb = dd.dfa_table_bytes(len(p))
+                t = dd.Table(p, into=self.tab[slot][toff:toff + tb], stream=st)
+                toff += (tb + 255) // 256 * 256
+                tabs.append(t)
+                dd.dfa_count(self.seqs[seq], t, out[i:i + 1], stream=st)
+            host = torch.empty(len(patterns), dtype=torch.int64, pin_memory=True)
+            host.copy_(out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return {"ev": ev, "host": host, "keep": (tabs, out)}
+
+    # -- find stage: the single-pattern find of each positions pattern into
+    #    the admitted arena region, then one copy of the region to the host
+    def launch_find(self, slot: int, seq: int, patterns, counts, region):
+        dd, torch = self.dd, self.torch
+        st = self.streams[slot]
+        off, nbytes = region
+        base = off // 8
+        tabs = []
+        need = sum((dd.dfa_table_bytes(len(p)) + 255) // 256 * 256 for p, c in zip(patterns, counts) if c)
+        if need > self.tab[slot].numel():
+            self.tab[slot] = torch.empty(need, dtype=torch.uint8, device=self.device)
+        text = self.seqs[seq]
+        total = int(sum(int(c) for c in counts))
+        with torch.cuda.stream(st):
+            cnt = torch.zeros(max(len(patterns), 1), dtype=torch.int64, device=self.device)
+            toff, poff = 0, base
+            for i, (p, c) in enumerate(zip(patterns, counts)):
+                if not c:
+                    continue                        # nothing to locate
+                tb = dd.dfa_table_bytes(len(p))
+                t = dd.Table(p, into=self.tab[slot][toff:toff + tb], stream=st)
+                toff += (tb + 255) // 256 * 256
+                tabs.append(t)
+                dd.dfa_find(text, t, self.arena[poff:poff + int(c)], cnt[i:i + 1], self.ws[slot], stream=st)
+                poff += int(c)
+            host = torch.empty(max(total, 1), dtype=torch.int64, pin_memory=True)
+            host[:total].copy_(self.arena[base:base + total], non_blocking=True)
+            hcnt = torch.empty(cnt.numel(), dtype=torch.int64, pin_memory=True)
+            hcnt.copy_(cnt, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return {"ev": ev, "host": host, "hcnt": hcnt, "keep": tabs, "counts": [int(c) for c in counts]}
+
+    @staticmethod
+    def done(job) -> bool:
+        return job["ev"].query()
+
+    @staticmethod
+    def count_result(job) -> np.ndarray:
+        return job["host"].numpy().astype(np.uint64)
+
+    @staticmethod
+    def find_result(job):
+        counts = job["counts"]
+        got = job["hcnt"].numpy()[:len(counts)]
+        if not np.array_equal(got, np.asarray(counts, dtype=np.int64)):
+            raise RuntimeError("find counts differ from the count stage")
+        h = job["host"].numpy()
+        out, o = [], 0
+        for c in counts:
+            out.append(h[o:o + c].copy())
+            o += c
+        for t in job["keep"]:
+            t.free()
+        return out
+
+
+class Server:
+    """Continuous-batching scheduler over an engine (see module doc)."""
+
+    def __init__(self, engine, max_batch_patterns: int = 2048, clock=time.perf_counter,
+                 max_batch_queries: int = 1 << 30):
+        self.engine = engine
+        self.clock = clock
+        self.max_batch_patterns = max_batch_patterns
+        self.max_batch_queries = max_batch_queries
+        self.arena = Arena(engine.arena_bytes)
+        self.free_slots = collections.deque(range(engine.nslots))
+        self.waiting = collections.deque()    # queries not yet in a batch
+        self.mem_wait = collections.deque()   # batches waiting for position memory
+        self.find_ready = collections.deque() # admitted batches waiting for a slot
+        self.active = []                       # (batch, slot) with a job in flight
+        self.done = []
+        self._lock = threading.Lock()
+        self._inbox = collections.deque()
+        self._next_q = 0
+        self._next_b = 0
+        self.stats = collections.Counter()
+
+    # -- public API
+    def submit(self, q: Query) -> Query:
+        with self._lock:
+            if q.qid < 0:
+                q.qid = self._next_q
+            self._next_q = max(self._next_q, q.qid + 1)
+            if not q.t_arrive:
+                q.t_arrive = self.clock()
+            self._inbox.append(q)
+        return q
+
+    def idle(self) -> bool:
+        return not (self._inbox or self.waiting or self.mem_wait or self.find_ready or self.active)
+
+    def step(self) -> int:
+        """One scheduler iteration; returns how many state changes it made."""
+        moved = 0
+        with self._lock:
+            while self._inbox:
+                self.waiting.append(self._inbox.popleft())
+                moved += 1
+        moved += self._poll()
+        moved += self._admit()
+        moved += self._launch_finds()
+        moved += self._launch_counts()
+        return moved
+
+    def run_until_idle(self, poll_s: float = 0.0):
+        while not self.idle():
+            if not self.step() and poll_s:
+                time.sleep(poll_s)
+
+    def replay(self, trace, speed: float = 1.0, poll_s: float = 0.0):
+        """Open-loop replay of a trace (dicts with t, seq, patterns, mode):
+        each query arrives at its scheduled time, the latency is measured from
+        that time.  Returns the completed queries in arrival order."""
+        t0 = self.clock()
+        order = sorted(range(len(trace)), key=lambda i: trace[i]["t"])
+        qs = [None] * len(trace)
+        k = 0
+        while k < len(order) or not self.idle():
+            now = self.clock()
+            while k < len(order) and t0 + trace[order[k]]["t"] / speed <= now:
+                e = trace[order[k]]
+                qs[order[k]] = self.submit(Query(seq=e["seq"], patterns=list(e["patterns"]),
+                                                 mode=e["mode"], t_arrive=t0 + e["t"] / speed,
+                                                 qid=order[k]))
+                k += 1
+            if not self.step() and poll_s:
+                time.sleep(poll_s)
+        return qs
+
+    # -- internals
+    def _finish(self, q: Query, now: float):
+        q.t_done = now
+        self.done.append(q)
+
+    def _poll(self) -> int:
+        moved = 0
+        still = []
+        for b, slot in self.active:
+            if not self.engine.done(b.job):
+                still.append((b, slot))
+                continue
+            moved += 1
+            self.free_slots.append(slot)
+            now = self.clock()
+            if b.state == "count":
+                b.counts = self.engine.count_result(b.job)
+                b.job = None
+                need = set()
+                for q in b.queries:
+                    q.counts = np.array([b.counts[b.index[_key(p)]] for p in q.patterns], dtype=np.uint64)
+                    if q.mode == "count":
+                        self._finish(q, now)
+                    else:
+                        need.update(_key(p) for p in q.patterns)
+                if need:
+                    b.find_patterns = sorted(need, key=lambda k: b.index[k])
+                    b.state = "wait_mem"
+                    self.mem_wait.append(b)
+                else:
+                    b.state = "done"
+                    self.stats["batches"] += 1
+            else:                                   # find stage done
+                pos = self.engine.find_result(b.job)
+                b.job = None
+                self.arena.release(*b.region)
+                got = dict(zip(b.find_patterns, pos))
+                for q in b.queries:
+                    if q.mode == "positions" and q.error is None:
+                        q.positions = [got[_key(p)] for p in q.patterns]
+                        self._finish(q, now)
+                b.state = "done"
+                self.stats["batches"] += 1
+        self.active = still
+        return moved
+
+    def _admit(self) -> int:
+        moved = 0
+        while self.mem_wait:
+            b = self.mem_wait[0]
+            nbytes = 8 * sum(int(b.counts[b.index[k]]) for k in b.find_patterns)
+            if nbytes > self.arena.size:
+                self.mem_wait.popleft()
+                now = self.clock()
+                for q in b.queries:
+                    if q.mode == "positions":
+                        q.error = (f"positions need {nbytes} bytes, more than the {self.arena.size}-byte"
+                                   " position arena")
+                        self._finish(q, now)
+                self.stats["rejected_batches"] += 1
+                moved += 1
+                continue
+            r = self.arena.alloc(max(nbytes, 8))
+            if r is None:
+                self.stats["mem_stalls"] += 1
+                break                               # arrival order: wait for memory
+            b.region = r
+            self.mem_wait.popleft()
+            self.find_ready.append(b)
+            moved += 1
+        return moved
+
+    def _launch_finds(self) -> int:
+        moved = 0
+        while self.find_ready and self.free_slots:
+            b = self.find_ready.popleft()
+            slot = self.free_slots.popleft()
+            counts = [int(b.counts[b.index[k]]) for k in b.find_patterns]
+            b.job = self.engine.launch_find(slot, b.seq, b.find_patterns, counts, b.region)
+            b.state = "find"
+            self.active.append((b, slot))
+            moved += 1
+        return moved
+
+    def _launch_counts(self) -> int:
+        moved = 0
+        while self.waiting and self.free_slots:
+            seq = self.waiting[0].seq
+            take, keep = [], collections.deque()
+            index = {}
+            prefixes = {b""}                        # the trie's states: distinct prefixes
+            for q in self.waiting:
+                if q.seq != seq:
+                    keep.append(q)
+                    continue
+                new = {_key(p) for p in q.patterns} - index.keys()
+                grow = set()
+                for k in new:
+                    grow.update(new_prefixes(prefixes, k))
+                if take and (len(index) + len(new) > self.max_batch_patterns
+                             or len(prefixes) + len(grow) > MAX_STATES
+                             or len(take) >= self.max_batch_queries):
+                    keep.append(q)
+                    continue
+                for p in q.patterns:
+                    k = _key(p)
+                    if k not in index:
+                        index[k] = len(index)
+                prefixes |= grow
+                take.append(q)
+            self.waiting = keep
+            b = Batch(bid=self._next_b, seq=seq, queries=take, patterns=list(index), index=index)
+            self._next_b += 1
+            for q in take:
+                q.batch = b.bid
+            slot = self.free_slots.popleft()
+            b.job = self.engine.launch_count(slot, seq, b.patterns)
+            self.active.append((b, slot))
+            self.stats["queries_batched"] += len(take)
+            moved += 1
+        return moved
+
+
+def latency_summary(queries) -> dict:
+    """Throughput and latency percentiles of completed queries."""
+    ok = [q for q in queries if q is not None and q.t_done and q.error is None]
+    if not ok:
+        return {"completed": 0}
+    lat = np.sort(np.array([q.latency for q in ok]))
+    span = max(q.t_done for q in ok) - min(q.t_arrive for q in ok)
+
+    def pct(p):
+        return float(lat[min(len(lat) - 1, int(np.ceil(p / 100.0 * len(lat))) - 1)])
+
+    return {"completed": len(ok), "errors": sum(1 for q in queries if q is not None and q.error),
+            "qps": len(ok) / span if span > 0 else float("inf"),
+            "p50_ms": pct(50) * 1e3, "p99_ms": pct(99) * 1e3, "max_ms": float(lat[-1]) * 1e3,
+            "mean_ms": float(lat.mean()) * 1e3}

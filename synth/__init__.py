@@ -151,3 +151,25 @@ def random_text(n: int, seed: int, alphabet: bytes = b"ACGT") -> np.ndarray:
 if __name__ == "__main__":  # pragma: no cover
     build(force="--force" in sys.argv)
     print(_SO)
+
+
+def query_trace(k: int, rate: float, nseq: int, seed: int, max_patterns: int = 64,
+                m_lo: int = 4, m_hi: int = 64) -> list[dict]:
+    """k seeded pattern queries with Poisson arrivals at ``rate`` per second:
+    each {"t": arrival offset in s, "seq": uniform in [0, nseq), "patterns":
+    1..max_patterns uniform patterns of length uniform in [m_lo, m_hi],
+    "mode": "count" or "positions" with probability 1/2}.  Inter-arrival gaps
+    are -ln(U)/rate with U uniform in (0, 1]."""
+    import math
+    gaps = uniform_ints(k, 1 << 53, seed, stream=11)
+    seqs = uniform_ints(k, nseq, seed, stream=12)
+    npats = uniform_ints(k, max_patterns, seed, stream=13) + 1
+    modes = uniform_ints(k, 2, seed, stream=14)
+    out, t = [], 0.0
+    for i in range(k):
+        t += -math.log((int(gaps[i]) + 1) / float(1 << 53)) / rate
+        lens = uniform_ints(int(npats[i]), m_hi - m_lo + 1, seed * 1_000_003 + i, stream=15) + m_lo
+        pats = [pattern(int(m), (seed << 24) + (i << 7) + j) for j, m in enumerate(lens)]
+        out.append({"t": t, "seq": int(seqs[i]), "patterns": pats,
+                    "mode": "positions" if modes[i] else "count"})
+    return out

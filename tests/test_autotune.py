@@ -102,12 +102,26 @@ def test_forced_config(monkeypatch):
     assert autotune.forced_config() is None
 
 
+def _trie_states(pats):
+    bs = [p.encode() if isinstance(p, str) else bytes(p) for p in pats]
+    return len({p.upper()[:k] for p in bs for k in range(len(p) + 1)})
+
+
 def test_group_patterns_fits_the_automaton_limits():
-    pats = [b"A" * 64] * 300 + [b"ACGT"] * 10
+    import itertools
+    import synth
+    pats = [synth.pattern(64, 50 + i) for i in range(300)] + [b"ACGT"] * 10
     groups = group_patterns(pats)
     assert [i for g in groups for i in g] == list(range(len(pats)))
     for g in groups:
-        assert 1 + sum(len(pats[i]) for i in g) <= MAX_STATES
+        assert _trie_states([pats[i] for i in g]) <= MAX_STATES
     assert len(groups) == 2
     assert group_patterns([b"ACG"] * 5, max_pat=2) == [[0, 1], [2, 3], [4]]
-    assert group_patterns([b"A" * 64] * 256) == [list(range(255)), [255]]
+    # shared prefixes cost nothing: 300 copies of one pattern, one group;
+    # all 4096 6-mers share their prefixes (5461 states), one group
+    assert group_patterns([b"A" * 64] * 300) == [list(range(300))]
+    kmers = ["".join(x) for x in itertools.product("ACGT", repeat=6)]
+    assert group_patterns(kmers) == [list(range(4096))]
+    assert _trie_states(kmers) == 5461
+    assert group_patterns(["acgt", "ACGA"], max_states=6) == [[0, 1]]      # case folded
+    assert group_patterns(["acgt", "ACGA"], max_states=5) == [[0], [1]]

@@ -43,11 +43,14 @@ def _dev(a):
 
 def test_genome_scale_single_pattern_all_positions(gpu):
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     text = synth.genome_text(GENOME_N, 2)
     td = _dev(text)
-    for m, seed in zip((4, 8, 16, 32, 64), (3, 4, 5, 6, 7)):
-        pat = synth.pattern(m, seed)
-        want_c, want_p = oracle.find_brute(text, pat)
+    pats = [synth.pattern(m, seed) for m, seed in zip((4, 8, 16, 32, 64), (3, 4, 5, 6, 7))]
+    with ThreadPoolExecutor(len(pats)) as ex:      # independent window compares
+        wants = list(ex.map(lambda p: oracle.find_brute(text, p), pats))
+    for pat, (want_c, want_p) in zip(pats, wants):
+        m = len(pat)
         c, pos = gpu.find(td, pat)
         assert c == want_c, (m, c, want_c)
         assert np.array_equal(pos.cpu().numpy(), want_p), m
@@ -69,7 +72,7 @@ def test_batched_six_sequences_sampled(gpu):
     b.run()
     got = b.result()
     # the smallest sequence: every pattern
-    want0 = np.array([oracle.count_brute(texts[0], p) for p in pats], dtype=np.uint64)
+    want0 = oracle.multi_count([texts[0]], pats)[0]
     assert np.array_equal(got[0], want0)
     # one pair per sequence, the shortest patterns first (non-zero counts)
     order = np.argsort(lens, kind="stable")
