@@ -175,10 +175,11 @@ def measured_peak_hbm():
 
 
 def kernel_source_digest():
+    """Digest of the single-pattern scan's sources (the kernels dfa_find runs)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1506_08612_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cpp", ".h")):
+        if f in ("scan.cu", "automaton.cpp", "dnadfa_internal.h"):
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(f.encode())
                 h.update(fh.read())
