@@ -201,6 +201,26 @@ int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int6
                   int64_t seg, void* stream);
 
 /*
+ * dfa_find_host for several patterns over one host text: each segment is
+ * copied to the device once (with the m_max - 1 byte overlap of the longest
+ * pattern, Algorithm 1) and every pattern's find runs on it, so the text
+ * crosses the host link once for all patterns.  Blocking.
+ *   tables / npat: 1 <= npat <= 1024 automata (dfa_build).
+ *   h_pos[i] / caps[i]: host buffer for up to caps[i] start positions of
+ *            pattern i (h_pos may be NULL when every cap is 0).
+ *   h_counts: host uint64[npat], the exact counts.
+ *   d_stage / stage_bytes: caller-owned device staging memory of at least
+ *            dfa_host_stage_bytes_multi(seg, caps, npat) bytes; seg >= 1 MiB.
+ * Returns DFA_ETRUNC when some count exceeds its cap (the counts are exact,
+ * the first caps[i] positions valid), DFA_ETIMEOUT if a bounded device wait
+ * gave up, else as dfa_find.
+ */
+int64_t dfa_host_stage_bytes_multi(int64_t seg, const int64_t* caps, int32_t npat);
+int dfa_find_host_multi(const uint8_t* h_text, int64_t n, const dfa_table* const* tables, int32_t npat,
+                        int64_t* const* h_pos, const int64_t* caps, uint64_t* h_counts, void* d_stage,
+                        int64_t stage_bytes, int64_t seg, void* stream);
+
+/*
  * dfa_find for callers that must not allocate device memory.  The paper has
  * no counterpart; this is a library service.  Some callers cannot allocate:
  * code running in a process where another allocator already holds the

@@ -34,7 +34,7 @@ _lib = _native.lib
 
 __all__ = ["Table", "DfaError", "dfa_build", "dfa_free", "dfa_export_stt", "dfa_count",
            "dfa_find", "dfa_find_workspace_bytes", "dfa_table_bytes", "dfa_find_status", "dfa_host_stage_bytes",
-           "dfa_find_host", "dfa_find_noalloc", "MultiTable", "dfa_multi_count", "multi_count",
+           "dfa_find_host", "dfa_find_host_multi", "dfa_host_stage_bytes_multi", "dfa_find_noalloc", "MultiTable", "dfa_multi_count", "multi_count",
            "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
            "DFA_OK", "DFA_EINVAL", "DFA_ETRUNC", "DFA_ETIMEOUT", "DFA_ECUDA", "DFA_EWORKSPACE",
            "DFA_ENOMEM", "DFA_MAX_M"]
@@ -202,6 +202,28 @@ def dfa_find_host(h_text, table: Table, h_positions, stage, seg: int, stream=Non
     if rc not in (DFA_OK, DFA_ETRUNC):
         raise DfaError(rc, "dfa_find_host")
     return rc, int(h.value)
+
+
+def dfa_host_stage_bytes_multi(seg: int, caps) -> int:
+    c = (ctypes.c_int64 * len(caps))(*[int(x) for x in caps])
+    return int(_lib.dfa_host_stage_bytes_multi(int(seg), c, len(caps)))
+
+
+def dfa_find_host_multi(h_text, tables, h_positions, stage, seg: int, stream=None):
+    """Several patterns over one host text, each segment copied once:
+    ``h_positions`` a list of CPU int64 tensors (or None), one per table.
+    Returns (return code, list of counts)."""
+    k = len(tables)
+    caps = [int(p.numel()) if p is not None else 0 for p in h_positions]
+    th = (ctypes.c_void_p * k)(*[t.handle.value for t in tables])
+    ph = (ctypes.c_void_p * k)(*[p.data_ptr() if p is not None and p.numel() else 0 for p in h_positions])
+    cp = (ctypes.c_int64 * k)(*caps)
+    hc = (ctypes.c_uint64 * k)()
+    rc = _lib.dfa_find_host_multi(_ptr(h_text), int(h_text.numel()), th, k, ph, cp, hc, _ptr(stage),
+                                  int(stage.numel()), int(seg), _stream(stream))
+    if rc not in (DFA_OK, DFA_ETRUNC):
+        raise DfaError(rc, "dfa_find_host_multi")
+    return rc, [int(x) for x in hc]
 
 
 # ------------------------------------------------------- many patterns

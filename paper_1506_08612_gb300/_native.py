@@ -40,6 +40,9 @@ def _declare(lib):
         "dfa_find_host": ([vp, i64, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64), vp, i64, i64, vp],
                           ctypes.c_int),
         "dfa_find_noalloc": ([vp, i64, vp, vp, i64, vp, cfgp, vp], ctypes.c_int),
+        "dfa_host_stage_bytes_multi": ([i64, ctypes.POINTER(i64), i32], i64),
+        "dfa_find_host_multi": ([vp, i64, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                 ctypes.POINTER(ctypes.c_uint64), vp, i64, i64, vp], ctypes.c_int),
         "dfa_multi_build": ([ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32), i32, ctypes.POINTER(vp)],
                             ctypes.c_int),
         "dfa_multi_free": ([vp], None),

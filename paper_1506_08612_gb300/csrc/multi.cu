@@ -16,9 +16,12 @@
 // starts of its chunk [s, e), walks from q0 at s through
 // min(e + m_max - 1, n) and keeps pattern p's occurrence ending at j iff it
 // starts before e, i.e. j - m_p + 1 < e; every byte outside ACGTacgt sends
-// the walk back to q0 (Sec. III-B).  Counts go to per-CTA shared-memory
-// counters per pattern and are added to the global per-(sequence, pattern)
-// counts when the CTA moves to another sequence and at its end.
+// the walk back to q0 (Sec. III-B).  Inside the chunk every occurrence is
+// owned, so a step into a state with outputs adds one to that state's
+// shared-memory counter; in the overlap the lengths decide (out of line).
+// When the CTA moves to another sequence, and at its end, each state's count
+// goes to every pattern of its output list in the global per-(sequence,
+// pattern) counts.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,7 +43,7 @@ struct dfa_multi {
     std::vector<uint16_t> out_ids;      // concatenated output lists
     int device = 0;
     void* d_mem = nullptr;
-    int32_t delta_bytes = 0, out1_bytes = 0, off_bytes = 0, ids_bytes = 0, mlen_bytes = 0;
+    int32_t delta_bytes = 0, off_bytes = 0, ids_bytes = 0, mlen_bytes = 0, span_bytes = 0;
     bool owns_mem = true;               // false: d_mem is the caller's (dfa_multi_attach)
     std::vector<uint8_t> img;           // device image, kept until the table is freed
 };
@@ -53,28 +56,27 @@ constexpr int kMultiMaxPat = 8192;       // per-CTA counters: 32 KiB
 
 int round16(int64_t b) { return (int)((b + 15) & ~(int64_t)15); }
 
-constexpr uint32_t kMany = 0xFFFFu;      // out1 entry of a state with 0 or >= 2 outputs
-
 struct MultiArgs {
     const uint8_t* text[kMultiMaxSeq];
     int64_t n[kMultiMaxSeq];
     int64_t tile0[kMultiMaxSeq + 1];     // first tile of each sequence; tile0[nseq] = all tiles
     int32_t nseq, npat, mmax, chunk;
-    int32_t delta_bytes, out1_bytes;     // the parts copied to shared memory
-    const uint8_t* tab;                  // device image: [delta][out1][off][ids][mlen]
-    const uint32_t* off;
+    int32_t nstates;
+    int32_t delta_bytes;                 // the part copied to shared memory
+    const uint8_t* tab;                  // device image: [delta][off][ids][mlen][span]
+    const uint32_t* off;                 // output list of state q: ids[off[q] .. off[q+1])
     const uint16_t* ids;
-    const uint8_t* mlen;
+    const uint8_t* mlen;                 // pattern lengths
+    const uint8_t* span;                 // per state: shortest and longest output length
     unsigned long long* counts;         // [nseq][npat]
 };
 
-__device__ __forceinline__ uint4 ldg16m(const uint4* p)
+// 32 bytes of text (one sector) per load.
+__device__ __forceinline__ void ldg32m(const uint8_t* p, uint4& a, uint4& b)
 {
-    uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+    asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
                  : "l"(p));
-    return v;
 }
 
 // Per byte of x: zero iff the byte is a base (A C G T a c g t).
@@ -84,41 +86,50 @@ __device__ __forceinline__ uint32_t word_bad_m(uint32_t x)
     return ((x ^ (t * 0x11u)) & 0xD9D9D9D9u) ^ 0x41414141u;
 }
 
+// Shared-memory view of one CTA: the transition table and one counter per
+// automaton state (occurrences of every pattern the state outputs, at owned
+// starts); the launch arguments for the rare out-of-line paths.
 struct MultiTab {
-    const uint16_t* delta;   // shared: 4 * state + code -> 4 * next | (out(next) not empty)
-    const uint16_t* out1;    // shared: the one pattern a state outputs, or kMany
-    uint32_t* hist;          // shared: per-pattern counts of this CTA
-    const MultiArgs* args;   // the launch's arguments (output lists in global memory)
+    const uint16_t* delta;   // 4 * state + code -> 4 * next | (out(next) not empty)
+    uint32_t* hs;            // per-state counters
+    const MultiArgs* args;
+    unsigned long long* row; // this sequence's per-pattern global counts
 };
 
-// Outputs of state st at end offset j, one by one from the list
-// (ids[off[st] .. off[st+1])), each kept iff its start j - m_p + 1 lies
-// below own (the chunk's owned starts).
-__device__ __noinline__ void emit_list(const MultiArgs* a, uint32_t* hist, uint32_t st, uint32_t j, uint32_t own)
+// A flagged step in the overlap, d = (end offset) - own + 1 >= 1 bytes past
+// the chunk: an output of length m_p started before the chunk's end (is
+// owned) iff m_p > d.  All of the state's outputs owned: its counter; some:
+// those patterns one by one in global memory.
+__device__ __noinline__ void emit_overlap(const MultiArgs* a, uint32_t* hs, unsigned long long* row, uint32_t st,
+                                          uint32_t d)
 {
-    const uint32_t* off = a->off;
-    const uint32_t k1 = __ldg(off + st + 1);
-    for (uint32_t k = __ldg(off + st); k < k1; k++) {
+    const uint32_t shortest = __ldg(a->span + 2 * st), longest = __ldg(a->span + 2 * st + 1);
+    if (longest <= d) return;
+    if (shortest > d) {
+        atomicAdd(hs + st, 1u);
+        return;
+    }
+    const uint32_t k1 = __ldg(a->off + st + 1);
+    for (uint32_t k = __ldg(a->off + st); k < k1; k++) {
         const uint32_t p = __ldg(a->ids + k);
-        if (j + 1u < own + __ldg(a->mlen + p)) atomicAdd(hist + p, 1u);
+        if (__ldg(a->mlen + p) > d) atomicAdd(row + p, 1ull);
     }
 }
 
-// Entry e has its output flag set: count the patterns ending at j.  A state
-// with one output inside the owned part (every start there is owned) takes
-// the shared-memory fast path.
+// Output flag set on entry e ending at offset j: owned (CHECK false, or
+// j < own) adds one to the state's counter.
+template <bool CHECK>
 __device__ __forceinline__ void emit(const MultiTab& M, uint32_t e, uint32_t j, uint32_t own)
 {
-    const uint32_t st = e >> 2;
-    const uint32_t p = M.out1[st];
-    if (p != kMany && j < own)
-        atomicAdd(M.hist + p, 1u);
+    if (!CHECK || j < own)
+        atomicAdd(M.hs + (e >> 2), 1u);
     else
-        emit_list(M.args, M.hist, st, j, own);
+        emit_overlap(M.args, M.hs, M.row, e >> 2, j - own + 1u);
 }
 
 // Four bases of a word w, byte k ending at offset j + k: four dependent
 // lookups, one test of the output flags.
+template <bool CHECK>
 __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
 {
     const uint32_t c = (w >> 1) & 0x03030303u;
@@ -128,35 +139,40 @@ __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uin
     const uint32_t e3 = M.delta[(e2 & ~3u) | (c >> 24)];
     ent = e3;
     if ((e0 | e1 | e2 | e3) & 1u) {
-        if (e0 & 1u) emit(M, e0, j, own);
-        if (e1 & 1u) emit(M, e1, j + 1, own);
-        if (e2 & 1u) emit(M, e2, j + 2, own);
-        if (e3 & 1u) emit(M, e3, j + 3, own);
+        if (e0 & 1u) emit<CHECK>(M, e0, j, own);
+        if (e1 & 1u) emit<CHECK>(M, e1, j + 1, own);
+        if (e2 & 1u) emit<CHECK>(M, e2, j + 2, own);
+        if (e3 & 1u) emit<CHECK>(M, e3, j + 3, own);
     }
 }
 
-// A word holding bases and non-bases: byte by byte, every non-base resets
-// the walk to q0 (Sec. III-B: columns outside the alphabet lead to q0).
-__device__ __noinline__ uint32_t word_mixed(const MultiTab M, uint32_t ent, uint32_t w, uint32_t j, uint32_t own)
+// One byte, any value: a non-base sends the walk back to q0 (Sec. III-B:
+// columns outside the alphabet lead to q0).
+__device__ __forceinline__ void byte_any(const MultiTab& M, uint32_t& ent, uint32_t b, uint32_t j, uint32_t own)
 {
-    for (int k = 0; k < 4; k++) {
-        const uint32_t b = (w >> (8 * k)) & 0xFFu;
-        const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
-        if (((b ^ (t * 0x11u)) & 0xD9u) == 0x41u) {
-            ent = M.delta[(ent & ~3u) | ((b >> 1) & 3u)];
-            if (ent & 1u) emit(M, ent, j + k, own);
-        } else {
-            ent = 0u;
-        }
+    const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
+    if (((b ^ (t * 0x11u)) & 0xD9u) == 0x41u) {
+        ent = M.delta[(ent & ~3u) | ((b >> 1) & 3u)];
+        if (ent & 1u) emit<true>(M, ent, j, own);
+    } else {
+        ent = 0u;
     }
+}
+
+// A word holding bases and non-bases, byte by byte.
+__device__ __forceinline__ uint32_t word_mixed(const MultiTab& M, uint32_t ent, uint32_t w, uint32_t j, uint32_t own)
+{
+#pragma unroll 1
+    for (int k = 0; k < 4; k++) byte_any(M, ent, (w >> (8 * k)) & 0xFFu, j + k, own);
     return ent;
 }
 
+template <bool CHECK>
 __device__ __forceinline__ void word_any(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
 {
     const uint32_t bad = word_bad_m(w);
     if (bad == 0u) {
-        word_bases(M, ent, w, j, own);
+        word_bases<CHECK>(M, ent, w, j, own);
     } else if (((bad - 0x01010101u) & ~bad & 0x80808080u) == 0u) {
         ent = 0u;                                   // four non-bases (an N block)
     } else {
@@ -164,31 +180,43 @@ __device__ __forceinline__ void word_any(const MultiTab& M, uint32_t& ent, uint3
     }
 }
 
+template <bool CHECK>
+__device__ __forceinline__ void vec_any(const MultiTab& M, uint32_t& ent, uint4 v, uint32_t j, uint32_t own)
+{
+    word_any<CHECK>(M, ent, v.x, j, own);
+    word_any<CHECK>(M, ent, v.y, j + 4, own);
+    word_any<CHECK>(M, ent, v.z, j + 8, own);
+    word_any<CHECK>(M, ent, v.w, j + 12, own);
+}
+
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const __grid_constant__ MultiArgs a)
 {
     extern __shared__ __align__(16) uint8_t msm[];
     {
-        const int bytes = a.delta_bytes + a.out1_bytes;
         const uint4* src = reinterpret_cast<const uint4*>(a.tab);
         uint4* dst = reinterpret_cast<uint4*>(msm);
-        for (int i = threadIdx.x; i < (bytes >> 4); i += THREADS) dst[i] = src[i];
+        for (int i = threadIdx.x; i < (a.delta_bytes >> 4); i += THREADS) dst[i] = src[i];
     }
     MultiTab M;
     M.delta = reinterpret_cast<const uint16_t*>(msm);
-    M.out1 = reinterpret_cast<const uint16_t*>(msm + a.delta_bytes);
-    M.hist = reinterpret_cast<uint32_t*>(msm + a.delta_bytes + a.out1_bytes);
+    M.hs = reinterpret_cast<uint32_t*>(msm + a.delta_bytes);
     M.args = &a;
-    for (int p = threadIdx.x; p < a.npat; p += THREADS) M.hist[p] = 0u;
+    for (int q = threadIdx.x; q < a.nstates; q += THREADS) M.hs[q] = 0u;
     __syncthreads();
 
+    // the per-state counters go to the per-pattern counts of sequence sq:
+    // each pattern of a state's (failure-closed) output list gets its count
     auto flush = [&](int sq) {
         __syncthreads();
-        for (int p = threadIdx.x; p < a.npat; p += THREADS) {
-            const uint32_t v = M.hist[p];
+        unsigned long long* row = a.counts + (int64_t)sq * a.npat;
+        for (int q = threadIdx.x; q < a.nstates; q += THREADS) {
+            const uint32_t v = M.hs[q];
             if (v) {
-                atomicAdd(a.counts + (int64_t)sq * a.npat + p, (unsigned long long)v);
-                M.hist[p] = 0u;
+                M.hs[q] = 0u;
+                const uint32_t k1 = __ldg(a.off + q + 1);
+                for (uint32_t k = __ldg(a.off + q); k < k1; k++)
+                    atomicAdd(row + __ldg(a.ids + k), (unsigned long long)v);
             }
         }
         __syncthreads();
@@ -204,6 +232,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
         if (sq != cur) {
             if (cur >= 0) flush(cur);
             cur = sq;
+            M.row = a.counts + (int64_t)sq * a.npat;
         }
         const int64_t n = a.n[sq];
         const uint8_t* text = a.text[sq];
@@ -213,39 +242,34 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
         const int64_t hi = min(e + (int64_t)a.mmax - 1, n);
         const uint32_t own = (uint32_t)(e - s);
         const uint32_t len = (uint32_t)(hi - s);
+        const uint8_t* base = text + s;
         uint32_t ent = 0u;
-        uint32_t done = 0;
-        if ((((uintptr_t)text) & 15u) == 0 && len >= 16) {
-            // 16-byte vectors, two in flight ahead of the one walked
-            const uint4* p = reinterpret_cast<const uint4*>(text + s);
-            const uint32_t nv = len >> 4;
-            uint4 b0 = ldg16m(p);
-            uint4 b1 = nv > 1 ? ldg16m(p + 1) : b0;
-            uint4 b2 = nv > 2 ? ldg16m(p + 2) : b0;
+        uint32_t j = 0;
+        if ((((uintptr_t)base) & 15u) == 0) {
+            if ((((uintptr_t)base) & 31u) != 0 && len >= 16) {
+                vec_any<true>(M, ent, *reinterpret_cast<const uint4*>(base), 0u, own);
+                j = 16;
+            }
+            // owned 32-byte blocks, the next one in flight while one is walked
+            const uint32_t nb = j < own ? (own - j) >> 5 : 0u;
+            if (nb) {
+                uint4 a0, a1;
+                ldg32m(base + j, a0, a1);
 #pragma unroll 1
-            for (uint32_t g = 0; g < nv; g++) {
-                const uint4 v = b0;
-                b0 = b1;
-                b1 = b2;
-                if (g + 3 < nv) b2 = ldg16m(p + g + 3);
-                const uint32_t j = 16u * g;
-                word_any(M, ent, v.x, j, own);
-                word_any(M, ent, v.y, j + 4, own);
-                word_any(M, ent, v.z, j + 8, own);
-                word_any(M, ent, v.w, j + 12, own);
+                for (uint32_t g = 0; g < nb; g++) {
+                    const uint4 c0 = a0, c1 = a1;
+                    if (g + 1 < nb) ldg32m(base + j + 32 * (g + 1), a0, a1);
+                    const uint32_t jj = j + 32u * g;
+                    vec_any<false>(M, ent, c0, jj, own);
+                    vec_any<false>(M, ent, c1, jj + 16, own);
+                }
+                j += nb << 5;
             }
-            done = nv << 4;
+            // the rest of the chunk and its overlap, 16 bytes at a time
+            for (; j + 16 <= len; j += 16)
+                vec_any<true>(M, ent, *reinterpret_cast<const uint4*>(base + j), j, own);
         }
-        for (uint32_t j = done; j < len; j++) {
-            const uint32_t b = text[s + j];
-            const uint32_t tt = (b >> 2) & ~(b >> 1) & 1u;
-            if (((b ^ (tt * 0x11u)) & 0xD9u) == 0x41u) {
-                ent = M.delta[(ent & ~3u) | ((b >> 1) & 3u)];
-                if (ent & 1u) emit(M, ent, j, own);
-            } else {
-                ent = 0u;
-            }
-        }
+        for (; j < len; j++) byte_any(M, ent, base[j], j, own);
     }
     if (cur >= 0) flush(cur);
 }
@@ -340,28 +364,36 @@ int dfa_multi_build_host(const char* const* patterns, const int32_t* lengths, in
         t->out_ids.insert(t->out_ids.end(), outs[u].begin(), outs[u].end());
     }
     // device image: [delta][out_off][out_ids][mlen], 16-byte aligned parts
-    // out1[q]: the pattern of a state with exactly one output, else kMany
-    std::vector<uint16_t> out1(S, (uint16_t)kMany);
-    for (int i = 0; i < S; i++)
-        if (t->out_off[i + 1] - t->out_off[i] == 1) out1[i] = t->out_ids[t->out_off[i]];
+    // span[q]: the shortest and longest length among the state's outputs
+    std::vector<uint8_t> span((size_t)S * 2, 0);
+    for (int i = 0; i < S; i++) {
+        uint32_t lo = 255, hi = 0;
+        for (uint32_t k = t->out_off[i]; k < t->out_off[i + 1]; k++) {
+            lo = std::min<uint32_t>(lo, t->mlen[t->out_ids[k]]);
+            hi = std::max<uint32_t>(hi, t->mlen[t->out_ids[k]]);
+        }
+        span[2 * i] = (uint8_t)(hi ? lo : 0);
+        span[2 * i + 1] = (uint8_t)hi;
+    }
     t->delta_bytes = round16((int64_t)S * 4 * 2);
-    t->out1_bytes = round16((int64_t)S * 2);
     t->off_bytes = round16((int64_t)(S + 1) * 4);
     t->ids_bytes = round16((int64_t)std::max<size_t>(t->out_ids.size(), 1) * 2);
     t->mlen_bytes = round16(npat);
-    const size_t bytes = (size_t)t->delta_bytes + t->out1_bytes + t->off_bytes + t->ids_bytes + t->mlen_bytes;
+    t->span_bytes = round16((int64_t)S * 2);
+    const size_t bytes =
+        (size_t)t->delta_bytes + t->off_bytes + t->ids_bytes + t->mlen_bytes + t->span_bytes;
     std::vector<uint8_t>& img = t->img;
     img.assign(bytes, 0);
     uint8_t* q = img.data();
     memcpy(q, t->delta.data(), t->delta.size() * 2);
     q += t->delta_bytes;
-    memcpy(q, out1.data(), out1.size() * 2);
-    q += t->out1_bytes;
     memcpy(q, t->out_off.data(), t->out_off.size() * 4);
     q += t->off_bytes;
     if (!t->out_ids.empty()) memcpy(q, t->out_ids.data(), t->out_ids.size() * 2);
     q += t->ids_bytes;
     memcpy(q, t->mlen.data(), npat);
+    q += t->mlen_bytes;
+    memcpy(q, span.data(), span.size());
     t->owns_mem = false;
     *out = t;
     return DFA_OK;
@@ -429,7 +461,7 @@ int dfa_multi_export(const dfa_multi* t, int32_t* h_next, int32_t* h_nout, int64
 int64_t dfa_multi_smem_bytes(const dfa_multi* t)
 {
     if (!t) return -1;
-    return (int64_t)t->delta_bytes + t->out1_bytes + (int64_t)t->npat * 4;
+    return (int64_t)t->delta_bytes + (int64_t)t->nstates * 4;
 }
 
 int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32_t nseq, const dfa_multi* t,
@@ -461,11 +493,12 @@ int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32
     a.mmax = t->mmax;
     a.chunk = chunk;
     a.delta_bytes = t->delta_bytes;
-    a.out1_bytes = t->out1_bytes;
+    a.nstates = t->nstates;
     a.tab = static_cast<const uint8_t*>(t->d_mem);
-    a.off = reinterpret_cast<const uint32_t*>(a.tab + t->delta_bytes + t->out1_bytes);
-    a.ids = reinterpret_cast<const uint16_t*>(a.tab + t->delta_bytes + t->out1_bytes + t->off_bytes);
-    a.mlen = a.tab + t->delta_bytes + t->out1_bytes + t->off_bytes + t->ids_bytes;
+    a.off = reinterpret_cast<const uint32_t*>(a.tab + t->delta_bytes);
+    a.ids = reinterpret_cast<const uint16_t*>(a.tab + t->delta_bytes + t->off_bytes);
+    a.mlen = a.tab + t->delta_bytes + t->off_bytes + t->ids_bytes;
+    a.span = a.mlen + t->mlen_bytes;
     a.counts = reinterpret_cast<unsigned long long*>(d_counts);
     if ((err = cudaMemsetAsync(d_counts, 0, (size_t)nseq * t->npat * 8, st)) != cudaSuccess)
         return multi_fail("dfa_multi_count", err);

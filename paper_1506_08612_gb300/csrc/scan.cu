@@ -408,6 +408,49 @@ struct Walker {
         }
     }
 
+    // vec4_map of a dense pattern (m <= 8) without the up-front base test:
+    // the words are walked through their 2-bit codes alone (a relaxed walk:
+    // a non-base is read as the base with its code), which never misses an
+    // exact accept (see relaxed_words).  The relaxed state equals the exact
+    // one whenever the last 8 >= m bytes are bases: both are then the longest
+    // suffix within those bytes that is a prefix of P.  So a stage whose
+    // relaxed walk accepts nothing has no accept, and a stage that accepted
+    // is exact when it and the 8 bytes before it are bases (the caller tests
+    // that and then calls put_map, else walks the stage exactly).  Returns the
+    // 64-bit map of relaxed accept ends (bit j: end r + j).
+    __device__ __forceinline__ uint2 vec4_relaxed_map(uint4 v0, uint4 v1, uint4 v2, uint4 v3)
+    {
+        const uint32_t x[16] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w,
+                                v2.x, v2.y, v2.z, v2.w, v3.x, v3.y, v3.z, v3.w};
+        uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            e = k4_next<LAYOUT>(T.k4, e, x[k]);
+            const uint32_t acc = e & (0xFu << K4_ACC_SHIFT);
+            const int sh = 4 * (k & 7) - (int)K4_ACC_SHIFT;
+            const uint32_t a = sh >= 0 ? acc << (sh & 31) : acc >> ((-sh) & 31);
+            if (k < 8) lo |= a; else hi |= a;
+        }
+        return make_uint2(lo, hi);
+    }
+
+    // Count and record a map of accept ends (bit j: end r + j).
+    __device__ __forceinline__ void put_map(uint2 map, uint32_t r)
+    {
+        uint32_t lo = map.x, hi = map.y;
+        cnt += __popc(lo) + __popc(hi);
+        if (Sink::kRecord) {
+            while (lo) {
+                sink.put(r + (uint32_t)(__ffs(lo) - 1));
+                lo &= lo - 1u;
+            }
+            while (hi) {
+                sink.put(r + 32u + (uint32_t)(__ffs(hi) - 1));
+                hi &= hi - 1u;
+            }
+        }
+    }
+
     __device__ __forceinline__ void vec(uint4 v, uint32_t r, uint32_t lim)
     {
         if (LAYOUT == kLayoutK4S) {
@@ -737,6 +780,7 @@ constexpr int kTicketRing = 8;
 // (TmaArgs::ahead).  Counting uses a static schedule and runs a full ring
 // ahead.
 constexpr int kDenseMaxM = 6;                     // patterns this short record inline
+static_assert(kDenseMaxM <= 8, "the relaxed dense walk settles the exact state from the last 8 bytes");
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
 struct TmaArgs {
@@ -939,6 +983,34 @@ __device__ __noinline__ uint32_t replay_halo(SmemTab T, uint32_t slots, uint32_t
     if (m > 33) hr.vec(lds128_fresh(rp + (ob ^ 32u)), C + 32, lim);
     if (m > 49) hr.vec(lds128_fresh(rp + (ob ^ 48u)), C + 48, lim);
     return ss.n;
+}
+
+// The exact state after the 8 bytes of (p0, p1), walked from q0; for a
+// pattern of m <= 8 it is the exact state after any text ending in them.
+__device__ __forceinline__ uint32_t exact_state8(const SmemTab& T, uint32_t p0, uint32_t p1)
+{
+    uint32_t q = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) q = byte_next(T.d1, q, (p0 >> (8 * i)) & 0xFFu);
+#pragma unroll
+    for (int i = 0; i < 4; i++) q = byte_next(T.d1, q, (p1 >> (8 * i)) & 0xFFu);
+    return q;
+}
+
+// A dense pattern's stage that the relaxed walk could not settle (an accept
+// near a non-base): walked again exactly from the exact state at its start
+// (q0 at the row start, r == 0; else the state the 8 bytes before it give),
+// its accepts recorded.  Returns (accepts, slots used, exact end state).
+template <int LAYOUT, uint32_t CAP>
+__device__ __forceinline__ uint4 redo_stage_exact(const SmemTab& T, uint32_t slots, uint32_t n, uint32_t p0, uint32_t p1,
+                                               const uint8_t* rp, uint32_t ob, uint32_t r)
+{
+    const uint32_t q = r != 0u ? exact_state8(T, p0, p1) : 0u;
+    RowSlots<CAP> ss{slots, n};
+    Walker<LAYOUT, false, RowSlots<CAP>> w{T, ss, q, 0u};
+    w.vec4(lds128_fresh(rp + ob), lds128_fresh(rp + (ob ^ 16u)), lds128_fresh(rp + (ob ^ 32u)),
+           lds128_fresh(rp + (ob ^ 48u)), r);
+    return make_uint4(w.cnt, ss.n, w.e, 0u);
 }
 
 template <int LAYOUT, class Sink>
@@ -1311,6 +1383,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
         bool ok[kRPL];
         uint32_t e[kRPL], cnt[kRPL];
         uint64_t fmask[kRPL];                     // relaxed walks: stages to replay exactly
+        uint32_t tl0[kRPL], tl1[kRPL];            // dense finds: the row's last 8 bytes walked
         RowSlots<KS> ss[kRPL];
 #pragma unroll
         for (int i = 0; i < kRPL; i++) {
@@ -1321,6 +1394,8 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
             e[i] = 0;
             cnt[i] = 0;
             fmask[i] = 0;
+            tl0[i] = 0x41414141u;                 // no byte before the row start: bases
+            tl1[i] = 0x41414141u;
             ss[i] = RowSlots<KS>{slots_sa + (uint32_t)(((uint32_t)kb * KS * kRows + wrow0 + 32 * i) * 2), 0u};
         }
         for (uint32_t s = 0; s < spt; s++) {
@@ -1355,10 +1430,36 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                     for (int i = 0; i < kRPL; i++) {
                         if (!ok[i]) continue;
                         Walker<LAYOUT, false, RowSlots<KS>> wd{T, ss[i], e[i], cnt[i]};
-                        if (LAYOUT == kLayoutK4)
-                            wd.vec4_map(v[i][0], v[i][1], v[i][2], v[i][3], r);
-                        else
+                        if (LAYOUT == kLayoutK4) {
+                            const uint32_t p0 = tl0[i], p1 = tl1[i];
+                            tl0[i] = v[i][3].z;
+                            tl1[i] = v[i][3].w;
+                            const uint2 map = wd.vec4_relaxed_map(v[i][0], v[i][1], v[i][2], v[i][3]);
+                            if ((map.x | map.y) != 0u) {
+                                // accepts: exact if the stage (read again from its
+                                // slot) and the 8 bytes before it are bases
+                                const uint8_t* q = rp + i * 32 * kStageW;
+                                const uint4 w0 = lds128_fresh(q + ob), w1 = lds128_fresh(q + (ob ^ 16u)),
+                                            w2 = lds128_fresh(q + (ob ^ 32u)), w3 = lds128_fresh(q + (ob ^ 48u));
+                                const uint32_t bad =
+                                    word_bad(p0) | word_bad(p1) | word_bad(w0.x) | word_bad(w0.y) |
+                                    word_bad(w0.z) | word_bad(w0.w) | word_bad(w1.x) | word_bad(w1.y) |
+                                    word_bad(w1.z) | word_bad(w1.w) | word_bad(w2.x) | word_bad(w2.y) |
+                                    word_bad(w2.z) | word_bad(w2.w) | word_bad(w3.x) | word_bad(w3.y) |
+                                    word_bad(w3.z) | word_bad(w3.w);
+                                if (bad == 0u) {
+                                    wd.put_map(map, r);
+                                } else {
+                                    const uint4 rr = redo_stage_exact<LAYOUT, KS>(T, ss[i].base, ss[i].n, p0, p1,
+                                                                                  q, ob, r);
+                                    wd.cnt += rr.x;
+                                    ss[i].n = rr.y;
+                                    wd.e = rr.z;
+                                }
+                            }
+                        } else {
                             wd.vec4(v[i][0], v[i][1], v[i][2], v[i][3], r);
+                        }
                         e[i] = wd.e;
                         cnt[i] = wd.cnt;
                     }
@@ -1403,6 +1504,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                         }
                         fmask[i] |= (uint64_t)(flag != 0u) << s;
                     } else if (FIND && INLINE_REC) {
+                        // the relaxed walk's state is exact unless the last 8
+                        // bytes hold a non-base (vec4_map_relaxed)
+                        if (LAYOUT == kLayoutK4 && (word_bad(tl0[i]) | word_bad(tl1[i])) != 0u)
+                            e[i] = exact_state8(T, tl0[i], tl1[i]);
                         Walker<LAYOUT, true, RowSlots<KS>> h{T, ss[i], e[i], cnt[i]};
                         h.vec(h0, (uint32_t)C, lim);
                         if (m > 17) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 16u)), (uint32_t)C + 16, lim);
@@ -2086,6 +2191,14 @@ int set_last_error(int code, const char* msg)
 }
 }  // namespace dnadfa
 
+namespace {
+// acc |= the status word of a find's workspace (its bounded waits).
+__global__ void k_or_status(const unsigned long long* work, unsigned long long* acc)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *acc |= work[1];
+}
+}  // namespace
+
 // ==================================================================== C ABI
 
 namespace {
@@ -2367,6 +2480,124 @@ int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int6
     if (hdr[1]) return DFA_ETIMEOUT;
     if ((int64_t)cnt > cap) return DFA_ETRUNC;
     return DFA_OK;
+}
+
+// Segmented host path for several patterns: [2 segment buffers][positions
+// of each pattern][2 counters per pattern][status accumulator][workspace]
+static int64_t stage_layout_multi(int64_t seg, const int64_t* caps, int32_t npat, int64_t* seg_stride,
+                                  int64_t* pos_off, int64_t* cnt_off, int64_t* work_off)
+{
+    *seg_stride = (seg + DFA_MAX_M + 255) & ~(int64_t)255;
+    int64_t o = 2 * *seg_stride;
+    for (int32_t i = 0; i < npat; i++) {
+        if (pos_off) pos_off[i] = o;
+        o += (caps[i] * 8 + 255) & ~(int64_t)255;
+    }
+    *cnt_off = o;
+    o += ((int64_t)npat * 16 + 8 + 255) & ~(int64_t)255;
+    *work_off = o;
+    return o + dfa_find_workspace_bytes(seg, nullptr);
+}
+
+constexpr int32_t kHostMaxPat = 1024;
+
+int64_t dfa_host_stage_bytes_multi(int64_t seg, const int64_t* caps, int32_t npat)
+{
+    if (seg < (1 << 20) || !caps || npat < 1 || npat > kHostMaxPat) return -1;
+    for (int32_t i = 0; i < npat; i++)
+        if (caps[i] < 0) return -1;
+    int64_t a, c, d;
+    return stage_layout_multi(seg, caps, npat, &a, nullptr, &c, &d);
+}
+
+int dfa_find_host_multi(const uint8_t* h_text, int64_t n, const dfa_table* const* tables, int32_t npat,
+                        int64_t* const* h_pos, const int64_t* caps, uint64_t* h_counts, void* d_stage,
+                        int64_t stage_bytes, int64_t seg, void* stream)
+{
+    if (!tables || !caps || !h_counts || !d_stage || npat < 1 || npat > kHostMaxPat || n < 0 ||
+        (n > 0 && !h_text) || seg < (1 << 20))
+        return DFA_EINVAL;
+    int mmax = 1;
+    for (int32_t i = 0; i < npat; i++) {
+        if (!tables[i] || caps[i] < 0 || (caps[i] > 0 && (!h_pos || !h_pos[i]))) return DFA_EINVAL;
+        mmax = std::max(mmax, (int)tables[i]->m);
+    }
+    std::vector<int64_t> pos_off(npat);
+    int64_t seg_stride, cnt_off, work_off;
+    const int64_t need = stage_layout_multi(seg, caps, npat, &seg_stride, pos_off.data(), &cnt_off, &work_off);
+    if (stage_bytes < need) return DFA_EWORKSPACE;
+    uint8_t* stage = static_cast<uint8_t*>(d_stage);
+    uint64_t* d_cnt = reinterpret_cast<uint64_t*>(stage + cnt_off);   // 2 per pattern, then the status
+    unsigned long long* d_status = reinterpret_cast<unsigned long long*>(d_cnt + 2 * npat);
+    void* d_work = stage + work_off;
+    const int64_t work_bytes = stage_bytes - work_off;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    cudaStream_t cp;
+    cudaEvent_t copied[2], scanned[2];
+    if (cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking) != cudaSuccess) return DFA_ECUDA;
+    int rc = DFA_OK;
+    for (int i = 0; i < 2; i++) {
+        cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&scanned[i], cudaEventDisableTiming);
+    }
+    if (cudaMemsetAsync(d_cnt, 0, (size_t)npat * 16 + 8, st) != cudaSuccess) rc = DFA_ECUDA;
+    cudaEventRecord(scanned[1], st);
+    cudaEventRecord(scanned[0], st);
+    const int64_t nseg = n > 0 ? (n + seg - 1) / seg : 0;
+    for (int64_t k = 0; k < nseg && rc == DFA_OK; k++) {
+        const int b = (int)(k & 1);
+        const int64_t lo = k * seg;
+        const int64_t own = std::min(seg, n - lo);
+        const int64_t avail = std::min(own + mmax - 1, n - lo);
+        uint8_t* buf = stage + b * seg_stride;
+        // one copy of the segment (with the longest pattern's overlap) for
+        // every pattern; buffer b was last read by the scans of segment k-2
+        if (cudaStreamWaitEvent(cp, scanned[b], 0) != cudaSuccess ||
+            cudaMemcpyAsync(buf, h_text + lo, (size_t)avail, cudaMemcpyHostToDevice, cp) != cudaSuccess ||
+            cudaEventRecord(copied[b], cp) != cudaSuccess || cudaStreamWaitEvent(st, copied[b], 0) != cudaSuccess) {
+            rc = DFA_ECUDA;
+            break;
+        }
+        for (int32_t i = 0; i < npat && rc == DFA_OK; i++) {
+            uint64_t* ci = d_cnt + 2 * i;
+            const uint64_t* base = ci + ((k + 1) & 1);       // this pattern's running total
+            int64_t* d_pos = caps[i] > 0 ? reinterpret_cast<int64_t*>(stage + pos_off[i]) : nullptr;
+            rc = launch_find(buf, avail, own, tables[i], d_pos, caps[i], ci + (k & 1), k ? base : nullptr, lo,
+                             d_work, work_bytes, nullptr, st);
+            if (rc == DFA_OK) {
+                k_or_status<<<1, 32, 0, st>>>(static_cast<const unsigned long long*>(d_work), d_status);
+                if (cudaGetLastError() != cudaSuccess) rc = DFA_ECUDA;
+            }
+        }
+        if (rc == DFA_OK && cudaEventRecord(scanned[b], st) != cudaSuccess) rc = DFA_ECUDA;
+    }
+    std::vector<unsigned long long> hc((size_t)npat * 2 + 1, 0);
+    if (rc == DFA_OK) {
+        if (cudaMemcpyAsync(hc.data(), d_cnt, hc.size() * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = DFA_ECUDA;
+    }
+    bool trunc = false;
+    for (int32_t i = 0; rc == DFA_OK && i < npat; i++) {
+        const uint64_t c = nseg ? hc[2 * i + ((nseg - 1) & 1)] : 0;
+        h_counts[i] = c;
+        trunc |= (int64_t)c > caps[i];
+        const int64_t kk = std::min<int64_t>((int64_t)c, caps[i]);
+        if (kk > 0 && cudaMemcpyAsync(h_pos[i], stage + pos_off[i], (size_t)kk * 8, cudaMemcpyDeviceToHost, st) !=
+                          cudaSuccess)
+            rc = DFA_ECUDA;
+    }
+    if (rc == DFA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = DFA_ECUDA;
+    cudaStreamSynchronize(cp);
+    for (int i = 0; i < 2; i++) {
+        cudaEventDestroy(copied[i]);
+        cudaEventDestroy(scanned[i]);
+    }
+    cudaStreamDestroy(cp);
+    if (rc != DFA_OK) return rc;
+    if (hc[(size_t)npat * 2]) return DFA_ETIMEOUT;
+    return trunc ? DFA_ETRUNC : DFA_OK;
 }
 
 const char* dfa_strerror(int code)

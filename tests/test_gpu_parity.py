@@ -201,6 +201,37 @@ def test_host_buffer_path(gpu):
             assert np.array_equal(hp[:c].numpy(), want_p)
 
 
+def test_host_buffer_path_many_patterns(gpu):
+    # one copy of each segment serves every pattern; occurrences of the long
+    # patterns planted across segment borders, small caps truncate
+    import torch
+    n = 6_000_011
+    t = synth.genome_text(n, 19)
+    pats = [synth.pattern(m, 190 + m) for m in (4, 7, 8, 16, 33, 64)]
+    for p in pats[3:]:
+        at = [k * (1 << 20) - len(p) // 2 for k in range(1, 6)] + list(synth.uniform_ints(40, n - len(p), len(p)))
+        synth.plant(t, p, at)
+    ht = torch.from_numpy(t).pin_memory()
+    want = [oracle.find_brute(t, p) for p in pats]
+    tabs = [gpu.dfa_build(p) for p in pats]
+    for seg in (1 << 20, (1 << 20) + 16 * 1000 + 7):
+        caps = [c + 3 for c, _ in want]
+        hps = [torch.full((c,), -1, dtype=torch.int64) for c in caps]
+        stage = torch.empty(gpu.dfa_host_stage_bytes_multi(seg, caps), dtype=torch.uint8, device="cuda")
+        rc, cs = gpu.dfa_find_host_multi(ht, tabs, hps, stage, seg)
+        assert rc == gpu.DFA_OK
+        for (wc, wp), c, hp in zip(want, cs, hps):
+            assert c == wc and np.array_equal(hp[:c].numpy(), wp)
+    # truncation: the counts stay exact, the first cap positions are valid
+    caps = [max(c // 2, 1) for c, _ in want]
+    hps = [torch.zeros(c, dtype=torch.int64) for c in caps]
+    stage = torch.empty(gpu.dfa_host_stage_bytes_multi(1 << 20, caps), dtype=torch.uint8, device="cuda")
+    rc, cs = gpu.dfa_find_host_multi(ht, tabs, hps, stage, 1 << 20)
+    assert rc == gpu.DFA_ETRUNC
+    for (wc, wp), c, hp, cap in zip(want, cs, hps, caps):
+        assert c == wc and np.array_equal(hp.numpy()[:min(c, cap)], wp[:cap])
+
+
 def test_streams_and_concurrency(gpu):
     import torch
     t = synth.genome_text(2_000_000, 13)
@@ -260,6 +291,49 @@ def test_relaxed_walk_decoys(gpu, cfg):
             if (b // step) % 5 == 0:
                 t[st + m + 3:st + 2 * m + 3] = np.frombuffer(pat, np.uint8)
         assert _check(gpu, t, pat, cfg) > 0
+
+
+@pytest.mark.parametrize("cfg", [None, dict(loader=2, layout=1, chunk=128), dict(loader=2, layout=1, chunk=1280)])
+def test_dense_relaxed_decoys(gpu, cfg):
+    # short (dense) patterns walk by codes alone and test only the stages
+    # that accepted: decoys (one byte swapped for a non-base of the same code)
+    # ending in every stage and row, true copies right after a non-base that
+    # sits in the 8 bytes before a stage, and non-bases in a row's last bytes
+    # before its overlap
+    chunk = 128 if cfg is None else cfg["chunk"]
+    n = 512 * chunk * 3 + 4099
+    for m in (1, 2, 3, 4, 5, 6):
+        t = synth.genome_text(n, 140 + m, n_gap_mean=0)
+        pat = synth.pattern(m, 1900 + m)
+        codes = [(c >> 1) & 3 for c in pat]
+        rnd = synth.uniform_ints(6 * (n // 64) + 10, 1 << 30, 170 + m)
+        k = 0
+        for b in range(64, n - 80, 64):
+            kind = int(rnd[k] % 3); k += 1
+            if kind == 0:                              # a decoy ending near the border
+                st = b - int(rnd[k] % (m + 2)); k += 1
+                dec = bytearray(pat)
+                j = int(rnd[k] % m); k += 1
+                alts = _same_code_nonbases(codes[j])
+                dec[j] = alts[int(rnd[k] % len(alts))]; k += 1
+                t[st:st + m] = np.frombuffer(bytes(dec), np.uint8)
+            elif kind == 1:                            # a non-base shortly before a true copy
+                d = 1 + int(rnd[k] % 8); k += 1
+                t[b:b + m] = np.frombuffer(pat, np.uint8)
+                t[b - d] = _same_code_nonbases(int(rnd[k] % 4))[0]; k += 1
+            else:                                      # a true copy across the border
+                st = b - int(rnd[k] % m) if m > 1 else b; k += 1
+                t[st:st + m] = np.frombuffer(pat, np.uint8)
+        assert _check(gpu, t, pat, cfg) > 0
+
+
+def test_dense_patterns_on_nonbase_runs(gpu):
+    # N reads as G by its code: dense patterns of G's meet runs of N
+    n = 1_000_003
+    t = synth.genome_text(n, 78, n_gap_mean=2_000, n_run_mean=300)
+    for pat in (b"G", b"GG", b"GGGG", b"GGGGGG", b"AGGGG", b"GGGGT", b"CGG"):
+        for cfg in (None, dict(loader=2, layout=1, chunk=128), dict(loader=2, layout=1, chunk=640)):
+            _check(gpu, t, pat, cfg)
 
 
 def test_relaxed_walk_nonbase_runs(gpu):
