@@ -201,6 +201,23 @@ int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int6
                   int64_t seg, void* stream);
 
 /*
+ * dfa_find of several patterns over one device text (Algorithm 1's output
+ * for each): the finds run one after another on `stream`, sharing the one
+ * workspace d_work (at least dfa_find_workspace_bytes(n, cfg) bytes).
+ *   tables / npat: 1 <= npat <= 1024 automata.
+ *   d_pos[i] / caps[i]: device buffer for up to caps[i] start positions of
+ *            pattern i (d_pos may be NULL when every cap is 0).
+ *   d_counts: device uint64[npat], overwritten with the exact counts;
+ *            pattern i is truncated when d_counts[i] > caps[i].
+ * A bounded wait that gave up sets bit 63 of that pattern's count
+ * (DFA_COUNT_FAILED).  Asynchronous; allocates nothing.
+ * Errors: DFA_EINVAL, DFA_EWORKSPACE, DFA_ECUDA.
+ */
+int dfa_find_batched(const uint8_t* d_text, int64_t n, const dfa_table* const* tables, int32_t npat,
+                     int64_t* const* d_pos, const int64_t* caps, uint64_t* d_counts, void* d_work,
+                     int64_t work_bytes, const dfa_config* cfg, void* stream);
+
+/*
  * dfa_find_host for several patterns over one host text: each segment is
  * copied to the device once (with the m_max - 1 byte overlap of the longest
  * pattern, Algorithm 1) and every pattern's find runs on it, so the text
@@ -325,6 +342,19 @@ int64_t dfa_multi_smem_bytes(const dfa_multi* table);
 int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32_t nseq,
                     const dfa_multi* table, uint64_t* d_counts, const dfa_config* cfg,
                     void* stream);
+
+/*
+ * Diagnostics for failure detection (no counterpart in the paper): enqueue
+ * one warp that runs dfa_find's ordered-compaction look-back for tile
+ * `tile` (>= 1) on the workspace d_work (at least 8 * (2 + tile + 1)
+ * bytes).  It waits for tiles tile-1, tile-2, ... to publish their
+ * descriptors; on a zeroed workspace nothing ever publishes them, so every
+ * wait gives up after its bound (about two seconds), records the failure in
+ * the workspace's status word and returns.  dfa_find_status(d_work, ...)
+ * then reports DFA_ETIMEOUT, and the device stays usable.
+ * Errors: DFA_EINVAL, DFA_ECUDA.
+ */
+int dfa_debug_wait_timeout(void* d_work, int64_t work_bytes, int64_t tile, void* stream);
 
 /* Static text for a return code. */
 const char* dfa_strerror(int code);

@@ -34,7 +34,7 @@ _lib = _native.lib
 
 __all__ = ["Table", "DfaError", "dfa_build", "dfa_free", "dfa_export_stt", "dfa_count",
            "dfa_find", "dfa_find_workspace_bytes", "dfa_table_bytes", "dfa_find_status", "dfa_host_stage_bytes",
-           "dfa_find_host", "dfa_find_host_multi", "dfa_host_stage_bytes_multi", "dfa_find_noalloc", "MultiTable", "dfa_multi_count", "multi_count",
+           "dfa_find_host", "dfa_find_host_multi", "dfa_find_batched", "dfa_debug_wait_timeout", "dfa_host_stage_bytes_multi", "dfa_find_noalloc", "MultiTable", "dfa_multi_count", "multi_count",
            "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
            "DFA_OK", "DFA_EINVAL", "DFA_ETRUNC", "DFA_ETIMEOUT", "DFA_ECUDA", "DFA_EWORKSPACE",
            "DFA_ENOMEM", "DFA_MAX_M"]
@@ -185,6 +185,14 @@ def dfa_find_noalloc(text, table: Table, positions, count, cfg=None, stream=None
         raise err
 
 
+def dfa_debug_wait_timeout(workspace, tile: int, stream=None) -> None:
+    """Enqueue the look-back wait of ``tile`` on ``workspace`` (failure
+    detection test: on a zeroed workspace the wait gives up and
+    dfa_find_status reports DFA_ETIMEOUT)."""
+    _check(_lib.dfa_debug_wait_timeout(_ptr(workspace), int(workspace.numel() * workspace.element_size()),
+                                       int(tile), _stream(stream)), "dfa_debug_wait_timeout")
+
+
 def dfa_host_stage_bytes(seg: int, cap: int) -> int:
     return int(_lib.dfa_host_stage_bytes(int(seg), int(cap)))
 
@@ -202,6 +210,19 @@ def dfa_find_host(h_text, table: Table, h_positions, stage, seg: int, stream=Non
     if rc not in (DFA_OK, DFA_ETRUNC):
         raise DfaError(rc, "dfa_find_host")
     return rc, int(h.value)
+
+
+def dfa_find_batched(text, tables, positions, counts, workspace, cfg=None, stream=None) -> None:
+    """Enqueue the finds of several patterns over one device text:
+    ``positions`` a list of int64 device tensors (capacity = length, or
+    None), ``counts`` an int64 device tensor of len(tables)."""
+    k = len(tables)
+    th = (ctypes.c_void_p * k)(*[t.handle.value for t in tables])
+    ph = (ctypes.c_void_p * k)(*[p.data_ptr() if p is not None and p.numel() else 0 for p in positions])
+    cp = (ctypes.c_int64 * k)(*[int(p.numel()) if p is not None else 0 for p in positions])
+    _check(_lib.dfa_find_batched(_ptr(text), int(text.numel()), th, k, ph, cp, _ptr(counts), _ptr(workspace),
+                                 int(workspace.numel() * workspace.element_size()), _cfg(cfg), _stream(stream)),
+           "dfa_find_batched")
 
 
 def dfa_host_stage_bytes_multi(seg: int, caps) -> int:

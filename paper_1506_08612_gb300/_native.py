@@ -40,6 +40,8 @@ def _declare(lib):
         "dfa_find_host": ([vp, i64, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64), vp, i64, i64, vp],
                           ctypes.c_int),
         "dfa_find_noalloc": ([vp, i64, vp, vp, i64, vp, cfgp, vp], ctypes.c_int),
+        "dfa_find_batched": ([vp, i64, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64), vp,
+                              vp, i64, cfgp, vp], ctypes.c_int),
         "dfa_host_stage_bytes_multi": ([i64, ctypes.POINTER(i64), i32], i64),
         "dfa_find_host_multi": ([vp, i64, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                  ctypes.POINTER(ctypes.c_uint64), vp, i64, i64, vp], ctypes.c_int),
@@ -54,6 +56,7 @@ def _declare(lib):
         "dfa_multi_export": ([vp, vp, vp, i64], ctypes.c_int),
         "dfa_multi_smem_bytes": ([vp], i64),
         "dfa_multi_count": ([ctypes.POINTER(vp), ctypes.POINTER(i64), i32, vp, vp, cfgp, vp], ctypes.c_int),
+        "dfa_debug_wait_timeout": ([vp, i64, i64, vp], ctypes.c_int),
         "dfa_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "dfa_version": ([], ctypes.c_char_p),
         "dfa_last_error": ([], ctypes.c_char_p),

@@ -799,6 +799,9 @@ struct TmaArgs {
     // every tile's total (added up) go here; null otherwise
     uint16_t* rows;
     unsigned long long* tile_sum;
+    // and, for every row with a count, the stages holding its exact accepts
+    // (bit s: body stage s; bit sps: the overlap; all ones: walk the row)
+    unsigned long long* masks;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -1064,11 +1067,13 @@ __device__ __forceinline__ uint32_t relaxed_mask(uint32_t m)
 // stage is walked from q0 at the previous 64 bytes of the row (from the row
 // start for stage 0).  Every byte is read again from global memory, where
 // the tile was just streamed from.  With REC the accepts go to the row's
-// slots (base, n), in ascending order.  Returns (count, n).
+// slots (base, n), in ascending order.  Returns (count, n, and the mask of
+// the stages that hold exact accepts in .z (bits 0..31) and .w (32..63)).
 template <int LAYOUT, bool REC>
-__device__ __noinline__ uint2 replay_row(const ScanArgs* a, int64_t rs, uint32_t sps, uint64_t mask,
+__device__ __noinline__ uint4 replay_row(const ScanArgs* a, int64_t rs, uint32_t sps, uint64_t mask,
                                          uint32_t slot_base, uint32_t slot_n)
 {
+    uint64_t hit = 0ull;
     const SmemTab T = tab_view<LAYOUT>(*a);
     const uint32_t m = (uint32_t)a->m;
     const uint32_t C = sps * kStageW;
@@ -1094,6 +1099,7 @@ __device__ __noinline__ uint2 replay_row(const ScanArgs* a, int64_t rs, uint32_t
             Walker<LAYOUT, false, Sink> w{T, sink, e0, 0u};
             w.vec4(ldg16(g), ldg16(g + 1), ldg16(g + 2), ldg16(g + 3), s * kStageW);
             cnt += w.cnt;
+            if (w.cnt) hit |= 1ull << s;
         } else {
             const uint32_t lim = C + m - 1;
             Walker<LAYOUT, true, Sink> h{T, sink, e0, 0u};
@@ -1102,9 +1108,11 @@ __device__ __noinline__ uint2 replay_row(const ScanArgs* a, int64_t rs, uint32_t
             if (m > 33) h.vec(ldg16(g + 2), C + 32, lim);
             if (m > 49) h.vec(ldg16(g + 3), C + 48, lim);
             cnt += h.cnt;
+            if (h.cnt) hit |= 1ull << s;
         }
     }
-    return make_uint2(cnt, REC ? reinterpret_cast<RowSlots<kTSlots>*>(&sink)->n : 0u);
+    return make_uint4(cnt, REC ? reinterpret_cast<RowSlots<kTSlots>*>(&sink)->n : 0u, (uint32_t)hit,
+                      (uint32_t)(hit >> 32));
 }
 
 // The common case of a stage: kRPL rows of 64 bytes each, counted only.
@@ -1553,6 +1561,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                 cnt[i] = 0;
             } else if (!ok[i]) {
                 ss[i].n = 0;
+                fmask[i] = ~0ull;                 // a row walked cold: a re-walk takes it whole
                 if (FIND)
                     cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &ss[i]);
                 else {
@@ -1560,9 +1569,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                     cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &cs);
                 }
             } else if (OPT && fmask[i] != 0ull) {
-                const uint2 rc = replay_row<LAYOUT, FIND>(&a, s0, sps, fmask[i], ss[i].base, ss[i].n);
+                const uint4 rc = replay_row<LAYOUT, FIND>(&a, s0, sps, fmask[i], ss[i].base, ss[i].n);
                 cnt[i] += rc.x;
                 if (FIND) ss[i].n = rc.y;
+                fmask[i] = (uint64_t)rc.z | ((uint64_t)rc.w << 32);
             }
         }
         __syncwarp();
@@ -1575,7 +1585,9 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                 uint32_t ws = 0;
 #pragma unroll
                 for (int i = 0; i < kRPL; i++) {
-                    p.rows[(int64_t)tile * kRows + wrow0 + 32 * i] = (uint16_t)cnt[i];
+                    const int64_t row = (int64_t)tile * kRows + wrow0 + 32 * i;
+                    p.rows[row] = (uint16_t)cnt[i];
+                    if (p.masks && cnt[i]) p.masks[row] = OPT ? fmask[i] : ~0ull;
                     ws += cnt[i];
                 }
 #pragma unroll
@@ -1702,17 +1714,29 @@ __global__ void __launch_bounds__(1024)
 }
 
 // Pass 3: a CTA per tile holding accepts; its rows with a non-zero count are
-// listed with their offsets, and each is walked again exactly by one warp:
-// lane l takes the l-th 16-byte-aligned slice of the row plus the m-1 byte
-// overlap (Algorithm 1 within the row), counts, and after a warp scan walks
-// its slice once more writing the positions.
-__device__ __noinline__ void rewalk_row(const ScanArgs* a, int64_t row, unsigned long long first, int lane)
+// listed with their offsets, and each is walked again exactly by one warp.
+// The count pass left, per such row, the mask of the 64-byte stages holding
+// its exact accepts: every accept starts in [lo, hi), from 16 bytes at or
+// below m - 1 bytes before the first such stage to the end of the last one
+// (the overlap stage: the row's end), and every exact occurrence starting
+// there is one of them (its end lies in a masked stage).  Lane l takes the
+// l-th 16-byte-aligned slice of [lo, hi) plus the m-1 byte overlap
+// (Algorithm 1 within the row), counts, and after a warp scan walks its slice
+// once more writing the positions.  A mask of all ones takes the whole row.
+__device__ __noinline__ void rewalk_row(const ScanArgs* a, int64_t row, uint64_t mask, unsigned long long first,
+                                        int lane)
 {
     const SmemTab T = tab_view<kLayoutK4>(*a);
     const int64_t C = a->chunk;
-    const int64_t s = row * C;
-    const int64_t e = min(s + C, a->n_own);
-    const int64_t span = ((C + 32 * 16 - 1) / (32 * 16)) * 16;       // 16-byte multiple
+    const int64_t rs = row * C;
+    int64_t s = rs, e = min(rs + C, a->n_own);
+    if (mask != ~0ull) {
+        const int64_t lo_stage = __ffsll((long long)mask) - 1;
+        const int64_t hi_stage = 63 - __clzll((long long)mask);
+        s = max(rs, (rs + lo_stage * kStageW - (int64_t)(a->m - 1)) & ~(int64_t)15);
+        e = min(e, rs + (hi_stage + 1) * kStageW);
+    }
+    const int64_t span = ((e - s + 32 * 16 - 1) / (32 * 16)) * 16;   // 16-byte multiple
     const int64_t sl = min(s + lane * span, e);
     const int64_t el = min(sl + span, e);
     CountSink cs;
@@ -1730,7 +1754,8 @@ __device__ __noinline__ void rewalk_row(const ScanArgs* a, int64_t row, unsigned
 }
 
 __global__ void __launch_bounds__(kRows)
-    k_rewalk(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off)
+    k_rewalk(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
+             const unsigned long long* masks)
 {
     __shared__ uint32_t s_warp[kRows / 32];
     __shared__ uint32_t s_row[kRows];      // rows of the tile with accepts ...
@@ -1773,8 +1798,10 @@ __global__ void __launch_bounds__(kRows)
             s_first[slot] = before + x - rc;
         }
         __syncthreads();
-        for (uint32_t j = (uint32_t)warp; j < nz; j += kRows / 32)
-            rewalk_row(&a, tile * kRows + s_row[j], off + s_first[j], lane);
+        for (uint32_t j = (uint32_t)warp; j < nz; j += kRows / 32) {
+            const int64_t row = tile * kRows + s_row[j];
+            rewalk_row(&a, row, masks[row], off + s_first[j], lane);
+        }
         __syncthreads();
     }
 }
@@ -2002,7 +2029,7 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
 // Launch the TMA-staged kernel for the filled-in arguments `a`.
 int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
                const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr,
-               unsigned long long* tile_sum = nullptr)
+               unsigned long long* tile_sum = nullptr, unsigned long long* masks = nullptr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
     int rc = tensor_map_encoder(&encode);
@@ -2019,6 +2046,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.fail_bit = find || rows ? 2ull : (1ull << 63);
     p.rows = rows;
     p.tile_sum = tile_sum;
+    p.masks = masks;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
@@ -2106,8 +2134,9 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
 
 int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
 
-// Two-pass find: [header][one word per tile][one u16 per row of every tile].
-int64_t work_bytes_two_pass(int64_t ntiles) { return work_bytes_for(ntiles) + ntiles * kRows * 2; }
+// Two-pass find: [header][one word per tile][one u16 per row of every tile]
+// [one u64 stage mask per row of every tile].
+int64_t work_bytes_two_pass(int64_t ntiles) { return work_bytes_for(ntiles) + ntiles * kRows * (2 + 8); }
 
 bool two_pass_layout(const Resolved& r)
 {
@@ -2121,9 +2150,10 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
 {
     unsigned long long* tile_sum = a.work + kWorkHeader;
     uint16_t* rows = reinterpret_cast<uint16_t*>(tile_sum + a.ntiles);
+    unsigned long long* masks = reinterpret_cast<unsigned long long*>(rows + a.ntiles * kRows);
     ScanArgs a1 = a;
     a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
-    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, tile_sum);
+    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, tile_sum, masks);
     if (rc) return rc;
     k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
     CUDA_TRY(cudaGetLastError());
@@ -2131,7 +2161,7 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
     int occ = occupancy((const void*)k_rewalk, kRows, smem, dev, di->smem_optin);
     if (occ <= 0) return fail("re-walk kernel does not fit on an SM (occupancy 0)");
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
-    k_rewalk<<<(unsigned)grid, kRows, smem, st>>>(a, rows, tile_sum);
+    k_rewalk<<<(unsigned)grid, kRows, smem, st>>>(a, rows, tile_sum, masks);
     CUDA_TRY(cudaGetLastError());
     return DFA_OK;
 }
@@ -2196,6 +2226,19 @@ namespace {
 __global__ void k_or_status(const unsigned long long* work, unsigned long long* acc)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *acc |= work[1];
+}
+
+// A wait of the find that just ran gave up: mark its count (bit 63).
+__global__ void k_status_to_count(const unsigned long long* work, unsigned long long* count)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && work[1]) *count |= 1ull << 63;
+}
+
+// One warp runs the ordered compaction's look-back for `tile` on a
+// workspace (dfa_debug_wait_timeout).
+__global__ void k_debug_lookback(unsigned long long* work, int64_t tile)
+{
+    lookback_warp(work, tile, 1ull, (int)(threadIdx.x & 31));
 }
 }  // namespace
 
@@ -2598,6 +2641,38 @@ int dfa_find_host_multi(const uint8_t* h_text, int64_t n, const dfa_table* const
     if (rc != DFA_OK) return rc;
     if (hc[(size_t)npat * 2]) return DFA_ETIMEOUT;
     return trunc ? DFA_ETRUNC : DFA_OK;
+}
+
+int dfa_find_batched(const uint8_t* d_text, int64_t n, const dfa_table* const* tables, int32_t npat,
+                     int64_t* const* d_pos, const int64_t* caps, uint64_t* d_counts, void* d_work,
+                     int64_t work_bytes, const dfa_config* cfg, void* stream)
+{
+    if (!tables || !caps || !d_counts || !d_work || npat < 1 || npat > kHostMaxPat || n < 0 ||
+        (n > 0 && !d_text))
+        return DFA_EINVAL;
+    for (int32_t i = 0; i < npat; i++)
+        if (!tables[i] || caps[i] < 0 || (caps[i] > 0 && (!d_pos || !d_pos[i]))) return DFA_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int32_t i = 0; i < npat; i++) {
+        const int rc = launch_find(d_text, n, n, tables[i], caps[i] > 0 ? d_pos[i] : nullptr, caps[i],
+                                   d_counts + i, nullptr, 0, d_work, work_bytes, cfg, st);
+        if (rc) return rc;
+        if (n > 0) {
+            k_status_to_count<<<1, 32, 0, st>>>(static_cast<const unsigned long long*>(d_work),
+                                                reinterpret_cast<unsigned long long*>(d_counts + i));
+            CUDA_TRY(cudaGetLastError());
+        }
+    }
+    return DFA_OK;
+}
+
+int dfa_debug_wait_timeout(void* d_work, int64_t work_bytes, int64_t tile, void* stream)
+{
+    if (!d_work || tile < 1 || work_bytes < work_bytes_for(tile + 1)) return DFA_EINVAL;
+    k_debug_lookback<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<unsigned long long*>(d_work), tile);
+    CUDA_TRY(cudaGetLastError());
+    return DFA_OK;
 }
 
 const char* dfa_strerror(int code)

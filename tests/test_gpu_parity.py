@@ -232,6 +232,31 @@ def test_host_buffer_path_many_patterns(gpu):
         assert c == wc and np.array_equal(hp.numpy()[:min(c, cap)], wp[:cap])
 
 
+def test_find_batched(gpu):
+    # several patterns over one device text through one call and one
+    # workspace; one pattern's buffer is too small (truncated, count exact)
+    import torch
+    n = 2_000_003
+    t = synth.genome_text(n, 29)
+    pats = [synth.pattern(m, 290 + m) for m in (3, 4, 8, 16, 64)]
+    for p in pats[3:]:
+        synth.plant(t, p, synth.uniform_ints(25, n - len(p), len(p)))
+    td = _dev(gpu, t)
+    want = [oracle.find_brute(t, p) for p in pats]
+    tabs = [gpu.dfa_build(p) for p in pats]
+    caps = [c + 2 for c, _ in want]
+    caps[1] = want[1][0] // 3
+    pos = [torch.full((c,), -1, dtype=torch.int64, device="cuda") for c in caps]
+    cnt = torch.zeros(len(pats), dtype=torch.int64, device="cuda")
+    ws = torch.empty(gpu.dfa_find_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    gpu.dfa_find_batched(td, tabs, pos, cnt, ws)
+    got = cnt.cpu().numpy()
+    for i, ((wc, wp), cap) in enumerate(zip(want, caps)):
+        assert got[i] == wc, i
+        k = min(wc, cap)
+        assert np.array_equal(pos[i][:k].cpu().numpy(), wp[:k]), i
+
+
 def test_streams_and_concurrency(gpu):
     import torch
     t = synth.genome_text(2_000_000, 13)
@@ -324,6 +349,31 @@ def test_dense_relaxed_decoys(gpu, cfg):
             else:                                      # a true copy across the border
                 st = b - int(rnd[k] % m) if m > 1 else b; k += 1
                 t[st:st + m] = np.frombuffer(pat, np.uint8)
+        assert _check(gpu, t, pat, cfg) > 0
+
+
+@pytest.mark.parametrize("cfg", [None, dict(loader=2, layout=4, chunk=128), dict(loader=2, layout=4, chunk=1280),
+                                 dict(loader=2, layout=3, chunk=640)])
+def test_two_pass_stage_masks(gpu, cfg):
+    # the re-walk of a two-pass find walks only the stages that held exact
+    # accepts: copies at row starts, across every 64-byte stage border, ending
+    # in a row's overlap, several in one row, in the ragged last rows
+    chunk = 1280 if cfg is None else cfg["chunk"]
+    n = 512 * chunk * 2 + 7 * chunk + 77
+    for m in (8, 12, 33, 64):
+        t = synth.genome_text(n, 240 + m, n_gap_mean=30_000, n_run_mean=200)
+        pat = synth.pattern(m, 2400 + m)
+        rnd = synth.uniform_ints(n // 64 + 8, 1 << 30, 250 + m)
+        at = []
+        for k, b in enumerate(range(0, n - m - 1, 64 * 3)):
+            r = int(rnd[k] % 4)
+            st = b if r == 0 else b - int(rnd[k] >> 2) % m if r == 1 else b - m + 1 if r == 2 else b + 5
+            if 0 <= st <= n - m:
+                at.append(st)
+        for row_end in range(chunk, n, chunk * 37):        # ending in the overlap
+            at.append(row_end - m // 2)
+        at += [n - m, n - m - 70]                          # the ragged end
+        synth.plant(t, pat, sorted(set(at)))
         assert _check(gpu, t, pat, cfg) > 0
 
 
