@@ -257,6 +257,39 @@ def test_find_batched(gpu):
         assert np.array_equal(pos[i][:k].cpu().numpy(), wp[:k]), i
 
 
+def test_tables_in_caller_memory(gpu):
+    # dfa_build_into / dfa_multi_build_host + dfa_multi_attach: the tables
+    # land in caller-owned device memory (copied on a stream) and give the
+    # same results as the library-allocated ones
+    import torch
+    t = synth.genome_text(1_000_003, 33)
+    td = _dev(gpu, t)
+    s = torch.cuda.Stream()
+    for m in (1, 4, 9, 31, 64):
+        pat = synth.pattern(m, 330 + m)
+        buf = torch.empty(gpu.dfa_table_bytes(m) + 256, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(s):
+            tab = gpu.Table(pat, into=buf[256:], stream=s)
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            gpu.dfa_count(td, tab, cnt, stream=s)
+        s.synchronize()
+        assert int(cnt.item()) == oracle.count_brute(t, pat), m
+        tab.free()
+    with pytest.raises(gpu.DfaError):
+        gpu.Table(b"ACGT", into=torch.empty(16, dtype=torch.uint8, device="cuda"))       # too small
+    pats = [synth.pattern(m, 340 + m) for m in (3, 5, 8, 12)]
+    mt = gpu.MultiTable(pats, device=False)
+    with pytest.raises(gpu.DfaError):
+        gpu.dfa_multi_count([td], mt, torch.zeros(4, dtype=torch.int64, device="cuda"))  # not attached yet
+    img = torch.empty(mt.image_bytes(), dtype=torch.uint8, device="cuda")
+    mt.attach(img, stream=s)
+    out = torch.zeros(len(pats), dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(s):
+        gpu.dfa_multi_count([td], mt, out, stream=s)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy().astype(np.uint64), oracle.multi_count([t], pats)[0])
+
+
 def test_streams_and_concurrency(gpu):
     import torch
     t = synth.genome_text(2_000_000, 13)
