@@ -117,15 +117,22 @@ int dfa_export_stt(const dfa_table* table, uint8_t* h_stt, int64_t bytes);
 /*
  * Launch configuration (the knobs the autotuner sets).  Zero fields take the
  * library's defaults.
- *   layout:  0 = default; 1 = four-step composite table over 2-bit codes
- *            (u16 entries, (m+1)*256); 2 = the paper's sparse ASCII STT
- *            (u8 entries, (m+1)*256, one lookup per byte: Sec. III-B).
- *   threads: threads per CTA (64..1024, multiple of 32).
- *   chunk:   bytes walked per thread per tile (multiple of 16, 16..32768),
- *            each chunk carrying m-1 bytes of overlap (Algorithm 1).
- *   loader:  0 = default; 1 = direct 16-byte global loads; 2 = TMA-staged
- *            tiles (cp.async.bulk.tensor into shared memory).
- *   ctas_per_sm: persistent CTAs per SM (0 = as many as fit).
+ *   layout:  0 = default (4 for m >= 8, else 1); 1 = four-step composite
+ *            table over 2-bit codes (u16 entries, (m+1)*256), exact walk;
+ *            2 = the paper's sparse ASCII STT (u8 entries, (m+1)*256, one
+ *            lookup per byte: Sec. III-B); 3 = four-step table of states
+ *            only and 4 = four-step states with an accept flag, both walked
+ *            through the codes alone with exact replays of the stages that
+ *            may hold an accept (loader 2 only).
+ *   threads: threads per CTA for loader 1 (128, 256 or 512); loader 2 and
+ *            dfa_multi_count fix their own.
+ *   chunk:   bytes walked per thread (one row) per tile, each carrying m-1
+ *            bytes of overlap (Algorithm 1): loader 1 a multiple of 16 in
+ *            16..32768; loader 2 a multiple of 64 in 128..4032.
+ *   loader:  0 = default (2 when the text is 16-byte aligned and holds two
+ *            full rows, else 1); 1 = direct 16-byte global loads; 2 =
+ *            TMA-staged tiles (cp.async.bulk.tensor into shared memory).
+ *   ctas_per_sm: persistent CTAs per SM for loader 1 (0 = as many as fit).
  */
 typedef struct dfa_config {
     int32_t layout;

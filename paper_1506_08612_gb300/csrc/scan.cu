@@ -768,6 +768,13 @@ constexpr int kTSlotsDense = 16;                 // staged positions per row (de
 // streams at the HBM rate on GB300; deeper rings were measured to lose up to
 // half the throughput, so the depth is capped here.
 constexpr int kMaxStages = 4;
+constexpr int kRelaxedCountStages = 2;           // ring depth of the relaxed count pass
+// Default row length (stages of 64 bytes) of a long text: relaxed layouts
+// (m >= 8) 12 stages, exact layouts 15.  Measured on 3.2e9 bytes: finds of
+// m = 16..64 0.624 ms at 20 stages (1280 B), 0.55 at 12, 0.55-0.56 at 8;
+// the dense find of m = 4 0.960 at 20, 0.911 at 15, 0.945 at 12.
+constexpr int kDefaultStagesRelaxed = 12;
+constexpr int kDefaultStagesExact = 15;
 constexpr int kDefer = 4;                        // tiles whose positions wait for their offset
 constexpr int kTicketRing = 8;
 // How many tiles ahead of the slowest walker warp the ticket warp may claim
@@ -1919,9 +1926,12 @@ int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int
         if (cfg && cfg->chunk) {
             chunk = cfg->chunk;
         } else {
+            // at least four tiles per SM, rows of at most the measured best
             const int64_t per = (int64_t)kRows * kStageW * 4 * sms;
             int64_t sps = (n + per - 1) / per;
-            sps = std::min<int64_t>(std::max<int64_t>(sps, 2), 20);
+            const int64_t cap = (r->layout == kLayoutK4F || r->layout == kLayoutK4S) ? kDefaultStagesRelaxed
+                                                                                     : kDefaultStagesExact;
+            sps = std::min<int64_t>(std::max<int64_t>(sps, 2), cap);
             chunk = sps * kStageW;
         }
         const bool ok = aligned && n_avail / chunk >= 2;
@@ -2063,8 +2073,12 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
         find ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2 : 0;
     p.rings_off = (p.table_bytes + slot_bytes + 1023) & ~1023;
     const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.rings_off;
-    const int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
+    int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
     if (nst < 2) return DFA_EINVAL;
+    // the relaxed count pass streams faster with two stages per warp ring
+    // than with four (3.2e9 bytes, m = 16: 0.572 against 0.603 ms; the exact
+    // count is the same with 2, 3 or 4)
+    if (!find && (r.layout == kLayoutK4F || r.layout == kLayoutK4S)) nst = std::min(nst, kRelaxedCountStages);
     p.nst = nst;
     p.ahead = std::min(3 + (nst - 1) / (p.sps + 1), kTicketRing);
     const int smem = p.rings_off + kWalkWarps * nst * kWarpStage;
@@ -2706,8 +2720,9 @@ const char* dfa_last_error(void) { return g_last_error; }
 namespace {
 
 // Tiles the static workspace can describe.  A tile is the text one CTA
-// takes per ticket (threads x chunk bytes of the resolved launch; 640 KiB by
-// default for multi-GB texts, so the default limit is about 40 GiB).
+// takes per ticket (threads x chunk bytes of the resolved launch; by default
+// for multi-GB texts 384 KiB for patterns of 8 and more and 480 KiB below,
+// so the default limit is about 24 GiB).
 constexpr int64_t kNoAllocTiles = 65536;
 constexpr int kNoAllocMaxDevices = 64;
 

@@ -104,3 +104,27 @@ def test_empty_and_short_sequences(gpu):
     got = b.result()
     assert np.array_equal(got, oracle.multi_count(texts, pats))
     assert got.tolist() == [[0, 0, 0, 0], [0, 1, 0, 0], [2, 2, 2, 2]]
+
+
+def test_single_pattern_autotune_and_cache(gpu):
+    import json
+    import os
+
+    from paper_1506_08612_gb300 import autotune
+    n = 40_000_000
+    t = synth.genome_text(n, 51)
+    pat = synth.pattern(12, 5100)
+    synth.plant(t, pat, synth.uniform_ints(50, n - 12, 52))
+    td = _dev(t)
+    tab = gpu.dfa_build(pat)
+    cfg = autotune.tune_single(td, tab, reps=2)
+    assert cfg in autotune.single_candidates(12)
+    assert gpu.count(td, tab, cfg=cfg) == oracle.count_brute(t, pat)
+    c, pos = gpu.find(td, tab, cfg=cfg)
+    assert np.array_equal(pos.cpu().numpy(), oracle.find_brute(t, pat)[1])
+    # a second call is answered from the cache file
+    path = os.environ["DNADFA_AUTOTUNE_CACHE"]
+    key = autotune.single_key(autotune.device_name(), n, 12)
+    assert json.load(open(path))[key]["cfg"] == cfg
+    autotune.reset_memory_cache()
+    assert autotune.tune_single(td, tab) == cfg

@@ -410,6 +410,30 @@ def test_two_pass_stage_masks(gpu, cfg):
         assert _check(gpu, t, pat, cfg) > 0
 
 
+@pytest.mark.parametrize("chunk", [128, 640, 1280])
+def test_two_pass_row_end_offsets(gpu, chunk):
+    # the third pass of a two-pass find walks again the masked stages of
+    # every row with accepts: rows holding 0..7 occurrences in turn, some
+    # ending in the row's overlap, rows spilling into their successors
+    cfg = dict(loader=2, layout=4, chunk=chunk)
+    n = 512 * chunk * 2 + 3 * chunk + 41
+    for m in (8, 13, 40):
+        t = synth.genome_text(n, 260 + m, n_gap_mean=0)
+        pat = synth.pattern(m, 2600 + m)
+        at = []
+        for row in range(n // chunk):
+            k = row % 8
+            gap = max(m + 1, (chunk - m) // max(k, 1))
+            for j in range(k):
+                st = row * chunk + j * gap
+                if j == k - 1 and row % 3 == 0:
+                    st = row * chunk + chunk - m // 2          # ends in the overlap
+                if st + m <= n:
+                    at.append(st)
+        synth.plant(t, pat, sorted(set(at)))
+        assert _check(gpu, t, pat, cfg) > 0
+
+
 def test_dense_patterns_on_nonbase_runs(gpu):
     # N reads as G by its code: dense patterns of G's meet runs of N
     n = 1_000_003
