@@ -363,6 +363,34 @@ int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32
  */
 int dfa_debug_wait_timeout(void* d_work, int64_t work_bytes, int64_t tile, void* stream);
 
+/*
+ * Sorted start positions of every pattern of a multi-pattern automaton in one
+ * text, in one walk (the multi-pattern automaton of Sec. III-B; Algorithm 1's
+ * "location" output for each pattern).  For patterns with few occurrences:
+ * each occurrence is written into its pattern's segment of d_pos during the
+ * walk, then each segment is sorted on the device.
+ *   d_text / n: the text (device).
+ *   table:    the automaton (built with a device copy, or attached).
+ *   h_counts: HOST uint64[npat], the exact counts of the patterns in this
+ *             text (e.g. from dfa_multi_count); each at most DFA_LOCATE_MAX.
+ *   d_pos / cap: device int64 buffer of at least the sum of the counts;
+ *             pattern p's positions, ascending, start at index
+ *             h_counts[0] + ... + h_counts[p-1].
+ *   d_work / work_bytes: caller-owned device scratch of at least
+ *             dfa_multi_locate_work_bytes(npat) bytes (bases, counts,
+ *             cursors, a status word); not shared by calls that may overlap.
+ * Asynchronous on `stream`; allocates nothing.  dfa_multi_locate_status
+ * (synchronising) returns DFA_EINVAL when the counts did not match the text
+ * (a segment over- or under-filled), else DFA_OK.
+ * Errors: DFA_EINVAL (a count above DFA_LOCATE_MAX, cap too small, no device
+ * copy), DFA_EWORKSPACE, DFA_ECUDA.
+ */
+#define DFA_LOCATE_MAX 4096
+int64_t dfa_multi_locate_work_bytes(int32_t npat);
+int dfa_multi_locate(const uint8_t* d_text, int64_t n, const dfa_multi* table, const uint64_t* h_counts,
+                     int64_t* d_pos, int64_t cap, void* d_work, int64_t work_bytes, void* stream);
+int dfa_multi_locate_status(const void* d_work, int32_t npat, void* stream);
+
 /* Static text for a return code. */
 const char* dfa_strerror(int code);
 

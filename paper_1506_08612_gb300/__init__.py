@@ -28,13 +28,15 @@ import numpy as np
 
 from . import _native
 from ._native import (DFA_COUNT_FAILED, DFA_ECUDA, DFA_EINVAL, DFA_ENOMEM, DFA_ETIMEOUT,
-                      DFA_ETRUNC, DFA_EWORKSPACE, DFA_MAX_M, DFA_OK, LIBRARY_PATH, dfa_config)
+                      DFA_ETRUNC, DFA_EWORKSPACE, DFA_LOCATE_MAX, DFA_MAX_M, DFA_OK, LIBRARY_PATH,
+                      dfa_config)
 
 _lib = _native.lib
 
 __all__ = ["Table", "DfaError", "dfa_build", "dfa_free", "dfa_export_stt", "dfa_count",
            "dfa_find", "dfa_find_workspace_bytes", "dfa_table_bytes", "dfa_find_status", "dfa_host_stage_bytes",
-           "dfa_find_host", "dfa_find_host_multi", "dfa_find_batched", "dfa_debug_wait_timeout", "dfa_host_stage_bytes_multi", "dfa_find_noalloc", "MultiTable", "dfa_multi_count", "multi_count",
+           "dfa_find_host", "dfa_find_host_multi", "dfa_find_batched", "dfa_debug_wait_timeout", "dfa_host_stage_bytes_multi", "dfa_find_noalloc", "MultiTable", "dfa_multi_count", "multi_count", "dfa_multi_locate",
+           "dfa_multi_locate_work_bytes", "dfa_multi_locate_status",
            "dfa_strerror", "dfa_config", "find", "count", "LIBRARY_PATH",
            "DFA_OK", "DFA_EINVAL", "DFA_ETRUNC", "DFA_ETIMEOUT", "DFA_ECUDA", "DFA_EWORKSPACE",
            "DFA_ENOMEM", "DFA_MAX_M"]
@@ -322,6 +324,27 @@ def dfa_multi_count(texts, table: MultiTable, counts, cfg=None, stream=None) -> 
     lens = (ctypes.c_int64 * ns)(*[int(t.numel()) for t in texts])
     _check(_lib.dfa_multi_count(ptrs, lens, ns, table.handle, _ptr(counts), _cfg(cfg),
                                 _stream(stream)), "dfa_multi_count")
+
+
+def dfa_multi_locate_work_bytes(npat: int) -> int:
+    return int(_lib.dfa_multi_locate_work_bytes(int(npat)))
+
+
+def dfa_multi_locate(text, table: MultiTable, counts, positions, workspace, stream=None) -> None:
+    """Enqueue the sorted positions of every pattern of ``table`` in ``text``
+    into ``positions`` (int64 device tensor, pattern p's segment at the sum
+    of the counts before it); ``counts``: the exact per-pattern counts (host
+    sequence), each at most DFA_LOCATE_MAX."""
+    hc = (ctypes.c_uint64 * table.npat)(*[int(c) for c in counts])
+    rc = _lib.dfa_multi_locate(_ptr(text), int(text.numel()), table.handle, hc, _ptr(positions),
+                               int(positions.numel()) if positions is not None else 0, _ptr(workspace),
+                               int(workspace.numel() * workspace.element_size()), _stream(stream))
+    if rc != DFA_OK:
+        raise DfaError(rc, f"dfa_multi_locate [{_lib.dfa_last_error().decode(errors='replace')}]")
+
+
+def dfa_multi_locate_status(workspace, npat: int, stream=None) -> int:
+    return int(_lib.dfa_multi_locate_status(_ptr(workspace), int(npat), _stream(stream)))
 
 
 def multi_count(texts, patterns, cfg=None) -> np.ndarray:

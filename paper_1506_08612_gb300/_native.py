@@ -12,6 +12,7 @@ import os
 from . import build as _build
 
 DFA_OK, DFA_EINVAL, DFA_ETRUNC, DFA_ETIMEOUT, DFA_ECUDA, DFA_EWORKSPACE, DFA_ENOMEM = range(7)
+DFA_LOCATE_MAX = 4096
 DFA_MAX_M = 64
 DFA_COUNT_FAILED = 1 << 63
 
@@ -57,6 +58,9 @@ def _declare(lib):
         "dfa_multi_smem_bytes": ([vp], i64),
         "dfa_multi_count": ([ctypes.POINTER(vp), ctypes.POINTER(i64), i32, vp, vp, cfgp, vp], ctypes.c_int),
         "dfa_debug_wait_timeout": ([vp, i64, i64, vp], ctypes.c_int),
+        "dfa_multi_locate_work_bytes": ([i32], i64),
+        "dfa_multi_locate": ([vp, i64, vp, ctypes.POINTER(ctypes.c_uint64), vp, i64, vp, i64, vp], ctypes.c_int),
+        "dfa_multi_locate_status": ([vp, i32, vp], ctypes.c_int),
         "dfa_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "dfa_version": ([], ctypes.c_char_p),
         "dfa_last_error": ([], ctypes.c_char_p),

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <array>
 #include <cstdio>
 #include <cstring>
@@ -89,12 +90,53 @@ __device__ __forceinline__ uint32_t word_bad_m(uint32_t x)
 // Shared-memory view of one CTA: the transition table and one counter per
 // automaton state (occurrences of every pattern the state outputs, at owned
 // starts); the launch arguments for the rare out-of-line paths.
+struct LocateArgs;
+
 struct MultiTab {
     const uint16_t* delta;   // 4 * state + code -> 4 * next | (out(next) not empty)
     uint32_t* hs;            // per-state counters
     const MultiArgs* args;
     unsigned long long* row; // this sequence's per-pattern global counts
+    const LocateArgs* loc;   // dfa_multi_locate: where occurrences go
+    int64_t s0;              // dfa_multi_locate: text offset of the chunk
 };
+
+// dfa_multi_locate: one text, every occurrence written to its pattern's
+// segment of pos (base[p] .. base[p] + count[p]) at a slot taken from
+// cursor[p]; status bit 0 when a pattern meets more than count[p].
+struct LocateArgs {
+    const uint8_t* text;
+    int64_t n;
+    int64_t ntiles;
+    int32_t npat, mmax, chunk, nstates;
+    int32_t delta_bytes;
+    const uint8_t* tab;
+    const uint32_t* off;
+    const uint16_t* ids;
+    const uint8_t* mlen;
+    const unsigned long long* base;
+    const unsigned long long* count;
+    unsigned int* cursor;
+    unsigned long long* status;
+    int64_t* pos;
+};
+
+// Every owned output of state st ending at chunk offset j (owned: inside the
+// chunk, or in the overlap d = j - own + 1 bytes past it with m_p > d).
+__device__ __noinline__ void locate_out(const LocateArgs* a, uint32_t st, uint32_t j, uint32_t own, int64_t s0)
+{
+    const uint32_t k1 = __ldg(a->off + st + 1);
+    for (uint32_t k = __ldg(a->off + st); k < k1; k++) {
+        const uint32_t p = __ldg(a->ids + k);
+        const uint32_t m = __ldg(a->mlen + p);
+        if (j >= own && m <= j - own + 1u) continue;
+        const unsigned int slot = atomicAdd(a->cursor + p, 1u);
+        if (slot < __ldg(a->count + p))
+            a->pos[__ldg(a->base + p) + slot] = s0 + (int64_t)j - (int64_t)m + 1;
+        else
+            atomicOr(a->status, 1ull);
+    }
+}
 
 // A flagged step in the overlap, d = (end offset) - own + 1 >= 1 bytes past
 // the chunk: an output of length m_p started before the chunk's end (is
@@ -117,11 +159,13 @@ __device__ __noinline__ void emit_overlap(const MultiArgs* a, uint32_t* hs, unsi
 }
 
 // Output flag set on entry e ending at offset j: owned (CHECK false, or
-// j < own) adds one to the state's counter.
-template <bool CHECK>
+// j < own) adds one to the state's counter; a locate writes the positions.
+template <bool CHECK, bool LOC = false>
 __device__ __forceinline__ void emit(const MultiTab& M, uint32_t e, uint32_t j, uint32_t own)
 {
-    if (!CHECK || j < own)
+    if (LOC)
+        locate_out(M.loc, e >> 2, j, own, M.s0);
+    else if (!CHECK || j < own)
         atomicAdd(M.hs + (e >> 2), 1u);
     else
         emit_overlap(M.args, M.hs, M.row, e >> 2, j - own + 1u);
@@ -129,7 +173,7 @@ __device__ __forceinline__ void emit(const MultiTab& M, uint32_t e, uint32_t j, 
 
 // Four bases of a word w, byte k ending at offset j + k: four dependent
 // lookups, one test of the output flags.
-template <bool CHECK>
+template <bool CHECK, bool LOC = false>
 __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
 {
     const uint32_t c = (w >> 1) & 0x03030303u;
@@ -139,54 +183,56 @@ __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uin
     const uint32_t e3 = M.delta[(e2 & ~3u) | (c >> 24)];
     ent = e3;
     if ((e0 | e1 | e2 | e3) & 1u) {
-        if (e0 & 1u) emit<CHECK>(M, e0, j, own);
-        if (e1 & 1u) emit<CHECK>(M, e1, j + 1, own);
-        if (e2 & 1u) emit<CHECK>(M, e2, j + 2, own);
-        if (e3 & 1u) emit<CHECK>(M, e3, j + 3, own);
+        if (e0 & 1u) emit<CHECK, LOC>(M, e0, j, own);
+        if (e1 & 1u) emit<CHECK, LOC>(M, e1, j + 1, own);
+        if (e2 & 1u) emit<CHECK, LOC>(M, e2, j + 2, own);
+        if (e3 & 1u) emit<CHECK, LOC>(M, e3, j + 3, own);
     }
 }
 
 // One byte, any value: a non-base sends the walk back to q0 (Sec. III-B:
 // columns outside the alphabet lead to q0).
+template <bool LOC = false>
 __device__ __forceinline__ void byte_any(const MultiTab& M, uint32_t& ent, uint32_t b, uint32_t j, uint32_t own)
 {
     const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
     if (((b ^ (t * 0x11u)) & 0xD9u) == 0x41u) {
         ent = M.delta[(ent & ~3u) | ((b >> 1) & 3u)];
-        if (ent & 1u) emit<true>(M, ent, j, own);
+        if (ent & 1u) emit<true, LOC>(M, ent, j, own);
     } else {
         ent = 0u;
     }
 }
 
 // A word holding bases and non-bases, byte by byte.
+template <bool LOC = false>
 __device__ __forceinline__ uint32_t word_mixed(const MultiTab& M, uint32_t ent, uint32_t w, uint32_t j, uint32_t own)
 {
 #pragma unroll 1
-    for (int k = 0; k < 4; k++) byte_any(M, ent, (w >> (8 * k)) & 0xFFu, j + k, own);
+    for (int k = 0; k < 4; k++) byte_any<LOC>(M, ent, (w >> (8 * k)) & 0xFFu, j + k, own);
     return ent;
 }
 
-template <bool CHECK>
+template <bool CHECK, bool LOC = false>
 __device__ __forceinline__ void word_any(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
 {
     const uint32_t bad = word_bad_m(w);
     if (bad == 0u) {
-        word_bases<CHECK>(M, ent, w, j, own);
+        word_bases<CHECK, LOC>(M, ent, w, j, own);
     } else if (((bad - 0x01010101u) & ~bad & 0x80808080u) == 0u) {
         ent = 0u;                                   // four non-bases (an N block)
     } else {
-        ent = word_mixed(M, ent, w, j, own);
+        ent = word_mixed<LOC>(M, ent, w, j, own);
     }
 }
 
-template <bool CHECK>
+template <bool CHECK, bool LOC = false>
 __device__ __forceinline__ void vec_any(const MultiTab& M, uint32_t& ent, uint4 v, uint32_t j, uint32_t own)
 {
-    word_any<CHECK>(M, ent, v.x, j, own);
-    word_any<CHECK>(M, ent, v.y, j + 4, own);
-    word_any<CHECK>(M, ent, v.z, j + 8, own);
-    word_any<CHECK>(M, ent, v.w, j + 12, own);
+    word_any<CHECK, LOC>(M, ent, v.x, j, own);
+    word_any<CHECK, LOC>(M, ent, v.y, j + 4, own);
+    word_any<CHECK, LOC>(M, ent, v.z, j + 8, own);
+    word_any<CHECK, LOC>(M, ent, v.w, j + 12, own);
 }
 
 template <int THREADS>
@@ -272,6 +318,83 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
         for (; j < len; j++) byte_any(M, ent, base[j], j, own);
     }
     if (cur >= 0) flush(cur);
+}
+
+// dfa_multi_locate, pass 1: the walk of k_multi_count over one text, each
+// owned occurrence written to its pattern's segment (in no particular order
+// within it).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_locate(const __grid_constant__ LocateArgs a)
+{
+    extern __shared__ __align__(16) uint8_t msm[];
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.tab);
+        uint4* dst = reinterpret_cast<uint4*>(msm);
+        for (int i = threadIdx.x; i < (a.delta_bytes >> 4); i += THREADS) dst[i] = src[i];
+    }
+    MultiTab M;
+    M.delta = reinterpret_cast<const uint16_t*>(msm);
+    M.hs = nullptr;
+    M.args = nullptr;
+    M.row = nullptr;
+    M.loc = &a;
+    __syncthreads();
+    const int64_t C = a.chunk;
+    const int64_t tb = (int64_t)THREADS * C;
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const int64_t s = t * tb + (int64_t)threadIdx.x * C;
+        if (s >= a.n) continue;
+        const int64_t e = min(s + C, a.n);
+        const int64_t hi = min(e + (int64_t)a.mmax - 1, a.n);
+        const uint32_t own = (uint32_t)(e - s);
+        const uint32_t len = (uint32_t)(hi - s);
+        const uint8_t* base = a.text + s;
+        M.s0 = s;
+        uint32_t ent = 0u;
+        uint32_t j = 0;
+        if ((((uintptr_t)base) & 15u) == 0) {
+            for (; j + 16 <= own; j += 16)
+                vec_any<false, true>(M, ent, *reinterpret_cast<const uint4*>(base + j), j, own);
+            for (; j + 16 <= len; j += 16)
+                vec_any<true, true>(M, ent, *reinterpret_cast<const uint4*>(base + j), j, own);
+        }
+        for (; j < len; j++) byte_any<true>(M, ent, base[j], j, own);
+    }
+}
+
+// dfa_multi_locate, pass 2: one CTA per pattern sorts its segment (at most
+// DFA_LOCATE_MAX positions) in shared memory, bitonically; a segment whose
+// slots were not all filled, or overfilled, sets status bit 1.
+__global__ void __launch_bounds__(512) k_sort_segments(int64_t* pos, const unsigned long long* base,
+                                                       const unsigned long long* count, const unsigned int* cursor,
+                                                       unsigned long long* status)
+{
+    __shared__ long long sv[DFA_LOCATE_MAX];
+    const int p = blockIdx.x;
+    const int64_t b = (int64_t)base[p];
+    const int c = (int)count[p];
+    if (threadIdx.x == 0 && cursor[p] != (unsigned int)c) atomicOr(status, 2ull);
+    if (c <= 1) return;
+    int L = 1;
+    while (L < c) L <<= 1;
+    for (int i = threadIdx.x; i < L; i += 512) sv[i] = i < c ? pos[b + i] : LLONG_MAX;
+    __syncthreads();
+    for (int k = 2; k <= L; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < L; i += 512) {
+                const int ixj = i ^ jj;
+                if (ixj > i) {
+                    const long long x = sv[i], y = sv[ixj];
+                    if ((x > y) == ((i & k) == 0)) {
+                        sv[i] = y;
+                        sv[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < c; i += 512) pos[b + i] = sv[i];
 }
 
 typedef void (*MultiFn)(const MultiArgs);
@@ -521,6 +644,100 @@ int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32
     fn<<<(unsigned)grid, threads, smem, st>>>(a);
     if ((err = cudaGetLastError()) != cudaSuccess) return multi_fail("dfa_multi_count", err);
     return DFA_OK;
+}
+
+int64_t dfa_multi_locate_work_bytes(int32_t npat)
+{
+    if (npat < 1 || npat > kMultiMaxPat) return -1;
+    return (int64_t)npat * 8 * 2 + (((int64_t)npat * 4 + 15) & ~(int64_t)15) + 16;
+}
+
+int dfa_multi_locate(const uint8_t* d_text, int64_t n, const dfa_multi* t, const uint64_t* h_counts, int64_t* d_pos,
+                     int64_t cap, void* d_work, int64_t work_bytes, void* stream)
+{
+    if (!t || !h_counts || !d_work || n < 0 || (n > 0 && !d_text) || cap < 0) return DFA_EINVAL;
+    if (!t->d_mem)
+        return set_last_error(DFA_EINVAL, "dfa_multi_locate: the automaton has no device copy (dfa_multi_attach)");
+    if (work_bytes < dfa_multi_locate_work_bytes(t->npat)) return DFA_EWORKSPACE;
+    const int npat = t->npat;
+    std::vector<unsigned long long> host((size_t)npat * 2);
+    unsigned long long total = 0;
+    for (int p = 0; p < npat; p++) {
+        if (h_counts[p] > (uint64_t)DFA_LOCATE_MAX)
+            return set_last_error(DFA_EINVAL, "dfa_multi_locate: a count above DFA_LOCATE_MAX");
+        host[p] = total;
+        host[(size_t)npat + p] = h_counts[p];
+        total += h_counts[p];
+    }
+    if ((int64_t)total > cap || (total > 0 && !d_pos)) return DFA_EINVAL;
+    int dev;
+    cudaError_t err;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return multi_fail("dfa_multi_locate", err);
+    if (dev != t->device) return DFA_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long* w = static_cast<unsigned long long*>(d_work);
+    unsigned int* cursor = reinterpret_cast<unsigned int*>(w + 2 * npat);
+    unsigned long long* status =
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<uint8_t*>(cursor) + (((int64_t)npat * 4 + 15) & ~15));
+    // the pageable source is staged before the call returns
+    if ((err = cudaMemcpyAsync(w, host.data(), host.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (err = cudaMemsetAsync(cursor, 0, (size_t)npat * 4, st)) != cudaSuccess ||
+        (err = cudaMemsetAsync(status, 0, 8, st)) != cudaSuccess)
+        return multi_fail("dfa_multi_locate", err);
+    const int threads = 256, chunk = 1024;
+    LocateArgs a;
+    memset(&a, 0, sizeof(a));
+    a.text = d_text;
+    a.n = n;
+    a.ntiles = (n + (int64_t)threads * chunk - 1) / ((int64_t)threads * chunk);
+    a.npat = npat;
+    a.mmax = t->mmax;
+    a.chunk = chunk;
+    a.nstates = t->nstates;
+    a.delta_bytes = t->delta_bytes;
+    a.tab = static_cast<const uint8_t*>(t->d_mem);
+    a.off = reinterpret_cast<const uint32_t*>(a.tab + t->delta_bytes);
+    a.ids = reinterpret_cast<const uint16_t*>(a.tab + t->delta_bytes + t->off_bytes);
+    a.mlen = a.tab + t->delta_bytes + t->off_bytes + t->ids_bytes;
+    a.base = w;
+    a.count = w + npat;
+    a.cursor = cursor;
+    a.status = status;
+    a.pos = d_pos;
+    if (a.ntiles > 0 && total > 0) {
+        int optin = 0, sms = 0, occ = 0;
+        const int smem = t->delta_bytes;
+        if ((err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+            (err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return multi_fail("dfa_multi_locate", err);
+        if (smem > optin) return set_last_error(DFA_EINVAL, "dfa_multi_locate: the automaton does not fit in shared memory");
+        if ((err = cudaFuncSetAttribute((const void*)k_multi_locate<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        smem)) != cudaSuccess ||
+            (err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_multi_locate<256>, threads,
+                                                                 smem)) != cudaSuccess)
+            return multi_fail("dfa_multi_locate", err);
+        if (occ <= 0) return set_last_error(DFA_ECUDA, "dfa_multi_locate: kernel does not fit on an SM");
+        const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * sms);
+        k_multi_locate<256><<<(unsigned)grid, threads, smem, st>>>(a);
+        if ((err = cudaGetLastError()) != cudaSuccess) return multi_fail("dfa_multi_locate", err);
+    }
+    k_sort_segments<<<npat, 512, 0, st>>>(d_pos, w, w + npat, cursor, status);
+    if ((err = cudaGetLastError()) != cudaSuccess) return multi_fail("dfa_multi_locate", err);
+    return DFA_OK;
+}
+
+int dfa_multi_locate_status(const void* d_work, int32_t npat, void* stream)
+{
+    if (!d_work || npat < 1 || npat > kMultiMaxPat) return DFA_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint8_t* st_addr =
+        static_cast<const uint8_t*>(d_work) + (int64_t)npat * 16 + (((int64_t)npat * 4 + 15) & ~(int64_t)15);
+    unsigned long long v = 0;
+    cudaError_t err;
+    if ((err = cudaStreamSynchronize(st)) != cudaSuccess ||
+        (err = cudaMemcpy(&v, st_addr, 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return multi_fail("dfa_multi_locate_status", err);
+    return v ? DFA_EINVAL : DFA_OK;
 }
 
 }  // extern "C"

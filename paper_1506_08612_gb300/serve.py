@@ -19,9 +19,12 @@ GPU and answers queries {sequence, patterns, mode} as they arrive:
   positions are admitted when they fit in the position arena (a fixed
   device buffer, first-fit), in arrival order, and wait otherwise.  A request
   larger than the whole arena fails with an error instead of waiting forever.
-* **Find stage.**  Each distinct positions pattern is located with the
-  single-pattern find (sorted start positions, exact count as capacity) into
-  the admitted region, and the region is copied back in one transfer.
+* **Find stage.**  The distinct positions patterns with at most
+  DFA_LOCATE_MAX occurrences are located together: one walk of their
+  multi-pattern automaton writes each occurrence into its pattern's segment
+  of the admitted region and each segment is sorted on the device
+  (dfa_multi_locate); every other one by the single-pattern find (exact
+  count as capacity).  The region is copied back in one transfer.
 
 The GPU work sits behind an engine interface (``GpuEngine``) so the
 scheduler's policy can run against a stand-in engine on the CPU.
@@ -128,10 +131,11 @@ class GpuEngine:
     position arena, and the two stages as non-blocking jobs."""
 
     def __init__(self, sequences, slots: int = 4, arena_bytes: int = 8 << 30,
-                 table_bytes: int = 64 << 20, device=None, plain: bool = False):
-        """plain=True counts with one single-pattern launch per pattern
-        instead of the multi-pattern automaton (the unbatched form, for
-        comparison)."""
+                 table_bytes: int = 64 << 20, device=None, plain: bool = False, locate: bool | None = None):
+        """plain=True counts and locates with one single-pattern launch per
+        pattern instead of the multi-pattern automaton (the unbatched form,
+        for comparison); locate (default: not plain) locates the patterns
+        with few occurrences together in one walk."""
         import torch
 
         import paper_1506_08612_gb300 as dd
@@ -148,6 +152,7 @@ class GpuEngine:
         self.arena_bytes = int(arena_bytes)
         self.arena = torch.empty(self.arena_bytes // 8, dtype=torch.int64, device=self.device)
         self.plain = plain
+        self.locate = (not plain) if locate is None else bool(locate)
 
     # -- count stage: one multi-pattern launch over the batch's sequence
     def launch_count(self, slot: int, seq: int, patterns):
@@ -191,38 +196,61 @@ class GpuEngine:
             ev.record(st)
         return {"ev": ev, "host": host, "keep": (tabs, out)}
 
-    # -- find stage: the single-pattern find of each positions pattern into
-    #    the admitted arena region, then one copy of the region to the host
+    # -- find stage: positions of the batch's positions patterns into the
+    #    admitted arena region, then one copy of the region to the host.
+    #    Patterns with at most DFA_LOCATE_MAX occurrences are located
+    #    together in one walk of their multi-pattern automaton (each
+    #    pattern's segment sorted on the device); the others by the
+    #    single-pattern find, one each.
     def launch_find(self, slot: int, seq: int, patterns, counts, region):
         dd, torch = self.dd, self.torch
         st = self.streams[slot]
         off, nbytes = region
         base = off // 8
-        tabs = []
-        need = sum((dd.dfa_table_bytes(len(p)) + 255) // 256 * 256 for p, c in zip(patterns, counts) if c)
+        counts = [int(c) for c in counts]
+        sparse = [i for i, c in enumerate(counts) if 0 < c <= dd.DFA_LOCATE_MAX] if self.locate else []
+        sset = set(sparse)
+        dense = [i for i, c in enumerate(counts) if c and i not in sset]
+        order = sparse + dense                         # layout of the region
+        mt = None
+        if sparse:
+            mt = dd.MultiTable([patterns[i] for i in sparse], device=False)
+        mt_bytes = (mt.image_bytes() + 255) // 256 * 256 if mt is not None else 0
+        need = mt_bytes + sum((dd.dfa_table_bytes(len(patterns[i])) + 255) // 256 * 256 for i in dense)
         if need > self.tab[slot].numel():
             self.tab[slot] = torch.empty(need, dtype=torch.uint8, device=self.device)
         text = self.seqs[seq]
-        total = int(sum(int(c) for c in counts))
+        total = sum(counts)
+        tabs = []
         with torch.cuda.stream(st):
             cnt = torch.zeros(max(len(patterns), 1), dtype=torch.int64, device=self.device)
-            toff, poff = 0, base
-            for i, (p, c) in enumerate(zip(patterns, counts)):
-                if not c:
-                    continue                        # nothing to locate
+            poff = base
+            if mt is not None:
+                mt.attach(self.tab[slot][:mt_bytes], stream=st)
+                work = torch.empty(dd.dfa_multi_locate_work_bytes(len(sparse)), dtype=torch.uint8,
+                                   device=self.device)
+                ns = sum(counts[i] for i in sparse)
+                dd.dfa_multi_locate(text, mt, [counts[i] for i in sparse], self.arena[poff:poff + ns], work,
+                                    stream=st)
+                poff += ns
+                tabs.append((mt, work))
+            toff = mt_bytes
+            for i in dense:
+                p, c = patterns[i], counts[i]
                 tb = dd.dfa_table_bytes(len(p))
                 t = dd.Table(p, into=self.tab[slot][toff:toff + tb], stream=st)
                 toff += (tb + 255) // 256 * 256
                 tabs.append(t)
-                dd.dfa_find(text, t, self.arena[poff:poff + int(c)], cnt[i:i + 1], self.ws[slot], stream=st)
-                poff += int(c)
+                dd.dfa_find(text, t, self.arena[poff:poff + c], cnt[i:i + 1], self.ws[slot], stream=st)
+                poff += c
             host = torch.empty(max(total, 1), dtype=torch.int64, pin_memory=True)
             host[:total].copy_(self.arena[base:base + total], non_blocking=True)
             hcnt = torch.empty(cnt.numel(), dtype=torch.int64, pin_memory=True)
             hcnt.copy_(cnt, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        return {"ev": ev, "host": host, "hcnt": hcnt, "keep": tabs, "counts": [int(c) for c in counts]}
+        return {"ev": ev, "host": host, "hcnt": hcnt, "keep": tabs, "counts": counts, "order": order,
+                "dense": dense}
 
     @staticmethod
     def done(job) -> bool:
@@ -235,16 +263,21 @@ class GpuEngine:
     @staticmethod
     def find_result(job):
         counts = job["counts"]
-        got = job["hcnt"].numpy()[:len(counts)]
-        if not np.array_equal(got, np.asarray(counts, dtype=np.int64)):
-            raise RuntimeError("find counts differ from the count stage")
+        got = job["hcnt"].numpy()
+        for i in job["dense"]:
+            if int(got[i]) != counts[i]:
+                raise RuntimeError("find counts differ from the count stage")
         h = job["host"].numpy()
-        out, o = [], 0
-        for c in counts:
-            out.append(h[o:o + c].copy())
-            o += c
+        out = [np.zeros(0, np.int64) for _ in counts]
+        o = 0
+        for i in job["order"]:
+            out[i] = h[o:o + counts[i]].copy()
+            o += counts[i]
         for t in job["keep"]:
-            t.free()
+            if isinstance(t, tuple):
+                t[0].free()
+            else:
+                t.free()
         return out
 
 

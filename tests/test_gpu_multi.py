@@ -128,3 +128,54 @@ def test_graph_captured_launch(gpu):
         g.replay()
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_multi_locate_sorted_positions(gpu):
+    # every pattern's sorted start positions from one walk of the automaton:
+    # patterns of several lengths (a duplicate, nested ones), copies planted
+    # across chunk borders and in the overlap, an unaligned text
+    import torch
+    n = 3_000_011
+    t = synth.genome_text(n, 410, mask_mean=80, n_gap_mean=200_000, n_run_mean=3_000)
+    lens = synth.uniform_ints(40, 40, 411) + 7                      # 7..46
+    pats = [synth.pattern(int(m), 4200 + i) for i, m in enumerate(lens)]
+    pats += [pats[5], pats[9][:8], pats[9][:12], b"GATTACAGATTACA"]
+    for i, p in enumerate(pats):
+        at = synth.uniform_ints(30, n - len(p), 4300 + i)
+        at = np.concatenate([at, [1024 * k - len(p) // 2 for k in range(1, 40, 7)]])
+        synth.plant(t, p, at)
+    for text, td in ((t, _dev(t)), (t[3:], _dev(t)[3:])):
+        mt = gpu.MultiTable(pats)
+        counts = gpu.multi_count([td], mt)[0]
+        assert counts.max() <= gpu.DFA_LOCATE_MAX
+        total = int(counts.sum())
+        pos = torch.full((total,), -1, dtype=torch.int64, device="cuda")
+        work = torch.empty(gpu.dfa_multi_locate_work_bytes(len(pats)), dtype=torch.uint8, device="cuda")
+        gpu.dfa_multi_locate(td, mt, counts, pos, work)
+        assert gpu.dfa_multi_locate_status(work, len(pats)) == gpu.DFA_OK
+        got = pos.cpu().numpy()
+        o = 0
+        for p, c in zip(pats, counts):
+            want_c, want_p = oracle.find_brute(text, p)
+            assert int(c) == want_c
+            assert np.array_equal(got[o:o + want_c], want_p), p
+            o += want_c
+
+
+def test_multi_locate_rejects_and_reports(gpu):
+    import torch
+    t = synth.genome_text(500_000, 412)
+    td = _dev(t)
+    pats = [b"ACGTACGT", b"TTGACCA"]
+    mt = gpu.MultiTable(pats)
+    counts = gpu.multi_count([td], mt)[0]
+    work = torch.empty(gpu.dfa_multi_locate_work_bytes(2), dtype=torch.uint8, device="cuda")
+    pos = torch.empty(int(counts.sum()) + 8, dtype=torch.int64, device="cuda")
+    with pytest.raises(gpu.DfaError):                       # a count above the bound
+        gpu.dfa_multi_locate(td, mt, [gpu.DFA_LOCATE_MAX + 1, 0], pos, work)
+    with pytest.raises(gpu.DfaError):                       # positions buffer too small
+        gpu.dfa_multi_locate(td, mt, counts, pos[:1], work)
+    # counts that do not belong to the text: the segments do not fill exactly
+    wrong = [int(counts[0]) + 1, int(counts[1])]
+    gpu.dfa_multi_locate(td, mt, wrong, pos, work)
+    assert gpu.dfa_multi_locate_status(work, 2) == gpu.DFA_EINVAL
