@@ -38,7 +38,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .batched import MAX_STATES, new_prefixes
+from .batched import MAX_STATES
 
 
 # ------------------------------------------------------------------ queries
@@ -55,6 +55,8 @@ class Query:
     positions: list | None = None        # per pattern, sorted int64 start positions
     error: str | None = None
     batch: int = -1                      # id of the batch that served it
+    _keys: set | None = field(default=None, repr=False, compare=False)
+    _prefixes: set | None = field(default=None, repr=False, compare=False)
 
     @property
     def latency(self) -> float:
@@ -267,11 +269,13 @@ class GpuEngine:
         for i in job["dense"]:
             if int(got[i]) != counts[i]:
                 raise RuntimeError("find counts differ from the count stage")
+        # views into the batch's pinned buffer (no second copy); the buffer
+        # lives as long as any of them
         h = job["host"].numpy()
         out = [np.zeros(0, np.int64) for _ in counts]
         o = 0
         for i in job["order"]:
-            out[i] = h[o:o + counts[i]].copy()
+            out[i] = h[o:o + counts[i]]
             o += counts[i]
         for t in job["keep"]:
             if isinstance(t, tuple):
@@ -292,7 +296,8 @@ class Server:
         self.max_batch_queries = max_batch_queries
         self.arena = Arena(engine.arena_bytes)
         self.free_slots = collections.deque(range(engine.nslots))
-        self.waiting = collections.deque()    # queries not yet in a batch
+        self.waiting = {}                      # sequence -> FIFO of queries not yet in a batch
+        self.n_waiting = 0
         self.mem_wait = collections.deque()   # batches waiting for position memory
         self.find_ready = collections.deque() # admitted batches waiting for a slot
         self.active = []                       # (batch, slot) with a job in flight
@@ -315,14 +320,16 @@ class Server:
         return q
 
     def idle(self) -> bool:
-        return not (self._inbox or self.waiting or self.mem_wait or self.find_ready or self.active)
+        return not (self._inbox or self.n_waiting or self.mem_wait or self.find_ready or self.active)
 
     def step(self) -> int:
         """One scheduler iteration; returns how many state changes it made."""
         moved = 0
         with self._lock:
             while self._inbox:
-                self.waiting.append(self._inbox.popleft())
+                q = self._inbox.popleft()
+                self.waiting.setdefault(q.seq, collections.deque()).append(q)
+                self.n_waiting += 1
                 moved += 1
         moved += self._poll()
         moved += self._admit()
@@ -439,33 +446,42 @@ class Server:
             moved += 1
         return moved
 
+    @staticmethod
+    def _query_keys(q):
+        """The query's distinct case-folded patterns and every prefix of
+        them (its trie states), computed once."""
+        if q._keys is None:
+            keys = {_key(p) for p in q.patterns}
+            q._keys = keys
+            q._prefixes = {k[:i] for k in keys for i in range(len(k) + 1)}
+        return q._keys, q._prefixes
+
     def _launch_counts(self) -> int:
         moved = 0
-        while self.waiting and self.free_slots:
-            seq = self.waiting[0].seq
-            take, keep = [], collections.deque()
+        while self.n_waiting and self.free_slots:
+            # the sequence whose oldest waiting query arrived first, then its
+            # queries in arrival order while the automaton's limits allow
+            seq = min((d[0].t_arrive, sq) for sq, d in self.waiting.items() if d)[1]
+            queue = self.waiting[seq]
+            take = []
             index = {}
             prefixes = {b""}                        # the trie's states: distinct prefixes
-            for q in self.waiting:
-                if q.seq != seq:
-                    keep.append(q)
-                    continue
-                new = {_key(p) for p in q.patterns} - index.keys()
-                grow = set()
-                for k in new:
-                    grow.update(new_prefixes(prefixes, k))
+            while queue:
+                q = queue[0]
+                keys, pfx = self._query_keys(q)
+                new = keys - index.keys()
+                grow = len(pfx - prefixes)
                 if take and (len(index) + len(new) > self.max_batch_patterns
-                             or len(prefixes) + len(grow) > MAX_STATES
+                             or len(prefixes) + grow > MAX_STATES
                              or len(take) >= self.max_batch_queries):
-                    keep.append(q)
-                    continue
+                    break
                 for p in q.patterns:
                     k = _key(p)
                     if k not in index:
                         index[k] = len(index)
-                prefixes |= grow
-                take.append(q)
-            self.waiting = keep
+                prefixes |= pfx
+                take.append(queue.popleft())
+            self.n_waiting -= len(take)
             b = Batch(bid=self._next_b, seq=seq, queries=take, patterns=list(index), index=index)
             self._next_b += 1
             for q in take:
