@@ -95,3 +95,40 @@ def test_kmer_census_1GB(gpu):
     want = oracle.kmer_census(text, 6)
     assert np.array_equal(got, want)
     assert int(got.sum()) == oracle.valid_windows(text, 6)
+
+
+def test_serving_full_size_sampled(gpu):
+    # the serving workload's six resident sequences (11.9e9 bytes): a short
+    # Poisson trace of count and positions queries, one per sequence and two
+    # more, each answer checked against the oracle
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1506_08612_gb300.serve import GpuEngine, Server
+    texts, devs = [], []
+    for i, n in enumerate(BATCH_SIZES):
+        t = synth.genome_text(n, 10 + i)
+        texts.append(t)
+        devs.append(_dev(t))
+    trace = synth.query_trace(8, 200.0, len(texts), 31, max_patterns=5, m_lo=7, m_hi=40)
+    for i, e in enumerate(trace[:6]):
+        e["seq"] = i
+    srv = Server(GpuEngine(devs, slots=4, arena_bytes=2 << 30))
+    qs = srv.replay(trace)
+    jobs = [(q, j) for q in qs for j in range(len(q.patterns))]
+
+    def want(qj):
+        q, j = qj
+        if q.mode == "positions":
+            return oracle.find_brute(texts[q.seq], q.patterns[j])
+        return oracle.count_brute(texts[q.seq], q.patterns[j]), None
+
+    with ThreadPoolExecutor(16) as ex:
+        wants = list(ex.map(want, jobs))
+    for (q, j), (wc, wp) in zip(jobs, wants):
+        assert q.error is None, q.error
+        assert int(q.counts[j]) == wc, (q.qid, j)
+        if q.mode == "positions":
+            assert np.array_equal(q.positions[j], wp), (q.qid, j)
+    del devs, srv
+    torch.cuda.empty_cache()
