@@ -1485,7 +1485,51 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                         e_in[i] = e[i];
                         c_in[i] = cnt[i];
                     }
-                    count_stage<LAYOUT>(T, e, cnt, v, ok, r);
+                    if (!FIND && LAYOUT == kLayoutK4 && m <= 8u) {
+                        // count of a short pattern: the relaxed walk of the
+                        // dense find, tested only where it counted
+#pragma unroll
+                        for (int i = 0; i < kRPL; i++) {
+                            if (!ok[i]) continue;
+                            const uint32_t p0 = tl0[i], p1 = tl1[i];
+                            tl0[i] = v[i][3].z;
+                            tl1[i] = v[i][3].w;
+                            const uint32_t x[16] = {v[i][0].x, v[i][0].y, v[i][0].z, v[i][0].w,
+                                                    v[i][1].x, v[i][1].y, v[i][1].z, v[i][1].w,
+                                                    v[i][2].x, v[i][2].y, v[i][2].z, v[i][2].w,
+                                                    v[i][3].x, v[i][3].y, v[i][3].z, v[i][3].w};
+                            uint32_t ee = e[i], c = 0u;
+#pragma unroll
+                            for (int k = 0; k < 16; k++) {
+                                ee = k4_next<LAYOUT>(T.k4, ee, x[k]);
+                                c += ee >> K4_CNT_SHIFT;
+                            }
+                            if (c != 0u) {
+                                const uint8_t* q = rp + i * 32 * kStageW;
+                                const uint4 w0 = lds128_fresh(q + ob), w1 = lds128_fresh(q + (ob ^ 16u)),
+                                            w2 = lds128_fresh(q + (ob ^ 32u)), w3 = lds128_fresh(q + (ob ^ 48u));
+                                const uint32_t bad =
+                                    word_bad(p0) | word_bad(p1) | word_bad(w0.x) | word_bad(w0.y) |
+                                    word_bad(w0.z) | word_bad(w0.w) | word_bad(w1.x) | word_bad(w1.y) |
+                                    word_bad(w1.z) | word_bad(w1.w) | word_bad(w2.x) | word_bad(w2.y) |
+                                    word_bad(w2.z) | word_bad(w2.w) | word_bad(w3.x) | word_bad(w3.y) |
+                                    word_bad(w3.z) | word_bad(w3.w);
+                                if (bad != 0u) {
+                                    // a non-base near a count: this stage exactly
+                                    CountSink cs;
+                                    Walker<LAYOUT, false, CountSink> w{
+                                        T, cs, r != 0u ? exact_state8(T, p0, p1) : 0u, 0u};
+                                    w.vec4(w0, w1, w2, w3, r);
+                                    c = w.cnt;
+                                    ee = w.e;
+                                }
+                            }
+                            e[i] = ee;
+                            cnt[i] += c;
+                        }
+                    } else {
+                        count_stage<LAYOUT>(T, e, cnt, v, ok, r);
+                    }
                     if (FIND) {
 #pragma unroll
                         for (int i = 0; i < kRPL; i++) {
@@ -1530,6 +1574,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                         if (m > 49) h.vec(*reinterpret_cast<const uint4*>(q + (ob ^ 48u)), (uint32_t)C + 48, lim);
                         cnt[i] = h.cnt;
                     } else {
+                        // a short pattern's relaxed count: the exact state
+                        // from the last 8 bytes when they hold a non-base
+                        if (!FIND && LAYOUT == kLayoutK4 && m <= 8u && (word_bad(tl0[i]) | word_bad(tl1[i])) != 0u)
+                            e[i] = exact_state8(T, tl0[i], tl1[i]);
                         CountSink cs;
                         Walker<LAYOUT, true, CountSink> h{T, cs, e[i], cnt[i]};
                         h.vec(h0, (uint32_t)C, lim);
