@@ -770,10 +770,14 @@ constexpr int kTSlotsDense = 16;                 // staged positions per row (de
 constexpr int kMaxStages = 4;
 constexpr int kRelaxedCountStages = 2;           // ring depth of the relaxed count pass
 // Default row length (stages of 64 bytes) of a long text: relaxed layouts
-// (m >= 8) 12 stages, exact layouts 15.  Measured on 3.2e9 bytes: finds of
-// m = 16..64 0.624 ms at 20 stages (1280 B), 0.55 at 12, 0.55-0.56 at 8;
-// the dense find of m = 4 0.960 at 20, 0.911 at 15, 0.945 at 12.
+// 12 stages (16 below m = 12), exact layouts 15.  Measured on 3.2e9 bytes:
+// finds of m = 16 and 64 0.624 ms at 20 stages (1280 B), 0.553/0.557 at 12,
+// 0.565/0.579 at 10, 0.58-0.60 at 11 and 13; m = 8 0.713 at 12, 0.702 at
+// 15, 0.695 at 16 (more replayed stages, longer rows amortise the tile end);
+// the dense find of m = 4 0.960 at 20, 0.941 at 16, 0.911 at 15, 0.925 at 14.
 constexpr int kDefaultStagesRelaxed = 12;
+constexpr int kDefaultStagesRelaxedShort = 16;   // m < kShortRelaxedM
+constexpr int kShortRelaxedM = 12;
 constexpr int kDefaultStagesExact = 15;
 constexpr int kDefer = 4;                        // tiles whose positions wait for their offset
 constexpr int kTicketRing = 8;
@@ -1977,8 +1981,9 @@ int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int
             // at least four tiles per SM, rows of at most the measured best
             const int64_t per = (int64_t)kRows * kStageW * 4 * sms;
             int64_t sps = (n + per - 1) / per;
-            const int64_t cap = (r->layout == kLayoutK4F || r->layout == kLayoutK4S) ? kDefaultStagesRelaxed
-                                                                                     : kDefaultStagesExact;
+            const bool relaxed = r->layout == kLayoutK4F || r->layout == kLayoutK4S;
+            const int64_t cap = !relaxed ? kDefaultStagesExact
+                                         : (m < kShortRelaxedM ? kDefaultStagesRelaxedShort : kDefaultStagesRelaxed);
             sps = std::min<int64_t>(std::max<int64_t>(sps, 2), cap);
             chunk = sps * kStageW;
         }
@@ -2457,12 +2462,17 @@ int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg)
         (void)cudaGetLastError();
         sms = 152;
     }
-    Resolved r;
-    if (resolve(cfg, n, n, true, sms, kOptMinM, &r) == DFA_OK && r.loader == 2) {
-        const int64_t tile_bytes = (int64_t)kRows * r.chunk;
-        return std::max(single, work_bytes_two_pass((n + tile_bytes - 1) / tile_bytes));
+    // the default rows depend on m (shorter from kShortRelaxedM on): size
+    // for every pattern length that takes the two-pass find
+    int64_t need = single;
+    for (int m : {kOptMinM, kShortRelaxedM}) {
+        Resolved r;
+        if (resolve(cfg, n, n, true, sms, m, &r) == DFA_OK && r.loader == 2) {
+            const int64_t tile_bytes = (int64_t)kRows * r.chunk;
+            need = std::max(need, work_bytes_two_pass((n + tile_bytes - 1) / tile_bytes));
+        }
     }
-    return single;
+    return need;
 }
 
 int dfa_find(const uint8_t* d_text, int64_t n, const dfa_table* table, int64_t* d_pos, int64_t cap,

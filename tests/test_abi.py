@@ -90,3 +90,14 @@ def test_sources_share_nothing_with_oracle():
 def test_oracle_lib_builds():
     import oracle
     assert os.path.exists(oracle.build())
+
+
+def test_workspace_covers_every_default_row_length():
+    """With no configuration the workspace must hold the two-pass find of
+    every pattern length: the relaxed layouts take 768-byte rows from m = 12
+    on (the most rows) and 1024-byte rows below; one tile is 512 rows."""
+    import paper_1506_08612_gb300 as dd
+    n = 3_200_000_000
+    tiles = -(-n // (512 * 768))
+    need = 8 * (2 + tiles) + tiles * 512 * (2 + 8)        # header, tile words, row count + stage mask
+    assert dd._lib.dfa_find_workspace_bytes(n, None) >= need
