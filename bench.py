@@ -174,15 +174,25 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def _code_only(src: str) -> str:
+    """C/CUDA source without comments and blank lines (a comment edit does
+    not change the kernels)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+
+
 def kernel_source_digest():
-    """Digest of the single-pattern scan's sources (the kernels dfa_find runs)."""
+    """Digest of the single-pattern scan's code (the kernels dfa_find runs),
+    comments excluded."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1506_08612_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f in ("scan.cu", "automaton.cpp", "dnadfa_internal.h"):
-            with open(os.path.join(csrc, f), "rb") as fh:
+            with open(os.path.join(csrc, f), encoding="utf-8") as fh:
                 h.update(f.encode())
-                h.update(fh.read())
+                h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -11,14 +11,25 @@
 //     four-step composite table over 2-bit base codes, so one lookup
 //     advances the automaton by four bytes; the paper's sparse 256-column
 //     STT (Sec. III-B, Table I) is kept as a selectable layout;
-//   * text arrives in 16-byte vector loads; bytes outside A/C/G/T/a/c/g/t
-//     are detected four at a time and reset the walk to q0 (Sec. III-B);
+//   * the default kernel (k_scan_tma) is persistent, one CTA per SM: tiles
+//     of 512 rows x C bytes, each walker warp streaming its 32 rows through
+//     a ring of TMA boxes (64 bytes x 32 rows) in shared memory; unaligned
+//     or short texts take 16-byte vector loads (k_count / k_find);
+//   * bytes outside A/C/G/T/a/c/g/t reset the walk to q0 (Sec. III-B).  The
+//     walk reads bytes through their 2-bit codes alone (a non-base read as
+//     the base of its code never hides an occurrence) and the exact test
+//     runs only where that walk accepted: for short patterns the stage is
+//     tested with the 8 bytes before it, for patterns of 8 and more the
+//     flagged stages are walked again exactly at the end of the tile;
 //   * counts are reduced by warp shuffles, then one atomic per CTA;
-//   * positions are compacted in text order in one pass: tiles are taken in
-//     order from an atomic ticket, a CTA scans its threads' counts, learns
-//     its tile's global offset by decoupled look-back over its predecessors'
-//     published sums, and writes its positions there.  Every wait is bounded
-//     and reports DFA_ETIMEOUT instead of hanging.
+//   * positions are written in text order.  Patterns of 8 and more: a count
+//     pass leaving per-row counts and stage masks, a scan of the tile totals,
+//     and an exact re-walk of the masked bytes of the rows that accepted.
+//     Shorter patterns: one pass in which tiles are taken in order from an
+//     atomic ticket, a CTA learns its tile's global offset by decoupled
+//     look-back over its predecessors' published sums, and writes its
+//     positions there.  Every wait is bounded and reports DFA_ETIMEOUT
+//     instead of hanging.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
