@@ -82,6 +82,58 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
 
 
+def _nbytes(t) -> int:
+    return int(t.numel() * t.element_size())
+
+
+def _desc(t) -> str:
+    if not hasattr(t, "device"):
+        return type(t).__name__
+    return f"{t.dtype} on {t.device}" + ("" if t.is_contiguous() else ", not contiguous")
+
+
+def _dev(t, what: str, dtype=None, numel: int = 0):
+    """Checks a device-buffer argument: a contiguous CUDA tensor on the
+    current CUDA device (the library launches there), of ``dtype`` when
+    given, with at least ``numel`` elements.  The library reads and writes
+    such buffers as flat arrays at ``data_ptr()``, so a strided view, a host
+    tensor or a narrower element type would be misread or overrun."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{what}: expected a CUDA tensor, got {_desc(t)}")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{what}: tensor on {t.device}, current device is cuda:{torch.cuda.current_device()}")
+    if t.numel() < numel:
+        raise ValueError(f"{what}: {t.numel()} elements, at least {numel} needed")
+    return t
+
+
+def _host(t, what: str, dtype):
+    """Checks a host-buffer argument: a contiguous CPU tensor of ``dtype``."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise ValueError(f"{what}: expected a CPU tensor, got {_desc(t)}")
+    if t.dtype != dtype:
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous tensor")
+    return t
+
+
+def _u8():
+    import torch
+    return torch.uint8
+
+
+def _i64():
+    import torch
+    return torch.int64
+
+
 class Table:
     """Automaton of one pattern (library-owned host + device tables)."""
 
@@ -97,8 +149,9 @@ class Table:
         if into is None:
             _check(_lib.dfa_build(pattern, len(pattern), ctypes.byref(h)), "dfa_build")
         else:
+            _dev(into, "Table(into=)")
             _check(_lib.dfa_build_into(pattern, len(pattern), _ptr(into),
-                                       int(into.numel() * into.element_size()), _stream(stream),
+                                       _nbytes(into), _stream(stream),
                                        ctypes.byref(h)), "dfa_build_into")
         self._h = h
         self._into = into
@@ -145,6 +198,8 @@ def dfa_export_stt(table: Table) -> np.ndarray:
 
 def dfa_count(text, table: Table, count, cfg=None, stream=None) -> None:
     """Enqueue a count; ``count`` is a 1-element int64 device tensor."""
+    _dev(text, "dfa_count text", _u8())
+    _dev(count, "dfa_count count", _i64(), 1)
     _check(_lib.dfa_count(_ptr(text), int(text.numel()), table.handle, _ptr(count), _cfg(cfg),
                           _stream(stream)), "dfa_count")
 
@@ -157,15 +212,24 @@ def dfa_find(text, table: Table, positions, count, workspace, cfg=None, stream=N
              n: int | None = None) -> None:
     """Enqueue count + sorted start positions (int64 device tensor, capacity =
     its length) into ``count`` (1-element int64 device tensor)."""
+    _dev(text, "dfa_find text", _u8())
+    if positions is not None:
+        _dev(positions, "dfa_find positions", _i64())
+    _dev(count, "dfa_find count", _i64(), 1)
+    _dev(workspace, "dfa_find workspace")
     cap = int(positions.numel()) if positions is not None else 0
     nbytes = int(text.numel()) if n is None else int(n)
+    if not 0 <= nbytes <= text.numel():
+        raise ValueError(f"dfa_find: n={nbytes} outside [0, {text.numel()}]")
     _check(_lib.dfa_find(_ptr(text), nbytes, table.handle, _ptr(positions), cap, _ptr(count),
-                         _ptr(workspace), int(workspace.numel() * workspace.element_size()),
+                         _ptr(workspace), _nbytes(workspace),
                          _cfg(cfg), _stream(stream)), "dfa_find")
 
 
 def dfa_find_status(workspace, count, cap: int, stream=None):
     """Synchronise and return (return code, count)."""
+    _dev(workspace, "dfa_find_status workspace")
+    _dev(count, "dfa_find_status count", _i64(), 1)
     h = ctypes.c_uint64(0)
     rc = _lib.dfa_find_status(_ptr(workspace), _ptr(count), int(cap), ctypes.byref(h),
                               _stream(stream))
@@ -177,6 +241,10 @@ def dfa_find_noalloc(text, table: Table, positions, count, cfg=None, stream=None
     callers that may not allocate device memory.  A bounded wait that gave up
     sets bit 63 of ``count``; calls that may overlap on the GPU race on the
     shared workspace."""
+    _dev(text, "dfa_find_noalloc text", _u8())
+    if positions is not None:
+        _dev(positions, "dfa_find_noalloc positions", _i64())
+    _dev(count, "dfa_find_noalloc count", _i64(), 1)
     cap = int(positions.numel()) if positions is not None else 0
     rc = _lib.dfa_find_noalloc(_ptr(text), int(text.numel()), table.handle, _ptr(positions), cap,
                                _ptr(count), _cfg(cfg), _stream(stream))
@@ -191,7 +259,8 @@ def dfa_debug_wait_timeout(workspace, tile: int, stream=None) -> None:
     """Enqueue the look-back wait of ``tile`` on ``workspace`` (failure
     detection test: on a zeroed workspace the wait gives up and
     dfa_find_status reports DFA_ETIMEOUT)."""
-    _check(_lib.dfa_debug_wait_timeout(_ptr(workspace), int(workspace.numel() * workspace.element_size()),
+    _dev(workspace, "dfa_debug_wait_timeout workspace")
+    _check(_lib.dfa_debug_wait_timeout(_ptr(workspace), _nbytes(workspace),
                                        int(tile), _stream(stream)), "dfa_debug_wait_timeout")
 
 
@@ -204,10 +273,14 @@ def dfa_find_host(h_text, table: Table, h_positions, stage, seg: int, stream=Non
     copy bandwidth), ``h_positions`` a CPU int64 tensor (or None), ``stage``
     a device uint8 tensor of dfa_host_stage_bytes(seg, cap) bytes.
     Returns (return code, count)."""
+    _host(h_text, "dfa_find_host h_text", _u8())
+    if h_positions is not None:
+        _host(h_positions, "dfa_find_host h_positions", _i64())
+    _dev(stage, "dfa_find_host stage")
     cap = int(h_positions.numel()) if h_positions is not None else 0
     h = ctypes.c_uint64(0)
     rc = _lib.dfa_find_host(_ptr(h_text), int(h_text.numel()), table.handle, _ptr(h_positions), cap,
-                            ctypes.byref(h), _ptr(stage), int(stage.numel()), int(seg),
+                            ctypes.byref(h), _ptr(stage), _nbytes(stage), int(seg),
                             _stream(stream))
     if rc not in (DFA_OK, DFA_ETRUNC):
         raise DfaError(rc, "dfa_find_host")
@@ -219,11 +292,19 @@ def dfa_find_batched(text, tables, positions, counts, workspace, cfg=None, strea
     ``positions`` a list of int64 device tensors (capacity = length, or
     None), ``counts`` an int64 device tensor of len(tables)."""
     k = len(tables)
+    _dev(text, "dfa_find_batched text", _u8())
+    if len(positions) != k:
+        raise ValueError(f"dfa_find_batched: {len(positions)} position buffers for {k} tables")
+    for p in positions:
+        if p is not None:
+            _dev(p, "dfa_find_batched positions", _i64())
+    _dev(counts, "dfa_find_batched counts", _i64(), k)
+    _dev(workspace, "dfa_find_batched workspace")
     th = (ctypes.c_void_p * k)(*[t.handle.value for t in tables])
     ph = (ctypes.c_void_p * k)(*[p.data_ptr() if p is not None and p.numel() else 0 for p in positions])
     cp = (ctypes.c_int64 * k)(*[int(p.numel()) if p is not None else 0 for p in positions])
     _check(_lib.dfa_find_batched(_ptr(text), int(text.numel()), th, k, ph, cp, _ptr(counts), _ptr(workspace),
-                                 int(workspace.numel() * workspace.element_size()), _cfg(cfg), _stream(stream)),
+                                 _nbytes(workspace), _cfg(cfg), _stream(stream)),
            "dfa_find_batched")
 
 
@@ -237,13 +318,20 @@ def dfa_find_host_multi(h_text, tables, h_positions, stage, seg: int, stream=Non
     ``h_positions`` a list of CPU int64 tensors (or None), one per table.
     Returns (return code, list of counts)."""
     k = len(tables)
+    _host(h_text, "dfa_find_host_multi h_text", _u8())
+    if len(h_positions) != k:
+        raise ValueError(f"dfa_find_host_multi: {len(h_positions)} position buffers for {k} tables")
+    for p in h_positions:
+        if p is not None:
+            _host(p, "dfa_find_host_multi h_positions", _i64())
+    _dev(stage, "dfa_find_host_multi stage")
     caps = [int(p.numel()) if p is not None else 0 for p in h_positions]
     th = (ctypes.c_void_p * k)(*[t.handle.value for t in tables])
     ph = (ctypes.c_void_p * k)(*[p.data_ptr() if p is not None and p.numel() else 0 for p in h_positions])
     cp = (ctypes.c_int64 * k)(*caps)
     hc = (ctypes.c_uint64 * k)()
     rc = _lib.dfa_find_host_multi(_ptr(h_text), int(h_text.numel()), th, k, ph, cp, hc, _ptr(stage),
-                                  int(stage.numel()), int(seg), _stream(stream))
+                                  _nbytes(stage), int(seg), _stream(stream))
     if rc not in (DFA_OK, DFA_ETRUNC):
         raise DfaError(rc, "dfa_find_host_multi")
     return rc, [int(x) for x in hc]
@@ -299,7 +387,8 @@ class MultiTable:
     def attach(self, into, stream=None) -> None:
         """Copy the automaton into ``into`` (device uint8 tensor of at least
         image_bytes(), kept alive by the caller) on ``stream``."""
-        _check(_lib.dfa_multi_attach(self.handle, _ptr(into), int(into.numel() * into.element_size()),
+        _dev(into, "MultiTable.attach into")
+        _check(_lib.dfa_multi_attach(self.handle, _ptr(into), _nbytes(into),
                                      _stream(stream)), "dfa_multi_attach")
         self._into = into
 
@@ -320,6 +409,9 @@ def dfa_multi_count(texts, table: MultiTable, counts, cfg=None, stream=None) -> 
     (device uint8 tensors) into ``counts`` (device int64 tensor of
     len(texts) * npat, row-major by sequence)."""
     ns = len(texts)
+    for t in texts:
+        _dev(t, "dfa_multi_count text", _u8())
+    _dev(counts, "dfa_multi_count counts", _i64(), ns * table.npat)
     ptrs = (ctypes.c_void_p * ns)(*[t.data_ptr() if t.numel() else 0 for t in texts])
     lens = (ctypes.c_int64 * ns)(*[int(t.numel()) for t in texts])
     _check(_lib.dfa_multi_count(ptrs, lens, ns, table.handle, _ptr(counts), _cfg(cfg),
@@ -335,15 +427,22 @@ def dfa_multi_locate(text, table: MultiTable, counts, positions, workspace, stre
     into ``positions`` (int64 device tensor, pattern p's segment at the sum
     of the counts before it); ``counts``: the exact per-pattern counts (host
     sequence), each at most DFA_LOCATE_MAX."""
+    _dev(text, "dfa_multi_locate text", _u8())
+    if positions is not None:
+        _dev(positions, "dfa_multi_locate positions", _i64())
+    _dev(workspace, "dfa_multi_locate workspace")
+    if len(counts) != table.npat:
+        raise ValueError(f"dfa_multi_locate: {len(counts)} counts for {table.npat} patterns")
     hc = (ctypes.c_uint64 * table.npat)(*[int(c) for c in counts])
     rc = _lib.dfa_multi_locate(_ptr(text), int(text.numel()), table.handle, hc, _ptr(positions),
                                int(positions.numel()) if positions is not None else 0, _ptr(workspace),
-                               int(workspace.numel() * workspace.element_size()), _stream(stream))
+                               _nbytes(workspace), _stream(stream))
     if rc != DFA_OK:
         raise DfaError(rc, f"dfa_multi_locate [{_lib.dfa_last_error().decode(errors='replace')}]")
 
 
 def dfa_multi_locate_status(workspace, npat: int, stream=None) -> int:
+    _dev(workspace, "dfa_multi_locate_status workspace")
     return int(_lib.dfa_multi_locate_status(_ptr(workspace), int(npat), _stream(stream)))
 
 

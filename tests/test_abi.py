@@ -101,3 +101,40 @@ def test_workspace_covers_every_default_row_length():
     tiles = -(-n // (512 * 768))
     need = 8 * (2 + tiles) + tiles * 512 * (2 + 8)        # header, tile words, row count + stage mask
     assert dd._lib.dfa_find_workspace_bytes(n, None) >= need
+
+
+def test_binding_rejects_bad_buffers_before_the_library():
+    """The binding hands the library flat ``data_ptr()`` arrays, so it turns
+    host tensors where device buffers belong (and device ones where host
+    buffers belong), wrong element types, strided views and mismatched list
+    lengths into Python errors before any call; the table is never touched."""
+    import torch
+
+    import paper_1506_08612_gb300 as dd
+    text = torch.zeros(100, dtype=torch.uint8)
+    i64 = torch.zeros(4, dtype=torch.int64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dd.dfa_count(text, None, i64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dd.dfa_find(text, None, i64, i64, text)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dd.dfa_find_noalloc(b"ACGT", None, None, i64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dd.dfa_multi_count([text], None, i64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dd.dfa_multi_locate(text, None, [1], i64, text)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dd.dfa_find_status(text, i64, 4)
+    # host-buffer calls: element type, layout, list lengths, device stage
+    with pytest.raises(TypeError, match="torch.uint8"):
+        dd.dfa_find_host(torch.zeros(8, dtype=torch.int32), None, None, text, 1 << 20)
+    with pytest.raises(TypeError, match="torch.int64"):
+        dd.dfa_find_host(text, None, torch.zeros(8, dtype=torch.int32), text, 1 << 20)
+    with pytest.raises(ValueError, match="contiguous"):
+        dd.dfa_find_host(text[::2], None, None, text, 1 << 20)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dd.dfa_find_host(text, None, i64, text, 1 << 20)
+    with pytest.raises(ValueError, match="2 position buffers for 1 tables"):
+        dd.dfa_find_host_multi(text, [None], [i64, i64], text, 1 << 20)
+    with pytest.raises(ValueError, match="CPU tensor"):
+        dd.dfa_find_host(b"ACGT", None, None, text, 1 << 20)

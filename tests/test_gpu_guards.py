@@ -81,3 +81,31 @@ def test_multi_outputs_write_inside_their_buffers(gpu):
     for p, c in zip(pats, c0):
         assert np.array_equal(got[o:o + c], oracle.find_brute(texts[0], p)[1])
         o += c
+
+
+def test_binding_rejects_misfit_device_buffers(gpu):
+    """Device tensors the library would misread or overrun (a narrower
+    element type, a strided view, a count buffer too short) are refused in
+    Python, before any launch; a well-formed call after them still counts."""
+    import torch
+    t = synth.genome_text(100_003, 630)
+    pat = synth.pattern(6, 6300)
+    td = torch.from_numpy(t).cuda()
+    tab = gpu.dfa_build(pat)
+    ws = torch.empty(gpu.dfa_find_workspace_bytes(td.numel()), dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(TypeError, match="torch.int64"):
+        gpu.dfa_find(td, tab, torch.empty(64, dtype=torch.int32, device="cuda"), cnt, ws)
+    with pytest.raises(TypeError, match="torch.uint8"):
+        gpu.dfa_count(td.to(torch.int16), tab, cnt)
+    with pytest.raises(ValueError, match="contiguous"):
+        gpu.dfa_count(td[::2], tab, cnt)
+    with pytest.raises(ValueError, match="at least 1"):
+        gpu.dfa_count(td, tab, cnt[:0])
+    with pytest.raises(ValueError, match="outside"):
+        gpu.dfa_find(td, tab, None, cnt, ws, n=td.numel() + 1)
+    mt = gpu.MultiTable([pat, synth.pattern(9, 6301)])
+    with pytest.raises(ValueError, match="at least 4"):
+        gpu.dfa_multi_count([td, td], mt, torch.zeros(3, dtype=torch.int64, device="cuda"))
+    gpu.dfa_count(td, tab, cnt)
+    assert int(cnt.item()) == oracle.count_brute(t, pat)
