@@ -62,7 +62,9 @@ class BatchedCount:
     between runs, their storage may not).  patterns: bytes/str.  cfg:
     "auto" (autotuner), None (library default) or a dfa_config dict.
     ``run()`` enqueues the whole batch on ``stream`` (one graph replay when
-    captured); ``result()`` waits and returns uint64[nseq, npat].
+    captured), after the work already enqueued on the caller's current
+    stream (writes into the texts, for instance); ``result()`` waits and
+    returns uint64[nseq, npat].
     """
 
     def __init__(self, texts, patterns, cfg="auto", stream=None, capture: bool = True):
@@ -82,6 +84,9 @@ class BatchedCount:
                            for i in range(0, len(self.texts), MAX_SEQ_PER_LAUNCH)]
         self.out = [[torch.zeros(len(sg) * t.npat, dtype=torch.int64, device=self.device)
                      for t in self.tables] for sg in self.seq_groups]
+        # the outputs were zeroed, and the texts written, on the caller's
+        # stream; ``stream`` is a separate (non-blocking) stream
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
         if cfg == "auto":
             with torch.cuda.stream(self.stream):
                 self.cfgs = [autotune.tune_multi(self.texts, t, stream=self.stream)
@@ -107,8 +112,10 @@ class BatchedCount:
                 dfa_multi_count(seqs, t, self.out[si][ti], cfg=self.cfgs[ti], stream=self.stream)
 
     def run(self):
-        """Enqueue the batch (asynchronous)."""
+        """Enqueue the batch (asynchronous), ordered after the work already
+        enqueued on the caller's current stream."""
         import torch
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
         if self.graph is not None:
             with torch.cuda.stream(self.stream):
                 self.graph.replay()
@@ -126,6 +133,7 @@ class BatchedCount:
         return res
 
     def close(self):
+        self.stream.synchronize()
         self.graph = None
         for t in self.tables:
             t.free()

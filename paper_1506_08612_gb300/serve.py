@@ -155,6 +155,9 @@ class GpuEngine:
         self.arena = torch.empty(self.arena_bytes // 8, dtype=torch.int64, device=self.device)
         self.plain = plain
         self.locate = (not plain) if locate is None else bool(locate)
+        # the slots' streams are non-blocking: the sequences' contents must be
+        # on the device before the first batch reads them
+        torch.cuda.current_stream(self.device).synchronize()
 
     # -- count stage: one multi-pattern launch over the batch's sequence
     def launch_count(self, slot: int, seq: int, patterns):
