@@ -38,7 +38,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .batched import MAX_STATES
+from . import DFA_MAX_M
+from .batched import MAX_STATES, group_patterns
 
 
 # ------------------------------------------------------------------ queries
@@ -66,6 +67,29 @@ class Query:
 def _key(p) -> bytes:
     b = p.encode() if isinstance(p, str) else bytes(p)
     return b.upper()
+
+
+_LETTERS = frozenset(b"ACGTacgt")
+
+
+def query_error(q: Query, nseq: int | None = None) -> str | None:
+    """Why the query cannot be served (None if it can): an unknown mode or
+    sequence, no patterns, or a pattern that is not 1 to DFA_MAX_M letters
+    of {A,C,G,T} (either case), the alphabet of Sec. III-A."""
+    if q.mode not in ("count", "positions"):
+        return f"unknown mode {q.mode!r}"
+    if nseq is not None and not (isinstance(q.seq, (int, np.integer)) and 0 <= q.seq < nseq):
+        return f"no sequence {q.seq!r} (the server holds {nseq})"
+    if not q.patterns:
+        return "no patterns"
+    for p in q.patterns:
+        try:
+            b = p.encode("ascii") if isinstance(p, str) else bytes(p)
+        except (UnicodeEncodeError, TypeError, ValueError):
+            return f"pattern {p!r} is not a byte string of ACGT letters"
+        if not 1 <= len(b) <= DFA_MAX_M or not _LETTERS.issuperset(b):
+            return f"pattern {b[:80]!r}: 1 to {DFA_MAX_M} letters of ACGT expected"
+    return None
 
 
 # ------------------------------------------------------------------ arena
@@ -146,6 +170,7 @@ class GpuEngine:
         self.seqs = list(sequences)
         self.device = device or self.seqs[0].device
         self.nslots = slots
+        self.nseq = len(self.seqs)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         nmax = max(int(s.numel()) for s in self.seqs)
         self.ws = [torch.empty(dd.dfa_find_workspace_bytes(nmax), dtype=torch.uint8, device=self.device)
@@ -165,19 +190,25 @@ class GpuEngine:
         st = self.streams[slot]
         if self.plain:
             return self._launch_count_plain(slot, seq, patterns)
-        mt = dd.MultiTable(patterns, device=False)
-        need = mt.image_bytes()
-        if need > self.tab[slot].numel():
-            self.tab[slot] = torch.empty(need, dtype=torch.uint8, device=self.device)
+        # one automaton per group of patterns within its limits (a batch is
+        # formed to need one; a single query may need several)
+        groups = group_patterns(patterns)
+        mts = [dd.MultiTable([patterns[i] for i in g], device=False) for g in groups]
+        sizes = [(mt.image_bytes() + 255) // 256 * 256 for mt in mts]
+        if sum(sizes) > self.tab[slot].numel():
+            self.tab[slot] = torch.empty(sum(sizes), dtype=torch.uint8, device=self.device)
         with torch.cuda.stream(st):
-            mt.attach(self.tab[slot], stream=st)
             out = torch.empty(len(patterns), dtype=torch.int64, device=self.device)
-            dd.dfa_multi_count([self.seqs[seq]], mt, out, stream=st)
+            toff = 0
+            for g, mt, sz in zip(groups, mts, sizes):
+                mt.attach(self.tab[slot][toff:toff + sz], stream=st)
+                dd.dfa_multi_count([self.seqs[seq]], mt, out[g[0]:g[-1] + 1], stream=st)
+                toff += sz
             host = torch.empty(len(patterns), dtype=torch.int64, pin_memory=True)
             host.copy_(out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        return {"ev": ev, "host": host, "keep": (mt, out)}
+        return {"ev": ev, "host": host, "keep": (mts, out)}
 
     def _launch_count_plain(self, slot, seq, patterns):
         dd, torch = self.dd, self.torch
@@ -217,10 +248,10 @@ class GpuEngine:
         sset = set(sparse)
         dense = [i for i, c in enumerate(counts) if c and i not in sset]
         order = sparse + dense                         # layout of the region
-        mt = None
-        if sparse:
-            mt = dd.MultiTable([patterns[i] for i in sparse], device=False)
-        mt_bytes = (mt.image_bytes() + 255) // 256 * 256 if mt is not None else 0
+        sgroups = [[sparse[j] for j in g] for g in group_patterns([patterns[i] for i in sparse])]
+        mts = [dd.MultiTable([patterns[i] for i in g], device=False) for g in sgroups]
+        msizes = [(mt.image_bytes() + 255) // 256 * 256 for mt in mts]
+        mt_bytes = sum(msizes)
         need = mt_bytes + sum((dd.dfa_table_bytes(len(patterns[i])) + 255) // 256 * 256 for i in dense)
         if need > self.tab[slot].numel():
             self.tab[slot] = torch.empty(need, dtype=torch.uint8, device=self.device)
@@ -230,16 +261,17 @@ class GpuEngine:
         with torch.cuda.stream(st):
             cnt = torch.zeros(max(len(patterns), 1), dtype=torch.int64, device=self.device)
             poff = base
-            if mt is not None:
-                mt.attach(self.tab[slot][:mt_bytes], stream=st)
-                work = torch.empty(dd.dfa_multi_locate_work_bytes(len(sparse)), dtype=torch.uint8,
+            toff = 0
+            for g, mt, sz in zip(sgroups, mts, msizes):
+                mt.attach(self.tab[slot][toff:toff + sz], stream=st)
+                toff += sz
+                work = torch.empty(dd.dfa_multi_locate_work_bytes(len(g)), dtype=torch.uint8,
                                    device=self.device)
-                ns = sum(counts[i] for i in sparse)
-                dd.dfa_multi_locate(text, mt, [counts[i] for i in sparse], self.arena[poff:poff + ns], work,
+                ns = sum(counts[i] for i in g)
+                dd.dfa_multi_locate(text, mt, [counts[i] for i in g], self.arena[poff:poff + ns], work,
                                     stream=st)
                 poff += ns
                 tabs.append((mt, work))
-            toff = mt_bytes
             for i in dense:
                 p, c = patterns[i], counts[i]
                 tb = dd.dfa_table_bytes(len(p))
@@ -313,13 +345,22 @@ class Server:
 
     # -- public API
     def submit(self, q: Query) -> Query:
+        """Queue a query; one that cannot be served completes at once with
+        ``error`` set (see query_error)."""
+        err = query_error(q, getattr(self.engine, "nseq", None))
         with self._lock:
             if q.qid < 0:
                 q.qid = self._next_q
             self._next_q = max(self._next_q, q.qid + 1)
             if not q.t_arrive:
                 q.t_arrive = self.clock()
-            self._inbox.append(q)
+            if err is None:
+                self._inbox.append(q)
+            else:
+                q.error = err
+                q.t_done = self.clock()
+                self.done.append(q)
+                self.stats["rejected_queries"] += 1
         return q
 
     def idle(self) -> bool:

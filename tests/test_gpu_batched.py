@@ -71,6 +71,15 @@ def test_graph_replay_sees_new_text_contents(gpu):
         d.copy_(torch.from_numpy(t))
     b.run()
     assert np.array_equal(b.result(), oracle.multi_count(new, pats))
+    # writes still queued on the caller's stream (behind a ~10 ms spin)
+    # when run() is called are seen by the batch's own stream
+    src = [_dev(t) for t in texts]
+    torch.cuda.synchronize()
+    torch.cuda._sleep(20_000_000)
+    for d, s in zip(dts, src):
+        d.copy_(s, non_blocking=True)
+    b.run()
+    assert np.array_equal(b.result(), oracle.multi_count(texts, pats))
 
 
 def test_many_sequences_and_split_automata(gpu):

@@ -96,3 +96,30 @@ def test_admission_under_a_small_position_arena(gpu):
         assert all(np.array_equal(a, b) for a, b in zip(q.positions, pos))
     assert huge.error is not None and "position arena" in huge.error
     assert cnt.error is None and cnt.counts.tolist() == [oracle.count_brute(t, b"A")]
+
+
+def test_one_query_larger_than_an_automaton(gpu):
+    """A query whose patterns need more trie states than one automaton holds
+    (300 patterns of length 56..64) is split over several automata by the
+    engine, in the count stage and in the located positions."""
+    import torch
+    from paper_1506_08612_gb300.batched import MAX_STATES, group_patterns
+    from paper_1506_08612_gb300.serve import GpuEngine, Query, Server
+    t = synth.genome_text(1_000_003, 330)
+    lens = synth.uniform_ints(300, 9, 331) + 56
+    pats = [synth.pattern(int(m), 33_000 + i) for i, m in enumerate(lens)]
+    for i in range(0, 300, 3):
+        synth.plant(t, pats[i], synth.uniform_ints(2, t.size - 64, 332 + i))
+    assert len(group_patterns(pats)) >= 2
+    assert len({p[:k] for p in pats for k in range(len(p) + 1)}) > MAX_STATES
+    srv = Server(GpuEngine([torch.from_numpy(t).cuda()], slots=2, arena_bytes=8 << 20))
+    qc = srv.submit(Query(seq=0, patterns=pats, mode="count"))
+    qp = srv.submit(Query(seq=0, patterns=pats, mode="positions"))
+    srv.run_until_idle()
+    want = [oracle.find_brute(t, p) for p in pats]
+    for q in (qc, qp):
+        assert q.error is None, q.error
+        assert q.counts.tolist() == [c for c, _ in want]
+    assert sum(c for c, _ in want) >= 150                 # plants may overlap
+    for got, (_, pos) in zip(qp.positions, want):
+        assert np.array_equal(got, pos)

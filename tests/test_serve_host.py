@@ -251,3 +251,28 @@ def test_latency_percentiles_nearest_rank():
     s = latency_summary(qs)
     assert s["p50_ms"] == pytest.approx(50.0) and s["p99_ms"] == pytest.approx(99.0)
     assert s["max_ms"] == pytest.approx(100.0)
+
+
+def test_malformed_queries_complete_with_an_error():
+    from paper_1506_08612_gb300.serve import query_error
+    texts = _texts()
+    eng = FakeEngine(texts, slots=2)
+    eng.nseq = len(texts)
+    srv = Server(eng)
+    bad = [Query(seq=0, patterns=[b"ACGN"]), Query(seq=0, patterns=[b""]),
+           Query(seq=0, patterns=["A" * 65]), Query(seq=0, patterns=[]),
+           Query(seq=3, patterns=[b"ACG"]), Query(seq=-1, patterns=[b"ACG"]),
+           Query(seq=0, patterns=[b"ACG"], mode="regex"), Query(seq=0, patterns=["ACGÄ"])]
+    good = Query(seq=1, patterns=["acgT", b"A" * 64], mode="positions")
+    qs = [srv.submit(q) for q in bad[:4]] + [srv.submit(good)] + [srv.submit(q) for q in bad[4:]]
+    assert all(q.error and q.t_done >= q.t_arrive for q in bad)
+    assert srv.stats["rejected_queries"] == len(bad)
+    srv.run_until_idle()
+    _check(texts, good)
+    assert all(x[3] != [b"ACGN"] for x in eng.launched)      # nothing malformed reached the engine
+    assert len(srv.done) == len(qs)
+    assert query_error(good, 2) is None
+    assert "no sequence 1" in query_error(good, 1)
+    assert query_error(good) is None                          # engine without a sequence count
+    s = latency_summary(qs)
+    assert s["completed"] == 1 and s["errors"] == len(bad)
