@@ -145,17 +145,31 @@ def single_candidates(m: int) -> list[dict]:
     return out
 
 
+def _rejected(e: Exception) -> bool:
+    """True for a candidate the library refuses before launching (an
+    argument it does not take, memory it cannot get); False for a failure
+    that may have left the device unusable (a CUDA error), which must not be
+    retried with the next candidate."""
+    code = getattr(e, "code", None)
+    if code is not None:
+        from ._native import DFA_EINVAL, DFA_ENOMEM, DFA_EWORKSPACE
+        return code in (DFA_EINVAL, DFA_ENOMEM, DFA_EWORKSPACE)
+    return isinstance(e, ValueError)
+
+
 def select_best(candidates, time_ms, reps: int = 3):
     """Time every candidate ``reps`` times with ``time_ms(cfg) -> ms`` (the
     first call of each is a warm-up) and return (best cfg, its median ms).
-    Candidates whose timing raises are skipped; if all fail the last error
-    is raised."""
+    Candidates the library rejects are skipped (if all are, the last
+    rejection is raised); any other error is raised at once."""
     best, best_ms, err = None, float("inf"), None
     for cfg in candidates:
         try:
             time_ms(cfg)
             ts = sorted(time_ms(cfg) for _ in range(max(reps, 1)))
-        except Exception as e:      # a candidate the kernel rejects
+        except Exception as e:
+            if not _rejected(e):
+                raise
             err = e
             continue
         med = ts[len(ts) // 2]

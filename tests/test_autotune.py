@@ -125,3 +125,27 @@ def test_group_patterns_fits_the_automaton_limits():
     assert _trie_states(kmers) == 5461
     assert group_patterns(["acgt", "ACGA"], max_states=6) == [[0, 1]]      # case folded
     assert group_patterns(["acgt", "ACGA"], max_states=5) == [[0], [1]]
+
+
+def test_select_best_stops_at_a_device_error():
+    """A rejected configuration is skipped; a CUDA error is not retried with
+    the remaining candidates."""
+    import paper_1506_08612_gb300 as dd
+    seen = []
+
+    def timer(cfg):
+        seen.append(cfg["x"])
+        if cfg["x"] == "einval":
+            raise dd.DfaError(dd.DFA_EINVAL, "dfa_count")
+        if cfg["x"] == "cuda":
+            raise dd.DfaError(dd.DFA_ECUDA, "dfa_count")
+        return 1.0
+
+    best, _ = autotune.select_best([{"x": "einval"}, {"x": "ok"}], timer, reps=1)
+    assert best == {"x": "ok"}
+    seen.clear()
+    with pytest.raises(dd.DfaError) as ei:
+        autotune.select_best([{"x": "cuda"}, {"x": "ok"}], timer, reps=1)
+    assert ei.value.code == dd.DFA_ECUDA and seen == ["cuda"]
+    with pytest.raises(RuntimeError):
+        autotune.select_best([{"x": "ok2"}], lambda c: (_ for _ in ()).throw(RuntimeError("CUDA error")))
