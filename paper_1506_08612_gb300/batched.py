@@ -21,7 +21,7 @@ from . import MultiTable, autotune, dfa_multi_count
 
 MAX_SEQ_PER_LAUNCH = 64
 MAX_PAT_PER_TABLE = 8192
-MAX_STATES = 16383
+MAX_STATES = 16384                 # trie states, the root included
 
 
 def new_prefixes(prefixes: set, pattern) -> list:

@@ -52,7 +52,7 @@ struct dfa_multi {
 namespace {
 
 constexpr int kMultiMaxSeq = 64;
-constexpr int kMultiMaxStates = 16383;   // 4 * state fits the u16 entry
+constexpr int kMultiMaxStates = 16383;   // largest state number: 4 * 16383 + 1 fits the u16 entry (16384 states)
 constexpr int kMultiMaxPat = 8192;       // per-CTA counters: 32 KiB
 
 int round16(int64_t b) { return (int)((b + 15) & ~(int64_t)15); }

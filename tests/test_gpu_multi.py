@@ -179,3 +179,28 @@ def test_multi_locate_rejects_and_reports(gpu):
     wrong = [int(counts[0]) + 1, int(counts[1])]
     gpu.dfa_multi_locate(td, mt, wrong, pos, work)
     assert gpu.dfa_multi_locate_status(work, 2) == gpu.DFA_EINVAL
+
+
+def test_count_with_the_largest_automaton(gpu):
+    """An automaton of exactly 16384 states (the last state number, 16383,
+    makes the largest transition entry, 4 * 16383 + 1) counts every pattern
+    exactly, the deepest states included."""
+    from test_multi_host import patterns_with_trie_states
+    pats = patterns_with_trie_states(16384, 72_000)
+    mt = gpu.MultiTable(pats)
+    assert mt.states() == 16384
+    texts = [synth.genome_text(2_000_003, 720), synth.genome_text(700_001, 721)]
+    for i, t in enumerate(texts):
+        for j in range(i, len(pats), 5):
+            synth.plant(t, pats[j], synth.uniform_ints(1, t.size - 64, 7200 + 10 * j + i))
+    counts = torch_zeros(len(texts) * len(pats))
+    gpu.dfa_multi_count([_dev(t) for t in texts], mt, counts)
+    want = oracle.multi_count(texts, pats)
+    got = counts.cpu().numpy().astype(np.uint64).reshape(want.shape)
+    assert np.array_equal(got, want), np.argwhere(got != want)[:5]
+    assert (want > 0).sum() >= len(pats) // 5
+
+
+def torch_zeros(n):
+    import torch
+    return torch.zeros(n, dtype=torch.int64, device="cuda")

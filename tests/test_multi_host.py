@@ -62,3 +62,45 @@ def test_host_limits_and_sizes():
     # a table not attached to device memory is refused by the device calls
     t = dd.MultiTable(["ACGT"], device=False)
     assert dd._lib.dfa_multi_attach(t.handle, None, 1 << 20, None) == dd.DFA_EINVAL
+
+
+def patterns_with_trie_states(states: int, seed: int):
+    """Patterns (length <= 64) whose trie has exactly ``states`` states, the
+    root included: random 64-mers while they fit, then one pattern that
+    leaves an existing one after a shared prefix to add the remainder."""
+    from paper_1506_08612_gb300.batched import new_prefixes
+    seen, pats, i = {b""}, [], 0
+    while True:
+        p = synth.pattern(64, seed + i)
+        i += 1
+        add = new_prefixes(seen, p)
+        if len(seen) + len(add) > states:
+            break
+        pats.append(p)
+        seen.update(add)
+    r = states - len(seen)
+    if r:
+        base = pats[-1]
+        k = 64 - r                                  # shared prefix; base[k] is replaced
+        alt = next(c for c in b"ACGT" if c != base[k])
+        p = base[:k] + bytes([alt]) + base[k + 1:]
+        assert len(new_prefixes(seen, p)) == r
+        pats.append(p)
+        seen.update(new_prefixes(seen, p))
+    assert len(seen) == states
+    return pats
+
+
+def test_state_limit_is_exact():
+    """16384 states (numbers 0..16383, 4 * 16383 + 1 < 2^16) build; one more
+    state is refused, and the batch grouping agrees with the library."""
+    import paper_1506_08612_gb300 as dd
+    from paper_1506_08612_gb300.batched import MAX_STATES, group_patterns
+    assert MAX_STATES == 16384
+    full = patterns_with_trie_states(16384, 71_000)
+    t = dd.MultiTable(full, device=False)
+    assert t.states() == 16384 and len(group_patterns(full)) == 1
+    over = patterns_with_trie_states(16385, 71_000)
+    with pytest.raises(dd.DfaError, match="16384 states"):
+        dd.MultiTable(over, device=False)
+    assert len(group_patterns(over)) == 2
