@@ -152,6 +152,20 @@ class Batch:
     region: tuple | None = None           # (offset, bytes) in the position arena
 
 
+def host_automata(dd, patterns):
+    """(groups, host automata) for ``patterns``: one automaton over all of
+    them when the library takes the set (the batches are formed to fit),
+    else one per group of group_patterns (a single query too large for one
+    automaton)."""
+    try:
+        return [list(range(len(patterns)))], [dd.MultiTable(patterns, device=False)]
+    except dd.DfaError as e:
+        if e.code != dd.DFA_EINVAL or len(patterns) < 2:
+            raise
+    groups = group_patterns(patterns)
+    return groups, [dd.MultiTable([patterns[i] for i in g], device=False) for g in groups]
+
+
 class GpuEngine:
     """The device side of the server: resident sequences, stream slots, the
     position arena, and the two stages as non-blocking jobs."""
@@ -192,8 +206,7 @@ class GpuEngine:
             return self._launch_count_plain(slot, seq, patterns)
         # one automaton per group of patterns within its limits (a batch is
         # formed to need one; a single query may need several)
-        groups = group_patterns(patterns)
-        mts = [dd.MultiTable([patterns[i] for i in g], device=False) for g in groups]
+        groups, mts = host_automata(dd, patterns)
         sizes = [(mt.image_bytes() + 255) // 256 * 256 for mt in mts]
         if sum(sizes) > self.tab[slot].numel():
             self.tab[slot] = torch.empty(sum(sizes), dtype=torch.uint8, device=self.device)
@@ -248,8 +261,8 @@ class GpuEngine:
         sset = set(sparse)
         dense = [i for i, c in enumerate(counts) if c and i not in sset]
         order = sparse + dense                         # layout of the region
-        sgroups = [[sparse[j] for j in g] for g in group_patterns([patterns[i] for i in sparse])]
-        mts = [dd.MultiTable([patterns[i] for i in g], device=False) for g in sgroups]
+        sgroups, mts = host_automata(dd, [patterns[i] for i in sparse]) if sparse else ([], [])
+        sgroups = [[sparse[j] for j in g] for g in sgroups]
         msizes = [(mt.image_bytes() + 255) // 256 * 256 for mt in mts]
         mt_bytes = sum(msizes)
         need = mt_bytes + sum((dd.dfa_table_bytes(len(patterns[i])) + 255) // 256 * 256 for i in dense)
