@@ -316,11 +316,37 @@ int dfa_multi_build_host(const char* const* patterns, const int32_t* lengths, in
 int64_t dfa_multi_image_bytes(const dfa_multi* table);
 int dfa_multi_attach(dfa_multi* table, void* d_mem, int64_t bytes, void* stream);
 
+/*
+ * Character-class patterns (the class cells of the paper's Table III,
+ * Sec. IV): each position allows a set of bases.  patterns[i] holds
+ * lengths[i] bytes of symbols, one position each: a base; an IUPAC
+ * nucleotide code, R (A/G), Y (C/T), S (C/G), W (A/T), K (G/T), M (A/C),
+ * B (not A), D (not C), H (not G), V (not T), N (any base); or a bracket set
+ * of those, e.g. "[CGT]"; either case.  1..DFA_MAX_M positions a pattern.
+ * An occurrence at i is a window T[i..i+m) whose every byte is a base (either
+ * case) in its position's set: text bytes outside ACGTacgt still match
+ * nothing.  The automaton (subset construction over the patterns'
+ * positions: a state is the set of (pattern, matched length) pairs; for
+ * patterns of single bases it is the trie automaton of dfa_multi_build)
+ * is used like dfa_multi_build's by dfa_multi_count, dfa_multi_locate,
+ * dfa_multi_attach and dfa_multi_export.  At most 8192 patterns and 16384
+ * states; a pattern with many wide positions can need more.
+ * Errors: DFA_EINVAL (bad syntax, too many states: see dfa_last_error),
+ * DFA_ENOMEM, DFA_ECUDA (device copy).
+ */
+int dfa_multi_build_class(const char* const* patterns, const int32_t* lengths, int32_t npat,
+                          dfa_multi** out);
+int dfa_multi_build_class_host(const char* const* patterns, const int32_t* lengths, int32_t npat,
+                               dfa_multi** out);
+
+/* Positions (length m) of pattern p of the automaton; -1 for a bad table or p. */
+int32_t dfa_multi_pattern_length(const dfa_multi* table, int32_t p);
+
 /* Release an automaton (its device copy too, unless the caller attached it
  * to its own memory).  NULL is ignored. */
 void dfa_multi_free(dfa_multi* table);
 
-/* Number of automaton states (trie states, root 0, breadth-first order). */
+/* Number of automaton states (root 0, breadth-first order). */
 int32_t dfa_multi_states(const dfa_multi* table);
 
 /*

@@ -15,6 +15,9 @@ module only marshals numpy arrays.  Functions:
 * ``alg1_scan(text, delta, m, p, v)`` — Algorithm 1's decomposition (Sec. III-A).
 * ``stt_ascii(strings, finals)`` — sparse 256-column STT (Sec. III-B, Table I).
 * ``kmer_census(text, k)`` and ``valid_windows(text, k)``.
+* ``class_sets(pattern)``, ``class_expansions(pattern)`` and
+  ``find_class_brute(text, pattern)`` — character-class patterns (the class
+  cells of Table III, Sec. IV) by their definition, in numpy.
 """
 from __future__ import annotations
 
@@ -235,4 +238,77 @@ def multi_count(texts, patterns, threads: int | None = None) -> np.ndarray:
     with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
         for (i, j), c in zip(jobs, ex.map(lambda ij: count_brute(ts[ij[0]], patterns[ij[1]]), jobs)):
             out[i, j] = c
+    return out
+
+
+# ------------------------------------------------------------ class patterns
+#
+# A class pattern allows a set of bases at each position (the class cells of
+# the paper's Table III, Sec. IV).  Symbols are the IUPAC nucleotide codes
+# (a base stands for itself); a bracket joins the sets of the symbols inside.
+
+IUPAC = {"A": "A", "C": "C", "G": "G", "T": "T",
+         "R": "AG", "Y": "CT", "S": "CG", "W": "AT", "K": "GT", "M": "AC",
+         "B": "CGT", "D": "AGT", "H": "ACT", "V": "ACG", "N": "ACGT"}
+
+
+def class_sets(pattern) -> list[str]:
+    """The bases (upper case, sorted) each position of a class pattern
+    allows; ValueError for an empty pattern, an unknown symbol, an empty or
+    unclosed bracket, or more than 64 positions."""
+    s = pattern.decode("ascii") if isinstance(pattern, (bytes, bytearray)) else str(pattern)
+    out, i = [], 0
+    while i < len(s):
+        if s[i] == "[":
+            j = s.find("]", i + 1)
+            if j < 0 or j == i + 1:
+                raise ValueError(f"bad bracket in {s!r}")
+            members = set()
+            for ch in s[i + 1:j]:
+                if ch.upper() not in IUPAC:
+                    raise ValueError(f"bad symbol {ch!r} in {s!r}")
+                members |= set(IUPAC[ch.upper()])
+            out.append("".join(sorted(members)))
+            i = j + 1
+        else:
+            if s[i].upper() not in IUPAC:
+                raise ValueError(f"bad symbol {s[i]!r} in {s!r}")
+            out.append(IUPAC[s[i].upper()])
+            i += 1
+    if not out or len(out) > 64:
+        raise ValueError(f"{len(out)} positions in {s!r}")
+    return out
+
+
+def class_expansions(pattern) -> list[bytes]:
+    """Every plain pattern the class pattern stands for."""
+    import itertools
+    return [("".join(t)).encode() for t in itertools.product(*class_sets(pattern))]
+
+
+def find_class_brute(text, pattern):
+    """Every window compared (the definition): an occurrence at i iff each
+    byte T[i + j] is a base, either case, in the set of position j.  Returns
+    ``(count, sorted start positions)``."""
+    t = _bytes(text)
+    sets = class_sets(pattern)
+    m, n = len(sets), t.size
+    if n < m:
+        return 0, np.zeros(0, np.int64)
+    ok = np.ones(n - m + 1, dtype=bool)
+    for j, bases in enumerate(sets):
+        allowed = np.zeros(256, dtype=bool)
+        for b in bases:
+            allowed[ord(b)] = allowed[ord(b.lower())] = True
+        ok &= allowed[t[j:n - m + 1 + j]]
+    pos = np.flatnonzero(ok).astype(np.int64)
+    return int(pos.size), pos
+
+
+def multi_count_class(texts, patterns) -> np.ndarray:
+    """uint64[len(texts), len(patterns)]: find_class_brute counts."""
+    out = np.zeros((len(texts), len(patterns)), dtype=np.uint64)
+    for i, t in enumerate(texts):
+        for j, p in enumerate(patterns):
+            out[i, j] = find_class_brute(t, p)[0]
     return out

@@ -342,15 +342,21 @@ def dfa_find_host_multi(h_text, tables, h_positions, stage, seg: int, stream=Non
 class MultiTable:
     """Owns a dfa_multi (multi-pattern automaton); frees it on close/del."""
 
-    def __init__(self, patterns, device: bool = True):
+    def __init__(self, patterns, device: bool = True, classes: bool = False):
         """device=False builds the host automaton only (dfa_multi_build_host);
-        ``attach`` then copies it into caller-owned device memory."""
+        ``attach`` then copies it into caller-owned device memory.
+        classes=True reads the patterns as character-class patterns (IUPAC
+        codes and bracket sets, dfa_multi_build_class)."""
         pats = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
         self.patterns = pats
+        self.classes = bool(classes)
         arr = (ctypes.c_char_p * len(pats))(*pats)
         lens = (ctypes.c_int32 * len(pats))(*[len(p) for p in pats])
         h = ctypes.c_void_p()
-        fn = _lib.dfa_multi_build if device else _lib.dfa_multi_build_host
+        if classes:
+            fn = _lib.dfa_multi_build_class if device else _lib.dfa_multi_build_class_host
+        else:
+            fn = _lib.dfa_multi_build if device else _lib.dfa_multi_build_host
         rc = fn(arr, lens, len(pats), ctypes.byref(h))
         if rc != DFA_OK:
             msg = _lib.dfa_last_error().decode(errors="replace")
@@ -358,7 +364,8 @@ class MultiTable:
         self._h = h
         self._into = None
         self.npat = len(pats)
-        self.mmax = max(len(p) for p in pats)
+        self.lengths = [int(_lib.dfa_multi_pattern_length(h, i)) for i in range(len(pats))]
+        self.mmax = max(self.lengths)
 
     @property
     def handle(self) -> ctypes.c_void_p:

@@ -51,6 +51,11 @@ def _declare(lib):
         "dfa_multi_free": ([vp], None),
         "dfa_multi_build_host": ([ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32), i32,
                                   ctypes.POINTER(vp)], ctypes.c_int),
+        "dfa_multi_build_class": ([ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32), i32,
+                                   ctypes.POINTER(vp)], ctypes.c_int),
+        "dfa_multi_build_class_host": ([ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32), i32,
+                                        ctypes.POINTER(vp)], ctypes.c_int),
+        "dfa_multi_pattern_length": ([vp, i32], i32),
         "dfa_multi_image_bytes": ([vp], i64),
         "dfa_multi_attach": ([vp, vp, i64, vp], ctypes.c_int),
         "dfa_multi_states": ([vp], i32),

@@ -30,6 +30,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "dnadfa_internal.h"
@@ -413,6 +415,223 @@ int multi_fail(const char* what, cudaError_t err)
     return set_last_error(DFA_ECUDA, buf);
 }
 
+// The table of an automaton whose states are numbered breadth first from
+// the root 0: next[s][a] is the state after code a, outs[s] the patterns an
+// occurrence of which ends on entering s (each pattern at most once).
+int make_multi(int32_t npat, const int32_t* lengths, const std::vector<std::array<int32_t, 4>>& next,
+               const std::vector<std::vector<uint16_t>>& outs, dfa_multi** out)
+{
+    const int S = (int)next.size();
+    dfa_multi* t = new (std::nothrow) dfa_multi();
+    if (!t) return DFA_ENOMEM;
+    t->npat = npat;
+    t->nstates = S;
+    t->mlen.resize(npat);
+    for (int p = 0; p < npat; p++) {
+        t->mlen[p] = (uint8_t)lengths[p];
+        t->mmax = std::max<int32_t>(t->mmax, lengths[p]);
+    }
+    t->delta.resize((size_t)S * 4);
+    t->out_off.assign(S + 1, 0);
+    for (int i = 0; i < S; i++) {
+        for (int a = 0; a < 4; a++) {
+            const int v = next[i][a];
+            t->delta[(size_t)i * 4 + a] = (uint16_t)(4 * v + (outs[v].empty() ? 0 : 1));
+        }
+        t->out_off[i + 1] = t->out_off[i] + (uint32_t)outs[i].size();
+        t->out_ids.insert(t->out_ids.end(), outs[i].begin(), outs[i].end());
+    }
+    // device image: [delta][out_off][out_ids][mlen], 16-byte aligned parts
+    // span[q]: the shortest and longest length among the state's outputs
+    std::vector<uint8_t> span((size_t)S * 2, 0);
+    for (int i = 0; i < S; i++) {
+        uint32_t lo = 255, hi = 0;
+        for (uint32_t k = t->out_off[i]; k < t->out_off[i + 1]; k++) {
+            lo = std::min<uint32_t>(lo, t->mlen[t->out_ids[k]]);
+            hi = std::max<uint32_t>(hi, t->mlen[t->out_ids[k]]);
+        }
+        span[2 * i] = (uint8_t)(hi ? lo : 0);
+        span[2 * i + 1] = (uint8_t)hi;
+    }
+    t->delta_bytes = round16((int64_t)S * 4 * 2);
+    t->off_bytes = round16((int64_t)(S + 1) * 4);
+    t->ids_bytes = round16((int64_t)std::max<size_t>(t->out_ids.size(), 1) * 2);
+    t->mlen_bytes = round16(npat);
+    t->span_bytes = round16((int64_t)S * 2);
+    const size_t bytes =
+        (size_t)t->delta_bytes + t->off_bytes + t->ids_bytes + t->mlen_bytes + t->span_bytes;
+    std::vector<uint8_t>& img = t->img;
+    img.assign(bytes, 0);
+    uint8_t* q = img.data();
+    memcpy(q, t->delta.data(), t->delta.size() * 2);
+    q += t->delta_bytes;
+    memcpy(q, t->out_off.data(), t->out_off.size() * 4);
+    q += t->off_bytes;
+    if (!t->out_ids.empty()) memcpy(q, t->out_ids.data(), t->out_ids.size() * 2);
+    q += t->ids_bytes;
+    memcpy(q, t->mlen.data(), npat);
+    q += t->mlen_bytes;
+    memcpy(q, span.data(), span.size());
+    t->owns_mem = false;
+    *out = t;
+    return DFA_OK;
+}
+
+// ------------------------------------------------------------ class patterns
+//
+// A class pattern allows a set of bases at each position (the character
+// classes of the paper's Table III cells, Sec. IV).  Symbols: a base, an
+// IUPAC nucleotide code (R = A/G, Y = C/T, S = C/G, W = A/T, K = G/T,
+// M = A/C, B = not A, D = not C, H = not G, V = not T, N = any), either case,
+// or a bracket set of those, "[CGT]".  The text side is unchanged: a text
+// byte outside ACGTacgt matches no position.
+
+// Mask over base codes (bit base_code: A 0, C 1, T 2, G 3) of one symbol; 0
+// if the byte is not a symbol.
+uint32_t symbol_mask(uint32_t c)
+{
+    constexpr uint32_t A = 1u, C = 2u, T = 4u, G = 8u;
+    switch (c | 0x20u) {
+    case 'a': return A;
+    case 'c': return C;
+    case 'g': return G;
+    case 't': return T;
+    case 'r': return A | G;
+    case 'y': return C | T;
+    case 's': return C | G;
+    case 'w': return A | T;
+    case 'k': return G | T;
+    case 'm': return A | C;
+    case 'b': return C | G | T;
+    case 'd': return A | G | T;
+    case 'h': return A | C | T;
+    case 'v': return A | C | G;
+    case 'n': return A | C | G | T;
+    default: return 0u;
+    }
+}
+
+// The per-position masks of a class pattern of len bytes; DFA_EINVAL for an
+// empty pattern, an unknown byte, an empty or unclosed bracket, or more than
+// DFA_MAX_M positions.
+int parse_class(const char* s, int32_t len, std::vector<uint8_t>& masks)
+{
+    masks.clear();
+    for (int32_t i = 0; i < len; i++) {
+        uint32_t mk = 0u;
+        if (s[i] == '[') {
+            int32_t j = i + 1;
+            for (; j < len && s[j] != ']'; j++) {
+                const uint32_t b = symbol_mask((uint8_t)s[j]);
+                if (!b) return DFA_EINVAL;
+                mk |= b;
+            }
+            if (j >= len || j == i + 1) return DFA_EINVAL;
+            i = j;
+        } else {
+            mk = symbol_mask((uint8_t)s[i]);
+            if (!mk) return DFA_EINVAL;
+        }
+        if ((int)masks.size() >= DFA_MAX_M) return DFA_EINVAL;
+        masks.push_back((uint8_t)mk);
+    }
+    return masks.empty() ? DFA_EINVAL : DFA_OK;
+}
+
+// The automaton of class patterns by the subset construction.  A state is
+// the set of pairs (p, k), k = 1..m_p, such that the last k bytes read match
+// the first k positions of pattern p (pair index pos0[p] + k - 1); the root
+// is the empty set, which every non-base leads back to.  Code a maps a set to
+// the (p, k + 1) of its pairs whose position k allows a, plus (p, 1) for
+// every p whose first position allows a; a state outputs each p with
+// (p, m_p) in its set.  States are numbered in the order found, breadth
+// first.  For patterns of single bases each set is that of one trie node
+// (the pattern prefixes that are suffixes of the node's string), found in
+// the trie's breadth-first order, so the tables equal the trie
+// construction's (up to the order within output lists).
+int build_class_automaton(const std::vector<std::vector<uint8_t>>& cls, std::vector<std::array<int32_t, 4>>& next,
+                          std::vector<std::vector<uint16_t>>& outs)
+{
+    const int npat = (int)cls.size();
+    std::vector<uint32_t> pos0(npat + 1, 0u);
+    for (int p = 0; p < npat; p++) pos0[p + 1] = pos0[p] + (uint32_t)cls[p].size();
+    const uint32_t L = pos0[npat];
+    std::vector<uint16_t> pat_of(L);
+    std::vector<uint8_t> allow_next(L), final_pair(L);   // mask of position k (none at k = m_p)
+    std::array<std::vector<uint32_t>, 4> first;
+    for (int p = 0; p < npat; p++) {
+        const uint32_t m = (uint32_t)cls[p].size();
+        for (uint32_t k = 1; k <= m; k++) {
+            const uint32_t x = pos0[p] + k - 1;
+            pat_of[x] = (uint16_t)p;
+            allow_next[x] = k < m ? cls[p][k] : 0u;
+            final_pair[x] = k == m;
+        }
+        for (int a = 0; a < 4; a++)
+            if ((cls[p][0] >> a) & 1u) first[a].push_back(pos0[p]);
+    }
+    // sets keyed by the bytes of their sorted pair indices
+    std::unordered_map<std::string, int32_t> id;
+    std::vector<const std::string*> sets;
+    auto intern = [&](std::string&& key, int32_t& sid) -> bool {
+        auto it = id.find(key);
+        if (it != id.end()) {
+            sid = it->second;
+            return true;
+        }
+        if ((int)sets.size() > kMultiMaxStates) return false;
+        auto r = id.emplace(std::move(key), (int32_t)sets.size());
+        sid = r.first->second;
+        sets.push_back(&r.first->first);
+        return true;
+    };
+    int32_t root;
+    intern(std::string(), root);
+    std::vector<uint32_t> cur, adv, nxt;
+    for (size_t h = 0; h < sets.size(); h++) {
+        const std::string& key = *sets[h];
+        cur.resize(key.size() / 4);
+        if (!cur.empty()) memcpy(cur.data(), key.data(), key.size());
+        std::vector<uint16_t> o;
+        for (uint32_t x : cur)
+            if (final_pair[x]) o.push_back(pat_of[x]);
+        outs.push_back(std::move(o));
+        std::array<int32_t, 4> nx;
+        for (int a = 0; a < 4; a++) {
+            adv.clear();
+            for (uint32_t x : cur)
+                if ((allow_next[x] >> a) & 1u) adv.push_back(x + 1);
+            nxt.resize(adv.size() + first[a].size());
+            std::merge(adv.begin(), adv.end(), first[a].begin(), first[a].end(), nxt.begin());
+            std::string k2(reinterpret_cast<const char*>(nxt.data()), nxt.size() * 4);
+            if (!intern(std::move(k2), nx[a]))
+                return set_last_error(DFA_EINVAL, "dfa_multi_build_class: the automaton needs more than 16384 states");
+        }
+        next.push_back(nx);
+    }
+    return DFA_OK;
+}
+
+// Copies a host-built automaton to a new allocation on the current device.
+int upload_multi(dfa_multi* t, const char* what, dfa_multi** out)
+{
+    const size_t bytes = t->img.size();
+    cudaError_t err;
+    if ((err = cudaGetDevice(&t->device)) != cudaSuccess || (err = cudaMalloc(&t->d_mem, bytes)) != cudaSuccess) {
+        t->d_mem = nullptr;
+        delete t;
+        return multi_fail(what, err);
+    }
+    t->owns_mem = true;
+    if ((err = cudaMemcpy(t->d_mem, t->img.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(t->d_mem);
+        delete t;
+        return multi_fail(what, err);
+    }
+    *out = t;
+    return DFA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -424,11 +643,9 @@ int dfa_multi_build_host(const char* const* patterns, const int32_t* lengths, in
     // trie
     std::vector<std::array<int32_t, 4>> child(1, {-1, -1, -1, -1});
     std::vector<std::vector<uint16_t>> own(1);
-    int mmax = 0;
     for (int p = 0; p < npat; p++) {
         const int m = lengths[p];
         if (m < 1 || m > DFA_MAX_M || !patterns[p]) return DFA_EINVAL;
-        mmax = std::max(mmax, m);
         int u = 0;
         for (int j = 0; j < m; j++) {
             const uint32_t c = (uint8_t)patterns[p][j];
@@ -468,58 +685,14 @@ int dfa_multi_build_host(const char* const* patterns, const int32_t* lengths, in
         }
     }
     for (int i = 0; i < S; i++) num[order[i]] = i;      // states numbered breadth first
-    dfa_multi* t = new (std::nothrow) dfa_multi();
-    if (!t) return DFA_ENOMEM;
-    t->npat = npat;
-    t->nstates = S;
-    t->mmax = mmax;
-    t->mlen.resize(npat);
-    for (int p = 0; p < npat; p++) t->mlen[p] = (uint8_t)lengths[p];
-    t->delta.resize((size_t)S * 4);
-    t->out_off.assign(S + 1, 0);
+    std::vector<std::array<int32_t, 4>> next(S);
+    std::vector<std::vector<uint16_t>> bouts(S);
     for (int i = 0; i < S; i++) {
         const int u = order[i];
-        for (int a = 0; a < 4; a++) {
-            const int v = delta[u][a];
-            t->delta[(size_t)i * 4 + a] = (uint16_t)(4 * num[v] + (outs[v].empty() ? 0 : 1));
-        }
-        t->out_off[i + 1] = t->out_off[i] + (uint32_t)outs[u].size();
-        t->out_ids.insert(t->out_ids.end(), outs[u].begin(), outs[u].end());
+        for (int a = 0; a < 4; a++) next[i][a] = num[delta[u][a]];
+        bouts[i] = std::move(outs[u]);
     }
-    // device image: [delta][out_off][out_ids][mlen], 16-byte aligned parts
-    // span[q]: the shortest and longest length among the state's outputs
-    std::vector<uint8_t> span((size_t)S * 2, 0);
-    for (int i = 0; i < S; i++) {
-        uint32_t lo = 255, hi = 0;
-        for (uint32_t k = t->out_off[i]; k < t->out_off[i + 1]; k++) {
-            lo = std::min<uint32_t>(lo, t->mlen[t->out_ids[k]]);
-            hi = std::max<uint32_t>(hi, t->mlen[t->out_ids[k]]);
-        }
-        span[2 * i] = (uint8_t)(hi ? lo : 0);
-        span[2 * i + 1] = (uint8_t)hi;
-    }
-    t->delta_bytes = round16((int64_t)S * 4 * 2);
-    t->off_bytes = round16((int64_t)(S + 1) * 4);
-    t->ids_bytes = round16((int64_t)std::max<size_t>(t->out_ids.size(), 1) * 2);
-    t->mlen_bytes = round16(npat);
-    t->span_bytes = round16((int64_t)S * 2);
-    const size_t bytes =
-        (size_t)t->delta_bytes + t->off_bytes + t->ids_bytes + t->mlen_bytes + t->span_bytes;
-    std::vector<uint8_t>& img = t->img;
-    img.assign(bytes, 0);
-    uint8_t* q = img.data();
-    memcpy(q, t->delta.data(), t->delta.size() * 2);
-    q += t->delta_bytes;
-    memcpy(q, t->out_off.data(), t->out_off.size() * 4);
-    q += t->off_bytes;
-    if (!t->out_ids.empty()) memcpy(q, t->out_ids.data(), t->out_ids.size() * 2);
-    q += t->ids_bytes;
-    memcpy(q, t->mlen.data(), npat);
-    q += t->mlen_bytes;
-    memcpy(q, span.data(), span.size());
-    t->owns_mem = false;
-    *out = t;
-    return DFA_OK;
+    return make_multi(npat, lengths, next, bouts, out);
 }
 
 int dfa_multi_build(const char* const* patterns, const int32_t* lengths, int32_t npat, dfa_multi** out)
@@ -528,20 +701,46 @@ int dfa_multi_build(const char* const* patterns, const int32_t* lengths, int32_t
     dfa_multi* t = nullptr;
     int rc = dfa_multi_build_host(patterns, lengths, npat, &t);
     if (rc) return rc;
-    const size_t bytes = t->img.size();
-    cudaError_t err;
-    if ((err = cudaGetDevice(&t->device)) != cudaSuccess || (err = cudaMalloc(&t->d_mem, bytes)) != cudaSuccess) {
-        delete t;
-        return multi_fail("dfa_multi_build", err);
+    return upload_multi(t, "dfa_multi_build", out);
+}
+
+int dfa_multi_build_class_host(const char* const* patterns, const int32_t* lengths, int32_t npat, dfa_multi** out)
+{
+    if (!patterns || !lengths || !out || npat < 1 || npat > kMultiMaxPat) return DFA_EINVAL;
+    *out = nullptr;
+    try {
+        std::vector<std::vector<uint8_t>> cls(npat);
+        std::vector<int32_t> m(npat);
+        for (int p = 0; p < npat; p++) {
+            if (!patterns[p] || lengths[p] < 1 || parse_class(patterns[p], lengths[p], cls[p]) != DFA_OK) {
+                char buf[96];
+                snprintf(buf, sizeof(buf), "dfa_multi_build_class: pattern %d is not a class pattern", p);
+                return set_last_error(DFA_EINVAL, buf);
+            }
+            m[p] = (int32_t)cls[p].size();
+        }
+        std::vector<std::array<int32_t, 4>> next;
+        std::vector<std::vector<uint16_t>> outs;
+        const int rc = build_class_automaton(cls, next, outs);
+        if (rc) return rc;
+        return make_multi(npat, m.data(), next, outs, out);
+    } catch (const std::bad_alloc&) {
+        return DFA_ENOMEM;
     }
-    t->owns_mem = true;
-    if ((err = cudaMemcpy(t->d_mem, t->img.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
-        cudaFree(t->d_mem);
-        delete t;
-        return multi_fail("dfa_multi_build", err);
-    }
-    *out = t;
-    return DFA_OK;
+}
+
+int dfa_multi_build_class(const char* const* patterns, const int32_t* lengths, int32_t npat, dfa_multi** out)
+{
+    if (!out) return DFA_EINVAL;
+    dfa_multi* t = nullptr;
+    int rc = dfa_multi_build_class_host(patterns, lengths, npat, &t);
+    if (rc) return rc;
+    return upload_multi(t, "dfa_multi_build_class", out);
+}
+
+int32_t dfa_multi_pattern_length(const dfa_multi* t, int32_t p)
+{
+    return t && p >= 0 && p < t->npat ? (int32_t)t->mlen[p] : -1;
 }
 
 int64_t dfa_multi_image_bytes(const dfa_multi* t) { return t ? (int64_t)t->img.size() : -1; }

@@ -104,3 +104,80 @@ def test_state_limit_is_exact():
     with pytest.raises(dd.DfaError, match="16384 states"):
         dd.MultiTable(over, device=False)
     assert len(group_patterns(over)) == 2
+
+
+# ------------------------------------------------------------ class patterns
+
+def _host_walk_total(nxt, nout, text) -> int:
+    """Occurrences of all the automaton's patterns in ``text``, walked
+    byte by byte on the host: a base takes its code's transition and adds
+    the state's output count, any other byte goes back to the root."""
+    q, c = 0, 0
+    for b in bytes(text):
+        if b in b"ACGTacgt":
+            q = nxt[q, (b >> 1) & 3]
+            c += int(nout[q])
+        else:
+            q = 0
+    return c
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_class_builder_on_plain_patterns_is_the_trie_automaton(seed):
+    """For patterns of single bases the subset construction finds the trie's
+    states in the trie's breadth-first order: equal tables and sizes."""
+    import paper_1506_08612_gb300 as dd
+    pats = [synth.pattern(int(m), 3000 * seed + i) for i, m in enumerate(synth.uniform_ints(150, 24, seed) + 1)]
+    pats[:4] = [b"ACG", b"ACT", b"CTA", b"acg"]
+    a = dd.MultiTable(pats, device=False)
+    b = dd.MultiTable(pats, device=False, classes=True)
+    assert a.states() == b.states() and a.image_bytes() == b.image_bytes()
+    for x, y in zip(a.export(), b.export()):
+        assert (x == y).all()
+    assert b.lengths == [len(p) for p in pats]
+
+
+def test_class_automaton_walk_equals_oracle():
+    """Each class pattern's automaton, walked on the host, counts what the
+    oracle's window compare finds; the automaton of all of them together
+    counts the sum."""
+    import numpy as np
+
+    import paper_1506_08612_gb300 as dd
+    rng = np.random.default_rng(5)
+    syms = list("ACGTRYSWKMBDHVN")
+    pats = []
+    for i in range(24):
+        m = int(rng.integers(1, 9))
+        pats.append("".join(str(rng.choice(syms)) if rng.random() < 0.6
+                            else "[" + "".join(rng.choice(list("ACGT"), size=2)) + "]" for _ in range(m)))
+    pats[:3] = ["R", "[AC]A", "nNn"]
+    texts = [synth.random_text(3000, 70 + k, b"ACGTacgtNn") for k in range(3)]
+    for p in pats:
+        t = dd.MultiTable([p], device=False, classes=True)
+        assert t.lengths == [len(oracle.class_sets(p))]
+        nxt, nout = t.export()
+        for tx in texts:
+            assert _host_walk_total(nxt, nout, tx) == oracle.find_class_brute(tx, p)[0], p
+    allt = dd.MultiTable(pats, device=False, classes=True)
+    nxt, nout = allt.export()
+    for tx in texts:
+        assert _host_walk_total(nxt, nout, tx) == sum(oracle.find_class_brute(tx, p)[0] for p in pats)
+
+
+def test_class_builder_limits_and_syntax():
+    import paper_1506_08612_gb300 as dd
+    for bad in ["", "[", "[]", "[AX]", "AZ", "A]", "[A[C]]", "N" * 65, "U"]:
+        with pytest.raises(dd.DfaError):
+            dd.MultiTable([bad], device=False, classes=True)
+    # remembering where each of the last 16 A's was takes more than 16384 states
+    with pytest.raises(dd.DfaError, match="16384 states"):
+        dd.MultiTable(["A" + "N" * 16 + "T"], device=False, classes=True)
+    # N^64 alone: the root and one state per number of bases read, 1..64
+    assert dd.MultiTable(["N" * 64], device=False, classes=True).states() == 65
+    # with [acgt] and RY: after k >= 2 bases the last one is a purine (RY cannot
+    # have just ended), or a pyrimidine after a purine (it has), or after a
+    # pyrimidine; after one base, purine or not: 1 + 2 + 63 * 3 states
+    t = dd.MultiTable(["N" * 64, "[acgt]", "ry"], device=False, classes=True)
+    assert t.lengths == [64, 1, 2] and t.mmax == 64
+    assert t.states() == 1 + 2 + 63 * 3

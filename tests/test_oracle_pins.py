@@ -412,3 +412,97 @@ def test_multi_count_equals_census_and_definition():
     assert oracle.multi_count([np.zeros(0, np.uint8)], ["A"]).tolist() == [[0]]
     aa = np.frombuffer(b"AAAAAA", np.uint8).copy()
     assert oracle.multi_count([aa], ["A", "AA", "AAAA"]).tolist() == [[6, 5, 3]]
+
+
+# --------------------------------------------------------------------------
+# character-class patterns (the class cells of Table III, Sec. IV)
+# --------------------------------------------------------------------------
+
+BASE_COMP = {"A": "T", "C": "G", "G": "C", "T": "A"}
+
+
+def test_iupac_table_structure():
+    """The IUPAC nucleotide codes by their structure: each base stands for
+    itself; the six two-base codes are the six pairs of bases, each once;
+    B, D, H, V are 'not A', 'not C', 'not G', 'not T'; N is any base; the
+    chemical names fix the pairs (puRine A/G, pYrimidine C/T, Strong C/G,
+    Weak A/T, Keto G/T, aMino A/C); complementing a code's set gives the set
+    of its complementary code (R-Y, K-M, B-V, D-H; S, W, N map to
+    themselves)."""
+    T = oracle.IUPAC
+    assert len(T) == 15
+    for b in "ACGT":
+        assert T[b] == b
+    pairs = sorted(v for v in T.values() if len(v) == 2)
+    assert pairs == sorted("".join(c) for c in itertools.combinations("ACGT", 2))
+    for code, missing in zip("BDHV", "ACGT"):
+        assert T[code] == "".join(sorted(set("ACGT") - {missing}))
+    assert T["N"] == "ACGT"
+    assert (T["R"], T["Y"], T["S"], T["W"], T["K"], T["M"]) == ("AG", "CT", "CG", "AT", "GT", "AC")
+    comp_code = dict(zip("ACGTRYKMBVDHSWN", "TGCAYRMKVBHDSWN"))
+    for k, v in T.items():
+        assert "".join(sorted(BASE_COMP[b] for b in v)) == T[comp_code[k]], k
+
+
+CLASS_FACTS = [
+    ("ACGTNacgtn", "R", [0, 2, 5, 7]),
+    ("AAACA", "[AC]A", [0, 1, 3]),
+    ("ACgtNa", "N", [0, 1, 2, 3, 5]),
+    ("ACNGT", "NN", [0, 3]),
+    ("ACGT", "[ACGT][acgt]", [0, 1, 2]),
+    ("GATTACA", "GAW", [0]),
+    ("TTTT", "[AG]", []),
+    ("ACG", "NNNN", []),
+    ("aCgT", "mS", [0, 1]),
+]
+
+
+@pytest.mark.parametrize("text,pat,pos", CLASS_FACTS)
+def test_class_fixed_facts(text, pat, pos):
+    c, p = oracle.find_class_brute(text.encode(), pat)
+    assert c == len(pos) and list(p) == pos
+
+
+def _class_regex(sets):
+    return b"(?=" + b"".join(b"[" + s.encode() + s.lower().encode() + b"]" for s in sets) + b")"
+
+
+def test_class_patterns_vs_regex_and_expansions():
+    """Against Python's regular expressions (a character class per
+    position, overlapping matches by look-ahead), and against the plain
+    brute force: a class pattern's occurrences are the disjoint union of its
+    expansions' occurrences (distinct strings of one length never start at
+    the same position)."""
+    rng = np.random.default_rng(11)
+    syms = list("ACGTRYSWKMBDHVNacgtrn")
+    for seed in range(12):
+        t = synth.random_text(4000, 60 + seed, b"ACGTacgtNn")
+        for _ in range(6):
+            m = int(rng.integers(1, 7))
+            pat = "".join(str(rng.choice(syms)) if rng.random() < 0.7
+                          else "[" + "".join(rng.choice(list("ACGTR"), size=2)) + "]" for _ in range(m))
+            c, p = oracle.find_class_brute(t, pat)
+            r = [mt.start() for mt in re.finditer(_class_regex(oracle.class_sets(pat)), t.tobytes())]
+            assert c == len(r) and list(p) == r, pat
+            exp = oracle.class_expansions(pat)
+            if len(exp) <= 256:
+                assert sum(oracle.count_brute(t, e) for e in exp) == c, pat
+                union = sorted(itertools.chain.from_iterable(oracle.find_brute(t, e)[1].tolist() for e in exp))
+                assert union == list(p), pat
+
+
+def test_single_base_classes_are_plain_patterns():
+    for seed in range(6):
+        t = synth.random_text(5000, 80 + seed, b"ACGTacgtN")
+        for m in (1, 3, 8, 20):
+            pat = synth.pattern(m, 800 + seed * 7 + m)
+            mixed = "".join(ch if i % 2 else "[" + ch + "]" for i, ch in enumerate(pat.decode().lower()))
+            c, p = oracle.find_class_brute(t, mixed)
+            c2, p2 = oracle.find_brute(t, pat)
+            assert c == c2 and np.array_equal(p, p2)
+
+
+@pytest.mark.parametrize("bad", ["", "[", "[]", "[AX]", "AZ", "A]", "[A[C]]", "N" * 65, "AC-GT", "U"])
+def test_class_syntax_errors(bad):
+    with pytest.raises(ValueError):
+        oracle.class_sets(bad)
