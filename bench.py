@@ -39,6 +39,7 @@ PATTERN_LENGTHS = (4, 8, 16, 32, 64)
 PATTERN_SEEDS = (3, 4, 5, 6, 7)
 TEXT_BYTES = 3_200_000_000
 TEXT_SEED = 2
+CLASS_PAIRS, CLASS_SEED = 9, 40          # class-pattern workload: 9 pairs = 18 patterns
 WORKLOAD = "genome-scale single-pattern scan"
 # one dfa_find per pattern: for m >= 8 the count pass k_scan_tma<4,count>
 # (relaxed walk) + k_tile_offsets + k_rewalk; for m < 8 the single-pass
@@ -59,9 +60,10 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: offered queries per second")
     ap.add_argument("--queries", type=int, default=2000, help="serve: queries in the timed trace")
     ap.add_argument("--slots", type=int, default=4, help="serve: CUDA stream slots")
-    ap.add_argument("--workload", default="genome", choices=["genome", "batched", "census", "serve"],
+    ap.add_argument("--workload", default="genome", choices=["genome", "batched", "census", "classes", "serve"],
                     help="genome: the single-pattern scan (the headline line); batched: six "
-                         "sequences x 256 patterns in one graph launch; census: all 4096 6-mers")
+                         "sequences x 256 patterns in one graph launch; census: all 4096 6-mers; "
+                         "classes: 18 character-class patterns over the genome text")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="steps of the one-pattern-per-launch comparison (batched/census)")
     return ap.parse_args()
@@ -439,8 +441,10 @@ def lds_peak_lookups():
 def run_batched(args):
     """Many patterns in one persistent graph-captured launch (batched: six
     genome-like sequences x 256 patterns of length U[4, 64]; census: all
-    4096 6-mers over 1e9 bytes), against the plain form: one dfa_count launch
-    per (sequence, pattern) on the same GPU."""
+    4096 6-mers over 1e9 bytes; classes: 18 character-class patterns shaped
+    like Table III's class cells over the 3.2e9-byte genome text), against
+    the plain form: one dfa_count launch per (sequence, pattern), for class
+    patterns one per plain expansion, summed."""
     import itertools
 
     import numpy as np
@@ -455,7 +459,18 @@ def run_batched(args):
     import paper_1506_08612_gb300 as dd
     import synth
 
-    if args.workload == "batched":
+    classes = args.workload == "classes"
+    expansions = None
+    if classes:
+        sizes = [args.n]
+        seeds = [TEXT_SEED + 1000 * rank]
+        cp = synth.class_pattern_pairs(CLASS_PAIRS, CLASS_SEED)
+        pats = [c for c, _ in cp]
+        expansions = [e for _, e in cp]
+        workload = ("class patterns: 9 pairs shaped like Table III's class cells (an 8-mer with one "
+                    "position widened to the 3 other bases, and its reverse complement) over one "
+                    "genome-like text")
+    elif args.workload == "batched":
         sizes = [max(int(s * args.n / TEXT_BYTES), 4096) for s in BATCH_SIZES]
         seeds = [10 + i + 1000 * rank for i in range(len(sizes))]
         lens = synth.uniform_ints(256, 61, 16) + 4
@@ -474,7 +489,7 @@ def run_batched(args):
     total = sum(sizes)
     cfg = json.loads(args.cfg) if args.cfg else "auto"
     t0 = time.perf_counter()
-    b = dd.BatchedCount(texts, pats, cfg=cfg)
+    b = dd.BatchedCount(texts, pats, cfg=cfg, classes=classes)
     setup_s = time.perf_counter() - t0
     for _ in range(max(args.warmup, 0)):
         b.run()
@@ -500,9 +515,11 @@ def run_batched(args):
     assert np.array_equal(b.result(), counts)
     value = len(pats) * total * world / (ms * 1e-3) / 1e9
 
-    # the plain form: one dfa_count launch per (sequence, pattern)
-    tables = [dd.dfa_build(p) for p in pats]
-    outs = torch.zeros(len(texts) * len(pats), dtype=torch.int64, device=dev)
+    # the plain form: one dfa_count launch per (sequence, pattern); a class
+    # pattern is the sum of its plain expansions
+    flat = [e for exp in expansions for e in exp] if classes else pats
+    tables = [dd.dfa_build(p) for p in flat]
+    outs = torch.zeros(len(texts) * len(flat), dtype=torch.int64, device=dev)
     st = torch.cuda.current_stream(dev)
 
     def plain():
@@ -513,7 +530,11 @@ def run_batched(args):
                 k += 1
     plain()
     torch.cuda.synchronize()
-    plain_counts = outs.cpu().numpy().astype(np.uint64).reshape(len(texts), len(pats))
+    plain_counts = outs.cpu().numpy().astype(np.uint64).reshape(len(texts), len(flat))
+    if classes:
+        ends = np.cumsum([len(x) for x in expansions])
+        plain_counts = np.stack([plain_counts[:, e - len(x):e].sum(axis=1) for e, x in zip(ends, expansions)],
+                                axis=1)
     assert np.array_equal(plain_counts, counts), "batched and plain counts differ"
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
@@ -529,13 +550,16 @@ def run_batched(args):
     lookups_per_s = total / (ms * 1e-3)            # one table lookup per text byte
     hbm_peak, hbm_kind = measured_peak_hbm()
     tab = b.tables[0]
-    line = {"metric": "patterns x GB/s of DNA text counted (batched, one graph launch)",
+    lens = [int(x) for t in b.tables for x in t.lengths]
+    metric = ("class patterns x GB/s of DNA text counted (one graph launch)" if classes
+              else "patterns x GB/s of DNA text counted (batched, one graph launch)")
+    line = {"metric": metric,
             "value": round(value, 1), "unit": "patterns*GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic", "workload": args.workload,
             "config": {"workload": workload, "sequence_bytes": sizes, "patterns": len(pats),
-                       "pattern_lengths": [int(min(len(p) for p in pats)), int(max(len(p) for p in pats))],
+                       "pattern_lengths": [min(lens), max(lens)],
                        "automaton_states": [t.states() for t in b.tables],
                        "launch_config": b.cfgs, "launches_per_step": b.launches,
                        "graph": b.graph is not None, "l2": "inputs larger than L2 (no flush)",
@@ -543,8 +567,10 @@ def run_batched(args):
             "text_gbs": round(total * world / (ms * 1e-3) / 1e9, 2),
             "plain_form": {"value": round(plain_value, 1), "unit": "patterns*GB/s",
                            "ms_per_step": round(plain_ms, 3),
-                           "launches_per_step": len(texts) * len(pats),
-                           "what": "one dfa_count launch per (sequence, pattern), library defaults"},
+                           "launches_per_step": len(texts) * len(flat),
+                           "what": ("one dfa_count launch per plain expansion of each class pattern, summed"
+                                    if classes else
+                                    "one dfa_count launch per (sequence, pattern), library defaults")},
             "speedup_vs_plain": round(plain_ms / ms, 2),
             "roofline": {"bound": "alu", "achieved": round(lookups_per_s / 1e12, 4),
                          "peak": round(peak_lk / 1e12, 4), "unit": "Tlookups/s",
@@ -636,7 +662,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("batched", "census"):
+    elif args.workload in ("batched", "census", "classes"):
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)

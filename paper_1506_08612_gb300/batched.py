@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import MultiTable, autotune, dfa_multi_count
+from . import DFA_EINVAL, DfaError, MultiTable, autotune, dfa_multi_count
 
 MAX_SEQ_PER_LAUNCH = 64
 MAX_PAT_PER_TABLE = 8192
@@ -55,19 +55,37 @@ def group_patterns(patterns, max_states: int = MAX_STATES, max_pat: int = MAX_PA
     return groups
 
 
+def class_groups(patterns, lo: int = 0, hi: int | None = None) -> list:
+    """Consecutive index groups of character-class patterns whose automata
+    the library takes: the whole range if it does, else each half in turn
+    (a class automaton's size is known only once it is built)."""
+    hi = len(patterns) if hi is None else hi
+    try:
+        MultiTable(patterns[lo:hi], device=False, classes=True).free()
+        return [list(range(lo, hi))]
+    except DfaError as e:
+        if e.code != DFA_EINVAL or hi - lo < 2:
+            raise
+    mid = (lo + hi) // 2
+    return class_groups(patterns, lo, mid) + class_groups(patterns, mid, hi)
+
+
 class BatchedCount:
     """Counts of every pattern in every sequence (overlaps included).
 
     texts: device uint8 tensors (kept referenced; their contents may change
     between runs, their storage may not).  patterns: bytes/str.  cfg:
     "auto" (autotuner), None (library default) or a dfa_config dict.
+    classes: read the patterns as character-class patterns (IUPAC codes,
+    bracket sets; dfa_multi_build_class).
     ``run()`` enqueues the whole batch on ``stream`` (one graph replay when
     captured), after the work already enqueued on the caller's current
     stream (writes into the texts, for instance); ``result()`` waits and
     returns uint64[nseq, npat].
     """
 
-    def __init__(self, texts, patterns, cfg="auto", stream=None, capture: bool = True):
+    def __init__(self, texts, patterns, cfg="auto", stream=None, capture: bool = True,
+                 classes: bool = False):
         import torch
 
         if not texts:
@@ -78,8 +96,8 @@ class BatchedCount:
         if not self.patterns:
             raise ValueError("no patterns")
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
-        self.groups = group_patterns(self.patterns)
-        self.tables = [MultiTable([self.patterns[i] for i in g]) for g in self.groups]
+        self.groups = class_groups(self.patterns) if classes else group_patterns(self.patterns)
+        self.tables = [MultiTable([self.patterns[i] for i in g], classes=classes) for g in self.groups]
         self.seq_groups = [list(range(i, min(i + MAX_SEQ_PER_LAUNCH, len(self.texts))))
                            for i in range(0, len(self.texts), MAX_SEQ_PER_LAUNCH)]
         self.out = [[torch.zeros(len(sg) * t.npat, dtype=torch.int64, device=self.device)

@@ -173,3 +173,29 @@ def query_trace(k: int, rate: float, nseq: int, seed: int, max_patterns: int = 6
         out.append({"t": t, "seq": int(seqs[i]), "patterns": pats,
                     "mode": "positions" if modes[i] else "count"})
     return out
+
+
+_RC = bytes.maketrans(b"ACGT", b"TGCA")
+
+
+def class_pattern_pairs(npairs: int, seed: int, m: int = 8) -> list:
+    """Seeded character-class patterns shaped like the class cells of the
+    paper's Table III (Sec. IV): a uniform m-mer with one position widened to
+    the three bases other than its own ("[CGT]" where the m-mer has A), then
+    the reverse complement of that pattern (the widened set complemented),
+    so 2 * npairs patterns.  Returns (class pattern, its plain expansions)
+    pairs; the expansions are the m-mers the class pattern stands for."""
+    out = []
+    for i in range(npairs):
+        w = pattern(m, seed * 1000 + i)
+        j = int(uniform_ints(1, m, seed * 1000 + i, stream=11)[0])
+        others = bytes(b for b in b"ACGT" if b != w[j])
+        exp = [w[:j] + bytes([b]) + w[j + 1:] for b in others]
+        cls = w[:j] + b"[" + others + b"]" + w[j + 1:]
+        out.append((cls, exp))
+        rexp = [e.translate(_RC)[::-1] for e in exp]
+        k = m - 1 - j
+        rw = w.translate(_RC)[::-1]
+        rothers = bytes(sorted(others.translate(_RC)))
+        out.append((rw[:k] + b"[" + rothers + b"]" + rw[k + 1:], rexp))
+    return out

@@ -137,3 +137,16 @@ def test_single_pattern_autotune_and_cache(gpu):
     assert json.load(open(path))[key]["cfg"] == cfg
     autotune.reset_memory_cache()
     assert autotune.tune_single(td, tab) == cfg
+
+
+def test_class_patterns_batched_and_split(gpu):
+    """Class patterns in the graph-captured batch: a set too large for one
+    automaton (four patterns of 6144 states each) is split into groups, one
+    launch each, and every count matches the oracle."""
+    pats = ["A" + "N" * 11 + "T", "C" + "N" * 11 + "G", "G" + "N" * 11 + "A", "T" + "N" * 11 + "C",
+            "ACGT", "R" * 5] + [c for c, _ in synth.class_pattern_pairs(5, 43)]
+    texts = [synth.genome_text(n, 750 + i) for i, n in enumerate((700_001, 1_300_003, 33))]
+    b = gpu.BatchedCount([_dev(t) for t in texts], pats, cfg=None, classes=True)
+    assert len(b.groups) >= 5 and b.graph is not None
+    b.run()
+    assert np.array_equal(b.result(), oracle.multi_count_class(texts, pats))

@@ -204,3 +204,65 @@ def test_count_with_the_largest_automaton(gpu):
 def torch_zeros(n):
     import torch
     return torch.zeros(n, dtype=torch.int64, device="cuda")
+
+
+CLASS_PATTERNS = ["R", "[AC]A", "NN", "GATTACA", "gaWtaca", "[CGT]GGGTAAA", "TTTACCC[ACG]",
+                  "ACGTRYSWKMBDHVN", "A" + "N" * 6 + "T", "[ac][gt][ac][gt][ac][gt]"]
+
+
+def test_class_patterns_count_and_locate(gpu):
+    """Character-class patterns through the multi-pattern kernels: counts of
+    every (sequence, pattern) and the sorted positions of the sparse ones,
+    bit-exact against the oracle's window compare, over sequences of several
+    tiles with ragged ends, soft-masked runs and N blocks."""
+    pairs = synth.class_pattern_pairs(9, 41)
+    pats = CLASS_PATTERNS + [c.decode() for c, _ in pairs]
+    texts = [synth.genome_text(n, 730 + i, mask_mean=80, n_gap_mean=40_000, n_run_mean=500)
+             for i, n in enumerate((1_000_003, 262_147, 50_001, 5))]
+    for i, t in enumerate(texts[:3]):
+        for j, (c, exp) in enumerate(pairs):
+            synth.plant(t, exp[j % 3], synth.uniform_ints(3, t.size - 8, 7300 + 10 * j + i))
+    mt = gpu.MultiTable(pats, classes=True)
+    assert mt.lengths == [len(oracle.class_sets(p)) for p in pats]
+    import torch
+    counts = torch.zeros(len(texts) * len(pats), dtype=torch.int64, device="cuda")
+    gpu.dfa_multi_count([_dev(t) for t in texts], mt, counts)
+    want = oracle.multi_count_class(texts, pats)
+    got = counts.cpu().numpy().astype(np.uint64).reshape(want.shape)
+    assert np.array_equal(got, want), np.argwhere(got != want)[:5]
+    assert (want[:3, len(CLASS_PATTERNS):] > 0).all()          # every planted class pattern found
+    # N^64 counts every window of 64 bases (it multiplies the states of any
+    # automaton it joins, so it has its own)
+    m64 = gpu.MultiTable(["N" * 64, "nnnn"], classes=True)
+    c64 = torch.zeros(len(texts) * 2, dtype=torch.int64, device="cuda")
+    gpu.dfa_multi_count([_dev(t) for t in texts], m64, c64)
+    w64 = oracle.multi_count_class(texts, ["N" * 64, "nnnn"])
+    assert np.array_equal(c64.cpu().numpy().astype(np.uint64).reshape(w64.shape), w64)
+    assert w64[0, 0] > 0 and w64[3, 0] == 0
+    # positions of the patterns with at most DFA_LOCATE_MAX occurrences
+    t = texts[0]
+    sparse = [p for p, c in zip(pats, want[0]) if 0 < c <= gpu.DFA_LOCATE_MAX]
+    assert len(sparse) >= 15
+    ms = gpu.MultiTable(sparse, classes=True)
+    c0 = [int(oracle.find_class_brute(t, p)[0]) for p in sparse]
+    pos = torch.empty(sum(c0), dtype=torch.int64, device="cuda")
+    work = torch.empty(gpu.dfa_multi_locate_work_bytes(len(sparse)), dtype=torch.uint8, device="cuda")
+    gpu.dfa_multi_locate(_dev(t), ms, c0, pos, work)
+    assert gpu.dfa_multi_locate_status(work, len(sparse)) == gpu.DFA_OK
+    h, o = pos.cpu().numpy(), 0
+    for p, c in zip(sparse, c0):
+        assert np.array_equal(h[o:o + c], oracle.find_class_brute(t, p)[1]), p
+        o += c
+
+
+def test_class_automaton_counts_the_sum_of_its_expansions(gpu):
+    """A class pattern counts what its plain expansions count together, on a
+    full-tile text: the class automaton against the single-pattern kernels."""
+    import torch
+    t = synth.genome_text(20_000_017, 740)
+    td = _dev(t)
+    for c, exp in synth.class_pattern_pairs(4, 42):
+        mt = gpu.MultiTable([c], classes=True)
+        out = torch.zeros(1, dtype=torch.int64, device="cuda")
+        gpu.dfa_multi_count([td], mt, out)
+        assert int(out.item()) == sum(gpu.count(td, e) for e in exp), c
