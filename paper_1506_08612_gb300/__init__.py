@@ -453,10 +453,11 @@ def dfa_multi_locate_status(workspace, npat: int, stream=None) -> int:
     return int(_lib.dfa_multi_locate_status(_ptr(workspace), int(npat), _stream(stream)))
 
 
-def multi_count(texts, patterns, cfg=None) -> np.ndarray:
-    """Synchronous batched count: returns uint64[len(texts), len(patterns)]."""
+def multi_count(texts, patterns, cfg=None, classes: bool = False) -> np.ndarray:
+    """Synchronous batched count: returns uint64[len(texts), len(patterns)].
+    classes: the patterns are character-class patterns."""
     import torch
-    t = patterns if isinstance(patterns, MultiTable) else MultiTable(patterns)
+    t = patterns if isinstance(patterns, MultiTable) else MultiTable(patterns, classes=classes)
     dev = texts[0].device
     out = torch.zeros(len(texts) * t.npat, dtype=torch.int64, device=dev)
     dfa_multi_count(texts, t, out, cfg=cfg)

@@ -255,6 +255,13 @@ def test_class_patterns_count_and_locate(gpu):
         o += c
 
 
+def test_multi_count_convenience_with_classes(gpu):
+    t = synth.genome_text(300_007, 745)
+    pats = ["R[AC]NT", "gattaca", "W" * 6]
+    got = gpu.multi_count([_dev(t)], pats, classes=True)
+    assert np.array_equal(got, oracle.multi_count_class([t], pats))
+
+
 def test_class_automaton_counts_the_sum_of_its_expansions(gpu):
     """A class pattern counts what its plain expansions count together, on a
     full-tile text: the class automaton against the single-pattern kernels."""
