@@ -218,6 +218,49 @@ def profiled_traffic():
 
 # ------------------------------------------------------------------ CPU side
 
+def cpu_model() -> str:
+    """The host CPU's model as /proc/cpuinfo names it (x86: model name;
+    Arm: implementer and part numbers), else the machine type."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        info = ""
+    for key in ("model name", "Model"):
+        for line in info.splitlines():
+            if line.split(":")[0].strip() == key:
+                return line.split(":", 1)[1].strip()
+    parts = sorted({line.split(":", 1)[1].strip() for line in info.splitlines()
+                    if line.split(":")[0].strip() in ("CPU implementer", "CPU part")})
+    return f"{platform.machine()} ({', '.join(parts)})" if parts else platform.machine()
+
+
+def oracle_timings(text_np, patterns, sample=20_000_000, reps=5):
+    """The oracle's single-core forms on a prefix of the text, median of
+    ``reps`` runs each: the sequential automaton walk (the paper's
+    sequential version, counting) and the brute-force window compare."""
+    import statistics
+
+    import oracle
+    t = text_np[:sample]
+    deltas = [(oracle.dfa_delta(p), len(p)) for p in patterns]
+
+    def med(fn):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+    seq = med(lambda: [oracle.dfa_scan(t, d, m, cap=0) for d, m in deltas])
+    brute = med(lambda: [oracle.count_brute(t, p) for p in patterns])
+    work = t.size * len(patterns)
+    return {"sample_bytes": int(t.size), "patterns": len(patterns), "reps": reps, "statistic": "median",
+            "sequential_dfa_1core_gbs": round(work / seq / 1e9, 4),
+            "brute_force_1core_gbs": round(work / brute / 1e9, 4),
+            "nproc": os.cpu_count(), "cpu": cpu_model()}
+
+
 def cpu_baseline(text_np, patterns, budget_s=12.0, scale_n=None):
     """The oracle's Algorithm 1 scan (OpenMP over every host core) on a
     bounded prefix of the same text; GB/s of text per pattern."""
@@ -239,7 +282,8 @@ def cpu_baseline(text_np, patterns, budget_s=12.0, scale_n=None):
     return {"value": round(gbs, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {sample} bytes of the {text_np.size}-byte text x {len(deltas)} patterns,"
                       f" Algorithm 1 (p={cores * 8} chunks, v=16 lanes, m-1 overlap), count + positions,"
-                      f" {dt:.1f} s"}
+                      f" {dt:.1f} s",
+            "oracle_timings": oracle_timings(text_np, patterns)}
 
 
 def run_reference(args):
