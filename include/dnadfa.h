@@ -368,7 +368,12 @@ int64_t dfa_multi_smem_bytes(const dfa_multi* table);
  * owned by the chunk holding their start (Algorithm 1 with patterns of
  * several lengths: each chunk reads m_max - 1 bytes past its end).
  *   cfg: threads (128, 256 or 512 per CTA) and chunk (bytes per thread per
- *        tile, multiple of 16); other fields ignored; NULL = 256 x 1024.
+ *        tile, multiple of 16); layout: the table in shared memory, 1 = one
+ *        copy (2 bytes an entry), 2 = 32 per-lane copies (4 bytes an entry
+ *        each, every warp's lookups conflict-free; DFA_EINVAL when they do
+ *        not fit), 0 = the copies when CTAs of 1024 threads a SM still fit
+ *        in 200 KiB (about 198 states at 512 threads); other fields
+ *        ignored; NULL = 256 x 1024, layout 0.
  * Asynchronous on `stream`; allocates nothing (capturable in a CUDA graph).
  * Errors: DFA_EINVAL, DFA_ECUDA.
  */

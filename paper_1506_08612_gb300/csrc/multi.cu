@@ -56,6 +56,9 @@ namespace {
 constexpr int kMultiMaxSeq = 64;
 constexpr int kMultiMaxStates = 16383;   // largest state number: 4 * 16383 + 1 fits the u16 entry (16384 states)
 constexpr int kMultiMaxPat = 8192;       // per-CTA counters: 32 KiB
+// Shared memory per SM that the per-lane table copies may take: the copies
+// (4 * 32 * 4 bytes a state) are used when the CTAs of 1024 threads fit in it.
+constexpr int64_t kRepSmemPerSm = 200 * 1024;
 
 int round16(int64_t b) { return (int)((b + 15) & ~(int64_t)15); }
 
@@ -96,6 +99,8 @@ struct LocateArgs;
 
 struct MultiTab {
     const uint16_t* delta;   // 4 * state + code -> 4 * next | (out(next) not empty)
+    const uint32_t* rep;     // per-lane copies: entry i of lane l at rep[32 * i + l]
+    uint32_t lane;           // threadIdx.x % 32
     uint32_t* hs;            // per-state counters
     const MultiArgs* args;
     unsigned long long* row; // this sequence's per-pattern global counts
@@ -175,14 +180,23 @@ __device__ __forceinline__ void emit(const MultiTab& M, uint32_t e, uint32_t j, 
 
 // Four bases of a word w, byte k ending at offset j + k: four dependent
 // lookups, one test of the output flags.
-template <bool CHECK, bool LOC = false>
+// One table lookup.  REP: the lane's own copy of the entry; the 32 copies
+// of an entry sit in the 32 banks, so a warp's 32 lookups never conflict.
+template <bool REP>
+__device__ __forceinline__ uint32_t lookup(const MultiTab& M, uint32_t idx)
+{
+    if (REP) return M.rep[(idx << 5) | M.lane];
+    return M.delta[idx];
+}
+
+template <bool CHECK, bool LOC = false, bool REP = false>
 __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
 {
     const uint32_t c = (w >> 1) & 0x03030303u;
-    const uint32_t e0 = M.delta[(ent & ~3u) | (c & 3u)];
-    const uint32_t e1 = M.delta[(e0 & ~3u) | ((c >> 8) & 3u)];
-    const uint32_t e2 = M.delta[(e1 & ~3u) | ((c >> 16) & 3u)];
-    const uint32_t e3 = M.delta[(e2 & ~3u) | (c >> 24)];
+    const uint32_t e0 = lookup<REP>(M, (ent & ~3u) | (c & 3u));
+    const uint32_t e1 = lookup<REP>(M, (e0 & ~3u) | ((c >> 8) & 3u));
+    const uint32_t e2 = lookup<REP>(M, (e1 & ~3u) | ((c >> 16) & 3u));
+    const uint32_t e3 = lookup<REP>(M, (e2 & ~3u) | (c >> 24));
     ent = e3;
     if ((e0 | e1 | e2 | e3) & 1u) {
         if (e0 & 1u) emit<CHECK, LOC>(M, e0, j, own);
@@ -194,12 +208,12 @@ __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uin
 
 // One byte, any value: a non-base sends the walk back to q0 (Sec. III-B:
 // columns outside the alphabet lead to q0).
-template <bool LOC = false>
+template <bool LOC = false, bool REP = false>
 __device__ __forceinline__ void byte_any(const MultiTab& M, uint32_t& ent, uint32_t b, uint32_t j, uint32_t own)
 {
     const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
     if (((b ^ (t * 0x11u)) & 0xD9u) == 0x41u) {
-        ent = M.delta[(ent & ~3u) | ((b >> 1) & 3u)];
+        ent = lookup<REP>(M, (ent & ~3u) | ((b >> 1) & 3u));
         if (ent & 1u) emit<true, LOC>(M, ent, j, own);
     } else {
         ent = 0u;
@@ -207,48 +221,60 @@ __device__ __forceinline__ void byte_any(const MultiTab& M, uint32_t& ent, uint3
 }
 
 // A word holding bases and non-bases, byte by byte.
-template <bool LOC = false>
+template <bool LOC = false, bool REP = false>
 __device__ __forceinline__ uint32_t word_mixed(const MultiTab& M, uint32_t ent, uint32_t w, uint32_t j, uint32_t own)
 {
 #pragma unroll 1
-    for (int k = 0; k < 4; k++) byte_any<LOC>(M, ent, (w >> (8 * k)) & 0xFFu, j + k, own);
+    for (int k = 0; k < 4; k++) byte_any<LOC, REP>(M, ent, (w >> (8 * k)) & 0xFFu, j + k, own);
     return ent;
 }
 
-template <bool CHECK, bool LOC = false>
+template <bool CHECK, bool LOC = false, bool REP = false>
 __device__ __forceinline__ void word_any(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
 {
     const uint32_t bad = word_bad_m(w);
     if (bad == 0u) {
-        word_bases<CHECK, LOC>(M, ent, w, j, own);
+        word_bases<CHECK, LOC, REP>(M, ent, w, j, own);
     } else if (((bad - 0x01010101u) & ~bad & 0x80808080u) == 0u) {
         ent = 0u;                                   // four non-bases (an N block)
     } else {
-        ent = word_mixed<LOC>(M, ent, w, j, own);
+        ent = word_mixed<LOC, REP>(M, ent, w, j, own);
     }
 }
 
-template <bool CHECK, bool LOC = false>
+template <bool CHECK, bool LOC = false, bool REP = false>
 __device__ __forceinline__ void vec_any(const MultiTab& M, uint32_t& ent, uint4 v, uint32_t j, uint32_t own)
 {
-    word_any<CHECK, LOC>(M, ent, v.x, j, own);
-    word_any<CHECK, LOC>(M, ent, v.y, j + 4, own);
-    word_any<CHECK, LOC>(M, ent, v.z, j + 8, own);
-    word_any<CHECK, LOC>(M, ent, v.w, j + 12, own);
+    word_any<CHECK, LOC, REP>(M, ent, v.x, j, own);
+    word_any<CHECK, LOC, REP>(M, ent, v.y, j + 4, own);
+    word_any<CHECK, LOC, REP>(M, ent, v.z, j + 8, own);
+    word_any<CHECK, LOC, REP>(M, ent, v.w, j + 12, own);
 }
 
-template <int THREADS>
+// REP: the table as 32 per-lane copies (4 bytes an entry) instead of one
+// (2 bytes an entry), for automata small enough (kMultiRepStates).
+template <int THREADS, bool REP>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const __grid_constant__ MultiArgs a)
 {
     extern __shared__ __align__(16) uint8_t msm[];
-    {
+    int64_t table_bytes;
+    if (REP) {
+        const uint16_t* src = reinterpret_cast<const uint16_t*>(a.tab);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(msm);
+        const int nrep = a.nstates * 4 * 32;
+        for (int i = threadIdx.x; i < nrep; i += THREADS) dst[i] = src[i >> 5];
+        table_bytes = (int64_t)nrep * 4;
+    } else {
         const uint4* src = reinterpret_cast<const uint4*>(a.tab);
         uint4* dst = reinterpret_cast<uint4*>(msm);
         for (int i = threadIdx.x; i < (a.delta_bytes >> 4); i += THREADS) dst[i] = src[i];
+        table_bytes = a.delta_bytes;
     }
     MultiTab M;
     M.delta = reinterpret_cast<const uint16_t*>(msm);
-    M.hs = reinterpret_cast<uint32_t*>(msm + a.delta_bytes);
+    M.rep = reinterpret_cast<const uint32_t*>(msm);
+    M.lane = threadIdx.x & 31u;
+    M.hs = reinterpret_cast<uint32_t*>(msm + table_bytes);
     M.args = &a;
     for (int q = threadIdx.x; q < a.nstates; q += THREADS) M.hs[q] = 0u;
     __syncthreads();
@@ -295,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
         uint32_t j = 0;
         if ((((uintptr_t)base) & 15u) == 0) {
             if ((((uintptr_t)base) & 31u) != 0 && len >= 16) {
-                vec_any<true>(M, ent, *reinterpret_cast<const uint4*>(base), 0u, own);
+                vec_any<true, false, REP>(M, ent, *reinterpret_cast<const uint4*>(base), 0u, own);
                 j = 16;
             }
             // owned 32-byte blocks, the next one in flight while one is walked
@@ -308,16 +334,16 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
                     const uint4 c0 = a0, c1 = a1;
                     if (g + 1 < nb) ldg32m(base + j + 32 * (g + 1), a0, a1);
                     const uint32_t jj = j + 32u * g;
-                    vec_any<false>(M, ent, c0, jj, own);
-                    vec_any<false>(M, ent, c1, jj + 16, own);
+                    vec_any<false, false, REP>(M, ent, c0, jj, own);
+                    vec_any<false, false, REP>(M, ent, c1, jj + 16, own);
                 }
                 j += nb << 5;
             }
             // the rest of the chunk and its overlap, 16 bytes at a time
             for (; j + 16 <= len; j += 16)
-                vec_any<true>(M, ent, *reinterpret_cast<const uint4*>(base + j), j, own);
+                vec_any<true, false, REP>(M, ent, *reinterpret_cast<const uint4*>(base + j), j, own);
         }
-        for (; j < len; j++) byte_any(M, ent, base[j], j, own);
+        for (; j < len; j++) byte_any<false, REP>(M, ent, base[j], j, own);
     }
     if (cur >= 0) flush(cur);
 }
@@ -336,6 +362,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_locate(const 
     }
     MultiTab M;
     M.delta = reinterpret_cast<const uint16_t*>(msm);
+    M.rep = nullptr;
+    M.lane = threadIdx.x & 31u;
     M.hs = nullptr;
     M.args = nullptr;
     M.row = nullptr;
@@ -401,11 +429,16 @@ __global__ void __launch_bounds__(512) k_sort_segments(int64_t* pos, const unsig
 
 typedef void (*MultiFn)(const MultiArgs);
 
-MultiFn pick_multi(int threads)
+MultiFn pick_multi(int threads, bool rep)
 {
-    if (threads == 128) return k_multi_count<128>;
-    if (threads == 512) return k_multi_count<512>;
-    return k_multi_count<256>;
+    if (rep) {
+        if (threads == 128) return k_multi_count<128, true>;
+        if (threads == 512) return k_multi_count<512, true>;
+        return k_multi_count<256, true>;
+    }
+    if (threads == 128) return k_multi_count<128, false>;
+    if (threads == 512) return k_multi_count<512, false>;
+    return k_multi_count<256, false>;
 }
 
 int multi_fail(const char* what, cudaError_t err)
@@ -795,6 +828,12 @@ int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32
     const int chunk = cfg && cfg->chunk ? cfg->chunk : 1024;
     if (threads != 128 && threads != 256 && threads != 512) return DFA_EINVAL;
     if (chunk < 16 || chunk > 32768 || (chunk & 15)) return DFA_EINVAL;
+    // table layout: 1 = one shared copy, 2 = 32 per-lane copies, 0 = the
+    // copies when the SM still holds 1024 threads' worth of CTAs
+    const int layout = cfg ? cfg->layout : 0;
+    if (layout < 0 || layout > 2) return DFA_EINVAL;
+    const int64_t rep_smem = (int64_t)t->nstates * (4 * 32 * 4 + 4);
+    const bool rep = layout == 2 || (layout == 0 && rep_smem * (1024 / threads) <= kRepSmemPerSm);
     int dev;
     cudaError_t err;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return multi_fail("dfa_multi_count", err);
@@ -825,8 +864,8 @@ int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32
     if ((err = cudaMemsetAsync(d_counts, 0, (size_t)nseq * t->npat * 8, st)) != cudaSuccess)
         return multi_fail("dfa_multi_count", err);
     if (a.tile0[nseq] == 0) return DFA_OK;
-    MultiFn fn = pick_multi(threads);
-    const int smem = (int)dfa_multi_smem_bytes(t);
+    MultiFn fn = pick_multi(threads, rep);
+    const int smem = (int)(rep ? rep_smem : dfa_multi_smem_bytes(t));
     int optin = 0, sms = 0;
     if ((err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
         (err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)

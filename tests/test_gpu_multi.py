@@ -273,3 +273,35 @@ def test_class_automaton_counts_the_sum_of_its_expansions(gpu):
         out = torch.zeros(1, dtype=torch.int64, device="cuda")
         gpu.dfa_multi_count([td], mt, out)
         assert int(out.item()) == sum(gpu.count(td, e) for e in exp), c
+
+
+@pytest.mark.parametrize("layout", [1, 2])
+def test_table_layouts_agree(gpu, layout):
+    """The table as one shared copy (layout 1) and as 32 per-lane copies
+    (layout 2, conflict-free lookups) count the same, bit-exact against the
+    oracle, for plain and class automata and every block size."""
+    import torch
+    texts = [synth.genome_text(n, 760 + i, mask_mean=60, n_gap_mean=30_000, n_run_mean=300)
+             for i, n in enumerate((2_000_003, 333_331, 17))]
+    sets = [([p.encode() for p in PATTERN_SETS[3]], False),
+            ([c.decode() for c, _ in synth.class_pattern_pairs(9, 44)], True),
+            (["R", "[AC]A", "NN", "gaWtaca", "ACGTRYSWKMBDHVN"], True)]
+    for pats, cls in sets:
+        mt = gpu.MultiTable(pats, classes=cls)
+        want = oracle.multi_count_class(texts, pats) if cls else oracle.multi_count(texts, pats)
+        for threads in (128, 256, 512):
+            out = torch.zeros(len(texts) * len(pats), dtype=torch.int64, device="cuda")
+            gpu.dfa_multi_count([_dev(t) for t in texts], mt, out,
+                                cfg=dict(layout=layout, threads=threads, chunk=256))
+            got = out.cpu().numpy().astype(np.uint64).reshape(want.shape)
+            assert np.array_equal(got, want), (pats[:2], threads, np.argwhere(got != want)[:3])
+
+
+def test_per_lane_copies_refused_when_too_large(gpu):
+    import torch
+    mt = gpu.MultiTable(["".join(x) for x in itertools.product("ACGT", repeat=6)])   # 5461 states
+    out = torch.zeros(4096, dtype=torch.int64, device="cuda")
+    with pytest.raises(gpu.DfaError):
+        gpu.dfa_multi_count([_dev(synth.genome_text(10_000, 3))], mt, out, cfg=dict(layout=2))
+    gpu.dfa_multi_count([_dev(synth.genome_text(10_000, 3))], mt, out, cfg=dict(layout=1))
+    assert int(out.sum().item()) == oracle.valid_windows(synth.genome_text(10_000, 3), 6)
