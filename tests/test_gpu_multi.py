@@ -206,7 +206,7 @@ def torch_zeros(n):
     return torch.zeros(n, dtype=torch.int64, device="cuda")
 
 
-CLASS_PATTERNS = ["R", "[AC]A", "NN", "GATTACA", "gaWtaca", "[CGT]GGGTAAA", "TTTACCC[ACG]",
+CLASS_PATTERNS = ["R", "[AC]A", "NN", "GATTACA", "gaWtaca", "[ACT]TCGGAGC", "GCCTAAG[ACG]",
                   "ACGTRYSWKMBDHVN", "A" + "N" * 6 + "T", "[ac][gt][ac][gt][ac][gt]"]
 
 
