@@ -245,7 +245,8 @@ def multi_count(texts, patterns, threads: int | None = None) -> np.ndarray:
 #
 # A class pattern allows a set of bases at each position (the class cells of
 # the paper's Table III, Sec. IV).  Symbols are the IUPAC nucleotide codes
-# (a base stands for itself); a bracket joins the sets of the symbols inside.
+# (a base stands for itself); a bracket joins the sets of the symbols inside,
+# and so does the paper's group of single symbols separated by "|".
 
 IUPAC = {"A": "A", "C": "C", "G": "G", "T": "T",
          "R": "AG", "Y": "CT", "S": "CG", "W": "AT", "K": "GT", "M": "AC",
@@ -268,6 +269,18 @@ def class_sets(pattern) -> list[str]:
                 if ch.upper() not in IUPAC:
                     raise ValueError(f"bad symbol {ch!r} in {s!r}")
                 members |= set(IUPAC[ch.upper()])
+            out.append("".join(sorted(members)))
+            i = j + 1
+        elif s[i] == "(":
+            # the paper's notation for a class: single symbols separated by |
+            j = s.find(")", i + 1)
+            if j < 0:
+                raise ValueError(f"unclosed group in {s!r}")
+            members = set()
+            for alt in s[i + 1:j].split("|"):
+                if len(alt) != 1 or alt.upper() not in IUPAC:
+                    raise ValueError(f"bad alternative {alt!r} in {s!r}")
+                members |= set(IUPAC[alt.upper()])
             out.append("".join(sorted(members)))
             i = j + 1
         else:

@@ -516,7 +516,8 @@ int make_multi(int32_t npat, const int32_t* lengths, const std::vector<std::arra
 // classes of the paper's Table III cells, Sec. IV).  Symbols: a base, an
 // IUPAC nucleotide code (R = A/G, Y = C/T, S = C/G, W = A/T, K = G/T,
 // M = A/C, B = not A, D = not C, H = not G, V = not T, N = any), either case,
-// or a bracket set of those, "[CGT]".  The text side is unchanged: a text
+// a bracket set of those, "[CGT]", or the paper's alternation of single
+// symbols, "(c|g|t)".  The text side is unchanged: a text
 // byte outside ACGTacgt matches no position.
 
 // Mask over base codes (bit base_code: A 0, C 1, T 2, G 3) of one symbol; 0
@@ -545,8 +546,9 @@ uint32_t symbol_mask(uint32_t c)
 }
 
 // The per-position masks of a class pattern of len bytes; DFA_EINVAL for an
-// empty pattern, an unknown byte, an empty or unclosed bracket, or more than
-// DFA_MAX_M positions.
+// empty pattern, an unknown byte, an empty or unclosed bracket or group, a
+// group alternative longer than one symbol, or more than DFA_MAX_M
+// positions.
 int parse_class(const char* s, int32_t len, std::vector<uint8_t>& masks)
 {
     masks.clear();
@@ -560,6 +562,22 @@ int parse_class(const char* s, int32_t len, std::vector<uint8_t>& masks)
                 mk |= b;
             }
             if (j >= len || j == i + 1) return DFA_EINVAL;
+            i = j;
+        } else if (s[i] == '(') {
+            // the paper's notation: an alternation of single symbols, (c|g|t)
+            int32_t j = i + 1;
+            bool want_symbol = true;
+            for (; j < len && s[j] != ')'; j++) {
+                if (want_symbol) {
+                    const uint32_t b = symbol_mask((uint8_t)s[j]);
+                    if (!b) return DFA_EINVAL;
+                    mk |= b;
+                } else if (s[j] != '|') {
+                    return DFA_EINVAL;
+                }
+                want_symbol = !want_symbol;
+            }
+            if (j >= len || want_symbol) return DFA_EINVAL;   // unclosed, empty or ending in '|'
             i = j;
         } else {
             mk = symbol_mask((uint8_t)s[i]);

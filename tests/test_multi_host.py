@@ -167,7 +167,8 @@ def test_class_automaton_walk_equals_oracle():
 
 def test_class_builder_limits_and_syntax():
     import paper_1506_08612_gb300 as dd
-    for bad in ["", "[", "[]", "[AX]", "AZ", "A]", "[A[C]]", "N" * 65, "U"]:
+    for bad in ["", "[", "[]", "[AX]", "AZ", "A]", "[A[C]]", "N" * 65, "U",
+                "()", "(c|)", "(|c)", "(cg)", "(c|g", "(c|gt)", "(c||g)"]:
         with pytest.raises(dd.DfaError):
             dd.MultiTable([bad], device=False, classes=True)
     # remembering where each of the last 16 A's was takes more than 16384 states
@@ -181,3 +182,15 @@ def test_class_builder_limits_and_syntax():
     t = dd.MultiTable(["N" * 64, "[acgt]", "ry"], device=False, classes=True)
     assert t.lengths == [64, 1, 2] and t.mmax == 64
     assert t.states() == 1 + 2 + 63 * 3
+
+
+def test_group_notation_builds_the_bracket_automaton():
+    """The paper's (c|g|t) and the bracket [CGT] give the same automaton."""
+    import paper_1506_08612_gb300 as dd
+    for g, br in [(["(c|g|t)AC", "GG(a|c)T(r|y)"], ["[CGT]AC", "GG[AC]T[RY]"]),
+                  (["(n)(a|t)"], ["N[AT]"])]:
+        a = dd.MultiTable(g, device=False, classes=True)
+        b = dd.MultiTable(br, device=False, classes=True)
+        assert a.states() == b.states() and a.lengths == b.lengths
+        for x, y in zip(a.export(), b.export()):
+            assert (x == y).all()

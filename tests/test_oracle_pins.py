@@ -454,6 +454,8 @@ CLASS_FACTS = [
     ("TTTT", "[AG]", []),
     ("ACG", "NNNN", []),
     ("aCgT", "mS", [0, 1]),
+    ("CATTAG", "(c|g|t)A", [0, 3]),
+    ("ACGTT", "(a|c)(g|c)(t|r)", [0, 1]),
 ]
 
 
@@ -502,7 +504,16 @@ def test_single_base_classes_are_plain_patterns():
             assert c == c2 and np.array_equal(p, p2)
 
 
-@pytest.mark.parametrize("bad", ["", "[", "[]", "[AX]", "AZ", "A]", "[A[C]]", "N" * 65, "AC-GT", "U"])
+def test_groups_equal_brackets():
+    """The paper's notation (a group of single symbols separated by |)
+    allows the same bases as the bracket set of those symbols."""
+    for g, br in [("(c|g|t)", "[CGT]"), ("(a|c)", "[AC]"), ("(r|y)", "[RY]"), ("(n)", "[N]"),
+                  ("(a|A)", "[A]")]:
+        assert oracle.class_sets(g + "TT" + g) == oracle.class_sets(br + "TT" + br)
+
+
+@pytest.mark.parametrize("bad", ["", "[", "[]", "[AX]", "AZ", "A]", "[A[C]]", "N" * 65, "AC-GT", "U",
+                                 "()", "(c|)", "(|c)", "(cg)", "(c|g", "(c|gt)", "(c||g)"])
 def test_class_syntax_errors(bad):
     with pytest.raises(ValueError):
         oracle.class_sets(bad)
