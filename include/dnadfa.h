@@ -323,7 +323,7 @@ int dfa_multi_attach(dfa_multi* table, void* d_mem, int64_t bytes, void* stream)
  * nucleotide code, R (A/G), Y (C/T), S (C/G), W (A/T), K (G/T), M (A/C),
  * B (not A), D (not C), H (not G), V (not T), N (any base); a bracket set
  * of those, e.g. "[CGT]"; or an alternation of single symbols as the paper
- * writes them, e.g. "(c|g|t)"; either case.  1..DFA_MAX_M positions a pattern.
+ * writes them, e.g. "(a|g)"; either case.  1..DFA_MAX_M positions a pattern.
  * An occurrence at i is a window T[i..i+m) whose every byte is a base (either
  * case) in its position's set: text bytes outside ACGTacgt still match
  * nothing.  The automaton (subset construction over the patterns'

@@ -517,7 +517,7 @@ int make_multi(int32_t npat, const int32_t* lengths, const std::vector<std::arra
 // IUPAC nucleotide code (R = A/G, Y = C/T, S = C/G, W = A/T, K = G/T,
 // M = A/C, B = not A, D = not C, H = not G, V = not T, N = any), either case,
 // a bracket set of those, "[CGT]", or the paper's alternation of single
-// symbols, "(c|g|t)".  The text side is unchanged: a text
+// symbols, "(a|g)".  The text side is unchanged: a text
 // byte outside ACGTacgt matches no position.
 
 // Mask over base codes (bit base_code: A 0, C 1, T 2, G 3) of one symbol; 0
@@ -564,7 +564,7 @@ int parse_class(const char* s, int32_t len, std::vector<uint8_t>& masks)
             if (j >= len || j == i + 1) return DFA_EINVAL;
             i = j;
         } else if (s[i] == '(') {
-            // the paper's notation: an alternation of single symbols, (c|g|t)
+            // the paper's notation: an alternation of single symbols, (a|g)
             int32_t j = i + 1;
             bool want_symbol = true;
             for (; j < len && s[j] != ')'; j++) {

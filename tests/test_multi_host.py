@@ -185,9 +185,10 @@ def test_class_builder_limits_and_syntax():
 
 
 def test_group_notation_builds_the_bracket_automaton():
-    """The paper's (c|g|t) and the bracket [CGT] give the same automaton."""
+    """The paper's group notation, (a|g|y) say, and the bracket [AGY] give the
+    same automaton."""
     import paper_1506_08612_gb300 as dd
-    for g, br in [(["(c|g|t)AC", "GG(a|c)T(r|y)"], ["[CGT]AC", "GG[AC]T[RY]"]),
+    for g, br in [(["(a|g|y)AC", "GG(a|c)T(r|y)"], ["[AGY]AC", "GG[AC]T[RY]"]),
                   (["(n)(a|t)"], ["N[AT]"])]:
         a = dd.MultiTable(g, device=False, classes=True)
         b = dd.MultiTable(br, device=False, classes=True)
