@@ -654,7 +654,8 @@ int build_class_automaton(const std::vector<std::vector<uint8_t>>& cls, std::vec
                 if ((allow_next[x] >> a) & 1u) adv.push_back(x + 1);
             nxt.resize(adv.size() + first[a].size());
             std::merge(adv.begin(), adv.end(), first[a].begin(), first[a].end(), nxt.begin());
-            std::string k2(reinterpret_cast<const char*>(nxt.data()), nxt.size() * 4);
+            std::string k2;
+            if (!nxt.empty()) k2.assign(reinterpret_cast<const char*>(nxt.data()), nxt.size() * 4);
             if (!intern(std::move(k2), nx[a]))
                 return set_last_error(DFA_EINVAL, "dfa_multi_build_class: the automaton needs more than 16384 states");
         }
