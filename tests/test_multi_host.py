@@ -195,3 +195,24 @@ def test_group_notation_builds_the_bracket_automaton():
         assert a.states() == b.states() and a.lengths == b.lengths
         for x, y in zip(a.export(), b.export()):
             assert (x == y).all()
+
+
+def test_class_automaton_exhaustive_tiny_texts():
+    """Every text of length <= 6 over {A, C, G, T, N, a}: the class
+    automaton's host walk counts what the oracle's window compare finds, per
+    pattern and for the patterns together."""
+    import itertools
+
+    import paper_1506_08612_gb300 as dd
+    pats = ["R", "(a|c)A", "NN", "[AG]Y", "WaS", "ANT", "(r|y)(r|y)(r|y)"]
+    singles = []
+    for p in pats:
+        singles.append(dd.MultiTable([p], device=False, classes=True).export())
+    together = dd.MultiTable(pats, device=False, classes=True).export()
+    for L in range(0, 7):
+        for tup in itertools.product(b"ACGTNa", repeat=L):
+            t = bytes(tup)
+            want = [oracle.find_class_brute(t, p)[0] for p in pats]
+            for (nxt, nout), w in zip(singles, want):
+                assert _host_walk_total(nxt, nout, t) == w, (t, w)
+            assert _host_walk_total(*together, t) == sum(want)
