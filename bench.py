@@ -16,6 +16,13 @@ position written) per launch over its CUDA-event duration against the
 measured HBM copy bandwidth.  ``cpu_baseline`` times the CPU oracle's
 Algorithm 1 scan on the host cores on a bounded sample of the same text.
 
+``workloads`` (N = 1, after the headline, on the same GPU) holds the other
+workloads, each with its own roofline: the 16 MiB single-pattern case (m =
+8) timed after an L2 flush and as CUDA-graph back-to-back finds; the six
+sequences x 256 patterns in one graph launch and the 4096 6-mer census,
+each against its one-pattern-per-launch plain form; and serving at the
+offered Poisson rate against the plain form.  ``--no-workloads`` skips them.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) each rank scans its own replica (weak scaling).
 """
@@ -66,6 +73,11 @@ def parse():
                          "classes: 18 character-class patterns over the genome text")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="steps of the one-pattern-per-launch comparison (batched/census)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="genome: skip the other workloads (16 MiB single pattern, batched, census, "
+                         "serving) reported under 'workloads'")
+    ap.add_argument("--serve-queries", type=int, default=600,
+                    help="genome: queries of the serving trace reported under 'workloads'")
     return ap.parse_args()
 
 
@@ -450,6 +462,12 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu and world == 1:
         cpu = cpu_baseline(host.numpy(), patterns)
 
+    workloads = None
+    if world == 1 and not args.no_workloads:
+        del text, pos, ws
+        torch.cuda.empty_cache()
+        workloads = other_workloads(args, dd, dev, stream, local)
+
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -457,7 +475,7 @@ def run_ours(args):
                 "data": "synthetic", "config": config_dict(n, world, cfg), "clocks": clk,
                 "e2e": e2e, "gpu_launches": args.steps * sum(kernels_per_find(m, cfg) for m in PATTERN_LENGTHS),
                 "roofline": roof,
-                "cpu_baseline": cpu, "counts": counts}
+                "cpu_baseline": cpu, "counts": counts, "workloads": workloads}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -482,31 +500,47 @@ def lds_peak_lookups():
     return sms * 32 * mhz * 1e6, sms, mhz
 
 
-def run_batched(args):
-    """Many patterns in one persistent graph-captured launch (batched: six
-    genome-like sequences x 256 patterns of length U[4, 64]; census: all
-    4096 6-mers over 1e9 bytes; classes: 18 character-class patterns shaped
-    like Table III's class cells over the 3.2e9-byte genome text), against
-    the plain form: one dfa_count launch per (sequence, pattern), for class
-    patterns one per plain expansion, summed."""
+def _brief(line):
+    """A workload's line without the keys the headline line already states."""
+    drop = ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "e2e", "warmup")
+    return {k: v for k, v in line.items() if k not in drop}
+
+
+def other_workloads(args, dd, dev, stream, local):
+    """The other workloads, measured after the headline on the same GPU (the
+    genome text freed first): the 16 MiB single-pattern case; the batched
+    six sequences x 256 patterns and the 6-mer census, each against its
+    one-pattern-per-launch plain form; serving on the same six resident
+    sequences against the plain form.  Sizes scale with --n."""
+    import torch
+    out = {"small_16MiB_m8": measure_small(dd, dev, stream)}
+    steps = max(3, min(args.steps, 20))
+    texts, sizes, pats, exp, wl = make_many("batched", args.n, 0, dev)
+    out["batched_6seq_256pat"] = _brief(measure_many("batched", texts, sizes, pats, exp, wl, dev, steps,
+                                                     max(args.warmup, 3), 1, local=local))
+    ctexts, csizes, cpats, cexp, cwl = make_many("census", args.n, 0, dev)
+    out["census_4096_6mers"] = _brief(measure_many("census", ctexts, csizes, cpats, cexp, cwl, dev, steps,
+                                                   max(args.warmup, 3), 1, local=local))
+    del ctexts
+    torch.cuda.empty_cache()
+    out["serve_200qps"] = _brief(measure_serve(texts, sizes, args.rate, args.serve_queries, args.slots,
+                                               local, search_sustainable=False))
+    del texts
+    torch.cuda.empty_cache()
+    return out
+
+
+def make_many(kind, n_scale, rank=0, dev=None, texts=None):
+    """Inputs of a many-pattern workload: (device texts, sizes, patterns,
+    class expansions or None, description).  ``texts`` reuses sequences
+    already resident (the batched and serving workloads share theirs)."""
     import itertools
 
-    import numpy as np
     import torch
-
-    world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    import paper_1506_08612_gb300 as dd
     import synth
-
-    classes = args.workload == "classes"
     expansions = None
-    if classes:
-        sizes = [args.n]
+    if kind == "classes":
+        sizes = [n_scale]
         seeds = [TEXT_SEED + 1000 * rank]
         cp = synth.class_pattern_pairs(CLASS_PAIRS, CLASS_SEED)
         pats = [c for c, _ in cp]
@@ -514,28 +548,44 @@ def run_batched(args):
         workload = ("class patterns: 9 pairs shaped like Table III's class cells (an 8-mer with one "
                     "position widened to the 3 other bases, and its reverse complement) over one "
                     "genome-like text")
-    elif args.workload == "batched":
-        sizes = [max(int(s * args.n / TEXT_BYTES), 4096) for s in BATCH_SIZES]
+    elif kind == "batched":
+        sizes = [max(int(s * n_scale / TEXT_BYTES), 4096) for s in BATCH_SIZES]
         seeds = [10 + i + 1000 * rank for i in range(len(sizes))]
         lens = synth.uniform_ints(256, 61, 16) + 4
         pats = [synth.pattern(int(m), 16 * 100_000 + i) for i, m in enumerate(lens)]
         workload = "batched: 6 genome-like sequences x 256 patterns, lengths U[4,64]"
     else:
-        sizes = [max(int(1_000_000_000 * args.n / TEXT_BYTES), 4096)]
+        sizes = [max(int(1_000_000_000 * n_scale / TEXT_BYTES), 4096)]
         seeds = [20 + 1000 * rank]
         pats = ["".join(x).encode() for x in itertools.product("ACGT", repeat=6)]
         workload = "k-mer census: all 4096 6-mers over one genome-like text"
-    texts = []
-    for n, sd in zip(sizes, seeds):
-        h = synth.genome_text(n, sd)
-        texts.append(torch.from_numpy(h).to(dev))
-        del h
+    if texts is None:
+        texts = []
+        for n, sd in zip(sizes, seeds):
+            h = synth.genome_text(n, sd)
+            texts.append(torch.from_numpy(h).to(dev))
+            del h
+    return texts, sizes, pats, expansions, workload
+
+
+def measure_many(kind, texts, sizes, pats, expansions, workload, dev, steps, warmup, plain_steps,
+                 cfg="auto", world=1, local=0):
+    """Many patterns in one persistent graph-captured launch (batched: six
+    genome-like sequences x 256 patterns of length U[4, 64]; census: all
+    4096 6-mers over 1e9 bytes; classes: 18 character-class patterns shaped
+    like Table III's class cells over the 3.2e9-byte genome text), against
+    the plain form: one dfa_count launch per (sequence, pattern), for class
+    patterns one per plain expansion, summed.  Returns the JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1506_08612_gb300 as dd
+    classes = kind == "classes"
     total = sum(sizes)
-    cfg = json.loads(args.cfg) if args.cfg else "auto"
     t0 = time.perf_counter()
     b = dd.BatchedCount(texts, pats, cfg=cfg, classes=classes)
     setup_s = time.perf_counter() - t0
-    for _ in range(max(args.warmup, 0)):
+    for _ in range(max(warmup, 0)):
         b.run()
     counts = b.result()
     if world > 1:
@@ -546,12 +596,12 @@ def run_batched(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(b.stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         b.run()
     e1.record(b.stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -583,25 +633,25 @@ def run_batched(args):
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
     p0.record(st)
-    for _ in range(args.plain_steps):
+    for _ in range(plain_steps):
         plain()
     p1.record(st)
     torch.cuda.synchronize()
-    plain_ms = p0.elapsed_time(p1) / args.plain_steps
+    plain_ms = p0.elapsed_time(p1) / plain_steps
     plain_value = len(pats) * total * world / (plain_ms * 1e-3) / 1e9
+    del tables, outs
 
     peak_lk, sms, mhz = lds_peak_lookups()
     lookups_per_s = total / (ms * 1e-3)            # one table lookup per text byte
     hbm_peak, hbm_kind = measured_peak_hbm()
-    tab = b.tables[0]
     lens = [int(x) for t in b.tables for x in t.lengths]
     metric = ("class patterns x GB/s of DNA text counted (one graph launch)" if classes
               else "patterns x GB/s of DNA text counted (batched, one graph launch)")
     line = {"metric": metric,
             "value": round(value, 1), "unit": "patterns*GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "steps": steps, "warmup": warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "workload": args.workload,
+            "data": "synthetic", "workload": kind,
             "config": {"workload": workload, "sequence_bytes": sizes, "patterns": len(pats),
                        "pattern_lengths": [min(lens), max(lens)],
                        "automaton_states": [t.states() for t in b.tables],
@@ -623,42 +673,46 @@ def run_batched(args):
                          "peak_kind": f"derived: {sms} SMs x 32 shared-memory lanes/clk x {mhz:.0f} MHz",
                          "hbm_frac": round(total / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                          "hbm_peak": f"{hbm_peak} GB/s ({hbm_kind})"},
-            "clocks": clk, "gpu_launches": args.steps * b.launches, "e2e": None,
+            "clocks": clk, "gpu_launches": steps * b.launches, "e2e": None,
             "checksum": int(counts.sum())}
+    b.close()
+    torch.cuda.empty_cache()
+    return line
+
+
+def run_batched(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    texts, sizes, pats, expansions, workload = make_many(args.workload, args.n, rank, dev)
+    cfg = json.loads(args.cfg) if args.cfg else "auto"
+    line = measure_many(args.workload, texts, sizes, pats, expansions, workload, dev, args.steps,
+                        args.warmup, args.plain_steps, cfg=cfg, world=world, local=local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_serve(args):
+def measure_serve(seqs, sizes, rate, queries, slots, local=0, search_sustainable=True):
     """Serving: the six batched-workload sequences resident in HBM, a Poisson
     trace of queries (sequence uniform over the six, 1-64 patterns of length
     U[4, 64], count or positions with probability 1/2) replayed open-loop at
     the offered rate; p50/p99 latency from arrival to the answer on the
     host.  The same trace head also runs through the plain form (each query
-    alone, one single-pattern launch per pattern)."""
-    import numpy as np
+    alone, one single-pattern launch per pattern).  Returns the JSON line."""
     import torch
-
-    world, rank, local = dist_env()
-    if world > 1 and rank != 0:
-        return                                   # one server per box: rank 0 only
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     import synth
     from paper_1506_08612_gb300.serve import GpuEngine, Server, latency_summary
-
-    sizes = [max(int(s * args.n / TEXT_BYTES), 4096) for s in BATCH_SIZES]
-    seqs = []
-    for i, n in enumerate(sizes):
-        h = synth.genome_text(n, 10 + i)
-        seqs.append(torch.from_numpy(h).to(dev))
-        del h
     arena = 8 << 30
 
     def run(rate, k, seed, plain=False):
-        eng = GpuEngine(seqs, slots=args.slots, arena_bytes=arena, plain=plain)
+        eng = GpuEngine(seqs, slots=slots, arena_bytes=arena, plain=plain)
         srv = Server(eng, max_batch_queries=1) if plain else Server(eng)
         srv.replay(synth.query_trace(8, rate, len(seqs), seed + 1))          # warm-up
         trace = synth.query_trace(k, rate, len(seqs), seed)
@@ -680,26 +734,118 @@ def run_serve(args):
         torch.cuda.empty_cache()
         return st, clk
 
-    main, clk = run(args.rate, args.queries, 30)
+    main, clk = run(rate, queries, 30)
     sustainable = None
-    if not main["sustained"]:
+    if search_sustainable and not main["sustained"]:
         for r in (0.7, 0.5, 0.35, 0.25, 0.15):
-            st, _ = run(args.rate * r, max(100, args.queries // 5), 40)
+            st, _ = run(rate * r, max(100, queries // 5), 40)
             if st["sustained"]:
                 sustainable = st
                 break
-    plain, _ = run(args.rate, max(50, args.queries // 20), 30, plain=True)
-    line = {"metric": "serving: completed queries per second at the offered Poisson rate",
-            "value": main["qps"], "unit": "queries/s", "n_gpus": 1, "steps": args.queries,
+    plain, _ = run(rate, max(50, queries // 20), 30, plain=True)
+    return {"metric": "serving: completed queries per second at the offered Poisson rate",
+            "value": main["qps"], "unit": "queries/s", "n_gpus": 1, "steps": queries,
             "warmup": 8, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u8", "data": "synthetic", "workload": "serve",
             "config": {"workload": "serving: six resident genome-like sequences, Poisson queries",
-                       "sequence_bytes": sizes, "offered_qps": args.rate, "slots": args.slots,
+                       "sequence_bytes": sizes, "offered_qps": rate, "slots": slots,
                        "position_arena_bytes": arena,
                        "query": "seq U{0..5}, 1-64 patterns of length U[4,64], count or positions p=1/2"},
             "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "serving": main,
-            "max_sustainable": sustainable, "plain_form": plain, "clocks": clk, "e2e": None}
+            "max_sustainable": sustainable, "plain_form": plain,
+            "speedup_vs_plain_qps": round(main["qps"] / max(plain["qps"], 1e-9), 2),
+            "clocks": clk, "e2e": None}
+
+
+def run_serve(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1 and rank != 0:
+        return                                   # one server per box: rank 0 only
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seqs, sizes, _, _, _ = make_many("batched", args.n, 0, dev)
+    line = measure_serve(seqs, sizes, args.rate, args.queries, args.slots, local)
     print(json.dumps(line), flush=True)
+
+
+C1_BYTES, C1_SEED, C1_M, C1_PSEED = 16 << 20, 0, 8, 1
+
+
+def measure_small(dd, dev, stream, reps=20, graph_reps=200):
+    """The plain single-pattern method on a 16 MiB uniform A/C/G/T text
+    (seed 0) and an 8-mer (seed 1): dfa_find (count + sorted positions)
+    timed alone after an L2 flush (a 512 MiB write, 4x the L2) before each
+    of ``reps`` repetitions (median, p10, p90), and as ``graph_reps`` finds
+    back to back in one CUDA graph (the text then stays in L2)."""
+    import numpy as np
+    import torch
+    import synth
+    host = synth.uniform_text(C1_BYTES, C1_SEED)
+    pat = synth.pattern(C1_M, C1_PSEED)
+    text = torch.from_numpy(host).to(dev)
+    table = dd.dfa_build(pat)
+    want = dd.count(text, table)
+    cap = max(16, want)
+    pos = torch.empty(cap, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = torch.empty(dd.dfa_find_workspace_bytes(C1_BYTES), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for _ in range(3):
+        dd.dfa_find(text, table, pos, cnt, ws, stream=stream)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i, (a, b) in enumerate(evs):
+            flush.fill_(i & 0xFF)
+            a.record(stream)
+            dd.dfa_find(text, table, pos, cnt, ws, stream=stream)
+            b.record(stream)
+    torch.cuda.synchronize()
+    rc, c = dd.dfa_find_status(ws, cnt, cap, stream=stream)
+    assert rc == dd.DFA_OK and c == want, (rc, c, want)
+    us = np.array([a.elapsed_time(b) * 1e3 for a, b in evs])
+    # graph: graph_reps finds back to back, one replay
+    g_stream = torch.cuda.Stream(dev)
+    g_stream.wait_stream(torch.cuda.current_stream(dev))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=g_stream):
+        for _ in range(graph_reps):
+            dd.dfa_find(text, table, pos, cnt, ws, stream=g_stream)
+    with torch.cuda.stream(g_stream):
+        g.replay()
+    g_stream.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(g_stream):
+        g0.record(g_stream)
+        g.replay()
+        g1.record(g_stream)
+    g_stream.synchronize()
+    graph_us = g0.elapsed_time(g1) * 1e3 / graph_reps
+    assert int(cnt.item()) == want
+    peak, kind = measured_peak_hbm()
+    med = float(np.median(us))
+    algo = C1_BYTES + 8 * want
+    del g, flush
+    torch.cuda.empty_cache()
+    return {"workload": "single pattern, plain method: 16 MiB uniform A/C/G/T (seed 0), m = 8 (seed 1),"
+                        " count + sorted int64 positions",
+            "count": want,
+            "flushed": {"reps": reps, "median_us": round(med, 2),
+                        "p10_us": round(float(np.percentile(us, 10)), 2),
+                        "p90_us": round(float(np.percentile(us, 90)), 2),
+                        "gbs": round(C1_BYTES / (med * 1e-6) / 1e9, 1),
+                        "l2": "512 MiB write (4x L2) before each find"},
+            "graph_back_to_back": {"finds": graph_reps, "us_per_find": round(graph_us, 2),
+                                   "gbs": round(C1_BYTES / (graph_us * 1e-6) / 1e9, 1),
+                                   "l2": "text resident in L2 across the finds"},
+            "roofline": {"bound": "hbm", "achieved": round(algo / (med * 1e-6) / 1e9, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(algo / (med * 1e-6) / 1e9 / peak, 4),
+                         "traffic": None, "peak_kind": f"{kind} (hbm_gbs copy bandwidth)",
+                         "note": "16 MiB is a few microseconds of HBM time: launch latency bounds it"},
+            "launches_per_find": 3}
 
 
 def main():

@@ -29,6 +29,11 @@
  *     enqueued.
  *   - Alignment: a text pointer that is 16-byte aligned gets the vectorised
  *     path; any other pointer is accepted and scanned with byte loads.
+ *   - Device reset: tables and the per-device settings the library caches
+ *     (kernel attributes, workspace addresses) belong to the CUDA context in
+ *     which they were made.  cudaDeviceReset destroys them; build tables
+ *     again afterwards, and expect the first launches to redo their set-up
+ *     only where the library can see the change of context.
  */
 #ifndef DNADFA_H
 #define DNADFA_H
@@ -269,7 +274,10 @@ int dfa_find_host_multi(const uint8_t* h_text, int64_t n, const dfa_table* const
  *
  * First call on each device: it resolves the array's address on the current
  * device (cudaGetSymbolAddress), which may load the library's device code.
- * Make that first call before any stream capture begins.
+ * Make that first call before any stream capture begins.  The address belongs
+ * to the context that was current then; a later call that finds a different
+ * context current resolves it again.  After cudaDeviceReset the library's
+ * tables and per-device state are invalid (see the conventions above).
  *
  * Every call on a device shares the one array, which keeps the previous
  * call's contents; each call clears the part it uses at its start, on

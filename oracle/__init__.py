@@ -15,6 +15,10 @@ module only marshals numpy arrays.  Functions:
 * ``alg1_scan(text, delta, m, p, v)`` — Algorithm 1's decomposition (Sec. III-A).
 * ``stt_ascii(strings, finals)`` — sparse 256-column STT (Sec. III-B, Table I).
 * ``kmer_census(text, k)`` and ``valid_windows(text, k)``.
+* ``find_set(text, patterns)`` and ``count_set(texts, patterns)`` — the
+  definition for a set of patterns: each window start compared with every
+  pattern, the comparisons of patterns sharing a prefix done once (a trie
+  descent per start; no failure links), threaded over contiguous ranges.
 * ``class_sets(pattern)``, ``class_expansions(pattern)`` and
   ``find_class_brute(text, pattern)`` — character-class patterns (the class
   cells of Table III, Sec. IV) by their definition, in numpy.
@@ -76,6 +80,8 @@ def _load():
         lib.oracle_kmer_census.restype = ctypes.c_int
         lib.oracle_valid_windows.argtypes = [u8p, i64, i32]
         lib.oracle_valid_windows.restype = i64
+        lib.oracle_find_set.argtypes = [u8p, i64, u8p, i32p, i32, u64p, i64p, i64p, i32]
+        lib.oracle_find_set.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -239,6 +245,47 @@ def multi_count(texts, patterns, threads: int | None = None) -> np.ndarray:
         for (i, j), c in zip(jobs, ex.map(lambda ij: count_brute(ts[ij[0]], patterns[ij[1]]), jobs)):
             out[i, j] = c
     return out
+
+
+def _pattern_block(patterns):
+    ps = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
+    if not ps:
+        raise OracleError("no patterns")
+    buf = np.frombuffer(b"".join(ps), dtype=np.uint8).copy()
+    lens = np.array([len(p) for p in ps], dtype=np.int32)
+    return buf, lens
+
+
+def find_set(text, patterns, positions: bool = True, threads: int | None = None):
+    """(uint64 counts[len(patterns)], list of sorted int64 position arrays or
+    None) of every pattern of a set in one text, by the definition (every
+    window start compared with every pattern; Sec. II-A)."""
+    t = _bytes(text)
+    buf, lens = _pattern_block(patterns)
+    lib = _load()
+    nt = int(threads or num_threads())
+    counts = np.zeros(lens.size, dtype=np.uint64)
+    if lib.oracle_find_set(_p(t, ctypes.c_uint8), int(t.size), _p(buf, ctypes.c_uint8),
+                           _p(lens, ctypes.c_int32), int(lens.size), _p(counts, ctypes.c_uint64),
+                           None, None, nt) != 0:
+        raise OracleError("invalid pattern")
+    if not positions:
+        return counts, None
+    off = np.zeros(lens.size, dtype=np.int64)
+    off[1:] = np.cumsum(counts.astype(np.int64))[:-1]
+    pos = np.empty(max(int(counts.sum()), 1), dtype=np.int64)
+    again = np.zeros_like(counts)
+    if lib.oracle_find_set(_p(t, ctypes.c_uint8), int(t.size), _p(buf, ctypes.c_uint8),
+                           _p(lens, ctypes.c_int32), int(lens.size), _p(again, ctypes.c_uint64),
+                           _p(pos, ctypes.c_int64), _p(off, ctypes.c_int64), nt) != 0:
+        raise OracleError("invalid pattern")
+    return counts, [pos[o:o + int(c)].copy() for o, c in zip(off, counts)]
+
+
+def count_set(texts, patterns, threads: int | None = None) -> np.ndarray:
+    """uint64[len(texts), len(patterns)]: find_set's counts of every pattern
+    in every text."""
+    return np.stack([find_set(t, patterns, positions=False, threads=threads)[0] for t in texts])
 
 
 # ------------------------------------------------------------ class patterns

@@ -26,6 +26,10 @@
  *                       Sec. III-B (Table I layout) of the failure-less
  *                       automaton (Fig. 4) of a set of strings, finals
  *                       numbered last.
+ *   oracle_find_set     the definition for a set of patterns: every window
+ *                       start compared with all patterns at once, patterns
+ *                       that share a prefix sharing those comparisons (a
+ *                       trie descent from each start, no failure links).
  *   oracle_kmer_census  count of every k-mer by definition.
  *   oracle_valid_windows number of windows of k bytes all in ACGTacgt,
  *                       computed from the lengths of the valid runs.
@@ -112,6 +116,131 @@ int64_t oracle_find_brute(const uint8_t* text, int64_t n, const uint8_t* pattern
     }
     free(P);
     return count;
+}
+
+/* ------------------------------------------------------------------ */
+/* The definition for a set of patterns.                               */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Every occurrence of every pattern of a set (Sec. II-A problem statement,
+ * applied to each pattern; overlaps included): pattern p occurs at i iff
+ * T[i..i+m_p) = P_p.  For each window start i the patterns are compared
+ * together, character by character, by descending a trie of the patterns
+ * (node = a distinct prefix, child[node][base]): the descent stops at the
+ * first byte that is not a base or that no pattern continues with, and every
+ * pattern that ends on a node passed counts one occurrence at i.  This is
+ * the window compare of oracle_find_brute with the comparisons of patterns
+ * that share a prefix done once; it is not the Aho-Corasick automaton (no
+ * failure links: each window is compared from its first byte).
+ *
+ * Inputs: npat patterns concatenated in pats, lengths in lens (1..255 bytes
+ * of ACGTacgt each; duplicates allowed and counted separately).
+ * Outputs: counts[p] = occurrences of pattern p.  With pos non-NULL, pattern
+ * p's start positions, ascending, go to pos[pos_off[p] ...] (the caller
+ * sizes pos and pos_off from the counts of an earlier call).  nthreads > 1
+ * splits the window starts into contiguous ranges over OpenMP threads.
+ * Returns 0, or -1 for invalid arguments.
+ */
+typedef struct {
+    int32_t child[4];
+    int32_t first_end;      /* head of the list of patterns ending here, -1 */
+} trie_node;
+
+int oracle_find_set(const uint8_t* text, int64_t n, const uint8_t* pats, const int32_t* lens, int32_t npat,
+                    uint64_t* counts, int64_t* pos, const int64_t* pos_off, int32_t nthreads)
+{
+    if (n < 0 || (n > 0 && !text) || !pats || !lens || npat < 1 || !counts) return -1;
+    if (pos && !pos_off) return -1;
+    int64_t total = 0;
+    for (int32_t p = 0; p < npat; p++) {
+        if (lens[p] < 1 || lens[p] > 255) return -1;
+        total += lens[p];
+    }
+    trie_node* node = (trie_node*)malloc(sizeof(trie_node) * (size_t)(total + 1));
+    int32_t* next_end = (int32_t*)malloc(sizeof(int32_t) * (size_t)npat);   /* list links */
+    if (!node || !next_end) {
+        free(node);
+        free(next_end);
+        return -1;
+    }
+    int32_t nodes = 1;
+    for (int b = 0; b < 4; b++) node[0].child[b] = -1;
+    node[0].first_end = -1;
+    const uint8_t* q = pats;
+    for (int32_t p = 0; p < npat; p++) {
+        int32_t v = 0;
+        for (int32_t j = 0; j < lens[p]; j++) {
+            const int b = base_index(q[j]);
+            if (b < 0) {
+                free(node);
+                free(next_end);
+                return -1;
+            }
+            if (node[v].child[b] < 0) {
+                for (int c = 0; c < 4; c++) node[nodes].child[c] = -1;
+                node[nodes].first_end = -1;
+                node[v].child[b] = nodes++;
+            }
+            v = node[v].child[b];
+        }
+        next_end[p] = node[v].first_end;
+        node[v].first_end = p;
+        q += lens[p];
+    }
+    const int T = nthreads > 0 ? nthreads : 1;
+    /* per range r of window starts: its occurrence count of each pattern */
+    uint64_t* part = (uint64_t*)calloc((size_t)T * (size_t)npat, sizeof(uint64_t));
+    if (!part) {
+        free(node);
+        free(next_end);
+        return -1;
+    }
+    for (int pass = 0; pass < (pos ? 2 : 1); pass++) {
+        if (pass == 1) {
+            /* exclusive offsets: pattern p's positions from range r start at
+             * pos_off[p] + (occurrences of p in ranges before r) */
+            for (int32_t p = 0; p < npat; p++) {
+                uint64_t run = 0;
+                for (int r = 0; r < T; r++) {
+                    const uint64_t c = part[(size_t)r * npat + p];
+                    part[(size_t)r * npat + p] = run;
+                    run += c;
+                }
+            }
+        }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static, 1) num_threads(T)
+#endif
+        for (int r = 0; r < T; r++) {
+            const int64_t lo = n * r / T, hi = n * (r + 1) / T;
+            uint64_t* mine = part + (size_t)r * npat;
+            for (int64_t i = lo; i < hi; i++) {
+                int32_t v = 0;
+                for (int64_t j = i; j < n; j++) {
+                    const int b = base_index(text[j]);
+                    if (b < 0) break;
+                    v = node[v].child[b];
+                    if (v < 0) break;
+                    for (int32_t p = node[v].first_end; p >= 0; p = next_end[p]) {
+                        if (pass == 1) pos[pos_off[p] + (int64_t)mine[p]] = i;
+                        mine[p]++;
+                    }
+                }
+            }
+        }
+        if (pass == 0) {
+            for (int32_t p = 0; p < npat; p++) {
+                uint64_t c = 0;
+                for (int r = 0; r < T; r++) c += part[(size_t)r * npat + p];
+                counts[p] = c;
+            }
+        }
+    }
+    free(part);
+    free(node);
+    free(next_end);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */

@@ -2806,10 +2806,31 @@ static __device__ __align__(256) unsigned long long g_noalloc_work[kWorkHeader +
 namespace {
 
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoAllocMaxDevices];   // device address of g_noalloc_work, per device
+void* g_noalloc_addr[kNoAllocMaxDevices];      // device address of g_noalloc_work, per device
+CUcontext g_noalloc_ctx[kNoAllocMaxDevices];   // the context that address belongs to
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+// cuCtxGetCurrent from the driver (the library links the runtime only).
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    }
+    return fn;
+}
 
 // Set-up, once per device, with that device current: resolve the address of
-// g_noalloc_work on it.
+// g_noalloc_work on it.  The address belongs to the device's current context;
+// when a call finds another context current (a different handle after a
+// device reset, or a context the caller made current), set-up runs again.
 int noalloc_workspace(int dev, void** out)
 {
     if (dev < 0 || dev >= kNoAllocMaxDevices) {
@@ -2819,11 +2840,15 @@ int noalloc_workspace(int dev, void** out)
         return DFA_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    CUcontext ctx = nullptr;
+    if (CtxGetCurrentFn get = ctx_get_current()) get(&ctx);
+    if (!g_noalloc_addr[dev] || g_noalloc_ctx[dev] != ctx) {
         void* p = nullptr;
         cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_work);
         if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(g_noalloc_work)");
         g_noalloc_addr[dev] = p;
+        if (ctx == nullptr && ctx_get_current()) ctx_get_current()(&ctx);   // made by the call above
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = g_noalloc_addr[dev];
     return DFA_OK;

@@ -7,9 +7,9 @@ launch for many).
   position against the oracle's window compare, which finishes in seconds
   per pattern at this size.
 * Batched: the six sequences (0.2 .. 3.2 GB, seeds 10..15) x 256 patterns of
-  length uniform in [4, 64] (seed 16) in one graph-captured launch; one
-  (sequence, pattern) pair per sequence, plus every pattern on the smallest
-  sequence, checked one by one against the oracle.
+  length uniform in [4, 64] (seed 16) in one graph-captured launch; every
+  one of the 1536 (sequence, pattern) counts against the oracle's set
+  compare (each window start compared with all 256 patterns).
 * 6-mer census: 1e9 bytes (seed 20), all 4096 6-mers in one batched launch,
   against the oracle's census and the invariant sum = valid windows.
 """
@@ -59,7 +59,7 @@ def test_genome_scale_single_pattern_all_positions(gpu):
     torch.cuda.empty_cache()
 
 
-def test_batched_six_sequences_sampled(gpu):
+def test_batched_six_sequences_every_pair(gpu):
     import torch
     lens = synth.uniform_ints(256, 61, 16) + 4
     pats = [synth.pattern(int(m), 16 * 100_000 + i) for i, m in enumerate(lens)]
@@ -71,18 +71,15 @@ def test_batched_six_sequences_sampled(gpu):
     b = gpu.BatchedCount(devs, pats, cfg="auto")
     b.run()
     got = b.result()
-    # the smallest sequence: every pattern
-    want0 = oracle.multi_count([texts[0]], pats)[0]
-    assert np.array_equal(got[0], want0)
-    # one pair per sequence, the shortest patterns first (non-zero counts)
-    order = np.argsort(lens, kind="stable")
-    for i in range(1, len(texts)):
-        j = int(order[i])
-        assert int(got[i, j]) == oracle.count_brute(texts[i], pats[j]), (i, j)
-    assert (got[:, order[:6]] > 0).all()
     b.close()
     del devs
     torch.cuda.empty_cache()
+    # all 6 x 256 counts, bit for bit
+    want = oracle.count_set(texts, pats)
+    assert got.shape == want.shape == (len(BATCH_SIZES), len(pats))
+    bad = np.argwhere(got != want)
+    assert bad.size == 0, [(int(i), int(j), int(got[i, j]), int(want[i, j])) for i, j in bad[:10]]
+    assert (want.sum(axis=1) > 0).all()
 
 
 def test_kmer_census_1GB(gpu):
@@ -97,12 +94,12 @@ def test_kmer_census_1GB(gpu):
     assert int(got.sum()) == oracle.valid_windows(text, 6)
 
 
-def test_serving_full_size_sampled(gpu):
-    # the serving workload's six resident sequences (11.9e9 bytes): a short
-    # Poisson trace of count and positions queries, one per sequence and two
-    # more, each answer checked against the oracle
+def test_serving_full_size_300_queries(gpu):
+    # the serving workload's six resident sequences (11.9e9 bytes): a Poisson
+    # trace of 300 count and positions queries (1-8 patterns of length
+    # 7..40 each), every answer checked against the oracle's set compare
+    # (all patterns asked of one sequence in one pass over it)
     import torch
-    from concurrent.futures import ThreadPoolExecutor
 
     from paper_1506_08612_gb300.serve import GpuEngine, Server
     texts, devs = [], []
@@ -110,25 +107,24 @@ def test_serving_full_size_sampled(gpu):
         t = synth.genome_text(n, 10 + i)
         texts.append(t)
         devs.append(_dev(t))
-    trace = synth.query_trace(8, 200.0, len(texts), 31, max_patterns=5, m_lo=7, m_hi=40)
+    trace = synth.query_trace(300, 200.0, len(texts), 31, max_patterns=8, m_lo=7, m_hi=40)
     for i, e in enumerate(trace[:6]):
         e["seq"] = i
     srv = Server(GpuEngine(devs, slots=4, arena_bytes=2 << 30))
     qs = srv.replay(trace)
-    jobs = [(q, j) for q in qs for j in range(len(q.patterns))]
-
-    def want(qj):
-        q, j = qj
-        if q.mode == "positions":
-            return oracle.find_brute(texts[q.seq], q.patterns[j])
-        return oracle.count_brute(texts[q.seq], q.patterns[j]), None
-
-    with ThreadPoolExecutor(16) as ex:
-        wants = list(ex.map(want, jobs))
-    for (q, j), (wc, wp) in zip(jobs, wants):
-        assert q.error is None, q.error
-        assert int(q.counts[j]) == wc, (q.qid, j)
-        if q.mode == "positions":
-            assert np.array_equal(q.positions[j], wp), (q.qid, j)
     del devs, srv
     torch.cuda.empty_cache()
+    assert len(qs) == 300
+    for sq in range(len(texts)):
+        mine = [q for q in qs if q.seq == sq]
+        pats = sorted({p for q in mine for p in q.patterns})
+        if not pats:
+            continue
+        wc, wp = oracle.find_set(texts[sq], pats)
+        idx = {p: k for k, p in enumerate(pats)}
+        for q in mine:
+            assert q.error is None, q.error
+            for j, p in enumerate(q.patterns):
+                assert int(q.counts[j]) == int(wc[idx[p]]), (q.qid, j)
+                if q.mode == "positions":
+                    assert np.array_equal(q.positions[j], wp[idx[p]]), (q.qid, j)

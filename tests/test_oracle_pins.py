@@ -415,6 +415,69 @@ def test_multi_count_equals_census_and_definition():
 
 
 # --------------------------------------------------------------------------
+# the definition for a set of patterns (trie descent per window start)
+# --------------------------------------------------------------------------
+
+SET_PATS = [b"A", b"C", b"AA", b"AC", b"CA", b"AAA", b"ACA", b"TGT", b"AC", b"ACAT"]
+
+
+def test_find_set_exhaustive_tiny_texts_vs_regex():
+    # every text of length <= 6 over {A,C,G,T,N,a}: each pattern of a set with
+    # shared prefixes, nested patterns and a duplicate, against the regex
+    # engine's overlapping look-ahead (a library routine)
+    alphabet = b"ACGTNa"
+    for L in range(0, 7):
+        for tup in itertools.product(alphabet, repeat=L):
+            t = bytes(tup)
+            c, pos = oracle.find_set(t, SET_PATS, threads=1)
+            for pat, cc, pp in zip(SET_PATS, c, pos):
+                r = _regex_find(t, pat)
+                assert int(cc) == len(r) and list(pp) == r, (t, pat)
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_find_set_random_texts_vs_regex(threads):
+    for seed in range(6):
+        t = synth.random_text(4000, 300 + seed, b"ACGTacgtNn\n")
+        pats = [synth.pattern(m, 2000 + seed * 17 + m) for m in range(1, 13)]
+        pats += [pats[3][:2], pats[5], pats[7].lower()]       # a prefix, a duplicate, lower case
+        c, pos = oracle.find_set(t, pats, threads=threads)
+        for pat, cc, pp in zip(pats, c, pos):
+            r = _regex_find(t.tobytes(), pat)
+            assert int(cc) == len(r) and list(pp) == r, (seed, pat)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_find_set_de_bruijn_all_kmers_once(k):
+    # B(4, k) holds every k-mer exactly once, at a position fixed by the
+    # sequence; lower case matches too
+    seq = _de_bruijn(k)
+    pats = ["".join(x) for x in itertools.product("ACGT", repeat=k)]
+    for text in (seq, seq.lower()):
+        c, pos = oracle.find_set(text, pats, threads=4)
+        assert (c == 1).all()
+        assert [int(p[0]) for p in pos] == [text.upper().find(q.encode()) for q in pats]
+
+
+def test_find_set_sum_is_valid_windows_and_homopolymer():
+    # over all 4^k k-mers the counts add up to the windows of k bases
+    # (computed from run lengths), and A, AA, ..., A^j on A^n give n - j + 1
+    t = synth.genome_text(80_000, 9, mask_mean=30, n_gap_mean=3000, n_run_mean=100)
+    for k in (2, 4):
+        pats = ["".join(x) for x in itertools.product("ACGT", repeat=k)]
+        c, _ = oracle.find_set(t, pats, positions=False, threads=5)
+        assert int(c.sum()) == oracle.valid_windows(t, k)
+    n = 40
+    hp = b"A" * n
+    c, pos = oracle.find_set(hp, [b"A" * j for j in range(1, 12)], threads=3)
+    assert [int(x) for x in c] == [n - j + 1 for j in range(1, 12)]
+    assert all(list(p) == list(range(n - j + 1)) for j, p in zip(range(1, 12), pos))
+    assert oracle.find_set(b"", [b"A"])[0].tolist() == [0]
+    with pytest.raises(oracle.OracleError):
+        oracle.find_set(b"ACGT", [b"ACNT"])
+
+
+# --------------------------------------------------------------------------
 # character-class patterns (the class cells of Table III, Sec. IV)
 # --------------------------------------------------------------------------
 

@@ -5,7 +5,11 @@ process whose memory a framework's pool already holds, a latency-bound
 stream on which cudaMalloc/cudaFree would synchronise the device, a plug-in
 handed only its buffers).  Every call shares one workspace array that keeps
 the previous call's contents, so the checks run two calls in a row and
-compare each with dfa_find on a caller-owned workspace, bit for bit.
+compare each, bit for bit, with the oracle's window compare and with
+dfa_find on a caller-owned workspace.  The static array holds tile
+descriptors only, so this entry point always takes the single-pass ordered
+find; one case plants occurrences across every 64-byte border (every stage,
+row and tile border) of a pattern long enough for the relaxed walk.
 
 The file name makes pytest collect it last; it passes both alone in a fresh
 process and after the other tests.
@@ -13,6 +17,7 @@ process and after the other tests.
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -59,17 +64,19 @@ def _text(gpu, n, seed, pat):
     t = synth.genome_text(n, seed)
     pos = np.unique(synth.uniform_ints(2_000, n - len(pat), seed + 1000) // len(pat) * len(pat))
     synth.plant(t, pat, pos)
-    return torch.from_numpy(t).cuda()
+    return t, torch.from_numpy(t).cuda()
 
 
-def test_matches_dfa_find_on_consecutive_calls(gpu):
+def test_matches_oracle_and_dfa_find_on_consecutive_calls(gpu):
     for n, seed, m, pseed, cfg in CASES:
         pat = synth.pattern(m, pseed)
-        td = _text(gpu, n, seed, pat)
+        host, td = _text(gpu, n, seed, pat)
         table = gpu.dfa_build(pat)
-        want_c, want_p = _with_workspace(gpu, td, table, 1 << 20, cfg)
-        got_c, got_p = _without_workspace(gpu, td, table, 1 << 20, cfg)
+        want_c, want_p = oracle.find_brute(host, pat)
+        ws_c, ws_p = _with_workspace(gpu, td, table, 1 << 20, cfg)
         assert want_c > 0
+        assert ws_c == want_c and np.array_equal(ws_p, want_p), (n, m, cfg)
+        got_c, got_p = _without_workspace(gpu, td, table, 1 << 20, cfg)
         assert got_c == want_c, (n, m, cfg)
         assert np.array_equal(got_p, want_p), (n, m, cfg)
         # the same input again right after: identical result
@@ -77,12 +84,34 @@ def test_matches_dfa_find_on_consecutive_calls(gpu):
         assert again_c == want_c and np.array_equal(again_p, want_p)
 
 
+def test_occurrences_across_every_64_byte_border(gpu):
+    # tiles, rows and TMA stages all start at multiples of 64 bytes: an
+    # occurrence of a 12-mer straddles every such border at a different
+    # depth d = 1 .. 11, plus one starting exactly on a border, in a text with
+    # N blocks and soft-masked runs; the default launch (relaxed walk)
+    import torch
+    m, n = 12, 3_000_017
+    pat = synth.pattern(m, 65)
+    host = synth.genome_text(n, 10)
+    starts = np.arange(64, n - 64, 64, dtype=np.int64)
+    depth = starts // 64 % m                               # 0 .. m - 1 bytes before the border
+    pos = starts - depth
+    synth.plant(host, pat, pos)
+    want_c, want_p = oracle.find_brute(host, pat)
+    assert set(pos.tolist()) <= set(want_p.tolist())
+    td = torch.from_numpy(host).cuda()
+    table = gpu.dfa_build(pat)
+    for _ in range(2):
+        got_c, got_p = _without_workspace(gpu, td, table, want_c + 16, None)
+        assert got_c == want_c and np.array_equal(got_p, want_p)
+
+
 def test_truncation_and_empty_text(gpu):
     import torch
     pat = synth.pattern(4, 71)
     table = gpu.dfa_build(pat)
-    td = _text(gpu, 5_000_000, 9, pat)
-    want_c, want_p = _with_workspace(gpu, td, table, 1 << 20, None)
+    host, td = _text(gpu, 5_000_000, 9, pat)
+    want_c, want_p = oracle.find_brute(host, pat)
     cap = want_c // 3
     pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
