@@ -48,10 +48,13 @@ TEXT_BYTES = 3_200_000_000
 TEXT_SEED = 2
 CLASS_PAIRS, CLASS_SEED = 9, 40          # class-pattern workload: 9 pairs = 18 patterns
 WORKLOAD = "genome-scale single-pattern scan"
-# one dfa_find per pattern: for m >= 8 the count pass k_scan_tma<4,count>
-# (relaxed walk) + k_tile_offsets + k_rewalk; for m < 8 the single-pass
-# k_scan_tma<1,find,dense>; the events time the whole call
-DOMINANT_KERNEL = "dfa_find = k_scan_tma (TMA-staged scan) + k_tile_offsets + k_rewalk"
+# one dfa_find per pattern, the staged two-pass find: the count pass
+# k_scan_tma (m >= 8: relaxed walk, exact replays of the flagged stages;
+# m < 8: relaxed walk with each accept's window tested) staging every row's
+# exact end offsets, k_tile_offsets (scan of the tile totals) and k_place
+# (copy of the staged offsets to the sorted positions); the events time the
+# whole call
+DOMINANT_KERNEL = "dfa_find = k_scan_tma (TMA-staged count pass) + k_tile_offsets + k_place"
 
 
 def parse():
@@ -78,6 +81,10 @@ def parse():
                          "serving) reported under 'workloads'")
     ap.add_argument("--serve-queries", type=int, default=600,
                     help="genome: queries of the serving trace reported under 'workloads'")
+    ap.add_argument("--shard", action="store_true",
+                    help="genome: split ONE text over the ranks (owned starts + m-1 overlap), "
+                         "gather counts and positions over the process group (strong scaling); "
+                         "the default runs one replica per rank")
     return ap.parse_args()
 
 
@@ -89,13 +96,16 @@ def dist_env():
 
 
 def kernels_per_find(m, cfg):
-    """Kernels one dfa_find launches with the library defaults: the two-pass
-    find of the relaxed-walk layout (count pass, tile scan, re-walk) from
-    m = 8 on, the single-pass find kernel below (the workspace bench.py
-    passes always has room for the two-pass form)."""
+    """Kernels one dfa_find launches on the TMA path: the staged two-pass
+    find (count pass, tile scan, placement) for the relaxed layouts at any m
+    and for layout 1 up to m = 8 (the library's defaults: layout 1 below
+    m = 8, layout 4 from there; the workspace bench.py passes always has
+    room for it), else the single-pass find kernel."""
     layout = (cfg or {}).get("layout", 0)
-    relaxed = layout in (3, 4) or (layout == 0 and m >= 8)
-    return 3 if relaxed else 1
+    if layout == 0:
+        layout = 4 if m >= 8 else 1
+    staged = layout in (3, 4) or (layout == 1 and m <= 8)
+    return 3 if staged else 1
 
 
 def config_dict(n, world, cfg):
@@ -848,10 +858,104 @@ def measure_small(dd, dev, stream, reps=20, graph_reps=200):
             "launches_per_find": 3}
 
 
+def run_shard(args):
+    """One genome split over the ranks, Algorithm 1's chunking one level up:
+    rank r finds the occurrences that start in its shard (4 KiB-aligned
+    slices, so each keeps the TMA path), reading m - 1 bytes past it; per
+    pattern the counts and positions are gathered over the process group
+    (NCCL: device tensors, no host copy) and merged in rank order.  A step is
+    the five finds plus their exchanges; ``value`` is the whole text x
+    patterns over the slowest rank's time.  Rank 0 checks the merged counts
+    against one whole-text count on its GPU and the positions' order."""
+    import numpy as np
+    import torch
+
+    import paper_1506_08612_gb300 as dd
+    import synth
+    from paper_1506_08612_gb300 import shard
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    align = 4096
+    host = synth.genome_text(n, TEXT_SEED)               # every rank: the same text
+    patterns = [synth.pattern(m, sd) for m, sd in zip(PATTERN_LENGTHS, PATTERN_SEEDS)]
+    tables = [dd.dfa_build(p) for p in patterns]
+    s, e = shard.shard_range(n, world, rank, align)
+    rs, re = shard.read_range(n, world, rank, max(PATTERN_LENGTHS), align)
+    text = torch.from_numpy(np.ascontiguousarray(host[rs:re])).to(dev)
+    # pattern i reads [s, min(e + m_i - 1, n)): every occurrence found starts in [s, e)
+    lens = [min(e + len(p) - 1, n) - s if e > s else 0 for p in patterns]
+    local_counts = [dd.count(text[:k], t) if k else 0 for k, t in zip(lens, tables)]
+    caps = [max(16, c) for c in local_counts]
+    pos = [torch.empty(c, dtype=torch.int64, device=dev) for c in caps]
+    cnt = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in tables]
+    ws = torch.empty(dd.dfa_find_workspace_bytes(max(max(lens), 1)), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        out = []
+        for i, t in enumerate(tables):
+            if lens[i]:
+                dd.dfa_find(text, t, pos[i], cnt[i], ws, stream=stream, n=lens[i])
+        for i in range(len(tables)):
+            c = local_counts[i]
+            mine = pos[i][:c] + s
+            if world > 1:
+                out.append(shard.gather_find(c, mine))
+            else:
+                out.append((c, mine))
+        return out
+
+    for _ in range(max(args.warmup, 0)):
+        merged = step()
+    torch.cuda.synchronize()
+    if rank == 0:
+        whole = torch.from_numpy(host).to(dev)
+        want = [dd.count(whole, t) for t in tables]
+        del whole
+        torch.cuda.empty_cache()
+        for (c, p), w in zip(merged, want):
+            assert c == w, (c, w)
+            if c > 1:
+                assert bool((p[1:] > p[:-1]).all())
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([dt], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        dt = float(tt.item())
+    value = n * len(tables) * args.steps / dt / 1e9
+    if rank == 0:
+        cfgd = config_dict(n, world, None)
+        cfgd["parallelism"] = f"shard x{world} (4 KiB-aligned shards, m-1 overlap, all-gather of counts + positions)"
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 4),
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic", "config": cfgd, "e2e": None,
+                "gpu_launches": args.steps * sum(kernels_per_find(m, None) for m in PATTERN_LENGTHS),
+                "counts": [int(c) for c, _ in merged], "shard_bytes": [s, e]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard:
+        run_shard(args)
     elif args.workload in ("batched", "census", "classes"):
         run_batched(args)
     elif args.workload == "serve":

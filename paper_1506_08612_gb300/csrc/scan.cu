@@ -821,9 +821,11 @@ struct TmaArgs {
     // every tile's total (added up) go here; null otherwise
     uint16_t* rows;
     unsigned long long* tile_sum;
-    // and, for every row with a count, the stages holding its exact accepts
-    // (bit s: body stage s; bit sps: the overlap; all ones: walk the row)
-    unsigned long long* masks;
+    // and the rows' exact accept end offsets (u16, relative to the row
+    // start): each walker warp of tile t writes those of its 32 rows, at most
+    // KS a row, packed in row order into its own region of 32 * KS entries
+    // at stage + (t * kWalkWarps + warp) * 32 * KS
+    uint16_t* stage;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -1038,6 +1040,58 @@ __device__ __forceinline__ uint4 redo_stage_exact(const SmemTab& T, uint32_t slo
     return make_uint4(w.cnt, ss.n, w.e, 0u);
 }
 
+// The exact accepts of a stage walked through codes alone, for patterns of
+// m <= 8.  The relaxed walk is the automaton run on the text with every byte
+// replaced by the base of its 2-bit code, so it accepts at end j exactly when
+// the codes of the m bytes ending at j are those of P; the exact walk accepts
+// there exactly when, in addition, those m bytes are bases (each base is the
+// one byte, in either case, with its code).  So an exact accept is a relaxed
+// accept whose window holds no non-base, whatever came before the window.
+// map: bit j = a relaxed accept ending at stage offset j; the window of j
+// covers buffer bytes [j + 9 - m, j + 8] of the 8 bytes before the stage
+// (p0, p1) followed by the stage's 64 (its ring slot: 16-byte piece k at
+// q + (ob ^ (k << 4))).  Exact accepts go to the row's slots at end offset
+// r + j; returns their number.
+template <uint32_t CAP>
+__device__ __forceinline__ uint32_t window_accepts(uint2 map, uint32_t r, uint32_t m, uint32_t p0, uint32_t p1,
+                                                   const uint8_t* q, uint32_t ob, RowSlots<CAP>& ss)
+{
+    const uint32_t qa = smem_u32(q);
+    uint32_t c = 0;
+    uint64_t mp = ((uint64_t)map.y << 32) | map.x;
+    while (mp) {
+        const uint32_t j = (uint32_t)__ffsll((long long)mp) - 1u;
+        mp &= mp - 1ull;
+        const uint32_t J = j + 8u, S = J + 1u - m;          // window: buffer bytes [S, J]
+        uint32_t bad = 0u;
+#pragma unroll
+        for (uint32_t d = 0; d < 3; d++) {
+            const uint32_t k = (S >> 2) + d;                 // buffer word
+            if (4u * k > J) break;
+            uint32_t w;
+            if (k == 0u) {
+                w = p0;
+            } else if (k == 1u) {
+                w = p1;
+            } else {
+                const uint32_t sw = k - 2u;                  // stage word
+                asm volatile("ld.shared.u32 %0, [%1];"
+                             : "=r"(w)
+                             : "r"(qa + (ob ^ ((sw >> 2) << 4)) + ((sw & 3u) << 2)));
+            }
+            uint32_t keep = 0xFFFFFFFFu;                     // the word's bytes inside [S, J]
+            if (S > 4u * k) keep <<= 8u * (S - 4u * k);
+            if (J < 4u * k + 3u) keep &= 0xFFFFFFFFu >> (8u * (4u * k + 3u - J));
+            bad |= word_bad(w) & keep;
+        }
+        if (bad == 0u) {
+            ss.put(r + j);
+            c++;
+        }
+    }
+    return c;
+}
+
 template <int LAYOUT, class Sink>
 __device__ __noinline__ uint32_t walk_cold(const ScanArgs* a, int64_t s, int64_t e, Sink* sink)
 {
@@ -1225,11 +1279,17 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
     __shared__ unsigned long long s_sum[kWalkWarps];
     __shared__ int s_abort;
 
-    constexpr int KS = DENSE ? kTSlotsDense : kTSlots;
     // layouts 3 and 4: relaxed walk, exact replay of the rare flagged stages;
-    // dense patterns: exact walk recording every accept inline
-    constexpr bool OPT = !DENSE && (LAYOUT == kLayoutK4S || LAYOUT == kLayoutK4F);
-    constexpr bool INLINE_REC = DENSE;
+    // dense patterns: every accept recorded inline during the walk.
+    // STAGED (count mode with DENSE): pass 1 of the staged two-pass find,
+    // every exact accept recorded to the row's slots and, at the end of the
+    // tile, written out to the workspace (TmaArgs::stage)
+    constexpr bool STAGED = !FIND && DENSE;
+    constexpr bool OPT = LAYOUT == kLayoutK4S || LAYOUT == kLayoutK4F;
+    constexpr bool INLINE_REC = DENSE && !OPT;
+    constexpr int KS = INLINE_REC ? kTSlotsDense : kTSlots;
+    static_assert(!STAGED || kRPL == 1, "the staged pass writes one row per lane");
+    static_assert(!STAGED || LAYOUT != kLayoutStt, "the staged pass walks a four-step table");
     const ScanArgs& a = p.a;
     const int nst = p.nst;
     // [tables][position slots][rings], rings 1024-byte aligned for the TMA swizzle
@@ -1426,7 +1486,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
             fmask[i] = 0;
             tl0[i] = 0x41414141u;                 // no byte before the row start: bases
             tl1[i] = 0x41414141u;
-            ss[i] = RowSlots<KS>{slots_sa + (uint32_t)(((uint32_t)kb * KS * kRows + wrow0 + 32 * i) * 2), 0u};
+            ss[i] = RowSlots<KS>{slots_sa + (uint32_t)(((uint32_t)(FIND ? kb : 0) * KS * kRows + wrow0 + 32 * i) * 2), 0u};
         }
         for (uint32_t s = 0; s < spt; s++) {
             if (!warp_wait(&full[c_slot], c_par, abort_flag, p)) {
@@ -1455,7 +1515,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                         const uint32_t flag = relaxed_words<LAYOUT, 16>(relaxed_mask<LAYOUT>(m), e[i], x);
                         fmask[i] |= (uint64_t)(flag != 0u) << s;
                     }
-                } else if (FIND && INLINE_REC) {
+                } else if (INLINE_REC) {
 #pragma unroll
                     for (int i = 0; i < kRPL; i++) {
                         if (!ok[i]) continue;
@@ -1465,7 +1525,11 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                             tl0[i] = v[i][3].z;
                             tl1[i] = v[i][3].w;
                             const uint2 map = wd.vec4_relaxed_map(v[i][0], v[i][1], v[i][2], v[i][3]);
-                            if ((map.x | map.y) != 0u) {
+                            if (STAGED) {
+                                // each relaxed accept is exact iff its m bytes are bases
+                                if ((map.x | map.y) != 0u)
+                                    wd.cnt += window_accepts<KS>(map, r, m, p0, p1, rp + i * 32 * kStageW, ob, ss[i]);
+                            } else if ((map.x | map.y) != 0u) {
                                 // accepts: exact if the stage (read again from its
                                 // slot) and the 8 bytes before it are bases
                                 const uint8_t* q = rp + i * 32 * kStageW;
@@ -1577,7 +1641,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                             }
                         }
                         fmask[i] |= (uint64_t)(flag != 0u) << s;
-                    } else if (FIND && INLINE_REC) {
+                    } else if (INLINE_REC) {
                         // the relaxed walk's state is exact unless the last 8
                         // bytes hold a non-base (vec4_map_relaxed)
                         if (LAYOUT == kLayoutK4 && (word_bad(tl0[i]) | word_bad(tl1[i])) != 0u)
@@ -1631,18 +1695,16 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                 cnt[i] = 0;
             } else if (!ok[i]) {
                 ss[i].n = 0;
-                fmask[i] = ~0ull;                 // a row walked cold: a re-walk takes it whole
-                if (FIND)
+                if (FIND || STAGED)
                     cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &ss[i]);
                 else {
                     CountSink cs;
                     cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &cs);
                 }
             } else if (OPT && fmask[i] != 0ull) {
-                const uint4 rc = replay_row<LAYOUT, FIND>(&a, s0, sps, fmask[i], ss[i].base, ss[i].n);
+                const uint4 rc = replay_row<LAYOUT, FIND || STAGED>(&a, s0, sps, fmask[i], ss[i].base, ss[i].n);
                 cnt[i] += rc.x;
-                if (FIND) ss[i].n = rc.y;
-                fmask[i] = (uint64_t)rc.z | ((uint64_t)rc.w << 32);
+                if (FIND || STAGED) ss[i].n = rc.y;
             }
         }
         __syncwarp();
@@ -1657,8 +1719,27 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                 for (int i = 0; i < kRPL; i++) {
                     const int64_t row = (int64_t)tile * kRows + wrow0 + 32 * i;
                     p.rows[row] = (uint16_t)cnt[i];
-                    if (p.masks && cnt[i]) p.masks[row] = OPT ? fmask[i] : ~0ull;
                     ws += cnt[i];
+                }
+                if (STAGED) {
+                    // the row's recorded end offsets (at most KS; a row with
+                    // more is walked again by the third pass), packed in row
+                    // order into this warp's region of the tile
+                    const uint32_t stw = min(cnt[0], (uint32_t)KS);
+                    if (__any_sync(0xffffffffu, stw != 0u)) {
+                        uint32_t x = stw;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                            if (lane >= o) x += y;
+                        }
+                        uint16_t* region = p.stage + ((size_t)tile * kWalkWarps + warp) * (32 * KS) + (x - stw);
+                        for (uint32_t j = 0; j < stw; j++) {
+                            uint32_t v;
+                            asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(ss[0].base + j * (uint32_t)(kRows * 2)));
+                            region[j] = (uint16_t)v;
+                        }
+                    }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
@@ -1783,71 +1864,40 @@ __global__ void __launch_bounds__(1024)
     if (threadIdx.x == 0) *count = s_carry;
 }
 
-// Pass 3: a CTA per tile holding accepts; its rows with a non-zero count are
-// listed with their offsets, and each is walked again exactly by one warp.
-// The count pass left, per such row, the mask of the 64-byte stages holding
-// its exact accepts: every accept starts in [lo, hi), from 16 bytes at or
-// below m - 1 bytes before the first such stage to the end of the last one
-// (the overlap stage: the row's end), and every exact occurrence starting
-// there is one of them (its end lies in a masked stage).  Lane l takes the
-// l-th 16-byte-aligned slice of [lo, hi) plus the m-1 byte overlap
-// (Algorithm 1 within the row), counts, and after a warp scan walks its slice
-// once more writing the positions.  A mask of all ones takes the whole row.
-__device__ __noinline__ void rewalk_row(const ScanArgs* a, int64_t row, uint64_t mask, unsigned long long first,
-                                        int lane)
-{
-    const SmemTab T = tab_view<kLayoutK4>(*a);
-    const int64_t C = a->chunk;
-    const int64_t rs = row * C;
-    int64_t s = rs, e = min(rs + C, a->n_own);
-    if (mask != ~0ull) {
-        const int64_t lo_stage = __ffsll((long long)mask) - 1;
-        const int64_t hi_stage = 63 - __clzll((long long)mask);
-        s = max(rs, (rs + lo_stage * kStageW - (int64_t)(a->m - 1)) & ~(int64_t)15);
-        e = min(e, rs + (hi_stage + 1) * kStageW);
-    }
-    const int64_t span = ((e - s + 32 * 16 - 1) / (32 * 16)) * 16;   // 16-byte multiple
-    const int64_t sl = min(s + lane * span, e);
-    const int64_t el = min(sl + span, e);
-    CountSink cs;
-    const uint32_t c = sl < el ? walk_chunk<kLayoutK4>(*a, T, sl, el, cs) : 0u;
-    uint32_t x = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (c) {
-        GlobalSink gs{a->pos, a->cap, (int64_t)(first + x - c), a->pos_base + sl - (int64_t)(a->m - 1)};
-        walk_chunk<kLayoutK4>(*a, T, sl, el, gs);
-    }
-}
-
+// Pass 3: a CTA per tile holding accepts.  The count pass staged every
+// row's exact end offsets (up to KS a row) in its warp's region of the tile,
+// packed in row order; here each row learns its first index (the tile's
+// offset from pass 2 plus a scan of the tile's row counts) and its entries'
+// place in the region (a scan of min(count, KS) within its warp), and copies
+// them as start positions.  A row with more than KS accepts is walked again
+// exactly from global memory, writing its positions directly.
 __global__ void __launch_bounds__(kRows)
-    k_rewalk(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
-             const unsigned long long* masks)
+    k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
+            const uint16_t* stage, int ks)
 {
     __shared__ uint32_t s_warp[kRows / 32];
-    __shared__ uint32_t s_row[kRows];      // rows of the tile with accepts ...
-    __shared__ uint32_t s_first[kRows];    // ... and their first index within the tile
     load_tables<kLayoutK4>(a, g_smem);
     __syncthreads();
+    const SmemTab T = tab_view<kLayoutK4>(a);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long end_all = *a.count;
+    const int64_t C = a.chunk;
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         const unsigned long long off = tile_off[tile];
         const unsigned long long nxt = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
         if (nxt == off) continue;
         const uint32_t rc = rows[tile * kRows + threadIdx.x];
-        // warp scans of the counts (offsets) and of the non-zero flags (list slots)
-        uint32_t x = rc, f = rc ? 1u : 0u;
+        const uint32_t st = min(rc, (uint32_t)ks);
+        // warp scans: the row's count (its index in the tile) and its staged
+        // entries (their place in the warp's region)
+        uint32_t x = rc, y = st;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            const uint32_t z = __shfl_up_sync(0xffffffffu, f, o);
+            const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t v = __shfl_up_sync(0xffffffffu, y, o);
             if (lane >= o) {
-                x += y;
-                f += z;
+                x += u;
+                y += v;
             }
         }
         if (lane == 31) s_warp[warp] = x;
@@ -1855,24 +1905,22 @@ __global__ void __launch_bounds__(kRows)
         uint32_t before = 0;
         for (int w = 0; w < warp; w++) before += s_warp[w];
         __syncthreads();
-        if (lane == 31) s_warp[warp] = f;
-        __syncthreads();
-        uint32_t fbefore = 0, nz = 0;
-        for (int w = 0; w < kRows / 32; w++) {
-            if (w < warp) fbefore += s_warp[w];
-            nz += s_warp[w];
-        }
         if (rc) {
-            const uint32_t slot = fbefore + f - 1u;
-            s_row[slot] = threadIdx.x;
-            s_first[slot] = before + x - rc;
+            const int64_t row = tile * kRows + threadIdx.x;
+            const int64_t rs = row * C;
+            const int64_t start0 = a.pos_base + rs - (int64_t)(a.m - 1);
+            const int64_t g0 = (int64_t)(off + before + x - rc);
+            if (rc <= (uint32_t)ks) {
+                const uint16_t* src = stage + ((size_t)tile * kWalkWarps + warp) * (32 * (size_t)ks) + (y - st);
+                for (uint32_t j = 0; j < rc; j++) {
+                    const int64_t g = g0 + j;
+                    if (g < a.cap) a.pos[g] = start0 + src[j];
+                }
+            } else if (g0 < a.cap) {
+                GlobalSink gs{a.pos, a.cap, g0, start0};
+                walk_chunk<kLayoutK4>(a, T, rs, min(rs + C, a.n_own), gs);
+            }
         }
-        __syncthreads();
-        for (uint32_t j = (uint32_t)warp; j < nz; j += kRows / 32) {
-            const int64_t row = tile * kRows + s_row[j];
-            rewalk_row(&a, row, masks[row], off + s_first[j], lane);
-        }
-        __syncthreads();
     }
 }
 
@@ -2069,12 +2117,21 @@ bool tma_dense(int layout, int m)
     return m <= kDenseMaxM && (layout == kLayoutK4 || layout == kLayoutStt);
 }
 
-TmaKernelFn pick_tma(int layout, bool find, int m)
+// staged: pass 1 of the staged two-pass find (count mode recording every
+// exact accept; layouts 1, 3 and 4).
+TmaKernelFn pick_tma(int layout, bool find, int m, bool staged)
 {
     const bool dense = tma_dense(layout, m);
-    if (layout == kLayoutK4S) return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
-    if (layout == kLayoutK4F) return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
+    if (layout == kLayoutK4S) {
+        if (staged) return k_scan_tma<kLayoutK4S, false, true>;
+        return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
+    }
+    if (layout == kLayoutK4F) {
+        if (staged) return k_scan_tma<kLayoutK4F, false, true>;
+        return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
+    }
     if (layout == kLayoutK4) {
+        if (staged) return k_scan_tma<kLayoutK4, false, true>;
         if (!find) return k_scan_tma<kLayoutK4, false, false>;
         return dense ? k_scan_tma<kLayoutK4, true, true> : k_scan_tma<kLayoutK4, true, false>;
     }
@@ -2101,9 +2158,14 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
 }
 
 // Launch the TMA-staged kernel for the filled-in arguments `a`.
+// Entries a row stages in pass 1 of the staged two-pass find: the dense
+// inline walk of layout 1 records up to kTSlotsDense, the replays of the
+// relaxed layouts up to kTSlots.
+int staged_slots(int layout) { return layout == kLayoutK4 ? kTSlotsDense : kTSlots; }
+
 int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
                const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr,
-               unsigned long long* tile_sum = nullptr, unsigned long long* masks = nullptr)
+               unsigned long long* tile_sum = nullptr, uint16_t* stage = nullptr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
     int rc = tensor_map_encoder(&encode);
@@ -2120,7 +2182,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.fail_bit = find || rows ? 2ull : (1ull << 63);
     p.rows = rows;
     p.tile_sum = tile_sum;
-    p.masks = masks;
+    p.stage = stage;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
@@ -2130,11 +2192,13 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return fail("cuTensorMapEncodeTiled failed");
-    TmaKernelFn fn = pick_tma(r.layout, find, t->m);
+    const bool staged = !find && stage != nullptr;
+    TmaKernelFn fn = pick_tma(r.layout, find, t->m, staged);
     cudaFuncAttributes fa;
     CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)fn));
-    const int slot_bytes =
-        find ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2 : 0;
+    const int slot_bytes = find     ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2
+                           : staged ? staged_slots(r.layout) * kRows * 2
+                                    : 0;
     p.rings_off = (p.table_bytes + slot_bytes + 1023) & ~1023;
     const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.rings_off;
     int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
@@ -2212,34 +2276,41 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
 
 int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
 
-// Two-pass find: [header][one word per tile][one u16 per row of every tile]
-// [one u64 stage mask per row of every tile].
-int64_t work_bytes_two_pass(int64_t ntiles) { return work_bytes_for(ntiles) + ntiles * kRows * (2 + 8); }
+// Staged two-pass find: [header][one word per tile][one u16 count per row of
+// every tile][ks u16 end offsets per row of every tile, 16-byte aligned].
+int64_t staged_rows_off(int64_t ntiles) { return work_bytes_for(ntiles); }
+int64_t staged_stage_off(int64_t ntiles) { return (staged_rows_off(ntiles) + ntiles * kRows * 2 + 15) & ~(int64_t)15; }
+int64_t work_bytes_two_pass(int64_t ntiles, int ks) { return staged_stage_off(ntiles) + ntiles * kRows * ks * 2; }
 
-bool two_pass_layout(const Resolved& r)
+// The staged two-pass find serves the TMA kernel's four-step layouts: the
+// relaxed ones (3, 4) at any m, layout 1 for m <= 8 (its accepts are tested
+// against their m-byte windows, which the 8 bytes kept before each stage
+// cover).
+bool two_pass_layout(const Resolved& r, int m)
 {
-    return r.loader == 2 && (r.layout == kLayoutK4F || r.layout == kLayoutK4S);
+    return r.loader == 2 && (r.layout == kLayoutK4F || r.layout == kLayoutK4S || (r.layout == kLayoutK4 && m <= 8));
 }
 
-// Passes 1-3 of the two-pass find (see k_tile_offsets); the header and tile
-// words of the workspace are already zero.
+// Passes 1-3 of the staged two-pass find (see k_tile_offsets, k_place); the
+// header and tile words of the workspace are already zero.
 int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, int dev, const DeviceInfo* di,
                     cudaStream_t st)
 {
     unsigned long long* tile_sum = a.work + kWorkHeader;
-    uint16_t* rows = reinterpret_cast<uint16_t*>(tile_sum + a.ntiles);
-    unsigned long long* masks = reinterpret_cast<unsigned long long*>(rows + a.ntiles * kRows);
+    uint8_t* wb = reinterpret_cast<uint8_t*>(a.work);
+    uint16_t* rows = reinterpret_cast<uint16_t*>(wb + staged_rows_off(a.ntiles));
+    uint16_t* stage = reinterpret_cast<uint16_t*>(wb + staged_stage_off(a.ntiles));
     ScanArgs a1 = a;
     a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
-    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, tile_sum, masks);
+    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, tile_sum, stage);
     if (rc) return rc;
     k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
     CUDA_TRY(cudaGetLastError());
     const int smem = table_smem(t, kLayoutK4);
-    int occ = occupancy((const void*)k_rewalk, kRows, smem, dev, di->smem_optin);
-    if (occ <= 0) return fail("re-walk kernel does not fit on an SM (occupancy 0)");
+    int occ = occupancy((const void*)k_place, kRows, smem, dev, di->smem_optin);
+    if (occ <= 0) return fail("placement kernel does not fit on an SM (occupancy 0)");
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
-    k_rewalk<<<(unsigned)grid, kRows, smem, st>>>(a, rows, tile_sum, masks);
+    k_place<<<(unsigned)grid, kRows, smem, st>>>(a, rows, tile_sum, stage, staged_slots(r.layout));
     CUDA_TRY(cudaGetLastError());
     return DFA_OK;
 }
@@ -2275,7 +2346,7 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     a.pos_base = pos_base;
     a.base_in = reinterpret_cast<const unsigned long long*>(d_base);
     a.work = static_cast<unsigned long long*>(d_work);
-    if (two_pass_layout(r) && work_bytes >= work_bytes_two_pass(a.ntiles))
+    if (two_pass_layout(r, t->m) && work_bytes >= work_bytes_two_pass(a.ntiles, staged_slots(r.layout)))
         return launch_two_pass(r, a, t, dev, di, st);
     if (r.loader == 2) return launch_tma(r, a, t, true, dev, di, st);
     KernelFn fn = pick_find(r.layout, r.threads);
@@ -2473,14 +2544,15 @@ int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg)
         (void)cudaGetLastError();
         sms = 152;
     }
-    // the default rows depend on m (shorter from kShortRelaxedM on): size
-    // for every pattern length that takes the two-pass find
+    // the default layout and rows depend on m (layout 1 below kOptMinM,
+    // shorter relaxed rows from kShortRelaxedM on): size for every pattern
+    // length that takes the staged two-pass find
     int64_t need = single;
-    for (int m : {kOptMinM, kShortRelaxedM}) {
+    for (int m : {1, kOptMinM, kShortRelaxedM}) {
         Resolved r;
-        if (resolve(cfg, n, n, true, sms, m, &r) == DFA_OK && r.loader == 2) {
+        if (resolve(cfg, n, n, true, sms, m, &r) == DFA_OK && two_pass_layout(r, m)) {
             const int64_t tile_bytes = (int64_t)kRows * r.chunk;
-            need = std::max(need, work_bytes_two_pass((n + tile_bytes - 1) / tile_bytes));
+            need = std::max(need, work_bytes_two_pass((n + tile_bytes - 1) / tile_bytes, staged_slots(r.layout)));
         }
     }
     return need;

@@ -93,13 +93,17 @@ def test_oracle_lib_builds():
 
 
 def test_workspace_covers_every_default_row_length():
-    """With no configuration the workspace must hold the two-pass find of
-    every pattern length: the relaxed layouts take 768-byte rows from m = 12
-    on (the most rows) and 1024-byte rows below; one tile is 512 rows."""
+    """With no configuration the workspace must hold the staged two-pass
+    find of every pattern length: below m = 8 layout 1 with 960-byte rows
+    staging up to 16 end offsets a row, from m = 8 the relaxed layout with
+    1024-byte rows (768 from m = 12 on, the most rows) staging up to 8; one
+    tile is 512 rows; per row a u16 count and the u16 offsets."""
     import paper_1506_08612_gb300 as dd
     n = 3_200_000_000
-    tiles = -(-n // (512 * 768))
-    need = 8 * (2 + tiles) + tiles * 512 * (2 + 8)        # header, tile words, row count + stage mask
+    need = 0
+    for row_bytes, ks in ((960, 16), (1024, 8), (768, 8)):
+        tiles = -(-n // (512 * row_bytes))
+        need = max(need, 8 * (2 + tiles) + tiles * 512 * (2 + 2 * ks))
     assert dd._lib.dfa_find_workspace_bytes(n, None) >= need
 
 

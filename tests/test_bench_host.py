@@ -9,11 +9,11 @@ import bench
 
 
 def test_kernels_per_find():
-    assert bench.kernels_per_find(4, None) == 1            # single-pass dense find
-    assert bench.kernels_per_find(7, None) == 1
-    for m in (8, 16, 64):
-        assert bench.kernels_per_find(m, None) == 3        # count pass, tile scan, re-walk
-    assert bench.kernels_per_find(16, {"layout": 1}) == 1
+    for m in (4, 7, 8, 16, 64):
+        assert bench.kernels_per_find(m, None) == 3        # count pass, tile scan, placement
+    assert bench.kernels_per_find(16, {"layout": 1}) == 1  # single-pass find
+    assert bench.kernels_per_find(8, {"layout": 1}) == 3
+    assert bench.kernels_per_find(4, {"layout": 2}) == 1
     assert bench.kernels_per_find(4, {"layout": 4}) == 3
 
 

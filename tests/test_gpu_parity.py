@@ -387,10 +387,11 @@ def test_dense_relaxed_decoys(gpu, cfg):
 
 @pytest.mark.parametrize("cfg", [None, dict(loader=2, layout=4, chunk=128), dict(loader=2, layout=4, chunk=1280),
                                  dict(loader=2, layout=3, chunk=640)])
-def test_two_pass_stage_masks(gpu, cfg):
-    # the re-walk of a two-pass find walks only the stages that held exact
-    # accepts: copies at row starts, across every 64-byte stage border, ending
-    # in a row's overlap, several in one row, in the ragged last rows
+def test_staged_find_borders(gpu, cfg):
+    # the staged two-pass find records each row's exact accepts in its count
+    # pass and copies them in the third: copies at row starts, across every
+    # 64-byte stage border, ending in a row's overlap, several in one row, in
+    # the ragged last rows
     chunk = 1280 if cfg is None else cfg["chunk"]
     n = 512 * chunk * 2 + 7 * chunk + 77
     for m in (8, 12, 33, 64):
@@ -411,10 +412,10 @@ def test_two_pass_stage_masks(gpu, cfg):
 
 
 @pytest.mark.parametrize("chunk", [128, 640, 1280])
-def test_two_pass_row_end_offsets(gpu, chunk):
-    # the third pass of a two-pass find walks again the masked stages of
-    # every row with accepts: rows holding 0..7 occurrences in turn, some
-    # ending in the row's overlap, rows spilling into their successors
+def test_staged_row_end_offsets(gpu, chunk):
+    # rows holding 0..11 occurrences in turn (the relaxed layout stages 8 a
+    # row: rows with more are walked again by the third pass), some ending in
+    # the row's overlap, rows spilling into their successors
     cfg = dict(loader=2, layout=4, chunk=chunk)
     n = 512 * chunk * 2 + 3 * chunk + 41
     for m in (8, 13, 40):
@@ -422,7 +423,7 @@ def test_two_pass_row_end_offsets(gpu, chunk):
         pat = synth.pattern(m, 2600 + m)
         at = []
         for row in range(n // chunk):
-            k = row % 8
+            k = row % 12
             gap = max(m + 1, (chunk - m) // max(k, 1))
             for j in range(k):
                 st = row * chunk + j * gap
@@ -431,6 +432,41 @@ def test_two_pass_row_end_offsets(gpu, chunk):
                 if st + m <= n:
                     at.append(st)
         synth.plant(t, pat, sorted(set(at)))
+        assert _check(gpu, t, pat, cfg) > 0
+
+
+@pytest.mark.parametrize("chunk", [128, 960])
+def test_staged_dense_rows_past_their_slots(gpu, chunk):
+    # layout 1 stages up to 16 end offsets a row: rows holding 0..23 true
+    # copies of a short pattern in turn (rows above 16 are walked again by
+    # the third pass), each copy preceded by a non-base at a varying
+    # distance, and decoys (one byte swapped for a non-base of the same code)
+    # between them
+    cfg = dict(loader=2, layout=1, chunk=chunk)
+    n = 512 * chunk * 2 + 5 * chunk + 19
+    for m in (3, 5, 8):
+        t = synth.genome_text(n, 270 + m, n_gap_mean=0)
+        pat = synth.pattern(m, 2700 + m)
+        codes = [(c >> 1) & 3 for c in pat]
+        rnd = synth.uniform_ints(4 * (n // chunk) * 24 + 8, 1 << 30, 280 + m)
+        k = 0
+        for row in range(n // chunk):
+            want = row % 24
+            gap = max(2 * m + 2, (chunk - m) // max(want, 1))
+            for j in range(want):
+                st = row * chunk + j * gap
+                if st + m > n:
+                    break
+                t[st:st + m] = np.frombuffer(pat, np.uint8)
+                d = 1 + int(rnd[k] % 8); k += 1
+                if st - d >= 0 and j % 3 == 1:
+                    t[st - d] = _same_code_nonbases(int(rnd[k] % 4))[0]; k += 1
+                ds = st + m + 1
+                if j % 4 == 2 and ds + m <= min(n, row * chunk + (j + 1) * gap):
+                    dec = bytearray(pat)
+                    q = int(rnd[k] % m); k += 1
+                    dec[q] = _same_code_nonbases(codes[q])[0]
+                    t[ds:ds + m] = np.frombuffer(bytes(dec), np.uint8)
         assert _check(gpu, t, pat, cfg) > 0
 
 
@@ -453,7 +489,7 @@ def test_relaxed_walk_nonbase_runs(gpu):
             _check(gpu, t, pat, cfg)
 
 
-@pytest.mark.parametrize("layout", [3, 4])
+@pytest.mark.parametrize("layout", [1, 3, 4])
 def test_single_pass_find_with_small_workspace(gpu, layout):
     # a workspace with room for the tile words only (no per-row counts) takes
     # the single-pass find; both forms must give the same exact result
@@ -463,7 +499,7 @@ def test_single_pass_find_with_small_workspace(gpu, layout):
     td = _dev(gpu, t)
     cfg = dict(loader=2, layout=layout, chunk=128)
     ntiles = -(-n // (512 * 128))
-    for m in (8, 13, 24, 31):
+    for m in ((1, 2, 4, 6, 8, 9) if layout == 1 else (8, 13, 24, 31)):
         pat = synth.pattern(m, 300 + m)
         pos_idx = synth.uniform_ints(300, n - m, 5 + m)
         synth.plant(t, pat, np.unique(pos_idx // m * m))
