@@ -471,9 +471,14 @@ def _as_table(p):
 
 
 def count(text, pattern, cfg=None) -> int:
-    """Synchronous count on the current stream (allocates its output)."""
+    """Synchronous count on the current stream (allocates its output).
+    cfg: None (library defaults), a dfa_config dict, or "auto" (the
+    autotuner's layout and row length for this pattern and text size)."""
     import torch
     t = _as_table(pattern)
+    if isinstance(cfg, str) and cfg == "auto":
+        from . import autotune
+        cfg = autotune.tune_single(text, t, op="count")
     out = torch.zeros(1, dtype=torch.int64, device=text.device)
     dfa_count(text, t, out, cfg=cfg)
     v = int(out.item()) & (2**64 - 1)
@@ -484,9 +489,13 @@ def count(text, pattern, cfg=None) -> int:
 
 def find(text, pattern, cap: int | None = None, cfg=None):
     """Synchronous find: returns (count, int64 positions tensor on device).
-    With cap=None the buffer grows until every position fits."""
+    With cap=None the buffer grows until every position fits.  cfg as for
+    ``count`` ("auto" tunes on dfa_find itself)."""
     import torch
     t = _as_table(pattern)
+    if isinstance(cfg, str) and cfg == "auto":
+        from . import autotune
+        cfg = autotune.tune_single(text, t, op="find")
     dev = text.device
     if cap is None:
         cap = max(1024, text.numel() // 4096)

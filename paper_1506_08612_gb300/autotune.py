@@ -7,15 +7,25 @@ Algorithm 1), the threads per CTA, and, for one pattern, the table layout.
 This module times a small set of candidates with CUDA events on a sample of
 the caller's own text and remembers the fastest per key:
 
-* key = (kind, device name and SM count, log2 bucket of the text bytes,
-  pattern bucket), where the pattern bucket is the pattern length for one
-  pattern and (log2 of the pattern count, m_max bucket, log2 of the automaton
-  states) for the multi-pattern automaton;
+* key = (kind, kernel version, device name and SM count, log2 bucket of the
+  text bytes, pattern bucket), where the pattern bucket is the pattern length
+  for one pattern and (log2 of the pattern count, m_max bucket, log2 of the
+  automaton states) for the multi-pattern automaton; the version tag changes
+  whenever the kernels' candidate space does, so entries timed on earlier
+  kernels miss and are tuned again;
 * cache = a JSON file (``DNADFA_AUTOTUNE_CACHE``, default
   ``~/.cache/dnadfa/autotune.json``), read once and rewritten atomically
   after each new entry;
 * ``DNADFA_CONFIG`` (a JSON object of dfa_config fields) forces one
-  configuration for every call and skips tuning.
+  configuration for every call and skips tuning; the multi-pattern tuner
+  keeps only the fields dfa_multi_count reads (threads, chunk, a layout of
+  its own 0..2, ctas_per_sm).
+
+Candidates: the multi-pattern count varies threads x chunk x table layout
+(one shared copy, or one copy per lane where the automaton is small enough:
+the library refuses the copies otherwise, and a refused candidate is
+skipped); one pattern varies the table layout x row length of the TMA
+kernel, timed on the call it will serve (dfa_count or dfa_find).
 
 Timing and selection are separate from the GPU so that the host logic runs
 (and is tested) without one: ``select_best`` takes any timing callable.
@@ -33,11 +43,15 @@ import threading
 # m_max - 1 so the overlap re-scan (Algorithm 1) stays a small fraction.
 MULTI_THREADS = (128, 256, 512)
 MULTI_CHUNKS = (256, 512, 1024, 2048, 4096)
+MULTI_LAYOUTS = (1, 2)            # one shared table copy / 32 per-lane copies
 # One pattern, TMA loader: chunk bytes per row (multiples of 64) x layout
-# (0 = library default for m, 1 = exact four-step table, 4 = relaxed walk on
-# the flagged four-step table, m >= 8 only).
-SINGLE_CHUNKS = (0, 512, 768, 1024, 1280)
-SINGLE_LAYOUTS = (0, 1, 4)
+# (0 = library default for m, 1 = four-step table with accept counts,
+# 3 = four-step states with exact replays, 4 = relaxed walk on the flagged
+# four-step table; 3 and 4 from m = 8 on).
+SINGLE_CHUNKS = (0, 512, 768, 960, 1024, 1280)
+SINGLE_LAYOUTS = (0, 1, 3, 4)
+# Bumped when a kernel or its candidate space changes.
+KERNEL_VERSION = "v3"
 
 _lock = threading.Lock()
 _cache: dict | None = None
@@ -82,7 +96,10 @@ def reset_memory_cache() -> None:
         _cache = None
 
 
-def forced_config() -> dict | None:
+def forced_config(kind: str = "single") -> dict | None:
+    """The configuration DNADFA_CONFIG forces, or None.  For the
+    multi-pattern count (kind "multi") only the fields it reads are kept: a
+    single-pattern layout (3, 4) or a loader would make it refuse the call."""
     s = os.environ.get("DNADFA_CONFIG")
     if not s:
         return None
@@ -93,20 +110,25 @@ def forced_config() -> dict | None:
     bad = set(d) - allowed
     if bad:
         raise ValueError(f"DNADFA_CONFIG: unknown fields {sorted(bad)}")
-    return {k: int(v) for k, v in d.items()}
+    out = {k: int(v) for k, v in d.items()}
+    if kind == "multi":
+        out.pop("loader", None)
+        if out.get("layout", 0) not in (0, 1, 2):
+            out.pop("layout")
+    return out
 
 
 def _log2_bucket(x: int) -> int:
     return int(math.floor(math.log2(x))) if x > 0 else 0
 
 
-def single_key(device: str, n: int, m: int) -> str:
-    return f"single|{device}|n2^{_log2_bucket(n)}|m{m}"
+def single_key(device: str, n: int, m: int, op: str = "count") -> str:
+    return f"single-{op}|{KERNEL_VERSION}|{device}|n2^{_log2_bucket(n)}|m{m}"
 
 
 def multi_key(device: str, total_bytes: int, npat: int, mmax: int, states: int) -> str:
     mb = 8 if mmax <= 8 else 16 if mmax <= 16 else 32 if mmax <= 32 else 64
-    return (f"multi|{device}|n2^{_log2_bucket(total_bytes)}|p2^{_log2_bucket(npat)}"
+    return (f"multi|{KERNEL_VERSION}|{device}|n2^{_log2_bucket(total_bytes)}|p2^{_log2_bucket(npat)}"
             f"|mmax{mb}|s2^{_log2_bucket(states)}")
 
 
@@ -125,17 +147,18 @@ def remember(key: str, cfg: dict, ms: float, candidates: int) -> None:
 
 def multi_candidates(mmax: int) -> list[dict]:
     out = []
-    for t in MULTI_THREADS:
-        for c in MULTI_CHUNKS:
-            if c >= 4 * max(mmax - 1, 1):
-                out.append({"threads": t, "chunk": c})
+    for lay in MULTI_LAYOUTS:
+        for t in MULTI_THREADS:
+            for c in MULTI_CHUNKS:
+                if c >= 4 * max(mmax - 1, 1):
+                    out.append({"threads": t, "chunk": c, "layout": lay})
     return out
 
 
 def single_candidates(m: int) -> list[dict]:
     out = []
     for lay in SINGLE_LAYOUTS:
-        if lay == 4 and m < 8:
+        if lay in (3, 4) and m < 8:
             continue
         for c in SINGLE_CHUNKS:
             d = {"layout": lay, "loader": 2}
@@ -221,7 +244,7 @@ def tune_multi(texts, table, sample_bytes: int = 1 << 30, reps: int = 3, stream=
     import torch
 
     from . import dfa_multi_count
-    forced = forced_config()
+    forced = forced_config("multi")
     if forced is not None:
         return forced
     total = sum(int(t.numel()) for t in texts)
@@ -242,16 +265,20 @@ def tune_multi(texts, table, sample_bytes: int = 1 << 30, reps: int = 3, stream=
 
 
 def tune_single(text, table, reps: int = 3, stream=None, retune: bool = False,
-                sample_bytes: int = 1 << 30) -> dict:
-    """Best (layout, chunk) for dfa_count of one pattern on this text."""
+                sample_bytes: int = 1 << 30, op: str = "count") -> dict:
+    """Best (layout, chunk) of the TMA kernel for one pattern on this text,
+    timed on ``op``: "count" (dfa_count) or "find" (dfa_find, count and
+    sorted positions, with a workspace of its own)."""
     import torch
 
-    from . import dfa_count
+    from . import dfa_count, dfa_find, dfa_find_workspace_bytes
     forced = forced_config()
     if forced is not None:
         return forced
+    if op not in ("count", "find"):
+        raise ValueError(f"tune_single: op {op!r}")
     n = int(text.numel())
-    key = single_key(device_name(), n, table.m)
+    key = single_key(device_name(), n, table.m, op)
     if not retune:
         hit = lookup(key)
         if hit is not None:
@@ -259,7 +286,27 @@ def tune_single(text, table, reps: int = 3, stream=None, retune: bool = False,
     stream = stream or torch.cuda.current_stream()
     sample = text[: min(n, sample_bytes) // 64 * 64] if n > sample_bytes else text
     out = torch.zeros(1, dtype=torch.int64, device=text.device)
-    timer = _event_timer(lambda cfg: dfa_count(sample, table, out, cfg=cfg, stream=stream), stream)
+    if op == "count":
+        timer = _event_timer(lambda cfg: dfa_count(sample, table, out, cfg=cfg, stream=stream), stream)
+    else:
+        cap = [1 << 16]
+        pos = [torch.empty(cap[0], dtype=torch.int64, device=text.device)]
+        ws = [torch.empty(0, dtype=torch.uint8, device=text.device)]
+
+        def launch(cfg):
+            need = dfa_find_workspace_bytes(int(sample.numel()), cfg)
+            if need < 0:
+                raise ValueError("configuration refused")
+            if ws[0].numel() < need:
+                ws[0] = torch.empty(need, dtype=torch.uint8, device=text.device)
+            dfa_find(sample, table, pos[0], out, ws[0], cfg=cfg, stream=stream)
+        timer = _event_timer(launch, stream)
+        # size the position buffer once (a truncated find writes only cap)
+        launch(None)
+        stream.synchronize()
+        c = int(out.item())
+        if c > cap[0]:
+            pos[0] = torch.empty(c, dtype=torch.int64, device=text.device)
     cands = single_candidates(table.m)
     best, ms = select_best(cands, timer, reps)
     remember(key, best, ms, len(cands))

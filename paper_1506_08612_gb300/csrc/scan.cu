@@ -824,8 +824,10 @@ struct TmaArgs {
     // and the rows' exact accept end offsets (u16, relative to the row
     // start): each walker warp of tile t writes those of its 32 rows, at most
     // KS a row, packed in row order into its own region of 32 * KS entries
-    // at stage + (t * kWalkWarps + warp) * 32 * KS
+    // at stage + (t * kWalkWarps + warp) * 32 * KS; and each warp's total
+    // count at warp_sum[t * kWalkWarps + warp]
     uint16_t* stage;
+    uint32_t* warp_sum;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -1040,63 +1042,23 @@ __device__ __forceinline__ uint4 redo_stage_exact(const SmemTab& T, uint32_t slo
     return make_uint4(w.cnt, ss.n, w.e, 0u);
 }
 
-// The exact accepts of a stage walked through codes alone, for patterns of
-// m <= 8.  The relaxed walk is the automaton run on the text with every byte
-// replaced by the base of its 2-bit code, so it accepts at end j exactly when
-// the codes of the m bytes ending at j are those of P; the exact walk accepts
-// there exactly when, in addition, those m bytes are bases (each base is the
-// one byte, in either case, with its code).  So an exact accept is a relaxed
-// accept whose window holds no non-base, whatever came before the window.
-// map: bit j = a relaxed accept ending at stage offset j; the window of j
-// covers buffer bytes [j + 9 - m, j + 8] of the 8 bytes before the stage
-// (p0, p1) followed by the stage's 64 (its ring slot: 16-byte piece k at
-// q + (ob ^ (k << 4))).  Exact accepts go to the row's slots at end offset
-// r + j; returns their number.
-template <uint32_t CAP>
-__device__ __forceinline__ uint32_t window_accepts(uint2 map, uint32_t r, uint32_t m, uint32_t p0, uint32_t p1,
-                                                   const uint8_t* q, uint32_t ob, RowSlots<CAP>& ss)
-{
-    const uint32_t qa = smem_u32(q);
-    uint32_t c = 0;
-    uint64_t mp = ((uint64_t)map.y << 32) | map.x;
-    while (mp) {
-        const uint32_t j = (uint32_t)__ffsll((long long)mp) - 1u;
-        mp &= mp - 1ull;
-        const uint32_t J = j + 8u, S = J + 1u - m;          // window: buffer bytes [S, J]
-        uint32_t bad = 0u;
-#pragma unroll
-        for (uint32_t d = 0; d < 3; d++) {
-            const uint32_t k = (S >> 2) + d;                 // buffer word
-            if (4u * k > J) break;
-            uint32_t w;
-            if (k == 0u) {
-                w = p0;
-            } else if (k == 1u) {
-                w = p1;
-            } else {
-                const uint32_t sw = k - 2u;                  // stage word
-                asm volatile("ld.shared.u32 %0, [%1];"
-                             : "=r"(w)
-                             : "r"(qa + (ob ^ ((sw >> 2) << 4)) + ((sw & 3u) << 2)));
-            }
-            uint32_t keep = 0xFFFFFFFFu;                     // the word's bytes inside [S, J]
-            if (S > 4u * k) keep <<= 8u * (S - 4u * k);
-            if (J < 4u * k + 3u) keep &= 0xFFFFFFFFu >> (8u * (4u * k + 3u - J));
-            bad |= word_bad(w) & keep;
-        }
-        if (bad == 0u) {
-            ss.put(r + j);
-            c++;
-        }
-    }
-    return c;
-}
-
 template <int LAYOUT, class Sink>
 __device__ __noinline__ uint32_t walk_cold(const ScanArgs* a, int64_t s, int64_t e, Sink* sink)
 {
     const SmemTab T = tab_view<LAYOUT>(*a);
     return walk_chunk<LAYOUT>(*a, T, s, e, *sink);
+}
+
+// walk_cold recording into a row's slots, which go in and out by value (no
+// address of the caller's row state is taken, so it stays in registers).
+// Returns (count, slots used).
+template <int LAYOUT, uint32_t CAP>
+__device__ __noinline__ uint2 walk_cold_rec(const ScanArgs* a, int64_t s, int64_t e, uint32_t base, uint32_t n)
+{
+    RowSlots<CAP> ss{base, n};
+    const SmemTab T = tab_view<LAYOUT>(*a);
+    const uint32_t c = walk_chunk<LAYOUT>(*a, T, s, e, ss);
+    return make_uint2(c, ss.n);
 }
 
 // Relaxed walk of layouts 3 and 4 (patterns of kOptMinM and more).  The
@@ -1525,11 +1487,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                             tl0[i] = v[i][3].z;
                             tl1[i] = v[i][3].w;
                             const uint2 map = wd.vec4_relaxed_map(v[i][0], v[i][1], v[i][2], v[i][3]);
-                            if (STAGED) {
-                                // each relaxed accept is exact iff its m bytes are bases
-                                if ((map.x | map.y) != 0u)
-                                    wd.cnt += window_accepts<KS>(map, r, m, p0, p1, rp + i * 32 * kStageW, ob, ss[i]);
-                            } else if ((map.x | map.y) != 0u) {
+                            if ((map.x | map.y) != 0u) {
                                 // accepts: exact if the stage (read again from its
                                 // slot) and the 8 bytes before it are bases
                                 const uint8_t* q = rp + i * 32 * kStageW;
@@ -1695,7 +1653,11 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                 cnt[i] = 0;
             } else if (!ok[i]) {
                 ss[i].n = 0;
-                if (FIND || STAGED)
+                if (STAGED) {
+                    const uint2 w2 = walk_cold_rec<LAYOUT, KS>(&a, s0, e0, ss[i].base, 0u);
+                    cnt[i] = w2.x;
+                    ss[i].n = w2.y;
+                } else if (FIND)
                     cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &ss[i]);
                 else {
                     CountSink cs;
@@ -1744,6 +1706,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
                 if (lane == 0 && ws) atomicAdd(p.tile_sum + tile, (unsigned long long)ws);
+                if (STAGED && lane == 0) p.warp_sum[(size_t)tile * kWalkWarps + warp] = ws;
             }
         } else {
             // exclusive offsets of this lane's rows among the warp's rows
@@ -1864,62 +1827,101 @@ __global__ void __launch_bounds__(1024)
     if (threadIdx.x == 0) *count = s_carry;
 }
 
-// Pass 3: a CTA per tile holding accepts.  The count pass staged every
-// row's exact end offsets (up to KS a row) in its warp's region of the tile,
-// packed in row order; here each row learns its first index (the tile's
-// offset from pass 2 plus a scan of the tile's row counts) and its entries'
-// place in the region (a scan of min(count, KS) within its warp), and copies
-// them as start positions.  A row with more than KS accepts is walked again
-// exactly from global memory, writing its positions directly.
-__global__ void __launch_bounds__(kRows)
-    k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
-            const uint16_t* stage, int ks)
+// Pass 3, one warp per (tile, walker warp) region.  The count pass staged,
+// per row, its exact end offsets (up to ks; packed in row order in the
+// warp's region) and left each warp's total; pass 2 turned the tile totals
+// into offsets.  A row's first index is its tile's offset + the totals of
+// the tile's earlier warps + a scan of the row counts within the warp; its
+// entries sit in the region after those of the earlier rows (a scan of
+// min(count, ks)).  A row with more than ks accepts is walked again here:
+// the warp splits it into 32 slices, each read with the m - 1 byte overlap
+// of Algorithm 1, walked exactly with the single-step table from global
+// memory (counted, scanned, walked again writing positions).
+__device__ __noinline__ void place_overflow_row(const ScanArgs& a, int64_t rs, int64_t g0, int lane)
 {
-    __shared__ uint32_t s_warp[kRows / 32];
-    load_tables<kLayoutK4>(a, g_smem);
-    __syncthreads();
-    const SmemTab T = tab_view<kLayoutK4>(a);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned long long end_all = *a.count;
+    const uint8_t* d1 = a.tab + a.k4_bytes;              // (m+1) x 4 single steps, A C T G by code
+    const uint32_t m = (uint32_t)a.m;
+    const int64_t re = min(rs + a.chunk, a.n_own);
+    const int64_t span = (re - rs + 31) / 32;
+    const int64_t s = min(rs + lane * span, re), e = min(s + span, re);
+    const int64_t hi = min(e + (int64_t)m - 1, a.n);
+    uint32_t c = 0;
+    for (int pass = 0; pass < 2; pass++) {
+        int64_t g = 0;
+        if (pass == 1) {
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            g = g0 + (int64_t)(x - c);
+        }
+        uint32_t q = 0;
+        if (s < e) {
+            for (int64_t j = s; j < hi; j++) {
+                const uint32_t b = __ldg(a.text + j);
+                const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
+                q = ((b ^ (t * 0x11u)) & 0xD9u) == 0x41u ? (uint32_t)__ldg(d1 + q * 4u + ((b >> 1) & 3u)) : 0u;
+                if (q == m) {
+                    if (pass == 0) {
+                        c++;
+                    } else {
+                        if (g < a.cap) a.pos[g] = a.pos_base + j - (int64_t)(m - 1);
+                        g++;
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const uint32_t* warp_sum,
+            const unsigned long long* tile_off, const uint16_t* stage, int ks)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t units = a.ntiles * kWalkWarps;
     const int64_t C = a.chunk;
-    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t tile = u / kWalkWarps;
+        const int w = (int)(u % kWalkWarps);
+        // this warp's total and the totals of the tile's earlier warps
+        const uint32_t wt = lane < kWalkWarps ? warp_sum[tile * kWalkWarps + lane] : 0u;
+        if (__shfl_sync(0xffffffffu, wt, w) == 0u) continue;
+        uint32_t before = lane < w ? wt : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
         const unsigned long long off = tile_off[tile];
-        const unsigned long long nxt = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
-        if (nxt == off) continue;
-        const uint32_t rc = rows[tile * kRows + threadIdx.x];
+        const uint32_t rc = rows[tile * kRows + w * 32 + lane];
         const uint32_t st = min(rc, (uint32_t)ks);
-        // warp scans: the row's count (its index in the tile) and its staged
-        // entries (their place in the warp's region)
         uint32_t x = rc, y = st;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
-            const uint32_t v = __shfl_up_sync(0xffffffffu, y, o);
+            const uint32_t p = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t q = __shfl_up_sync(0xffffffffu, y, o);
             if (lane >= o) {
-                x += u;
-                y += v;
+                x += p;
+                y += q;
             }
         }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; w++) before += s_warp[w];
-        __syncthreads();
-        if (rc) {
-            const int64_t row = tile * kRows + threadIdx.x;
-            const int64_t rs = row * C;
-            const int64_t start0 = a.pos_base + rs - (int64_t)(a.m - 1);
-            const int64_t g0 = (int64_t)(off + before + x - rc);
-            if (rc <= (uint32_t)ks) {
-                const uint16_t* src = stage + ((size_t)tile * kWalkWarps + warp) * (32 * (size_t)ks) + (y - st);
-                for (uint32_t j = 0; j < rc; j++) {
-                    const int64_t g = g0 + j;
-                    if (g < a.cap) a.pos[g] = start0 + src[j];
-                }
-            } else if (g0 < a.cap) {
-                GlobalSink gs{a.pos, a.cap, g0, start0};
-                walk_chunk<kLayoutK4>(a, T, rs, min(rs + C, a.n_own), gs);
+        const int64_t rs = (tile * kRows + w * 32 + lane) * C;
+        const int64_t start0 = a.pos_base + rs - (int64_t)(a.m - 1);
+        const int64_t g0 = (int64_t)(off + before + x - rc);
+        if (rc != 0u && rc <= (uint32_t)ks) {
+            const uint16_t* src = stage + u * (32 * (int64_t)ks) + (y - st);
+            for (uint32_t j = 0; j < rc; j++) {
+                const int64_t g = g0 + j;
+                if (g < a.cap) a.pos[g] = start0 + src[j];
             }
+        }
+        // rows past their slots, one at a time with the whole warp
+        uint32_t over = __ballot_sync(0xffffffffu, rc > (uint32_t)ks);
+        while (over) {
+            const int r = __ffs(over) - 1;
+            over &= over - 1u;
+            place_overflow_row(a, __shfl_sync(0xffffffffu, rs, r), __shfl_sync(0xffffffffu, g0, r), lane);
         }
     }
 }
@@ -2165,7 +2167,7 @@ int staged_slots(int layout) { return layout == kLayoutK4 ? kTSlotsDense : kTSlo
 
 int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
                const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr,
-               unsigned long long* tile_sum = nullptr, uint16_t* stage = nullptr)
+               unsigned long long* tile_sum = nullptr, uint16_t* stage = nullptr, uint32_t* warp_sum = nullptr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
     int rc = tensor_map_encoder(&encode);
@@ -2183,6 +2185,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.rows = rows;
     p.tile_sum = tile_sum;
     p.stage = stage;
+    p.warp_sum = warp_sum;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
@@ -2276,9 +2279,11 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
 
 int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
 
-// Staged two-pass find: [header][one word per tile][one u16 count per row of
-// every tile][ks u16 end offsets per row of every tile, 16-byte aligned].
-int64_t staged_rows_off(int64_t ntiles) { return work_bytes_for(ntiles); }
+// Staged two-pass find: [header][one word per tile][one u32 total per walker
+// warp of every tile][one u16 count per row of every tile][ks u16 end
+// offsets per row of every tile, 16-byte aligned].
+int64_t staged_wsum_off(int64_t ntiles) { return work_bytes_for(ntiles); }
+int64_t staged_rows_off(int64_t ntiles) { return staged_wsum_off(ntiles) + ntiles * kWalkWarps * 4; }
 int64_t staged_stage_off(int64_t ntiles) { return (staged_rows_off(ntiles) + ntiles * kRows * 2 + 15) & ~(int64_t)15; }
 int64_t work_bytes_two_pass(int64_t ntiles, int ks) { return staged_stage_off(ntiles) + ntiles * kRows * ks * 2; }
 
@@ -2298,19 +2303,20 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
 {
     unsigned long long* tile_sum = a.work + kWorkHeader;
     uint8_t* wb = reinterpret_cast<uint8_t*>(a.work);
+    uint32_t* wsum = reinterpret_cast<uint32_t*>(wb + staged_wsum_off(a.ntiles));
     uint16_t* rows = reinterpret_cast<uint16_t*>(wb + staged_rows_off(a.ntiles));
     uint16_t* stage = reinterpret_cast<uint16_t*>(wb + staged_stage_off(a.ntiles));
     ScanArgs a1 = a;
     a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
-    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, tile_sum, stage);
+    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, tile_sum, stage, wsum);
     if (rc) return rc;
     k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
     CUDA_TRY(cudaGetLastError());
-    const int smem = table_smem(t, kLayoutK4);
-    int occ = occupancy((const void*)k_place, kRows, smem, dev, di->smem_optin);
+    int occ = occupancy((const void*)k_place, 256, 0, dev, di->smem_optin);
     if (occ <= 0) return fail("placement kernel does not fit on an SM (occupancy 0)");
-    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)occ * di->sms);
-    k_place<<<(unsigned)grid, kRows, smem, st>>>(a, rows, tile_sum, stage, staged_slots(r.layout));
+    const int64_t warps = a.ntiles * kWalkWarps;
+    const int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)occ * di->sms);
+    k_place<<<(unsigned)grid, 256, 0, st>>>(a, rows, wsum, tile_sum, stage, staged_slots(r.layout));
     CUDA_TRY(cudaGetLastError());
     return DFA_OK;
 }
