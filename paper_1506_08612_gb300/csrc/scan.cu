@@ -817,16 +817,19 @@ struct TmaArgs {
     // word (bit 1), or bit 63 of the count for a count without workspace
     unsigned long long* fail_word;
     unsigned long long fail_bit;
-    // count mode, first pass of a two-pass find: every row's count (u16) and
-    // every tile's total (added up) go here; null otherwise
+    // count mode, first pass of a two-pass find: every row's count (u16)
+    // goes here; null otherwise
     uint16_t* rows;
-    unsigned long long* tile_sum;
     // and the rows' exact accept end offsets (u16, relative to the row
     // start): each walker warp of tile t writes those of its 32 rows, at most
     // KS a row, packed in row order into its own region of 32 * KS entries
-    // at stage + (t * kWalkWarps + warp) * 32 * KS; and each warp's total
-    // count at warp_sum[t * kWalkWarps + warp]
+    // at stage + (t * kWalkWarps + warp) * 32 * KS (layout 1); or, for the
+    // relaxed layouts, every row with a count has the mask of the 64-byte
+    // stages holding its exact accepts at masks[row] (bit s: body stage s; bit
+    // sps: the overlap; all ones: the whole row); and each warp's total count
+    // goes to warp_sum[t * kWalkWarps + warp]
     uint16_t* stage;
+    unsigned long long* masks;
     uint32_t* warp_sum;
 };
 
@@ -1107,10 +1110,12 @@ __device__ __forceinline__ uint32_t relaxed_mask(uint32_t m)
 // the tile was just streamed from.  With REC the accepts go to the row's
 // slots (base, n), in ascending order.  Returns (count, n, and the mask of
 // the stages that hold exact accepts in .z (bits 0..31) and .w (32..63)).
-template <int LAYOUT, bool REC>
+// MODE 0: count only; 1: accepts to the row's shared-memory slots (base, n).
+template <int LAYOUT, int MODE>
 __device__ __noinline__ uint4 replay_row(const ScanArgs* a, int64_t rs, uint32_t sps, uint64_t mask,
                                          uint32_t slot_base, uint32_t slot_n)
 {
+    constexpr bool REC = MODE == 1;
     uint64_t hit = 0ull;
     const SmemTab T = tab_view<LAYOUT>(*a);
     const uint32_t m = (uint32_t)a->m;
@@ -1251,7 +1256,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
     constexpr bool INLINE_REC = DENSE && !OPT;
     constexpr int KS = INLINE_REC ? kTSlotsDense : kTSlots;
     static_assert(!STAGED || kRPL == 1, "the staged pass writes one row per lane");
-    static_assert(!STAGED || LAYOUT != kLayoutStt, "the staged pass walks a four-step table");
+    static_assert(!STAGED || LAYOUT == kLayoutK4, "the staged pass records inline on the four-step table");
     const ScanArgs& a = p.a;
     const int nst = p.nst;
     // [tables][position slots][rings], rings 1024-byte aligned for the TMA swizzle
@@ -1653,6 +1658,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                 cnt[i] = 0;
             } else if (!ok[i]) {
                 ss[i].n = 0;
+                fmask[i] = ~0ull;                 // a row walked cold: the third pass takes it whole
                 if (STAGED) {
                     const uint2 w2 = walk_cold_rec<LAYOUT, KS>(&a, s0, e0, ss[i].base, 0u);
                     cnt[i] = w2.x;
@@ -1664,9 +1670,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                     cnt[i] = walk_cold<LAYOUT>(&a, s0, e0, &cs);
                 }
             } else if (OPT && fmask[i] != 0ull) {
-                const uint4 rc = replay_row<LAYOUT, FIND || STAGED>(&a, s0, sps, fmask[i], ss[i].base, ss[i].n);
+                const uint4 rc = replay_row<LAYOUT, FIND ? 1 : 0>(&a, s0, sps, fmask[i], ss[i].base, ss[i].n);
                 cnt[i] += rc.x;
-                if (FIND || STAGED) ss[i].n = rc.y;
+                if (FIND) ss[i].n = rc.y;
+                fmask[i] = (uint64_t)rc.z | ((uint64_t)rc.w << 32);
             }
         }
         __syncwarp();
@@ -1681,6 +1688,9 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                 for (int i = 0; i < kRPL; i++) {
                     const int64_t row = (int64_t)tile * kRows + wrow0 + 32 * i;
                     p.rows[row] = (uint16_t)cnt[i];
+                    // the stages holding the row's exact accepts (all ones:
+                    // the whole row), for the third pass of a relaxed layout
+                    if (p.masks && cnt[i]) p.masks[row] = OPT ? fmask[i] : ~0ull;
                     ws += cnt[i];
                 }
                 if (STAGED) {
@@ -1705,8 +1715,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
-                if (lane == 0 && ws) atomicAdd(p.tile_sum + tile, (unsigned long long)ws);
-                if (STAGED && lane == 0) p.warp_sum[(size_t)tile * kWalkWarps + warp] = ws;
+                if (lane == 0) p.warp_sum[(size_t)tile * kWalkWarps + warp] = ws;
             }
         } else {
             // exclusive offsets of this lane's rows among the warp's rows
@@ -1785,12 +1794,14 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
 // each writing its positions at its own offset (pass 3).  Sparse patterns
 // have few such rows, so the find costs little more than the count.
 
-// Pass 2 (one CTA of 1024 threads): tile_sum[t] becomes the global index of
-// tile t's first position (base included); *count becomes base + total.
+// Pass 2 (one CTA of 1024 threads): tile_off[t] becomes the global index of
+// tile t's first position (base included), from the tile's walker-warp
+// totals warp_sum[t * kWalkWarps ...]; *count becomes base + total.
 __global__ void __launch_bounds__(1024)
-    k_tile_offsets(unsigned long long* tile_sum, int64_t ntiles, const unsigned long long* base_in,
-                   unsigned long long* count)
+    k_tile_offsets(const uint32_t* warp_sum, unsigned long long* tile_off, int64_t ntiles,
+                   const unsigned long long* base_in, unsigned long long* count)
 {
+    static_assert(kWalkWarps == 16, "four 16-byte loads per tile");
     __shared__ unsigned long long s_warp[32];
     __shared__ unsigned long long s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1798,7 +1809,15 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
     for (int64_t t0 = 0; t0 < ntiles; t0 += 1024) {
         const int64_t t = t0 + threadIdx.x;
-        const unsigned long long v = t < ntiles ? tile_sum[t] : 0ull;
+        unsigned long long v = 0ull;
+        if (t < ntiles) {
+            const uint4* w4 = reinterpret_cast<const uint4*>(warp_sum + t * kWalkWarps);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint4 q = w4[k];
+                v += (unsigned long long)q.x + q.y + q.z + q.w;
+            }
+        }
         unsigned long long x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1819,7 +1838,7 @@ __global__ void __launch_bounds__(1024)
         __syncthreads();
         const unsigned long long carry = s_carry;
         const unsigned long long excl = carry + (warp ? s_warp[warp - 1] : 0ull) + x - v;
-        if (t < ntiles) tile_sum[t] = excl;
+        if (t < ntiles) tile_off[t] = excl;
         __syncthreads();
         if (threadIdx.x == 1023) s_carry = excl + v;
         __syncthreads();
@@ -1827,24 +1846,27 @@ __global__ void __launch_bounds__(1024)
     if (threadIdx.x == 0) *count = s_carry;
 }
 
-// Pass 3, one warp per (tile, walker warp) region.  The count pass staged,
-// per row, its exact end offsets (up to ks; packed in row order in the
-// warp's region) and left each warp's total; pass 2 turned the tile totals
-// into offsets.  A row's first index is its tile's offset + the totals of
-// the tile's earlier warps + a scan of the row counts within the warp; its
-// entries sit in the region after those of the earlier rows (a scan of
-// min(count, ks)).  A row with more than ks accepts is walked again here:
-// the warp splits it into 32 slices, each read with the m - 1 byte overlap
-// of Algorithm 1, walked exactly with the single-step table from global
-// memory (counted, scanned, walked again writing positions).
-__device__ __noinline__ void place_overflow_row(const ScanArgs& a, int64_t rs, int64_t g0, int lane)
+// Pass 3 of the staged two-pass find, one warp per (tile, walker warp)
+// unit: a row's first index is its tile's offset (pass 2) + the totals of the
+// tile's earlier walker warps + a scan of the row counts within the warp.
+// Layout 1 staged each row's exact end offsets (up to ks, packed in row order
+// in the warp's region): they are copied.  The relaxed layouts left, per row
+// with accepts, the mask of the stages holding them: the warp walks those
+// bytes again.  Rows past their slots are walked again too.
+
+// Every occurrence starting in [s, e) (the starts of one row, or a part of
+// them that holds all its occurrences), found by the whole warp and written
+// in order from index g0: lane l takes the l-th slice of the starts and reads
+// m - 1 bytes past it (Algorithm 1 within the range), walking exactly with
+// the single-step table from global memory; a count, a warp scan, then the
+// same walk writing the positions.
+__device__ __noinline__ void place_range(const ScanArgs& a, int64_t s, int64_t e, int64_t g0, int lane)
 {
-    const uint8_t* d1 = a.tab + a.k4_bytes;              // (m+1) x 4 single steps, A C T G by code
+    const uint8_t* d1 = a.tab + a.k4_bytes;              // (m+1) x 4 single steps, by 2-bit code
     const uint32_t m = (uint32_t)a.m;
-    const int64_t re = min(rs + a.chunk, a.n_own);
-    const int64_t span = (re - rs + 31) / 32;
-    const int64_t s = min(rs + lane * span, re), e = min(s + span, re);
-    const int64_t hi = min(e + (int64_t)m - 1, a.n);
+    const int64_t span = (e - s + 31) / 32;
+    const int64_t ls = min(s + lane * span, e), le = min(ls + span, e);
+    const int64_t hi = min(le + (int64_t)m - 1, a.n);
     uint32_t c = 0;
     for (int pass = 0; pass < 2; pass++) {
         int64_t g = 0;
@@ -1858,8 +1880,8 @@ __device__ __noinline__ void place_overflow_row(const ScanArgs& a, int64_t rs, i
             g = g0 + (int64_t)(x - c);
         }
         uint32_t q = 0;
-        if (s < e) {
-            for (int64_t j = s; j < hi; j++) {
+        if (ls < le) {
+            for (int64_t j = ls; j < hi; j++) {
                 const uint32_t b = __ldg(a.text + j);
                 const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
                 q = ((b ^ (t * 0x11u)) & 0xD9u) == 0x41u ? (uint32_t)__ldg(d1 + q * 4u + ((b >> 1) & 3u)) : 0u;
@@ -1876,52 +1898,108 @@ __device__ __noinline__ void place_overflow_row(const ScanArgs& a, int64_t rs, i
     }
 }
 
+// The unit's rows: (row start, own end of the row, first index, count) for
+// this lane, or false when the unit holds no accepts.
+struct PlaceRow {
+    int64_t rs, re, g0;
+    uint32_t rc;
+};
+
+__device__ __forceinline__ bool place_row(const ScanArgs& a, const uint16_t* rows, const uint32_t* warp_sum,
+                                          const unsigned long long* tile_off, unsigned long long end_all, int64_t u,
+                                          int lane, PlaceRow& pr)
+{
+    const int64_t tile = u / kWalkWarps;
+    const int w = (int)(u % kWalkWarps);
+    const unsigned long long off = tile_off[tile];
+    if (off == (tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all)) return false;   // no accepts in the tile
+    // this warp's total and the totals of the tile's earlier warps
+    const uint32_t wt = lane < kWalkWarps ? warp_sum[tile * kWalkWarps + lane] : 0u;
+    if (__shfl_sync(0xffffffffu, wt, w) == 0u) return false;
+    uint32_t before = lane < w ? wt : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+    pr.rc = rows[tile * kRows + w * 32 + lane];
+    uint32_t x = pr.rc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    pr.rs = (tile * kRows + w * 32 + lane) * a.chunk;
+    pr.re = min(pr.rs + a.chunk, a.n_own);
+    pr.g0 = (int64_t)(off + before + x - pr.rc);
+    return true;
+}
+
+// Layout 1: copy the staged offsets; rows past their ks slots walked again.
 __global__ void __launch_bounds__(256)
     k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const uint32_t* warp_sum,
             const unsigned long long* tile_off, const uint16_t* stage, int ks)
 {
     const int lane = threadIdx.x & 31;
     const int64_t units = a.ntiles * kWalkWarps;
-    const int64_t C = a.chunk;
+    const unsigned long long end_all = *a.count;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units;
          u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int64_t tile = u / kWalkWarps;
-        const int w = (int)(u % kWalkWarps);
-        // this warp's total and the totals of the tile's earlier warps
-        const uint32_t wt = lane < kWalkWarps ? warp_sum[tile * kWalkWarps + lane] : 0u;
-        if (__shfl_sync(0xffffffffu, wt, w) == 0u) continue;
-        uint32_t before = lane < w ? wt : 0u;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
-        const unsigned long long off = tile_off[tile];
-        const uint32_t rc = rows[tile * kRows + w * 32 + lane];
-        const uint32_t st = min(rc, (uint32_t)ks);
-        uint32_t x = rc, y = st;
+        PlaceRow pr;
+        if (!place_row(a, rows, warp_sum, tile_off, end_all, u, lane, pr)) continue;
+        const uint32_t st = min(pr.rc, (uint32_t)ks);
+        uint32_t y = st;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t p = __shfl_up_sync(0xffffffffu, x, o);
-            const uint32_t q = __shfl_up_sync(0xffffffffu, y, o);
-            if (lane >= o) {
-                x += p;
-                y += q;
-            }
+            const uint32_t v = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += v;
         }
-        const int64_t rs = (tile * kRows + w * 32 + lane) * C;
-        const int64_t start0 = a.pos_base + rs - (int64_t)(a.m - 1);
-        const int64_t g0 = (int64_t)(off + before + x - rc);
-        if (rc != 0u && rc <= (uint32_t)ks) {
+        const int64_t start0 = a.pos_base + pr.rs - (int64_t)(a.m - 1);
+        if (pr.rc != 0u && pr.rc <= (uint32_t)ks) {
             const uint16_t* src = stage + u * (32 * (int64_t)ks) + (y - st);
-            for (uint32_t j = 0; j < rc; j++) {
-                const int64_t g = g0 + j;
+            for (uint32_t j = 0; j < pr.rc; j++) {
+                const int64_t g = pr.g0 + j;
                 if (g < a.cap) a.pos[g] = start0 + src[j];
             }
         }
-        // rows past their slots, one at a time with the whole warp
-        uint32_t over = __ballot_sync(0xffffffffu, rc > (uint32_t)ks);
+        uint32_t over = __ballot_sync(0xffffffffu, pr.rc > (uint32_t)ks);
         while (over) {
             const int r = __ffs(over) - 1;
             over &= over - 1u;
-            place_overflow_row(a, __shfl_sync(0xffffffffu, rs, r), __shfl_sync(0xffffffffu, g0, r), lane);
+            place_range(a, __shfl_sync(0xffffffffu, pr.rs, r), __shfl_sync(0xffffffffu, pr.re, r),
+                        __shfl_sync(0xffffffffu, pr.g0, r), lane);
+        }
+    }
+}
+
+// Relaxed layouts: every row with accepts walked again over the bytes its
+// stage mask names: the starts from m - 1 bytes before its first masked
+// stage to the end of its last one (every accept of the row ends in a masked
+// stage, and every occurrence starting there is one of them).
+__global__ void __launch_bounds__(256)
+    k_place_masked(const __grid_constant__ ScanArgs a, const uint16_t* rows, const uint32_t* warp_sum,
+                   const unsigned long long* tile_off, const unsigned long long* masks)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t units = a.ntiles * kWalkWarps;
+    const unsigned long long end_all = *a.count;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        PlaceRow pr;
+        if (!place_row(a, rows, warp_sum, tile_off, end_all, u, lane, pr)) continue;
+        int64_t s = pr.rs, e = pr.re;
+        if (pr.rc) {
+            const unsigned long long mask = masks[(u / kWalkWarps) * kRows + (u % kWalkWarps) * 32 + lane];
+            if (mask != ~0ull) {
+                const int64_t lo_stage = __ffsll((long long)mask) - 1;
+                const int64_t hi_stage = 63 - __clzll((long long)mask);
+                s = max(pr.rs, pr.rs + lo_stage * kStageW - (int64_t)(a.m - 1));
+                e = min(e, pr.rs + (hi_stage + 1) * kStageW);
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, pr.rc != 0u);
+        while (todo) {
+            const int r = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            place_range(a, __shfl_sync(0xffffffffu, s, r), __shfl_sync(0xffffffffu, e, r),
+                        __shfl_sync(0xffffffffu, pr.g0, r), lane);
         }
     }
 }
@@ -2119,19 +2197,14 @@ bool tma_dense(int layout, int m)
     return m <= kDenseMaxM && (layout == kLayoutK4 || layout == kLayoutStt);
 }
 
-// staged: pass 1 of the staged two-pass find (count mode recording every
-// exact accept; layouts 1, 3 and 4).
+// staged: pass 1 of the staged two-pass find on layout 1 (count mode
+// recording every exact accept inline); the relaxed layouts' pass 1 is their
+// count kernel (with row counts and stage masks).
 TmaKernelFn pick_tma(int layout, bool find, int m, bool staged)
 {
     const bool dense = tma_dense(layout, m);
-    if (layout == kLayoutK4S) {
-        if (staged) return k_scan_tma<kLayoutK4S, false, true>;
-        return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
-    }
-    if (layout == kLayoutK4F) {
-        if (staged) return k_scan_tma<kLayoutK4F, false, true>;
-        return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
-    }
+    if (layout == kLayoutK4S) return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
+    if (layout == kLayoutK4F) return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
     if (layout == kLayoutK4) {
         if (staged) return k_scan_tma<kLayoutK4, false, true>;
         if (!find) return k_scan_tma<kLayoutK4, false, false>;
@@ -2160,14 +2233,9 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
 }
 
 // Launch the TMA-staged kernel for the filled-in arguments `a`.
-// Entries a row stages in pass 1 of the staged two-pass find: the dense
-// inline walk of layout 1 records up to kTSlotsDense, the replays of the
-// relaxed layouts up to kTSlots.
-int staged_slots(int layout) { return layout == kLayoutK4 ? kTSlotsDense : kTSlots; }
-
 int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
-               const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr,
-               unsigned long long* tile_sum = nullptr, uint16_t* stage = nullptr, uint32_t* warp_sum = nullptr)
+               const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr, uint16_t* stage = nullptr,
+               uint32_t* warp_sum = nullptr, unsigned long long* masks = nullptr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
     int rc = tensor_map_encoder(&encode);
@@ -2183,8 +2251,8 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.fail_word = find || rows ? a.work + 1 : a.count;
     p.fail_bit = find || rows ? 2ull : (1ull << 63);
     p.rows = rows;
-    p.tile_sum = tile_sum;
     p.stage = stage;
+    p.masks = masks;
     p.warp_sum = warp_sum;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
@@ -2200,7 +2268,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     cudaFuncAttributes fa;
     CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)fn));
     const int slot_bytes = find     ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2
-                           : staged ? staged_slots(r.layout) * kRows * 2
+                           : staged ? kTSlotsDense * kRows * 2
                                     : 0;
     p.rings_off = (p.table_bytes + slot_bytes + 1023) & ~1023;
     const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.rings_off;
@@ -2280,12 +2348,17 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
 int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
 
 // Staged two-pass find: [header][one word per tile][one u32 total per walker
-// warp of every tile][one u16 count per row of every tile][ks u16 end
-// offsets per row of every tile, 16-byte aligned].
+// warp of every tile][one u16 count per row of every tile][16-byte aligned:
+// layout 1, kTSlotsDense u16 end offsets per row; relaxed layouts, one u64
+// stage mask per row].
 int64_t staged_wsum_off(int64_t ntiles) { return work_bytes_for(ntiles); }
 int64_t staged_rows_off(int64_t ntiles) { return staged_wsum_off(ntiles) + ntiles * kWalkWarps * 4; }
-int64_t staged_stage_off(int64_t ntiles) { return (staged_rows_off(ntiles) + ntiles * kRows * 2 + 15) & ~(int64_t)15; }
-int64_t work_bytes_two_pass(int64_t ntiles, int ks) { return staged_stage_off(ntiles) + ntiles * kRows * ks * 2; }
+int64_t staged_tail_off(int64_t ntiles) { return (staged_rows_off(ntiles) + ntiles * kRows * 2 + 15) & ~(int64_t)15; }
+int64_t staged_row_bytes(int layout) { return layout == kLayoutK4 ? 2 * kTSlotsDense : 8; }
+int64_t work_bytes_two_pass(int64_t ntiles, int layout)
+{
+    return staged_tail_off(ntiles) + ntiles * kRows * staged_row_bytes(layout);
+}
 
 // The staged two-pass find serves the TMA kernel's four-step layouts: the
 // relaxed ones (3, 4) at any m, layout 1 for m <= 8 (its accepts are tested
@@ -2305,18 +2378,24 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
     uint8_t* wb = reinterpret_cast<uint8_t*>(a.work);
     uint32_t* wsum = reinterpret_cast<uint32_t*>(wb + staged_wsum_off(a.ntiles));
     uint16_t* rows = reinterpret_cast<uint16_t*>(wb + staged_rows_off(a.ntiles));
-    uint16_t* stage = reinterpret_cast<uint16_t*>(wb + staged_stage_off(a.ntiles));
+    const bool dense = r.layout == kLayoutK4;
+    uint16_t* stage = dense ? reinterpret_cast<uint16_t*>(wb + staged_tail_off(a.ntiles)) : nullptr;
+    unsigned long long* masks = dense ? nullptr : reinterpret_cast<unsigned long long*>(wb + staged_tail_off(a.ntiles));
     ScanArgs a1 = a;
     a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
-    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, tile_sum, stage, wsum);
+    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, stage, wsum, masks);
     if (rc) return rc;
-    k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
+    k_tile_offsets<<<1, 1024, 0, st>>>(wsum, tile_sum, a.ntiles, a.base_in, a.count);
     CUDA_TRY(cudaGetLastError());
-    int occ = occupancy((const void*)k_place, 256, 0, dev, di->smem_optin);
+    const void* fn = dense ? (const void*)k_place : (const void*)k_place_masked;
+    int occ = occupancy(fn, 256, 0, dev, di->smem_optin);
     if (occ <= 0) return fail("placement kernel does not fit on an SM (occupancy 0)");
     const int64_t warps = a.ntiles * kWalkWarps;
     const int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)occ * di->sms);
-    k_place<<<(unsigned)grid, 256, 0, st>>>(a, rows, wsum, tile_sum, stage, staged_slots(r.layout));
+    if (dense)
+        k_place<<<(unsigned)grid, 256, 0, st>>>(a, rows, wsum, tile_sum, stage, kTSlotsDense);
+    else
+        k_place_masked<<<(unsigned)grid, 256, 0, st>>>(a, rows, wsum, tile_sum, masks);
     CUDA_TRY(cudaGetLastError());
     return DFA_OK;
 }
@@ -2352,7 +2431,7 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     a.pos_base = pos_base;
     a.base_in = reinterpret_cast<const unsigned long long*>(d_base);
     a.work = static_cast<unsigned long long*>(d_work);
-    if (two_pass_layout(r, t->m) && work_bytes >= work_bytes_two_pass(a.ntiles, staged_slots(r.layout)))
+    if (two_pass_layout(r, t->m) && work_bytes >= work_bytes_two_pass(a.ntiles, r.layout))
         return launch_two_pass(r, a, t, dev, di, st);
     if (r.loader == 2) return launch_tma(r, a, t, true, dev, di, st);
     KernelFn fn = pick_find(r.layout, r.threads);
@@ -2558,7 +2637,7 @@ int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg)
         Resolved r;
         if (resolve(cfg, n, n, true, sms, m, &r) == DFA_OK && two_pass_layout(r, m)) {
             const int64_t tile_bytes = (int64_t)kRows * r.chunk;
-            need = std::max(need, work_bytes_two_pass((n + tile_bytes - 1) / tile_bytes, staged_slots(r.layout)));
+            need = std::max(need, work_bytes_two_pass((n + tile_bytes - 1) / tile_bytes, r.layout));
         }
     }
     return need;

@@ -40,13 +40,19 @@ def test_candidates_respect_kernel_limits():
             assert c["threads"] in (128, 256, 512)
             assert c["chunk"] % 16 == 0 and 16 <= c["chunk"] <= 32768
             assert c["chunk"] >= 4 * (mmax - 1)       # overlap at most a quarter of a chunk
+        # both table layouts of the multi-pattern count are timed
+        assert {c["layout"] for c in cands} == {1, 2}
+        assert len({(c["threads"], c["chunk"]) for c in cands if c["layout"] == 1}) == len(cands) // 2
     for m in (4, 7, 8, 64):
+        lays = set()
         for c in autotune.single_candidates(m):
             assert c["loader"] == 2
             ch = c.get("chunk", 0)
             assert ch == 0 or (ch % 64 == 0 and 128 <= ch <= 64 * 63)
-            assert c["layout"] in (0, 1, 4)
-            assert not (c["layout"] == 4 and m < 8)
+            assert c["layout"] in (0, 1, 3, 4)
+            assert not (c["layout"] in (3, 4) and m < 8)
+            lays.add(c["layout"])
+        assert lays == ({0, 1} if m < 8 else {0, 1, 3, 4})
 
 
 def test_select_best_with_fake_timer():
@@ -90,6 +96,22 @@ def test_corrupt_cache_is_ignored(cache):
     assert autotune.lookup("x") is None
     autotune.remember("x", {"chunk": 64}, 1.0, 1)
     assert json.loads(cache.read_text())["x"]["cfg"] == {"chunk": 64}
+
+
+def test_keys_carry_the_kernel_version_and_operation():
+    k = autotune.multi_key("d", 1 << 30, 256, 64, 8000)
+    assert autotune.KERNEL_VERSION in k
+    assert autotune.single_key("d", 1 << 30, 8, "find") != autotune.single_key("d", 1 << 30, 8, "count")
+
+
+def test_forced_single_pattern_fields_do_not_reach_the_multi_count(monkeypatch):
+    # a single-pattern layout (3, 4) or loader forced for every call must not
+    # make the multi-pattern count refuse its launches
+    monkeypatch.setenv("DNADFA_CONFIG", '{"layout": 4, "loader": 2, "chunk": 768}')
+    assert autotune.forced_config() == {"layout": 4, "loader": 2, "chunk": 768}
+    assert autotune.forced_config("multi") == {"chunk": 768}
+    monkeypatch.setenv("DNADFA_CONFIG", '{"layout": 2, "threads": 256}')
+    assert autotune.forced_config("multi") == {"layout": 2, "threads": 256}
 
 
 def test_forced_config(monkeypatch):
