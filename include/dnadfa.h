@@ -171,14 +171,17 @@ int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg);
  * first min(count, cap) start positions, ascending, to d_pos[0..cap) (device,
  * int64).  When count > cap the extra positions are dropped and
  * dfa_find_status reports DFA_ETRUNC.
- *   d_work / work_bytes: caller-owned device workspace of at least
- *            dfa_find_workspace_bytes(n, cfg) bytes (tile descriptors for the
- *            ordered single-pass compaction and a status word).  Its contents
- *            need no initialisation; one workspace must not be shared by two
- *            calls that may overlap on the device.
+ *   d_work / work_bytes: caller-owned device workspace, 16-byte aligned, of
+ *            at least dfa_find_workspace_bytes(n, cfg) bytes (a status word,
+ *            per-tile totals and offsets, and per-row counts and recorded
+ *            end offsets or stage masks for the two-pass find; with room for
+ *            the tile words only, the ordered single-pass find).  Its
+ *            contents need no initialisation; one workspace must not be
+ *            shared by two calls that may overlap on the device.
  * Asynchronous on `stream`; allocates nothing.
- * Errors: DFA_EINVAL, DFA_EWORKSPACE, DFA_ECUDA.  Device-side outcomes
- * (truncation, a wait that gave up) are read with dfa_find_status.
+ * Errors: DFA_EINVAL (also an unaligned d_work), DFA_EWORKSPACE, DFA_ECUDA.
+ * Device-side outcomes (truncation, a wait that gave up) are read with
+ * dfa_find_status.
  */
 int dfa_find(const uint8_t* d_text, int64_t n, const dfa_table* table, int64_t* d_pos,
              int64_t cap, uint64_t* d_count, void* d_work, int64_t work_bytes,

@@ -1801,7 +1801,6 @@ __global__ void __launch_bounds__(1024)
     k_tile_offsets(const uint32_t* warp_sum, unsigned long long* tile_off, int64_t ntiles,
                    const unsigned long long* base_in, unsigned long long* count)
 {
-    static_assert(kWalkWarps == 16, "four 16-byte loads per tile");
     __shared__ unsigned long long s_warp[32];
     __shared__ unsigned long long s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1811,12 +1810,8 @@ __global__ void __launch_bounds__(1024)
         const int64_t t = t0 + threadIdx.x;
         unsigned long long v = 0ull;
         if (t < ntiles) {
-            const uint4* w4 = reinterpret_cast<const uint4*>(warp_sum + t * kWalkWarps);
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint4 q = w4[k];
-                v += (unsigned long long)q.x + q.y + q.z + q.w;
-            }
+            for (int k = 0; k < kWalkWarps; k++) v += warp_sum[t * kWalkWarps + k];
         }
         unsigned long long x = v;
 #pragma unroll
@@ -2351,7 +2346,7 @@ int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
 // warp of every tile][one u16 count per row of every tile][16-byte aligned:
 // layout 1, kTSlotsDense u16 end offsets per row; relaxed layouts, one u64
 // stage mask per row].
-int64_t staged_wsum_off(int64_t ntiles) { return work_bytes_for(ntiles); }
+int64_t staged_wsum_off(int64_t ntiles) { return (work_bytes_for(ntiles) + 15) & ~(int64_t)15; }
 int64_t staged_rows_off(int64_t ntiles) { return staged_wsum_off(ntiles) + ntiles * kWalkWarps * 4; }
 int64_t staged_tail_off(int64_t ntiles) { return (staged_rows_off(ntiles) + ntiles * kRows * 2 + 15) & ~(int64_t)15; }
 int64_t staged_row_bytes(int layout) { return layout == kLayoutK4 ? 2 * kTSlotsDense : 8; }
@@ -2417,6 +2412,7 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     fill_args(&a, d_text, n, n_own, t, r);
     const int64_t need = work_bytes_for(a.ntiles);
     if (work_bytes < need) return DFA_EWORKSPACE;
+    if ((reinterpret_cast<uintptr_t>(d_work) & 15u) != 0) return DFA_EINVAL;   // u64 words, 16-byte parts
     CUDA_TRY(cudaMemsetAsync(d_work, 0, (size_t)need, st));
     if (a.ntiles == 0) {
         if (d_base)

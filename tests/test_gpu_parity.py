@@ -489,6 +489,25 @@ def test_relaxed_walk_nonbase_runs(gpu):
             _check(gpu, t, pat, cfg)
 
 
+def test_unaligned_workspace_rejected(gpu):
+    # the workspace holds u64 words and 16-byte aligned parts: a pointer off
+    # a 16-byte boundary is refused before anything runs
+    import torch
+    n = 1_000_003
+    td = _dev(gpu, synth.genome_text(n, 33))
+    tab = gpu.dfa_build(b"ACGTA")
+    W = gpu.dfa_find_workspace_bytes(n)
+    buf = torch.empty(W + 16, dtype=torch.uint8, device="cuda")
+    pos = torch.empty(1 << 16, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(gpu.DfaError) as e:
+        gpu.dfa_find(td, tab, pos, cnt, buf[8:8 + W])
+    assert e.value.code == gpu.DFA_EINVAL
+    gpu.dfa_find(td, tab, pos, cnt, buf[16:16 + W])
+    rc, c = gpu.dfa_find_status(buf[16:16 + W], cnt, pos.numel())
+    assert rc == gpu.DFA_OK and c == oracle.count_brute(synth.genome_text(n, 33), b"ACGTA")
+
+
 @pytest.mark.parametrize("layout", [1, 3, 4])
 def test_single_pass_find_with_small_workspace(gpu, layout):
     # a workspace with room for the tile words only (no per-row counts) takes
