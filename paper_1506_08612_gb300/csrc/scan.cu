@@ -1249,14 +1249,16 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
     // layouts 3 and 4: relaxed walk, exact replay of the rare flagged stages;
     // dense patterns: every accept recorded inline during the walk.
     // STAGED (count mode with DENSE): pass 1 of the staged two-pass find,
-    // every exact accept recorded to the row's slots and, at the end of the
-    // tile, written out to the workspace (TmaArgs::stage)
+    // writing every row's count and each walker warp's total; on layout 1
+    // every exact accept is also recorded to the row's slots and, at the end
+    // of the tile, written out (TmaArgs::stage); the relaxed layouts leave the
+    // row's stage mask instead (TmaArgs::masks)
     constexpr bool STAGED = !FIND && DENSE;
     constexpr bool OPT = LAYOUT == kLayoutK4S || LAYOUT == kLayoutK4F;
     constexpr bool INLINE_REC = DENSE && !OPT;
     constexpr int KS = INLINE_REC ? kTSlotsDense : kTSlots;
     static_assert(!STAGED || kRPL == 1, "the staged pass writes one row per lane");
-    static_assert(!STAGED || LAYOUT == kLayoutK4, "the staged pass records inline on the four-step table");
+    static_assert(!STAGED || LAYOUT != kLayoutStt, "the staged pass walks a four-step table");
     const ScanArgs& a = p.a;
     const int nst = p.nst;
     // [tables][position slots][rings], rings 1024-byte aligned for the TMA swizzle
@@ -1682,7 +1684,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
         if (!FIND) {
 #pragma unroll
             for (int i = 0; i < kRPL; i++) total += cnt[i];
-            if (p.rows) {
+            if (STAGED) {
                 uint32_t ws = 0;
 #pragma unroll
                 for (int i = 0; i < kRPL; i++) {
@@ -1690,10 +1692,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
                     p.rows[row] = (uint16_t)cnt[i];
                     // the stages holding the row's exact accepts (all ones:
                     // the whole row), for the third pass of a relaxed layout
-                    if (p.masks && cnt[i]) p.masks[row] = OPT ? fmask[i] : ~0ull;
+                    if (OPT && cnt[i]) p.masks[row] = fmask[i];
                     ws += cnt[i];
                 }
-                if (STAGED) {
+                if (INLINE_REC) {
                     // the row's recorded end offsets (at most KS; a row with
                     // more is walked again by the third pass), packed in row
                     // order into this warp's region of the tile
@@ -2192,14 +2194,20 @@ bool tma_dense(int layout, int m)
     return m <= kDenseMaxM && (layout == kLayoutK4 || layout == kLayoutStt);
 }
 
-// staged: pass 1 of the staged two-pass find on layout 1 (count mode
-// recording every exact accept inline); the relaxed layouts' pass 1 is their
-// count kernel (with row counts and stage masks).
+// staged: pass 1 of the staged two-pass find (count mode writing row counts
+// and warp totals, and layout 1's recorded accepts or the relaxed layouts'
+// stage masks).
 TmaKernelFn pick_tma(int layout, bool find, int m, bool staged)
 {
     const bool dense = tma_dense(layout, m);
-    if (layout == kLayoutK4S) return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
-    if (layout == kLayoutK4F) return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
+    if (layout == kLayoutK4S) {
+        if (staged) return k_scan_tma<kLayoutK4S, false, true>;
+        return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
+    }
+    if (layout == kLayoutK4F) {
+        if (staged) return k_scan_tma<kLayoutK4F, false, true>;
+        return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
+    }
     if (layout == kLayoutK4) {
         if (staged) return k_scan_tma<kLayoutK4, false, true>;
         if (!find) return k_scan_tma<kLayoutK4, false, false>;
@@ -2258,13 +2266,13 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return fail("cuTensorMapEncodeTiled failed");
-    const bool staged = !find && stage != nullptr;
+    const bool staged = !find && rows != nullptr;
     TmaKernelFn fn = pick_tma(r.layout, find, t->m, staged);
     cudaFuncAttributes fa;
     CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)fn));
-    const int slot_bytes = find     ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2
-                           : staged ? kTSlotsDense * kRows * 2
-                                    : 0;
+    const int slot_bytes = find ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2
+                           : staged && r.layout == kLayoutK4 ? kTSlotsDense * kRows * 2
+                                                              : 0;
     p.rings_off = (p.table_bytes + slot_bytes + 1023) & ~1023;
     const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.rings_off;
     int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
