@@ -113,7 +113,8 @@ def config_dict(n, world, cfg):
             " 5% N (blocks mean 50 kb), seed 2", "patterns": list(PATTERN_LENGTHS),
             "pattern_seeds": list(PATTERN_SEEDS), "outputs": "count + sorted int64 start positions",
             "finds_per_step": len(PATTERN_LENGTHS), "l2": "inputs larger than L2 (no flush)",
-            "parallelism": f"replicas x{world}", "launch_config": cfg or "library default"}
+            "parallelism": f"replicas x{world}",
+            "launch_config": cfg if cfg else "library default"}
 
 
 class ClockSampler:
@@ -363,7 +364,6 @@ def run_ours(args):
     import paper_1506_08612_gb300 as dd
     import synth
 
-    cfg = json.loads(args.cfg) if args.cfg else None
     n = args.n
     seed = TEXT_SEED + 1000 * rank         # each rank scans its own replica
     host = torch.empty(n, dtype=torch.uint8, pin_memory=True)
@@ -372,18 +372,26 @@ def run_ours(args):
     patterns = [synth.pattern(m, s) for m, s in zip(PATTERN_LENGTHS, PATTERN_SEEDS)]
     tables = [dd.dfa_build(p) for p in patterns]
     stream = torch.cuda.current_stream(dev)
+    # launch configuration per pattern: library defaults, one given
+    # configuration, or "auto" (the autotuner, timed on dfa_find itself)
+    if args.cfg == "auto":
+        from paper_1506_08612_gb300 import autotune
+        cfgs = [autotune.tune_single(text, t, stream=stream, op="find") for t in tables]
+    else:
+        cfgs = [json.loads(args.cfg) if args.cfg else None] * len(tables)
+    cfg = cfgs[0] if len(set(json.dumps(c, sort_keys=True) for c in cfgs)) == 1 else cfgs
 
     # exact counts first (sizes the position buffers), untimed
-    counts = [dd.count(text, t, cfg=cfg) for t in tables]
+    counts = [dd.count(text, t, cfg=c) for t, c in zip(tables, cfgs)]
     caps = [max(16, c) for c in counts]
     pos = [torch.empty(c, dtype=torch.int64, device=dev) for c in caps]
     cnt = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in tables]
-    ws = torch.empty(dd.dfa_find_workspace_bytes(n, cfg), dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(dd.dfa_find_workspace_bytes(n, c) for c in cfgs), dtype=torch.uint8, device=dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in tables]
 
     def step():
         for i, t in enumerate(tables):
-            dd.dfa_find(text, t, pos[i], cnt[i], ws, cfg=cfg, stream=stream)
+            dd.dfa_find(text, t, pos[i], cnt[i], ws, cfg=cfgs[i], stream=stream)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -423,7 +431,7 @@ def run_ours(args):
     for _ in range(args.steps):
         for i, t in enumerate(tables):
             ev[i][0].record(stream)
-            dd.dfa_find(text, t, pos[i], cnt[i], ws, cfg=cfg, stream=stream)
+            dd.dfa_find(text, t, pos[i], cnt[i], ws, cfg=cfgs[i], stream=stream)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         k_ms.append([ev[i][0].elapsed_time(ev[i][1]) for i in range(len(tables))])
@@ -435,6 +443,8 @@ def run_ours(args):
             "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
             "kernel": DOMINANT_KERNEL, "peak_kind": f"{peak_kind} (hbm_gbs copy bandwidth)",
             "per_pattern_ms": [round(float(np.mean([r[i] for r in k_ms])), 4) for i in range(len(tables))],
+            "per_pattern_frac": [round((n + 8 * counts[i]) / (float(np.mean([r[i] for r in k_ms])) * 1e-3) / 1e9
+                                       / peak, 4) for i in range(len(tables))],
             "algorithmic_bytes_per_launch": "n + 8 * count (text read once, positions written)"}
 
     e2e = None
@@ -483,7 +493,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
                 "data": "synthetic", "config": config_dict(n, world, cfg), "clocks": clk,
-                "e2e": e2e, "gpu_launches": args.steps * sum(kernels_per_find(m, cfg) for m in PATTERN_LENGTHS),
+                "e2e": e2e, "gpu_launches": args.steps * sum(kernels_per_find(m, c) for m, c in zip(PATTERN_LENGTHS, cfgs)),
                 "roofline": roof,
                 "cpu_baseline": cpu, "counts": counts, "workloads": workloads}
         print(json.dumps(line), flush=True)

@@ -166,8 +166,8 @@ int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg);
 
 /*
  * Count and locate every occurrence (overlaps included) of the table's
- * pattern in d_text[0..n) (Algorithm 1: "count of pattern matches and their
- * location").  Writes the exact count to *d_count (device, uint64) and the
+ * pattern in d_text[0..n) (Algorithm 1's two outputs: the number of matches
+ * and where they are).  Writes the exact count to *d_count (device, uint64) and the
  * first min(count, cap) start positions, ascending, to d_pos[0..cap) (device,
  * int64).  When count > cap the extra positions are dropped and
  * dfa_find_status reports DFA_ETRUNC.

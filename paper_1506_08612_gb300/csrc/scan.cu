@@ -1227,8 +1227,10 @@ __device__ __forceinline__ bool pend_over(uint32_t pr) { return (pr >> 31) != 0u
 template <int LAYOUT, bool FIND, bool DENSE>
 // A count has static tiles and no offsets to resolve: its CTA is the 16
 // walker warps alone (128 registers a thread); a find adds the ticket and
-// scheduler warps (96 registers a thread).
-__global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, 1)
+// scheduler warps (96 registers a thread).  The staged pass of layout 1 runs
+// two CTAs per SM (64 registers a thread, 32 walker warps to hide its table
+// lookups behind: 3.2e9 bytes, m = 4, find 0.934 -> 0.852 ms).
+__global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && DENSE && LAYOUT == kLayoutK4) ? 2 : 1)
     k_scan_tma(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TmaArgs p)
 {
     uint8_t* smem = g_smem;
@@ -2281,13 +2283,17 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     // than with four (3.2e9 bytes, m = 16: 0.572 against 0.603 ms; the exact
     // count is the same with 2, 3 or 4)
     if (!find && (r.layout == kLayoutK4F || r.layout == kLayoutK4S)) nst = std::min(nst, kRelaxedCountStages);
+    // the staged pass of layout 1: two CTAs per SM, each with two-stage rings
+    const int ctas = staged && r.layout == kLayoutK4 ? 2 : 1;
+    if (ctas == 2) nst = std::min(nst, 2);
     p.nst = nst;
     p.ahead = std::min(3 + (nst - 1) / (p.sps + 1), kTicketRing);
     const int smem = p.rings_off + kWalkWarps * nst * kWarpStage;
     const int threads = find ? kTmaThreads : kWalkThreads;
     int occ = occupancy((const void*)fn, threads, smem, dev, di->smem_optin);
     if (occ <= 0) return fail("TMA scan kernel does not fit on an SM (occupancy 0)");
-    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)di->sms);
+    if (occ < ctas) return fail("TMA scan kernel: two CTAs do not fit on an SM");
+    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)di->sms * ctas);
     fn<<<(unsigned)grid, threads, smem, st>>>(map, p);
     CUDA_TRY(cudaGetLastError());
     return DFA_OK;
