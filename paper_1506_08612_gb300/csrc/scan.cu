@@ -817,9 +817,10 @@ struct TmaArgs {
     // word (bit 1), or bit 63 of the count for a count without workspace
     unsigned long long* fail_word;
     unsigned long long fail_bit;
-    // count mode, first pass of a two-pass find: every row's count (u16)
-    // goes here; null otherwise
+    // count mode, first pass of a two-pass find: every row's count (u16) and
+    // every tile's total (added up) go here; null otherwise
     uint16_t* rows;
+    unsigned long long* tile_sum;
     // and the rows' exact accept end offsets (u16, relative to the row
     // start): each walker warp of tile t writes those of its 32 rows, at most
     // KS a row, packed in row order into its own region of 32 * KS entries
@@ -1719,7 +1720,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
-                if (lane == 0) p.warp_sum[(size_t)tile * kWalkWarps + warp] = ws;
+                if (lane == 0) {
+                    p.warp_sum[(size_t)tile * kWalkWarps + warp] = ws;
+                    if (ws) atomicAdd(p.tile_sum + tile, (unsigned long long)ws);
+                }
             }
         } else {
             // exclusive offsets of this lane's rows among the warp's rows
@@ -1798,12 +1802,11 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
 // each writing its positions at its own offset (pass 3).  Sparse patterns
 // have few such rows, so the find costs little more than the count.
 
-// Pass 2 (one CTA of 1024 threads): tile_off[t] becomes the global index of
-// tile t's first position (base included), from the tile's walker-warp
-// totals warp_sum[t * kWalkWarps ...]; *count becomes base + total.
+// Pass 2 (one CTA of 1024 threads): tile_sum[t] becomes the global index of
+// tile t's first position (base included); *count becomes base + total.
 __global__ void __launch_bounds__(1024)
-    k_tile_offsets(const uint32_t* warp_sum, unsigned long long* tile_off, int64_t ntiles,
-                   const unsigned long long* base_in, unsigned long long* count)
+    k_tile_offsets(unsigned long long* tile_sum, int64_t ntiles, const unsigned long long* base_in,
+                   unsigned long long* count)
 {
     __shared__ unsigned long long s_warp[32];
     __shared__ unsigned long long s_carry;
@@ -1812,11 +1815,7 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
     for (int64_t t0 = 0; t0 < ntiles; t0 += 1024) {
         const int64_t t = t0 + threadIdx.x;
-        unsigned long long v = 0ull;
-        if (t < ntiles) {
-#pragma unroll
-            for (int k = 0; k < kWalkWarps; k++) v += warp_sum[t * kWalkWarps + k];
-        }
+        const unsigned long long v = t < ntiles ? tile_sum[t] : 0ull;
         unsigned long long x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1837,7 +1836,7 @@ __global__ void __launch_bounds__(1024)
         __syncthreads();
         const unsigned long long carry = s_carry;
         const unsigned long long excl = carry + (warp ? s_warp[warp - 1] : 0ull) + x - v;
-        if (t < ntiles) tile_off[t] = excl;
+        if (t < ntiles) tile_sum[t] = excl;
         __syncthreads();
         if (threadIdx.x == 1023) s_carry = excl + v;
         __syncthreads();
@@ -1857,48 +1856,76 @@ __global__ void __launch_bounds__(1024)
 // them that holds all its occurrences), found by the whole warp and written
 // in order from index g0: lane l takes the l-th slice of the starts and reads
 // m - 1 bytes past it (Algorithm 1 within the range), walking exactly with
-// the single-step table from global memory; a count, a warp scan, then the
-// same walk writing the positions.
-__device__ __noinline__ void place_range(const ScanArgs& a, int64_t s, int64_t e, int64_t g0, int lane)
+// the single-step table (shared memory) over 16-byte loads of the text (16-B
+// aligned: the staged find runs on aligned texts only).  The first four
+// occurrences of each slice are kept in registers, so one walk serves count
+// and positions; a slice with more walks again after the warp's scan.
+// One lane's slice of place_range: the starts [ls, le), bytes read up to hi.
+// WRITE: every position to pos[g ...]; else the count, the first four
+// positions kept in k0..k3.
+template <bool WRITE>
+__device__ __forceinline__ uint32_t place_slice(const ScanArgs& a, const uint8_t* d1s, int64_t ls, int64_t le,
+                                                int64_t hi, int64_t g, int64_t (&keep)[4])
 {
-    const uint8_t* d1 = a.tab + a.k4_bytes;              // (m+1) x 4 single steps, by 2-bit code
     const uint32_t m = (uint32_t)a.m;
+    uint32_t c = 0, q = 0;
+    if (ls >= le) return 0;
+    for (int64_t base = ls & ~(int64_t)15; base < hi; base += 16) {
+        uint4 v;
+        if (base + 16 <= a.n) {
+            v = ldg16(reinterpret_cast<const uint4*>(a.text + base));
+        } else {                                  // the text's last bytes: no read past n
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            for (int64_t j = base; j < a.n; j++) w[(j - base) >> 2] |= (uint32_t)__ldg(a.text + j) << (8 * ((j - base) & 3));
+            v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        const int64_t j0 = max(ls, base), j1 = min(hi, base + 16);
+        for (int64_t j = j0; j < j1; j++) {
+            const uint32_t off = (uint32_t)(j - base);
+            const uint32_t wd = off < 8u ? (off < 4u ? v.x : v.y) : (off < 12u ? v.z : v.w);
+            const uint32_t b = (wd >> (8u * (off & 3u))) & 0xFFu;
+            const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
+            q = ((b ^ (t * 0x11u)) & 0xD9u) == 0x41u ? (uint32_t)d1s[q * 4u + ((b >> 1) & 3u)] : 0u;
+            if (q == m) {
+                const int64_t st = a.pos_base + j - (int64_t)(m - 1);
+                if (WRITE) {
+                    if (g + c < a.cap) a.pos[g + c] = st;
+                } else if (c < 4u) {
+                    keep[c] = st;
+                }
+                c++;
+            }
+        }
+    }
+    return c;
+}
+
+__device__ __noinline__ void place_range(const ScanArgs& a, const uint8_t* d1s, int64_t s, int64_t e, int64_t g0,
+                                         int lane)
+{
     const int64_t span = (e - s + 31) / 32;
     const int64_t ls = min(s + lane * span, e), le = min(ls + span, e);
-    const int64_t hi = min(le + (int64_t)m - 1, a.n);
-    uint32_t c = 0;
-    for (int pass = 0; pass < 2; pass++) {
-        int64_t g = 0;
-        if (pass == 1) {
-            uint32_t x = c;
+    const int64_t hi = min(le + (int64_t)a.m - 1, a.n);
+    int64_t keep[4];
+    const uint32_t c = place_slice<false>(a, d1s, ls, le, hi, 0, keep);
+    uint32_t x = c;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            g = g0 + (int64_t)(x - c);
-        }
-        uint32_t q = 0;
-        if (ls < le) {
-            for (int64_t j = ls; j < hi; j++) {
-                const uint32_t b = __ldg(a.text + j);
-                const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
-                q = ((b ^ (t * 0x11u)) & 0xD9u) == 0x41u ? (uint32_t)__ldg(d1 + q * 4u + ((b >> 1) & 3u)) : 0u;
-                if (q == m) {
-                    if (pass == 0) {
-                        c++;
-                    } else {
-                        if (g < a.cap) a.pos[g] = a.pos_base + j - (int64_t)(m - 1);
-                        g++;
-                    }
-                }
-            }
-        }
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int64_t g = g0 + (int64_t)(x - c);
+    if (c <= 4u) {
+        for (uint32_t k = 0; k < c; k++)
+            if (g + k < a.cap) a.pos[g + k] = keep[k];
+    } else {
+        place_slice<true>(a, d1s, ls, le, hi, g, keep);
     }
 }
 
 // The unit's rows: (row start, own end of the row, first index, count) for
-// this lane, or false when the unit holds no accepts.
+// this lane, or false when the unit holds no accepts.  The tile's offsets,
+// the warp totals and the row counts are loaded together.
 struct PlaceRow {
     int64_t rs, re, g0;
     uint32_t rc;
@@ -1911,14 +1938,15 @@ __device__ __forceinline__ bool place_row(const ScanArgs& a, const uint16_t* row
     const int64_t tile = u / kWalkWarps;
     const int w = (int)(u % kWalkWarps);
     const unsigned long long off = tile_off[tile];
-    if (off == (tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all)) return false;   // no accepts in the tile
-    // this warp's total and the totals of the tile's earlier warps
+    const unsigned long long nxt = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
     const uint32_t wt = lane < kWalkWarps ? warp_sum[tile * kWalkWarps + lane] : 0u;
+    pr.rc = rows[tile * kRows + w * 32 + lane];
+    if (off == nxt) return false;                         // no accepts in the tile
     if (__shfl_sync(0xffffffffu, wt, w) == 0u) return false;
+    // the totals of the tile's earlier warps
     uint32_t before = lane < w ? wt : 0u;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
-    pr.rc = rows[tile * kRows + w * 32 + lane];
     uint32_t x = pr.rc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1931,11 +1959,21 @@ __device__ __forceinline__ bool place_row(const ScanArgs& a, const uint16_t* row
     return true;
 }
 
+// The single-step table of the pattern, (m+1) x 4 bytes, into shared memory.
+__device__ __forceinline__ const uint8_t* place_table(const ScanArgs& a)
+{
+    __shared__ uint8_t d1s[(DFA_MAX_M + 1) * 4];
+    for (int i = threadIdx.x; i < (a.m + 1) * 4; i += blockDim.x) d1s[i] = a.tab[a.k4_bytes + i];
+    __syncthreads();
+    return d1s;
+}
+
 // Layout 1: copy the staged offsets; rows past their ks slots walked again.
 __global__ void __launch_bounds__(256)
     k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const uint32_t* warp_sum,
             const unsigned long long* tile_off, const uint16_t* stage, int ks)
 {
+    const uint8_t* d1s = place_table(a);
     const int lane = threadIdx.x & 31;
     const int64_t units = a.ntiles * kWalkWarps;
     const unsigned long long end_all = *a.count;
@@ -1962,7 +2000,7 @@ __global__ void __launch_bounds__(256)
         while (over) {
             const int r = __ffs(over) - 1;
             over &= over - 1u;
-            place_range(a, __shfl_sync(0xffffffffu, pr.rs, r), __shfl_sync(0xffffffffu, pr.re, r),
+            place_range(a, d1s, __shfl_sync(0xffffffffu, pr.rs, r), __shfl_sync(0xffffffffu, pr.re, r),
                         __shfl_sync(0xffffffffu, pr.g0, r), lane);
         }
     }
@@ -1976,6 +2014,7 @@ __global__ void __launch_bounds__(256)
     k_place_masked(const __grid_constant__ ScanArgs a, const uint16_t* rows, const uint32_t* warp_sum,
                    const unsigned long long* tile_off, const unsigned long long* masks)
 {
+    const uint8_t* d1s = place_table(a);
     const int lane = threadIdx.x & 31;
     const int64_t units = a.ntiles * kWalkWarps;
     const unsigned long long end_all = *a.count;
@@ -1997,7 +2036,7 @@ __global__ void __launch_bounds__(256)
         while (todo) {
             const int r = __ffs(todo) - 1;
             todo &= todo - 1u;
-            place_range(a, __shfl_sync(0xffffffffu, s, r), __shfl_sync(0xffffffffu, e, r),
+            place_range(a, d1s, __shfl_sync(0xffffffffu, s, r), __shfl_sync(0xffffffffu, e, r),
                         __shfl_sync(0xffffffffu, pr.g0, r), lane);
         }
     }
@@ -2256,6 +2295,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.fail_word = find || rows ? a.work + 1 : a.count;
     p.fail_bit = find || rows ? 2ull : (1ull << 63);
     p.rows = rows;
+    p.tile_sum = rows ? a.work + kWorkHeader : nullptr;
     p.stage = stage;
     p.masks = masks;
     p.warp_sum = warp_sum;
@@ -2394,7 +2434,7 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
     a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
     int rc = launch_tma(r, a1, t, false, dev, di, st, rows, stage, wsum, masks);
     if (rc) return rc;
-    k_tile_offsets<<<1, 1024, 0, st>>>(wsum, tile_sum, a.ntiles, a.base_in, a.count);
+    k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
     CUDA_TRY(cudaGetLastError());
     const void* fn = dense ? (const void*)k_place : (const void*)k_place_masked;
     int occ = occupancy(fn, 256, 0, dev, di->smem_optin);
