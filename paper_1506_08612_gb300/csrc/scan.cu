@@ -821,17 +821,15 @@ struct TmaArgs {
     // every tile's total (added up) go here; null otherwise
     uint16_t* rows;
     unsigned long long* tile_sum;
-    // and the rows' exact accept end offsets (u16, relative to the row
-    // start): each walker warp of tile t writes those of its 32 rows, at most
-    // KS a row, packed in row order into its own region of 32 * KS entries
-    // at stage + (t * kWalkWarps + warp) * 32 * KS (layout 1); or, for the
-    // relaxed layouts, every row with a count has the mask of the 64-byte
+    // and either (layout 1) the rows' exact accept end offsets (u16, relative
+    // to the row start): each walker warp of tile t writes those of its 32
+    // rows, at most KS a row, packed in row order into its own region of
+    // 32 * KS entries at stage + (t * kWalkWarps + warp) * 32 * KS; or
+    // (relaxed layouts) for every row with a count the mask of the 64-byte
     // stages holding its exact accepts at masks[row] (bit s: body stage s; bit
-    // sps: the overlap; all ones: the whole row); and each warp's total count
-    // goes to warp_sum[t * kWalkWarps + warp]
+    // sps: the overlap; all ones: the whole row)
     uint16_t* stage;
     unsigned long long* masks;
-    uint32_t* warp_sum;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -1251,17 +1249,16 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
 
     // layouts 3 and 4: relaxed walk, exact replay of the rare flagged stages;
     // dense patterns: every accept recorded inline during the walk.
-    // STAGED (count mode with DENSE): pass 1 of the staged two-pass find,
-    // writing every row's count and each walker warp's total; on layout 1
-    // every exact accept is also recorded to the row's slots and, at the end
-    // of the tile, written out (TmaArgs::stage); the relaxed layouts leave the
-    // row's stage mask instead (TmaArgs::masks)
+    // STAGED (count mode with DENSE, layout 1): pass 1 of the two-pass find
+    // of a dense pattern, every exact accept recorded to the row's slots and,
+    // at the end of the tile, written out (TmaArgs::stage).  The relaxed
+    // layouts' pass 1 is their count kernel with TmaArgs::rows set.
     constexpr bool STAGED = !FIND && DENSE;
     constexpr bool OPT = LAYOUT == kLayoutK4S || LAYOUT == kLayoutK4F;
     constexpr bool INLINE_REC = DENSE && !OPT;
     constexpr int KS = INLINE_REC ? kTSlotsDense : kTSlots;
     static_assert(!STAGED || kRPL == 1, "the staged pass writes one row per lane");
-    static_assert(!STAGED || LAYOUT != kLayoutStt, "the staged pass walks a four-step table");
+    static_assert(!STAGED || LAYOUT == kLayoutK4, "the staged pass records on the four-step table");
     const ScanArgs& a = p.a;
     const int nst = p.nst;
     // [tables][position slots][rings], rings 1024-byte aligned for the TMA swizzle
@@ -1687,7 +1684,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
         if (!FIND) {
 #pragma unroll
             for (int i = 0; i < kRPL; i++) total += cnt[i];
-            if (STAGED) {
+            if (STAGED || p.rows) {
                 uint32_t ws = 0;
 #pragma unroll
                 for (int i = 0; i < kRPL; i++) {
@@ -1695,10 +1692,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
                     p.rows[row] = (uint16_t)cnt[i];
                     // the stages holding the row's exact accepts (all ones:
                     // the whole row), for the third pass of a relaxed layout
-                    if (OPT && cnt[i]) p.masks[row] = fmask[i];
+                    if (OPT && p.masks && cnt[i]) p.masks[row] = fmask[i];
                     ws += cnt[i];
                 }
-                if (INLINE_REC) {
+                if (STAGED && INLINE_REC) {
                     // the row's recorded end offsets (at most KS; a row with
                     // more is walked again by the third pass), packed in row
                     // order into this warp's region of the tile
@@ -1720,10 +1717,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
-                if (lane == 0) {
-                    p.warp_sum[(size_t)tile * kWalkWarps + warp] = ws;
-                    if (ws) atomicAdd(p.tile_sum + tile, (unsigned long long)ws);
-                }
+                if (lane == 0 && ws) atomicAdd(p.tile_sum + tile, (unsigned long long)ws);
             }
         } else {
             // exclusive offsets of this lane's rows among the warp's rows
@@ -1860,9 +1854,11 @@ __global__ void __launch_bounds__(1024)
 // aligned: the staged find runs on aligned texts only).  The first four
 // occurrences of each slice are kept in registers, so one walk serves count
 // and positions; a slice with more walks again after the warp's scan.
-// One lane's slice of place_range: the starts [ls, le), bytes read up to hi.
+// An exact walk of the starts [ls, le) by one lane, reading bytes up to hi
+// in 16-byte loads (16-B aligned: the two-pass find runs on aligned texts
+// only; never past n) with the single-step table d1s in shared memory.
 // WRITE: every position to pos[g ...]; else the count, the first four
-// positions kept in k0..k3.
+// positions kept in keep.
 template <bool WRITE>
 __device__ __forceinline__ uint32_t place_slice(const ScanArgs& a, const uint8_t* d1s, int64_t ls, int64_t le,
                                                 int64_t hi, int64_t g, int64_t (&keep)[4])
@@ -1900,63 +1896,12 @@ __device__ __forceinline__ uint32_t place_slice(const ScanArgs& a, const uint8_t
     return c;
 }
 
-__device__ __noinline__ void place_range(const ScanArgs& a, const uint8_t* d1s, int64_t s, int64_t e, int64_t g0,
-                                         int lane)
+// Every occurrence starting in [s, e), walked by one lane alone (through
+// min(e + m - 1, n)) and written in order from index g.
+__device__ __noinline__ void place_row_lane(const ScanArgs& a, const uint8_t* d1s, int64_t s, int64_t e, int64_t g)
 {
-    const int64_t span = (e - s + 31) / 32;
-    const int64_t ls = min(s + lane * span, e), le = min(ls + span, e);
-    const int64_t hi = min(le + (int64_t)a.m - 1, a.n);
     int64_t keep[4];
-    const uint32_t c = place_slice<false>(a, d1s, ls, le, hi, 0, keep);
-    uint32_t x = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    const int64_t g = g0 + (int64_t)(x - c);
-    if (c <= 4u) {
-        for (uint32_t k = 0; k < c; k++)
-            if (g + k < a.cap) a.pos[g + k] = keep[k];
-    } else {
-        place_slice<true>(a, d1s, ls, le, hi, g, keep);
-    }
-}
-
-// The unit's rows: (row start, own end of the row, first index, count) for
-// this lane, or false when the unit holds no accepts.  The tile's offsets,
-// the warp totals and the row counts are loaded together.
-struct PlaceRow {
-    int64_t rs, re, g0;
-    uint32_t rc;
-};
-
-__device__ __forceinline__ bool place_row(const ScanArgs& a, const uint16_t* rows, const uint32_t* warp_sum,
-                                          const unsigned long long* tile_off, unsigned long long end_all, int64_t u,
-                                          int lane, PlaceRow& pr)
-{
-    const int64_t tile = u / kWalkWarps;
-    const int w = (int)(u % kWalkWarps);
-    const unsigned long long off = tile_off[tile];
-    const unsigned long long nxt = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
-    const uint32_t wt = lane < kWalkWarps ? warp_sum[tile * kWalkWarps + lane] : 0u;
-    pr.rc = rows[tile * kRows + w * 32 + lane];
-    if (off == nxt) return false;                         // no accepts in the tile
-    if (__shfl_sync(0xffffffffu, wt, w) == 0u) return false;
-    // the totals of the tile's earlier warps
-    uint32_t before = lane < w ? wt : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
-    uint32_t x = pr.rc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    pr.rs = (tile * kRows + w * 32 + lane) * a.chunk;
-    pr.re = min(pr.rs + a.chunk, a.n_own);
-    pr.g0 = (int64_t)(off + before + x - pr.rc);
-    return true;
+    place_slice<true>(a, d1s, s, e, min(e + (int64_t)a.m - 1, a.n), g, keep);
 }
 
 // The single-step table of the pattern, (m+1) x 4 bytes, into shared memory.
@@ -1968,76 +1913,125 @@ __device__ __forceinline__ const uint8_t* place_table(const ScanArgs& a)
     return d1s;
 }
 
-// Layout 1: copy the staged offsets; rows past their ks slots walked again.
-__global__ void __launch_bounds__(256)
-    k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const uint32_t* warp_sum,
-            const unsigned long long* tile_off, const uint16_t* stage, int ks)
+// A tile's 512 row counts, 16 a lane (lane l: rows 16 l .. 16 l + 15, from
+// two 16-byte loads), and the lane's first index within the tile (an
+// exclusive warp scan of the lanes' sums).
+__device__ __forceinline__ uint32_t tile_rows(const uint16_t* rows, int64_t tile, int lane, uint32_t (&c)[16])
 {
+    const uint4* src = reinterpret_cast<const uint4*>(rows + tile * kRows + lane * 16);
+    const uint4 u = src[0], v = src[1];
+    const uint32_t w[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+    uint32_t tot = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        c[2 * k] = w[k] & 0xFFFFu;
+        c[2 * k + 1] = w[k] >> 16;
+        tot += c[2 * k] + c[2 * k + 1];
+    }
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x - tot;
+}
+
+// Pass 3 of the two-pass find, one warp per tile (tiles without accepts are
+// skipped on their offsets alone).  A row's first index is its tile's offset
+// (pass 2) + a scan of the tile's row counts.
+
+// Layout 1: the count pass staged each row's exact end offsets (up to
+// kTSlotsDense), packed in row order in its walker warp's region (rows
+// 32 w .. 32 w + 31 of the tile, lanes 2w and 2w + 1 here): they are copied.
+// Rows past their slots are walked again, each by its lane.
+__global__ void __launch_bounds__(256, 2)
+    k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
+            const uint16_t* stage)
+{
+    constexpr uint32_t KS = kTSlotsDense;
     const uint8_t* d1s = place_table(a);
     const int lane = threadIdx.x & 31;
-    const int64_t units = a.ntiles * kWalkWarps;
     const unsigned long long end_all = *a.count;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units;
-         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        PlaceRow pr;
-        if (!place_row(a, rows, warp_sum, tile_off, end_all, u, lane, pr)) continue;
-        const uint32_t st = min(pr.rc, (uint32_t)ks);
-        uint32_t y = st;
+    const int64_t C = a.chunk;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < a.ntiles;
+         tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const unsigned long long off = tile_off[tile];
+        if (off == (tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all)) continue;
+        uint32_t c[16];
+        const uint32_t excl = tile_rows(rows, tile, lane, c);
+        // staged entries before this lane's rows in its walker warp's region
+        uint32_t st = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, y, o);
-            if (lane >= o) y += v;
-        }
-        const int64_t start0 = a.pos_base + pr.rs - (int64_t)(a.m - 1);
-        if (pr.rc != 0u && pr.rc <= (uint32_t)ks) {
-            const uint16_t* src = stage + u * (32 * (int64_t)ks) + (y - st);
-            for (uint32_t j = 0; j < pr.rc; j++) {
-                const int64_t g = pr.g0 + j;
-                if (g < a.cap) a.pos[g] = start0 + src[j];
+        for (int k = 0; k < 16; k++) st += min(c[k], KS);
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, st, 1);
+        const uint16_t* src = stage + ((size_t)tile * kWalkWarps + (lane >> 1)) * (32 * KS) + ((lane & 1) ? nb : 0u);
+        int64_t g = (int64_t)(off + excl);
+        uint32_t over = 0;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            if (c[k] <= KS) {
+                const int64_t start0 = a.pos_base + (tile * kRows + lane * 16 + k) * C - (int64_t)(a.m - 1);
+                for (uint32_t j = 0; j < c[k]; j++)
+                    if (g + j < a.cap) a.pos[g + j] = start0 + src[j];
+                src += c[k];
+            } else {
+                over |= 1u << k;
+                src += KS;
             }
+            g += c[k];
         }
-        uint32_t over = __ballot_sync(0xffffffffu, pr.rc > (uint32_t)ks);
-        while (over) {
-            const int r = __ffs(over) - 1;
-            over &= over - 1u;
-            place_range(a, d1s, __shfl_sync(0xffffffffu, pr.rs, r), __shfl_sync(0xffffffffu, pr.re, r),
-                        __shfl_sync(0xffffffffu, pr.g0, r), lane);
+        // rows past their slots: walked again, each by its lane
+        if (over) {
+            int64_t gk = (int64_t)(off + excl);
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                if ((over >> k) & 1u) {
+                    const int64_t rs = (tile * kRows + lane * 16 + k) * C;
+                    place_row_lane(a, d1s, rs, min(rs + C, a.n_own), gk);
+                }
+                gk += c[k];
+            }
         }
     }
 }
 
-// Relaxed layouts: every row with accepts walked again over the bytes its
-// stage mask names: the starts from m - 1 bytes before its first masked
-// stage to the end of its last one (every accept of the row ends in a masked
-// stage, and every occurrence starting there is one of them).
-__global__ void __launch_bounds__(256)
-    k_place_masked(const __grid_constant__ ScanArgs a, const uint16_t* rows, const uint32_t* warp_sum,
-                   const unsigned long long* tile_off, const unsigned long long* masks)
+// Relaxed layouts: every row with accepts walked again, each by the lane
+// that holds its count, over the bytes its stage mask names: the starts from
+// m - 1 bytes before its first masked stage to the end of its last one (every
+// accept of the row ends in a masked stage, and every occurrence starting
+// there is one of them).  Sparse patterns leave a few such rows a tile, so
+// the lanes walk them side by side.
+__global__ void __launch_bounds__(256, 2)
+    k_place_masked(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
+                   const unsigned long long* masks)
 {
     const uint8_t* d1s = place_table(a);
     const int lane = threadIdx.x & 31;
-    const int64_t units = a.ntiles * kWalkWarps;
     const unsigned long long end_all = *a.count;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units;
-         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        PlaceRow pr;
-        if (!place_row(a, rows, warp_sum, tile_off, end_all, u, lane, pr)) continue;
-        int64_t s = pr.rs, e = pr.re;
-        if (pr.rc) {
-            const unsigned long long mask = masks[(u / kWalkWarps) * kRows + (u % kWalkWarps) * 32 + lane];
-            if (mask != ~0ull) {
-                const int64_t lo_stage = __ffsll((long long)mask) - 1;
-                const int64_t hi_stage = 63 - __clzll((long long)mask);
-                s = max(pr.rs, pr.rs + lo_stage * kStageW - (int64_t)(a.m - 1));
-                e = min(e, pr.rs + (hi_stage + 1) * kStageW);
+    const int64_t C = a.chunk;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < a.ntiles;
+         tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const unsigned long long off = tile_off[tile];
+        if (off == (tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all)) continue;
+        uint32_t c[16];
+        int64_t g = (int64_t)(off + tile_rows(rows, tile, lane, c));
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            if (c[k]) {
+                const int64_t row = tile * kRows + lane * 16 + k;
+                const int64_t rs = row * C;
+                int64_t s = rs, e = min(rs + C, a.n_own);
+                const unsigned long long mask = masks[row];
+                if (mask != ~0ull) {
+                    const int64_t lo_stage = __ffsll((long long)mask) - 1;
+                    const int64_t hi_stage = 63 - __clzll((long long)mask);
+                    s = max(rs, rs + lo_stage * kStageW - (int64_t)(a.m - 1));
+                    e = min(e, rs + (hi_stage + 1) * kStageW);
+                }
+                place_row_lane(a, d1s, s, e, g);
+                g += c[k];
             }
-        }
-        uint32_t todo = __ballot_sync(0xffffffffu, pr.rc != 0u);
-        while (todo) {
-            const int r = __ffs(todo) - 1;
-            todo &= todo - 1u;
-            place_range(a, d1s, __shfl_sync(0xffffffffu, s, r), __shfl_sync(0xffffffffu, e, r),
-                        __shfl_sync(0xffffffffu, pr.g0, r), lane);
         }
     }
 }
@@ -2235,20 +2229,14 @@ bool tma_dense(int layout, int m)
     return m <= kDenseMaxM && (layout == kLayoutK4 || layout == kLayoutStt);
 }
 
-// staged: pass 1 of the staged two-pass find (count mode writing row counts
-// and warp totals, and layout 1's recorded accepts or the relaxed layouts'
-// stage masks).
+// staged: pass 1 of the two-pass find of a dense pattern on layout 1 (count
+// mode recording every exact accept); the relaxed layouts' pass 1 is their
+// count kernel.
 TmaKernelFn pick_tma(int layout, bool find, int m, bool staged)
 {
     const bool dense = tma_dense(layout, m);
-    if (layout == kLayoutK4S) {
-        if (staged) return k_scan_tma<kLayoutK4S, false, true>;
-        return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
-    }
-    if (layout == kLayoutK4F) {
-        if (staged) return k_scan_tma<kLayoutK4F, false, true>;
-        return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
-    }
+    if (layout == kLayoutK4S) return find ? k_scan_tma<kLayoutK4S, true, false> : k_scan_tma<kLayoutK4S, false, false>;
+    if (layout == kLayoutK4F) return find ? k_scan_tma<kLayoutK4F, true, false> : k_scan_tma<kLayoutK4F, false, false>;
     if (layout == kLayoutK4) {
         if (staged) return k_scan_tma<kLayoutK4, false, true>;
         if (!find) return k_scan_tma<kLayoutK4, false, false>;
@@ -2279,7 +2267,7 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
 // Launch the TMA-staged kernel for the filled-in arguments `a`.
 int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
                const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr, uint16_t* stage = nullptr,
-               uint32_t* warp_sum = nullptr, unsigned long long* masks = nullptr)
+               unsigned long long* masks = nullptr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
     int rc = tensor_map_encoder(&encode);
@@ -2298,7 +2286,6 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.tile_sum = rows ? a.work + kWorkHeader : nullptr;
     p.stage = stage;
     p.masks = masks;
-    p.warp_sum = warp_sum;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
@@ -2308,13 +2295,13 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return fail("cuTensorMapEncodeTiled failed");
-    const bool staged = !find && rows != nullptr;
+    const bool staged = !find && stage != nullptr;
     TmaKernelFn fn = pick_tma(r.layout, find, t->m, staged);
     cudaFuncAttributes fa;
     CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)fn));
-    const int slot_bytes = find ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2
-                           : staged && r.layout == kLayoutK4 ? kTSlotsDense * kRows * 2
-                                                              : 0;
+    const int slot_bytes = find     ? kDefer * (tma_dense(r.layout, t->m) ? kTSlotsDense : kTSlots) * kRows * 2
+                           : staged ? kTSlotsDense * kRows * 2
+                                    : 0;
     p.rings_off = (p.table_bytes + slot_bytes + 1023) & ~1023;
     const int budget = di->smem_optin - (int)fa.sharedSizeBytes - p.rings_off;
     int nst = std::min(budget / (kWalkWarps * kWarpStage), kMaxStages);
@@ -2324,7 +2311,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     // count is the same with 2, 3 or 4)
     if (!find && (r.layout == kLayoutK4F || r.layout == kLayoutK4S)) nst = std::min(nst, kRelaxedCountStages);
     // the staged pass of layout 1: two CTAs per SM, each with two-stage rings
-    const int ctas = staged && r.layout == kLayoutK4 ? 2 : 1;
+    const int ctas = staged ? 2 : 1;
     if (ctas == 2) nst = std::min(nst, 2);
     p.nst = nst;
     p.ahead = std::min(3 + (nst - 1) / (p.sps + 1), kTicketRing);
@@ -2396,12 +2383,10 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
 
 int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
 
-// Staged two-pass find: [header][one word per tile][one u32 total per walker
-// warp of every tile][one u16 count per row of every tile][16-byte aligned:
-// layout 1, kTSlotsDense u16 end offsets per row; relaxed layouts, one u64
-// stage mask per row].
-int64_t staged_wsum_off(int64_t ntiles) { return (work_bytes_for(ntiles) + 15) & ~(int64_t)15; }
-int64_t staged_rows_off(int64_t ntiles) { return staged_wsum_off(ntiles) + ntiles * kWalkWarps * 4; }
+// Two-pass find: [header][one word per tile][one u16 count per row of every
+// tile, 16-byte aligned][16-byte aligned: layout 1, kTSlotsDense u16 end
+// offsets per row; relaxed layouts, one u64 stage mask per row].
+int64_t staged_rows_off(int64_t ntiles) { return (work_bytes_for(ntiles) + 15) & ~(int64_t)15; }
 int64_t staged_tail_off(int64_t ntiles) { return (staged_rows_off(ntiles) + ntiles * kRows * 2 + 15) & ~(int64_t)15; }
 int64_t staged_row_bytes(int layout) { return layout == kLayoutK4 ? 2 * kTSlotsDense : 8; }
 int64_t work_bytes_two_pass(int64_t ntiles, int layout)
@@ -2425,26 +2410,24 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
 {
     unsigned long long* tile_sum = a.work + kWorkHeader;
     uint8_t* wb = reinterpret_cast<uint8_t*>(a.work);
-    uint32_t* wsum = reinterpret_cast<uint32_t*>(wb + staged_wsum_off(a.ntiles));
     uint16_t* rows = reinterpret_cast<uint16_t*>(wb + staged_rows_off(a.ntiles));
     const bool dense = r.layout == kLayoutK4;
     uint16_t* stage = dense ? reinterpret_cast<uint16_t*>(wb + staged_tail_off(a.ntiles)) : nullptr;
     unsigned long long* masks = dense ? nullptr : reinterpret_cast<unsigned long long*>(wb + staged_tail_off(a.ntiles));
     ScanArgs a1 = a;
     a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
-    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, stage, wsum, masks);
+    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, stage, masks);
     if (rc) return rc;
     k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
     CUDA_TRY(cudaGetLastError());
     const void* fn = dense ? (const void*)k_place : (const void*)k_place_masked;
     int occ = occupancy(fn, 256, 0, dev, di->smem_optin);
     if (occ <= 0) return fail("placement kernel does not fit on an SM (occupancy 0)");
-    const int64_t warps = a.ntiles * kWalkWarps;
-    const int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)occ * di->sms);
+    const int64_t grid = std::min<int64_t>((a.ntiles + 7) / 8, (int64_t)occ * di->sms);
     if (dense)
-        k_place<<<(unsigned)grid, 256, 0, st>>>(a, rows, wsum, tile_sum, stage, kTSlotsDense);
+        k_place<<<(unsigned)grid, 256, 0, st>>>(a, rows, tile_sum, stage);
     else
-        k_place_masked<<<(unsigned)grid, 256, 0, st>>>(a, rows, wsum, tile_sum, masks);
+        k_place_masked<<<(unsigned)grid, 256, 0, st>>>(a, rows, tile_sum, masks);
     CUDA_TRY(cudaGetLastError());
     return DFA_OK;
 }
