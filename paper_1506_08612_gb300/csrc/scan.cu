@@ -1937,15 +1937,16 @@ __device__ __forceinline__ uint32_t tile_rows(const uint16_t* rows, int64_t tile
     return x - tot;
 }
 
-// Pass 3 of the two-pass find, one warp per tile (tiles without accepts are
-// skipped on their offsets alone).  A row's first index is its tile's offset
-// (pass 2) + a scan of the tile's row counts.
+// Pass 3 of the two-pass find.  A row's first index is its tile's offset
+// (pass 2) + a scan of the counts of the tile's earlier rows.
 
-// Layout 1: the count pass staged each row's exact end offsets (up to
-// kTSlotsDense), packed in row order in its walker warp's region (rows
-// 32 w .. 32 w + 31 of the tile, lanes 2w and 2w + 1 here): they are copied.
-// Rows past their slots are walked again, each by its lane.
-__global__ void __launch_bounds__(256, 2)
+// Layout 1, one warp per (tile, walker warp) region of 32 rows: the count
+// pass staged each row's exact end offsets (up to kTSlotsDense), packed in
+// row order in the region; they are copied, each row by its lane.  The
+// region's first index adds the counts of the tile's earlier rows (the
+// lanes' row-count loads cover the whole tile).  Rows past their slots are
+// walked again, each by its lane.
+__global__ void __launch_bounds__(256)
     k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
             const uint16_t* stage)
 {
@@ -1954,60 +1955,66 @@ __global__ void __launch_bounds__(256, 2)
     const int lane = threadIdx.x & 31;
     const unsigned long long end_all = *a.count;
     const int64_t C = a.chunk;
-    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < a.ntiles;
-         tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t units = a.ntiles * kWalkWarps;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t tile = u / kWalkWarps;
+        const int w = (int)(u % kWalkWarps);
         const unsigned long long off = tile_off[tile];
-        if (off == (tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all)) continue;
-        uint32_t c[16];
-        const uint32_t excl = tile_rows(rows, tile, lane, c);
-        // staged entries before this lane's rows in its walker warp's region
-        uint32_t st = 0;
+        const unsigned long long nxt = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
+        // the counts of the tile's rows before this region: lane l sums rows
+        // 16 l .. 16 l + 15 of them (lanes 0 .. 2w - 1)
+        uint32_t pre = 0;
+        if (lane < 2 * w) {
+            const uint4* src = reinterpret_cast<const uint4*>(rows + tile * kRows + lane * 16);
+            const uint4 x0 = src[0], x1 = src[1];
+            const uint32_t q[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-        for (int k = 0; k < 16; k++) st += min(c[k], KS);
-        const uint32_t nb = __shfl_up_sync(0xffffffffu, st, 1);
-        const uint16_t* src = stage + ((size_t)tile * kWalkWarps + (lane >> 1)) * (32 * KS) + ((lane & 1) ? nb : 0u);
-        int64_t g = (int64_t)(off + excl);
-        uint32_t over = 0;
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-            if (c[k] <= KS) {
-                const int64_t start0 = a.pos_base + (tile * kRows + lane * 16 + k) * C - (int64_t)(a.m - 1);
-                for (uint32_t j = 0; j < c[k]; j++)
-                    if (g + j < a.cap) a.pos[g + j] = start0 + src[j];
-                src += c[k];
-            } else {
-                over |= 1u << k;
-                src += KS;
-            }
-            g += c[k];
+            for (int k = 0; k < 8; k++) pre += (q[k] & 0xFFFFu) + (q[k] >> 16);
         }
-        // rows past their slots: walked again, each by its lane
-        if (over) {
-            int64_t gk = (int64_t)(off + excl);
+        const uint32_t rc = rows[tile * kRows + w * 32 + lane];
+        if (off == nxt) continue;                           // no accepts in the tile
 #pragma unroll
-            for (int k = 0; k < 16; k++) {
-                if ((over >> k) & 1u) {
-                    const int64_t rs = (tile * kRows + lane * 16 + k) * C;
-                    place_row_lane(a, d1s, rs, min(rs + C, a.n_own), gk);
-                }
-                gk += c[k];
+        for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+        const uint32_t st = min(rc, KS);
+        uint32_t x = rc, y = st;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t p = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t q = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) {
+                x += p;
+                y += q;
             }
+        }
+        const int64_t rs = (tile * kRows + w * 32 + lane) * C;
+        const int64_t g0 = (int64_t)(off + pre + x - rc);
+        if (rc <= KS) {
+            const int64_t start0 = a.pos_base + rs - (int64_t)(a.m - 1);
+            const uint16_t* src = stage + u * (32 * (int64_t)KS) + (y - st);
+            for (uint32_t j = 0; j < rc; j++)
+                if (g0 + j < a.cap) a.pos[g0 + j] = start0 + src[j];
+        } else {
+            place_row_lane(a, d1s, rs, min(rs + C, a.n_own), g0);
         }
     }
 }
 
-// Relaxed layouts: every row with accepts walked again, each by the lane
-// that holds its count, over the bytes its stage mask names: the starts from
-// m - 1 bytes before its first masked stage to the end of its last one (every
-// accept of the row ends in a masked stage, and every occurrence starting
-// there is one of them).  Sparse patterns leave a few such rows a tile, so
-// the lanes walk them side by side.
-__global__ void __launch_bounds__(256, 2)
+// Relaxed layouts, one warp per tile: the tile's rows with accepts are listed
+// (their index in the tile and first index) in shared memory, then walked
+// side by side, one listed row per lane, over the bytes the row's stage mask
+// names: the starts from m - 1 bytes before its first masked stage to the
+// end of its last one (every accept of the row ends in a masked stage, and
+// every occurrence starting there is one of them).
+constexpr int kPlaceWarps = 8;
+__global__ void __launch_bounds__(kPlaceWarps * 32)
     k_place_masked(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
                    const unsigned long long* masks)
 {
+    __shared__ uint32_t s_row[kPlaceWarps][kRows];     // row in the tile
+    __shared__ uint32_t s_first[kPlaceWarps][kRows];   // first index within the tile
     const uint8_t* d1s = place_table(a);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned long long end_all = *a.count;
     const int64_t C = a.chunk;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < a.ntiles;
@@ -2015,24 +2022,42 @@ __global__ void __launch_bounds__(256, 2)
         const unsigned long long off = tile_off[tile];
         if (off == (tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all)) continue;
         uint32_t c[16];
-        int64_t g = (int64_t)(off + tile_rows(rows, tile, lane, c));
+        uint32_t first = tile_rows(rows, tile, lane, c);
+        uint32_t nr = 0;
+#pragma unroll
+        for (int k = 0; k < 16; k++) nr += c[k] != 0u ? 1u : 0u;
+        uint32_t slot = nr;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, slot, o);
+            if (lane >= o) slot += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, slot, 31);
+        slot -= nr;
 #pragma unroll
         for (int k = 0; k < 16; k++) {
             if (c[k]) {
-                const int64_t row = tile * kRows + lane * 16 + k;
-                const int64_t rs = row * C;
-                int64_t s = rs, e = min(rs + C, a.n_own);
-                const unsigned long long mask = masks[row];
-                if (mask != ~0ull) {
-                    const int64_t lo_stage = __ffsll((long long)mask) - 1;
-                    const int64_t hi_stage = 63 - __clzll((long long)mask);
-                    s = max(rs, rs + lo_stage * kStageW - (int64_t)(a.m - 1));
-                    e = min(e, rs + (hi_stage + 1) * kStageW);
-                }
-                place_row_lane(a, d1s, s, e, g);
-                g += c[k];
+                s_row[wid][slot] = (uint32_t)(lane * 16 + k);
+                s_first[wid][slot] = first;
+                slot++;
             }
+            first += c[k];
         }
+        __syncwarp();
+        for (uint32_t i = (uint32_t)lane; i < total; i += 32) {
+            const int64_t row = tile * kRows + s_row[wid][i];
+            const int64_t rs = row * C;
+            int64_t s = rs, e = min(rs + C, a.n_own);
+            const unsigned long long mask = masks[row];
+            if (mask != ~0ull) {
+                const int64_t lo_stage = __ffsll((long long)mask) - 1;
+                const int64_t hi_stage = 63 - __clzll((long long)mask);
+                s = max(rs, rs + lo_stage * kStageW - (int64_t)(a.m - 1));
+                e = min(e, rs + (hi_stage + 1) * kStageW);
+            }
+            place_row_lane(a, d1s, s, e, (int64_t)(off + s_first[wid][i]));
+        }
+        __syncwarp();
     }
 }
 
@@ -2423,7 +2448,9 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
     const void* fn = dense ? (const void*)k_place : (const void*)k_place_masked;
     int occ = occupancy(fn, 256, 0, dev, di->smem_optin);
     if (occ <= 0) return fail("placement kernel does not fit on an SM (occupancy 0)");
-    const int64_t grid = std::min<int64_t>((a.ntiles + 7) / 8, (int64_t)occ * di->sms);
+    // warps: one per 32-row region (layout 1) or one per tile
+    const int64_t warps = dense ? a.ntiles * kWalkWarps : a.ntiles;
+    const int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)occ * di->sms);
     if (dense)
         k_place<<<(unsigned)grid, 256, 0, st>>>(a, rows, tile_sum, stage);
     else
