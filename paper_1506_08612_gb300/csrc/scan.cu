@@ -1044,41 +1044,6 @@ __device__ __forceinline__ uint4 redo_stage_exact(const SmemTab& T, uint32_t slo
     return make_uint4(w.cnt, ss.n, w.e, 0u);
 }
 
-// The dense walk's base test, shared by the warp.  Every lane whose relaxed
-// walk accepted in this stage (want) must know whether the stage's 64 bytes
-// or the 8 bytes before them (its p0, p1) hold a non-base; a dense pattern
-// makes some lane of nearly every warp want it, and a lane testing its 72
-// bytes alone keeps the other 31 waiting.  Here the warp tests up to eight
-// wanted stages at once, four lanes a stage, each lane one 16-byte piece of
-// that row's ring slot (box: the warp's slot; row r at r * 64, piece k at
-// (r * 64 + ((r >> 1) & 3) * 16) ^ (k * 16)), the piece-0 lane adding the
-// row's 8 bytes before it; the four results are OR-ed and handed back.
-__device__ __forceinline__ bool warp_stage_bad(bool want, uint32_t p0, uint32_t p1, const uint8_t* box, int lane)
-{
-    const uint32_t need = __ballot_sync(0xffffffffu, want);
-    const uint32_t nreq = (uint32_t)__popc(need);
-    const uint32_t myq = (uint32_t)__popc(need & ((1u << lane) - 1u));   // this lane's request number
-    const uint32_t part = (uint32_t)lane & 3u;
-    bool res = false;
-    for (uint32_t base = 0; base < nreq; base += 8) {
-        const uint32_t q = base + ((uint32_t)lane >> 2);
-        const bool live = q < nreq;
-        const int req = live ? (int)__fns(need, 0, (int)q + 1) : lane;
-        const uint32_t rob = (uint32_t)req * (uint32_t)kStageW + ((((uint32_t)req >> 1) & 3u) << 4);
-        const uint4 v = lds128_fresh(box + (rob ^ (part << 4)));
-        uint32_t bad = word_bad(v.x) | word_bad(v.y) | word_bad(v.z) | word_bad(v.w);
-        const uint32_t r0 = __shfl_sync(0xffffffffu, p0, req), r1 = __shfl_sync(0xffffffffu, p1, req);
-        if (part == 0u) bad |= word_bad(r0) | word_bad(r1);
-        if (!live) bad = 0u;
-        bad |= __shfl_xor_sync(0xffffffffu, bad, 1);
-        bad |= __shfl_xor_sync(0xffffffffu, bad, 2);
-        const bool mine = want && myq >= base && myq < base + 8u;
-        const uint32_t got = __shfl_sync(0xffffffffu, bad, mine ? (int)(4u * (myq - base)) : lane);
-        if (mine) res = got != 0u;
-    }
-    return res;
-}
-
 template <int LAYOUT, class Sink>
 __device__ __noinline__ uint32_t walk_cold(const ScanArgs* a, int64_t s, int64_t e, Sink* sink)
 {
@@ -1518,35 +1483,6 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
                                                 v[i][3].x, v[i][3].y, v[i][3].z, v[i][3].w};
                         const uint32_t flag = relaxed_words<LAYOUT, 16>(relaxed_mask<LAYOUT>(m), e[i], x);
                         fmask[i] |= (uint64_t)(flag != 0u) << s;
-                    }
-                } else if (STAGED) {
-                    // every lane walks (rows outside the text on the zeros the
-                    // TMA box holds there, their results unused), so that the
-                    // warp can share the base test of the stages that accepted
-#pragma unroll
-                    for (int i = 0; i < kRPL; i++) {
-                        Walker<LAYOUT, false, RowSlots<KS>> wd{T, ss[i], e[i], cnt[i]};
-                        const uint32_t p0 = tl0[i], p1 = tl1[i];
-                        tl0[i] = v[i][3].z;
-                        tl1[i] = v[i][3].w;
-                        const uint2 map = wd.vec4_relaxed_map(v[i][0], v[i][1], v[i][2], v[i][3]);
-                        const bool want = ok[i] && (map.x | map.y) != 0u;
-                        const uint8_t* q = rp + i * 32 * kStageW;
-                        const bool bad = warp_stage_bad(want, p0, p1, q, lane);
-                        if (want) {
-                            if (!bad) {
-                                wd.put_map(map, r);
-                            } else {
-                                const uint4 rr = redo_stage_exact<LAYOUT, KS>(T, ss[i].base, ss[i].n, p0, p1, q, ob, r);
-                                wd.cnt += rr.x;
-                                ss[i].n = rr.y;
-                                wd.e = rr.z;
-                            }
-                        }
-                        if (ok[i]) {
-                            e[i] = wd.e;
-                            cnt[i] = wd.cnt;
-                        }
                     }
                 } else if (INLINE_REC) {
 #pragma unroll
