@@ -1896,6 +1896,40 @@ __device__ __forceinline__ uint32_t place_slice(const ScanArgs& a, const uint8_t
     return c;
 }
 
+// Every occurrence starting in [s, e) (a row, or the part of one that holds
+// all its occurrences), found by the whole warp and written in order from
+// index g0: lane l takes the l-th slice of the starts and reads m - 1 bytes
+// past it (Algorithm 1 within the range); a count (the first four positions
+// kept), a warp scan, and a second walk only in slices with more than four.
+// For the long ranges (a row walked whole): one lane alone would keep its
+// warp waiting for a thousand dependent steps.
+__device__ __noinline__ void place_range(const ScanArgs& a, const uint8_t* d1s, int64_t s, int64_t e, int64_t g0,
+                                         int lane)
+{
+    const int64_t span = (e - s + 31) / 32;
+    const int64_t ls = min(s + lane * span, e), le = min(ls + span, e);
+    const int64_t hi = min(le + (int64_t)a.m - 1, a.n);
+    int64_t keep[4];
+    const uint32_t c = place_slice<false>(a, d1s, ls, le, hi, 0, keep);
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int64_t g = g0 + (int64_t)(x - c);
+    if (c <= 4u) {
+        for (uint32_t k = 0; k < c; k++)
+            if (g + k < a.cap) a.pos[g + k] = keep[k];
+    } else {
+        place_slice<true>(a, d1s, ls, le, hi, g, keep);
+    }
+}
+
+// Ranges up to this many starts are walked by one lane; longer ones by the
+// warp (place_range).
+constexpr int64_t kLaneRange = 256;
+
 // Every occurrence starting in [s, e), walked by one lane alone (through
 // min(e + m - 1, n)) and written in order from index g.
 __device__ __noinline__ void place_row_lane(const ScanArgs& a, const uint8_t* d1s, int64_t s, int64_t e, int64_t g)
@@ -1994,8 +2028,14 @@ __global__ void __launch_bounds__(256)
             const uint16_t* src = stage + u * (32 * (int64_t)KS) + (y - st);
             for (uint32_t j = 0; j < rc; j++)
                 if (g0 + j < a.cap) a.pos[g0 + j] = start0 + src[j];
-        } else {
-            place_row_lane(a, d1s, rs, min(rs + C, a.n_own), g0);
+        }
+        // rows past their slots: each walked again by the whole warp
+        uint32_t over = __ballot_sync(0xffffffffu, rc > KS);
+        while (over) {
+            const int r = __ffs(over) - 1;
+            over &= over - 1u;
+            const int64_t rr = __shfl_sync(0xffffffffu, rs, r);
+            place_range(a, d1s, rr, min(rr + C, a.n_own), __shfl_sync(0xffffffffu, g0, r), lane);
         }
     }
 }
@@ -2044,18 +2084,32 @@ __global__ void __launch_bounds__(kPlaceWarps * 32)
             first += c[k];
         }
         __syncwarp();
-        for (uint32_t i = (uint32_t)lane; i < total; i += 32) {
-            const int64_t row = tile * kRows + s_row[wid][i];
-            const int64_t rs = row * C;
-            int64_t s = rs, e = min(rs + C, a.n_own);
-            const unsigned long long mask = masks[row];
-            if (mask != ~0ull) {
-                const int64_t lo_stage = __ffsll((long long)mask) - 1;
-                const int64_t hi_stage = 63 - __clzll((long long)mask);
-                s = max(rs, rs + lo_stage * kStageW - (int64_t)(a.m - 1));
-                e = min(e, rs + (hi_stage + 1) * kStageW);
+        for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+            const uint32_t i = i0 + (uint32_t)lane;
+            int64_t s = 0, e = 0, g = 0;
+            if (i < total) {
+                const int64_t row = tile * kRows + s_row[wid][i];
+                const int64_t rs = row * C;
+                s = rs;
+                e = min(rs + C, a.n_own);
+                g = (int64_t)(off + s_first[wid][i]);
+                const unsigned long long mask = masks[row];
+                if (mask != ~0ull) {
+                    const int64_t lo_stage = __ffsll((long long)mask) - 1;
+                    const int64_t hi_stage = 63 - __clzll((long long)mask);
+                    s = max(rs, rs + lo_stage * kStageW - (int64_t)(a.m - 1));
+                    e = min(e, rs + (hi_stage + 1) * kStageW);
+                }
             }
-            place_row_lane(a, d1s, s, e, (int64_t)(off + s_first[wid][i]));
+            const bool lng = e - s > kLaneRange;
+            if (i < total && !lng) place_row_lane(a, d1s, s, e, g);
+            uint32_t big = __ballot_sync(0xffffffffu, lng);      // long ranges: the whole warp
+            while (big) {
+                const int r = __ffs(big) - 1;
+                big &= big - 1u;
+                place_range(a, d1s, __shfl_sync(0xffffffffu, s, r), __shfl_sync(0xffffffffu, e, r),
+                            __shfl_sync(0xffffffffu, g, r), lane);
+            }
         }
         __syncwarp();
     }
