@@ -830,6 +830,9 @@ struct TmaArgs {
     // sps: the overlap; all ones: the whole row)
     uint16_t* stage;
     unsigned long long* masks;
+    // layout 1: each walker warp's total count of the tile, at
+    // warp_sum[t * kWalkWarps + warp]
+    uint32_t* warp_sum;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -1718,6 +1721,7 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
                 if (lane == 0 && ws) atomicAdd(p.tile_sum + tile, (unsigned long long)ws);
+                if (STAGED && lane == 0) p.warp_sum[(size_t)tile * kWalkWarps + warp] = ws;
             }
         } else {
             // exclusive offsets of this lane's rows among the warp's rows
@@ -1928,7 +1932,7 @@ __device__ __noinline__ void place_range(const ScanArgs& a, const uint8_t* d1s, 
 
 // Ranges up to this many starts are walked by one lane; longer ones by the
 // warp (place_range).
-constexpr int64_t kLaneRange = 256;
+constexpr int64_t kLaneRange = 128;
 
 // Every occurrence starting in [s, e), walked by one lane alone (through
 // min(e + m - 1, n)) and written in order from index g.
@@ -1976,13 +1980,13 @@ __device__ __forceinline__ uint32_t tile_rows(const uint16_t* rows, int64_t tile
 
 // Layout 1, one warp per (tile, walker warp) region of 32 rows: the count
 // pass staged each row's exact end offsets (up to kTSlotsDense), packed in
-// row order in the region; they are copied, each row by its lane.  The
-// region's first index adds the counts of the tile's earlier rows (the
-// lanes' row-count loads cover the whole tile).  Rows past their slots are
-// walked again, each by its lane.
+// row order in the region, and each walker warp's total; the offsets are
+// copied, each row by its lane, the region's first index adding the totals
+// of the tile's earlier walker warps.  Rows past their slots are walked
+// again by the warp.
 __global__ void __launch_bounds__(256)
     k_place(const __grid_constant__ ScanArgs a, const uint16_t* rows, const unsigned long long* tile_off,
-            const uint16_t* stage)
+            const uint16_t* stage, const uint32_t* warp_sum)
 {
     constexpr uint32_t KS = kTSlotsDense;
     const uint8_t* d1s = place_table(a);
@@ -1996,16 +2000,9 @@ __global__ void __launch_bounds__(256)
         const int w = (int)(u % kWalkWarps);
         const unsigned long long off = tile_off[tile];
         const unsigned long long nxt = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
-        // the counts of the tile's rows before this region: lane l sums rows
-        // 16 l .. 16 l + 15 of them (lanes 0 .. 2w - 1)
-        uint32_t pre = 0;
-        if (lane < 2 * w) {
-            const uint4* src = reinterpret_cast<const uint4*>(rows + tile * kRows + lane * 16);
-            const uint4 x0 = src[0], x1 = src[1];
-            const uint32_t q[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-            for (int k = 0; k < 8; k++) pre += (q[k] & 0xFFFFu) + (q[k] >> 16);
-        }
+        // the counts of the tile's rows before this region: the totals of the
+        // walker warps before it
+        uint32_t pre = lane < w ? warp_sum[tile * kWalkWarps + lane] : 0u;
         const uint32_t rc = rows[tile * kRows + w * 32 + lane];
         if (off == nxt) continue;                           // no accepts in the tile
 #pragma unroll
@@ -2346,7 +2343,7 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
 // Launch the TMA-staged kernel for the filled-in arguments `a`.
 int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
                const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr, uint16_t* stage = nullptr,
-               unsigned long long* masks = nullptr)
+               unsigned long long* masks = nullptr, uint32_t* warp_sum = nullptr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
     int rc = tensor_map_encoder(&encode);
@@ -2365,6 +2362,7 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.tile_sum = rows ? a.work + kWorkHeader : nullptr;
     p.stage = stage;
     p.masks = masks;
+    p.warp_sum = warp_sum;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
@@ -2464,13 +2462,16 @@ int64_t work_bytes_for(int64_t ntiles) { return 8 * (kWorkHeader + ntiles); }
 
 // Two-pass find: [header][one word per tile][one u16 count per row of every
 // tile, 16-byte aligned][16-byte aligned: layout 1, kTSlotsDense u16 end
-// offsets per row; relaxed layouts, one u64 stage mask per row].
+// offsets per row, then one u32 total per walker warp of every tile;
+// relaxed layouts, one u64 stage mask per row].
 int64_t staged_rows_off(int64_t ntiles) { return (work_bytes_for(ntiles) + 15) & ~(int64_t)15; }
 int64_t staged_tail_off(int64_t ntiles) { return (staged_rows_off(ntiles) + ntiles * kRows * 2 + 15) & ~(int64_t)15; }
 int64_t staged_row_bytes(int layout) { return layout == kLayoutK4 ? 2 * kTSlotsDense : 8; }
+int64_t staged_wsum_off(int64_t ntiles) { return staged_tail_off(ntiles) + ntiles * kRows * 2 * kTSlotsDense; }
 int64_t work_bytes_two_pass(int64_t ntiles, int layout)
 {
-    return staged_tail_off(ntiles) + ntiles * kRows * staged_row_bytes(layout);
+    const int64_t b = staged_tail_off(ntiles) + ntiles * kRows * staged_row_bytes(layout);
+    return layout == kLayoutK4 ? b + ntiles * kWalkWarps * 4 : b;
 }
 
 // The staged two-pass find serves the TMA kernel's four-step layouts: the
@@ -2495,7 +2496,8 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
     unsigned long long* masks = dense ? nullptr : reinterpret_cast<unsigned long long*>(wb + staged_tail_off(a.ntiles));
     ScanArgs a1 = a;
     a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
-    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, stage, masks);
+    uint32_t* wsum = dense ? reinterpret_cast<uint32_t*>(wb + staged_wsum_off(a.ntiles)) : nullptr;
+    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, stage, masks, wsum);
     if (rc) return rc;
     k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
     CUDA_TRY(cudaGetLastError());
@@ -2506,7 +2508,7 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
     const int64_t warps = dense ? a.ntiles * kWalkWarps : a.ntiles;
     const int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)occ * di->sms);
     if (dense)
-        k_place<<<(unsigned)grid, 256, 0, st>>>(a, rows, tile_sum, stage);
+        k_place<<<(unsigned)grid, 256, 0, st>>>(a, rows, tile_sum, stage, wsum);
     else
         k_place_masked<<<(unsigned)grid, 256, 0, st>>>(a, rows, tile_sum, masks);
     CUDA_TRY(cudaGetLastError());
