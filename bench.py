@@ -48,13 +48,14 @@ TEXT_BYTES = 3_200_000_000
 TEXT_SEED = 2
 CLASS_PAIRS, CLASS_SEED = 9, 40          # class-pattern workload: 9 pairs = 18 patterns
 WORKLOAD = "genome-scale single-pattern scan"
-# one dfa_find per pattern, the staged two-pass find: the count pass
-# k_scan_tma (m >= 8: relaxed walk, exact replays of the flagged stages;
-# m < 8: relaxed walk with each accept's window tested) staging every row's
-# exact end offsets, k_tile_offsets (scan of the tile totals) and k_place
-# (copy of the staged offsets to the sorted positions); the events time the
-# whole call
-DOMINANT_KERNEL = "dfa_find = k_scan_tma (TMA-staged count pass) + k_tile_offsets + k_place"
+# one dfa_find per pattern, the two-pass find: pass 1 k_scan_tma (m >= 8:
+# the relaxed count kernel, leaving row counts and the stage masks of its
+# exact replays; m < 8: the relaxed dense walk recording each row's end
+# offsets), k_tile_offsets (scan of the tile totals) and pass 3 (k_place
+# copies the recorded offsets; k_place_masked walks the masked bytes of the
+# rows with accepts); the events time the whole call
+DOMINANT_KERNEL = ("dfa_find = k_scan_tma (TMA-staged pass 1) + k_tile_offsets + k_place (m < 8) "
+                   "or k_place_masked (m >= 8)")
 
 
 def parse():
