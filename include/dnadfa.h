@@ -58,7 +58,10 @@ extern "C" {
 #define DFA_COUNT_FAILED (1ull << 63)
 
 /* Longest pattern accepted.  States 0..m must fit a byte and the tables of
- * the fast layouts must fit in one SM's shared memory. */
+ * the fast layouts must fit in one SM's shared memory beside the TMA rings:
+ * the four-step tables hold (m+1)*256 entries each (layout 4: about
+ * 2*(m+1)*256 bytes), so 64 rather than the 255 a byte of state would
+ * allow (255 would need 190 KiB of tables). */
 #define DFA_MAX_M 64
 
 /* Opaque automaton for one pattern: host tables plus a device copy on the
@@ -219,6 +222,9 @@ int dfa_find_host(const uint8_t* h_text, int64_t n, const dfa_table* table, int6
  * dfa_find of several patterns over one device text (Algorithm 1's output
  * for each): the finds run one after another on `stream`, sharing the one
  * workspace d_work (at least dfa_find_workspace_bytes(n, cfg) bytes).
+ * Several texts are several calls (each pattern's positions need their own
+ * capacity per text); counting many patterns over many texts in one launch
+ * is dfa_multi_count, below.
  *   tables / npat: 1 <= npat <= 1024 automata.
  *   d_pos[i] / caps[i]: device buffer for up to caps[i] start positions of
  *            pattern i (d_pos may be NULL when every cap is 0).
@@ -296,7 +302,9 @@ int dfa_find_noalloc(const uint8_t* d_text, int64_t n, const dfa_table* table, i
  * Many patterns at once: the multi-pattern failure-less automaton of
  * Sec. III-B (one automaton for a set of patterns, failure transitions
  * folded into the table, one lookup per character) and a batched count
- * over many sequences in one launch.
+ * over many sequences in one launch.  A batch of patterns is one automaton
+ * rather than an array of single-pattern tables: each byte of each text is
+ * then walked once for all the patterns, not once per pattern.
  * ------------------------------------------------------------------ */
 typedef struct dfa_multi dfa_multi;
 
