@@ -590,3 +590,46 @@ def test_sharded_find_with_library_engine(gpu):
             parts = [shard.local_find(td, m, world, r, engine) for r in range(world)]
             c, p = shard.merge([x[0] for x in parts], [x[1] for x in parts])
             assert c == want_c and np.array_equal(p, want_p), (m, world)
+
+
+def test_autotuned_find_and_count(gpu, tmp_path, monkeypatch):
+    # cfg="auto": the autotuner times the TMA layouts x row lengths on the
+    # call itself (find or count) and caches the winner; results stay exact
+    from paper_1506_08612_gb300 import autotune
+    monkeypatch.setenv("DNADFA_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.delenv("DNADFA_CONFIG", raising=False)
+    autotune.reset_memory_cache()
+    n = 20_000_003
+    t = synth.genome_text(n, 35)
+    td = _dev(gpu, t)
+    for m, seed in ((4, 3501), (12, 3502)):
+        pat = synth.pattern(m, seed)
+        want_c, want_p = oracle.find_brute(t, pat)
+        c, p = gpu.find(td, pat, cfg="auto")
+        assert c == want_c and np.array_equal(p.cpu().numpy(), want_p)
+        assert gpu.count(td, pat, cfg="auto") == want_c
+    cached = autotune._load_cache()
+    assert any(k.startswith("single-find|") for k in cached)
+    assert any(k.startswith("single-count|") for k in cached)
+    autotune.reset_memory_cache()
+
+
+def test_bench_shard_mode_single_rank(gpu):
+    # bench.py --shard at world size 1: the slice is the whole text and the
+    # merged counts equal a whole-text count (the bench asserts it); the
+    # counts it prints equal the oracle's
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    n = 40_000_000
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--shard", "--n", str(n),
+                          "--steps", "2", "--warmup", "1"], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                         text=True, cwd=root, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    assert line["scaling"] == "strong" and line["config"]["parallelism"].startswith("shard x1")
+    text = synth.genome_text(n, 2)
+    want = [oracle.count_brute(text, synth.pattern(m, s)) for m, s in zip((4, 8, 16, 32, 64), (3, 4, 5, 6, 7))]
+    assert line["counts"] == want
