@@ -1288,7 +1288,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
     __syncthreads();
     volatile int* abort_flag = &s_abort;
     const uint32_t sps = (uint32_t)p.sps;
-    const uint32_t spt = sps + 1;                 // stages per tile, halo included
+    // stages per tile, the halo (the next row's first 64 bytes) included;
+    // the staged dense pass (m <= 8) takes its halo from the next lane's
+    // first stage instead
+    const uint32_t spt = sps + (STAGED ? 0u : 1u);
     const int64_t C = a.chunk;
 
     if (FIND && warp == kProducerWarp) {
@@ -1446,6 +1449,8 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
         uint32_t e[kRPL], cnt[kRPL];
         uint64_t fmask[kRPL];                     // relaxed walks: stages to replay exactly
         uint32_t tl0[kRPL], tl1[kRPL];            // dense finds: the row's last 8 bytes walked
+        uint32_t hf0 = 0u, hf1 = 0u;              // staged: the row's first 8 bytes
+        uint2 hn = make_uint2(0u, 0u);            // staged, lane 31: the next warp's row's first 8
         RowSlots<KS> ss[kRPL];
 #pragma unroll
         for (int i = 0; i < kRPL; i++) {
@@ -1453,6 +1458,12 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
             // next row's first bytes); every other row is walked cold below
             const int64_t row = (int64_t)tile * kRows + wrow0 + 32 * i;
             ok[i] = (row + 1) * C <= a.n_own && row + 1 < p.nrows_full;
+            if (STAGED && lane == 31 && ok[i]) {
+                // the row after the warp's last: another warp's (or tile's)
+                asm volatile("ld.global.nc.v2.u32 {%0,%1}, [%2];"
+                             : "=r"(hn.x), "=r"(hn.y)
+                             : "l"(a.text + (row + 1) * C));
+            }
             e[i] = 0;
             cnt[i] = 0;
             fmask[i] = 0;
@@ -1488,6 +1499,10 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
                         fmask[i] |= (uint64_t)(flag != 0u) << s;
                     }
                 } else if (INLINE_REC) {
+                    if (STAGED && s == 0u) {              // the previous lane's halo
+                        hf0 = v[0][0].x;
+                        hf1 = v[0][0].y;
+                    }
 #pragma unroll
                     for (int i = 0; i < kRPL; i++) {
                         if (!ok[i]) continue;
@@ -1655,6 +1670,22 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
             }
         }
         if (aborted) break;
+        if (STAGED) {
+            // the overlap (m - 1 <= 7 bytes) of a dense pattern: the next
+            // row's first 8 bytes, which the next lane read in its first
+            // stage (lane 31: the next warp's row, loaded at the tile start);
+            // the relaxed state is exact unless the last 8 bytes hold a
+            // non-base (the relaxed dense walk)
+            const uint32_t n0 = __shfl_down_sync(0xffffffffu, hf0, 1);
+            const uint32_t n1 = __shfl_down_sync(0xffffffffu, hf1, 1);
+            const uint32_t lim = (uint32_t)C + m - 1;
+            if (ok[0]) {
+                if ((word_bad(tl0[0]) | word_bad(tl1[0])) != 0u) e[0] = exact_state8(T, tl0[0], tl1[0]);
+                Walker<LAYOUT, true, RowSlots<KS>> h{T, ss[0], e[0], cnt[0]};
+                h.vec(make_uint4(lane == 31 ? hn.x : n0, lane == 31 ? hn.y : n1, 0u, 0u), (uint32_t)C, lim);
+                cnt[0] = h.cnt;
+            }
+        }
 #pragma unroll
         for (int i = 0; i < kRPL; i++) {
             const int64_t s0 = ((int64_t)tile * kRows + wrow0 + 32 * i) * C;
