@@ -2025,45 +2025,60 @@ __global__ void __launch_bounds__(256)
     const unsigned long long end_all = *a.count;
     const int64_t C = a.chunk;
     const int64_t units = a.ntiles * kWalkWarps;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units;
-         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int64_t tile = u / kWalkWarps;
-        const int w = (int)(u % kWalkWarps);
-        const unsigned long long off = tile_off[tile];
-        const unsigned long long nxt = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
-        // the counts of the tile's rows before this region: the totals of the
-        // walker warps before it
-        uint32_t pre = lane < w ? warp_sum[tile * kWalkWarps + lane] : 0u;
-        const uint32_t rc = rows[tile * kRows + w * 32 + lane];
-        if (off == nxt) continue;                           // no accepts in the tile
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // two regions a round, their loads issued together
+    for (int64_t u0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u0 < units; u0 += 2 * stride) {
+        int64_t uu[2] = {u0, u0 + stride};
+        unsigned long long off[2], nxt[2];
+        uint32_t pre[2], rc[2];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
-        const uint32_t st = min(rc, KS);
-        uint32_t x = rc, y = st;
+        for (int h = 0; h < 2; h++) {
+            const int64_t u = uu[h] < units ? uu[h] : u0;
+            const int64_t tile = u / kWalkWarps;
+            const int w = (int)(u % kWalkWarps);
+            off[h] = tile_off[tile];
+            nxt[h] = tile + 1 < a.ntiles ? tile_off[tile + 1] : end_all;
+            // the counts of the tile's rows before this region: the totals of
+            // the walker warps before it
+            pre[h] = lane < w ? warp_sum[tile * kWalkWarps + lane] : 0u;
+            rc[h] = rows[tile * kRows + w * 32 + lane];
+        }
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t p = __shfl_up_sync(0xffffffffu, x, o);
-            const uint32_t q = __shfl_up_sync(0xffffffffu, y, o);
-            if (lane >= o) {
-                x += p;
-                y += q;
+        for (int h = 0; h < 2; h++) {
+            const int64_t u = uu[h];
+            if (u >= units || off[h] == nxt[h]) continue;       // no accepts in the tile
+            const int64_t tile = u / kWalkWarps;
+            const int w = (int)(u % kWalkWarps);
+            uint32_t p = pre[h];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+            const uint32_t st = min(rc[h], KS);
+            uint32_t x = rc[h], y = st;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t q = __shfl_up_sync(0xffffffffu, x, o);
+                const uint32_t r = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) {
+                    x += q;
+                    y += r;
+                }
             }
-        }
-        const int64_t rs = (tile * kRows + w * 32 + lane) * C;
-        const int64_t g0 = (int64_t)(off + pre + x - rc);
-        if (rc <= KS) {
-            const int64_t start0 = a.pos_base + rs - (int64_t)(a.m - 1);
-            const uint16_t* src = stage + u * (32 * (int64_t)KS) + (y - st);
-            for (uint32_t j = 0; j < rc; j++)
-                if (g0 + j < a.cap) a.pos[g0 + j] = start0 + src[j];
-        }
-        // rows past their slots: each walked again by the whole warp
-        uint32_t over = __ballot_sync(0xffffffffu, rc > KS);
-        while (over) {
-            const int r = __ffs(over) - 1;
-            over &= over - 1u;
-            const int64_t rr = __shfl_sync(0xffffffffu, rs, r);
-            place_range(a, d1s, rr, min(rr + C, a.n_own), __shfl_sync(0xffffffffu, g0, r), lane);
+            const int64_t rs = (tile * kRows + w * 32 + lane) * C;
+            const int64_t g0 = (int64_t)(off[h] + p + x - rc[h]);
+            if (rc[h] <= KS) {
+                const int64_t start0 = a.pos_base + rs - (int64_t)(a.m - 1);
+                const uint16_t* src = stage + u * (32 * (int64_t)KS) + (y - st);
+                for (uint32_t j = 0; j < rc[h]; j++)
+                    if (g0 + j < a.cap) a.pos[g0 + j] = start0 + src[j];
+            }
+            // rows past their slots: each walked again by the whole warp
+            uint32_t over = __ballot_sync(0xffffffffu, rc[h] > KS);
+            while (over) {
+                const int r = __ffs(over) - 1;
+                over &= over - 1u;
+                const int64_t rr = __shfl_sync(0xffffffffu, rs, r);
+                place_range(a, d1s, rr, min(rr + C, a.n_own), __shfl_sync(0xffffffffu, g0, r), lane);
+            }
         }
     }
 }
