@@ -425,10 +425,10 @@ struct Walker {
     // exact accept (see relaxed_words).  The relaxed state equals the exact
     // one whenever the last 8 >= m bytes are bases: both are then the longest
     // suffix within those bytes that is a prefix of P.  So a stage whose
-    // relaxed walk accepts nothing has no accept, and a stage that accepted
-    // is exact when it and the 8 bytes before it are bases (the caller tests
-    // that and then calls put_map, else walks the stage exactly).  Returns the
-    // 64-bit map of relaxed accept ends (bit j: end r + j).
+    // relaxed walk accepts nothing has no accept, and each relaxed accept is
+    // exact iff its m-byte window holds only bases (window_exact, which the
+    // caller applies).  Returns the 64-bit map of relaxed accept ends (bit j:
+    // end r + j).
     __device__ __forceinline__ uint2 vec4_relaxed_map(uint4 v0, uint4 v1, uint4 v2, uint4 v3)
     {
         const uint32_t x[16] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w,
@@ -988,6 +988,63 @@ struct RowSlots {
     }
 };
 
+// The exact accepts among a dense stage's relaxed accepts (m <= 8).  The
+// relaxed walk is the automaton run on the text with every byte replaced by
+// the base of its 2-bit code, so it accepts at end j exactly when the codes
+// of the m bytes ending at j are those of P; the exact automaton accepts
+// there exactly when, in addition, those m bytes are bases (each base is the
+// one byte, in either case, with its code).  So an accept is exact iff its
+// window holds no non-base, whatever came before it.  map: bit j = a relaxed
+// accept ending at stage offset j; the stage is the lane's 64 bytes in its
+// ring slot (16-byte piece k at q + (ob ^ (k << 4))), preceded by the 8
+// bytes p0, p1.  Each exact accept goes to the sink at end offset r + j;
+// returns their number.
+template <class Sink>
+__device__ __forceinline__ uint32_t window_exact(uint2 map, uint32_t r, uint32_t m, uint32_t p0, uint32_t p1,
+                                                 const uint8_t* q, uint32_t ob, Sink& sink)
+{
+    uint32_t c = 0u, lo = map.x, hi = map.y;
+    while ((lo | hi) != 0u) {
+        const bool low = lo != 0u;
+        const uint32_t j = (uint32_t)(__ffs(low ? lo : hi) - 1) + (low ? 0u : 32u);
+        if (low)
+            lo &= lo - 1u;
+        else
+            hi &= hi - 1u;
+        // the window ends in byte jl of stage word j >> 2 (wh); with the word
+        // before it (wl) and, for m > 5, the one before that (w0)
+        const uint32_t jl = j & 3u;
+        const uint32_t wh = *reinterpret_cast<const uint32_t*>(q + (ob ^ (j & 0x30u)) + (j & 0xCu));
+        uint32_t wl = p1;
+        if (j >= 4u) {
+            const uint32_t jp = j - 4u;
+            wl = *reinterpret_cast<const uint32_t*>(q + (ob ^ (jp & 0x30u)) + (jp & 0xCu));
+        }
+        // bytes of wl inside the window: from 5 + jl - m on (all of them
+        // when that is below 0, none when it is past 3: shl by >= 32 is 0)
+        uint32_t keep_l;
+        asm("shl.b32 %0, %1, %2;" : "=r"(keep_l) : "r"(0xFFFFFFFFu), "r"(5u + jl > m ? 8u * (5u + jl - m) : 0u));
+        // bytes of wh inside the window: from jl + 1 - m (when above 0) to jl
+        const uint32_t keep_h = (0xFFFFFFFFu >> (24u - 8u * jl)) & (0xFFFFFFFFu << (jl + 1u > m ? 8u * (jl + 1u - m) : 0u));
+        uint32_t bad = (word_bad(wh) & keep_h) | (word_bad(wl) & keep_l);
+        if (m > 5u && 5u + jl < m) {
+            uint32_t w0 = p0;
+            if (j >= 8u) {
+                const uint32_t jq = j - 8u;
+                w0 = *reinterpret_cast<const uint32_t*>(q + (ob ^ (jq & 0x30u)) + (jq & 0xCu));
+            } else if (j >= 4u) {
+                w0 = p1;
+            }
+            bad |= word_bad(w0) & (0xFFFFFFFFu << (8u * (9u + jl - m)));
+        }
+        if (bad == 0u) {
+            sink.put(r + j);
+            c++;
+        }
+    }
+    return c;
+}
+
 // Cold paths of the TMA walkers, kept out of line so that the hot loop's
 // register allocation does not pay for them.
 //   replay_stage: walk a 64-byte stage again from its start entry and record
@@ -1029,22 +1086,6 @@ __device__ __forceinline__ uint32_t exact_state8(const SmemTab& T, uint32_t p0, 
 #pragma unroll
     for (int i = 0; i < 4; i++) q = byte_next(T.d1, q, (p1 >> (8 * i)) & 0xFFu);
     return q;
-}
-
-// A dense pattern's stage that the relaxed walk could not settle (an accept
-// near a non-base): walked again exactly from the exact state at its start
-// (q0 at the row start, r == 0; else the state the 8 bytes before it give),
-// its accepts recorded.  Returns (accepts, slots used, exact end state).
-template <int LAYOUT, uint32_t CAP>
-__device__ __forceinline__ uint4 redo_stage_exact(const SmemTab& T, uint32_t slots, uint32_t n, uint32_t p0, uint32_t p1,
-                                               const uint8_t* rp, uint32_t ob, uint32_t r)
-{
-    const uint32_t q = r != 0u ? exact_state8(T, p0, p1) : 0u;
-    RowSlots<CAP> ss{slots, n};
-    Walker<LAYOUT, false, RowSlots<CAP>> w{T, ss, q, 0u};
-    w.vec4(lds128_fresh(rp + ob), lds128_fresh(rp + (ob ^ 16u)), lds128_fresh(rp + (ob ^ 32u)),
-           lds128_fresh(rp + (ob ^ 48u)), r);
-    return make_uint4(w.cnt, ss.n, w.e, 0u);
 }
 
 template <int LAYOUT, class Sink>
@@ -1512,28 +1553,8 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
                             tl0[i] = v[i][3].z;
                             tl1[i] = v[i][3].w;
                             const uint2 map = wd.vec4_relaxed_map(v[i][0], v[i][1], v[i][2], v[i][3]);
-                            if ((map.x | map.y) != 0u) {
-                                // accepts: exact if the stage (read again from its
-                                // slot) and the 8 bytes before it are bases
-                                const uint8_t* q = rp + i * 32 * kStageW;
-                                const uint4 w0 = lds128_fresh(q + ob), w1 = lds128_fresh(q + (ob ^ 16u)),
-                                            w2 = lds128_fresh(q + (ob ^ 32u)), w3 = lds128_fresh(q + (ob ^ 48u));
-                                const uint32_t bad =
-                                    word_bad(p0) | word_bad(p1) | word_bad(w0.x) | word_bad(w0.y) |
-                                    word_bad(w0.z) | word_bad(w0.w) | word_bad(w1.x) | word_bad(w1.y) |
-                                    word_bad(w1.z) | word_bad(w1.w) | word_bad(w2.x) | word_bad(w2.y) |
-                                    word_bad(w2.z) | word_bad(w2.w) | word_bad(w3.x) | word_bad(w3.y) |
-                                    word_bad(w3.z) | word_bad(w3.w);
-                                if (bad == 0u) {
-                                    wd.put_map(map, r);
-                                } else {
-                                    const uint4 rr = redo_stage_exact<LAYOUT, KS>(T, ss[i].base, ss[i].n, p0, p1,
-                                                                                  q, ob, r);
-                                    wd.cnt += rr.x;
-                                    ss[i].n = rr.y;
-                                    wd.e = rr.z;
-                                }
-                            }
+                            if ((map.x | map.y) != 0u)        // accepts: each window tested for bases
+                                wd.cnt += window_exact(map, r, m, p0, p1, rp + i * 32 * kStageW, ob, ss[i]);
                         } else {
                             wd.vec4(v[i][0], v[i][1], v[i][2], v[i][3], r);
                         }
@@ -1549,45 +1570,19 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
                     }
                     if (!FIND && LAYOUT == kLayoutK4 && m <= 8u) {
                         // count of a short pattern: the relaxed walk of the
-                        // dense find, tested only where it counted
+                        // dense find, each relaxed accept's window tested
 #pragma unroll
                         for (int i = 0; i < kRPL; i++) {
                             if (!ok[i]) continue;
                             const uint32_t p0 = tl0[i], p1 = tl1[i];
                             tl0[i] = v[i][3].z;
                             tl1[i] = v[i][3].w;
-                            const uint32_t x[16] = {v[i][0].x, v[i][0].y, v[i][0].z, v[i][0].w,
-                                                    v[i][1].x, v[i][1].y, v[i][1].z, v[i][1].w,
-                                                    v[i][2].x, v[i][2].y, v[i][2].z, v[i][2].w,
-                                                    v[i][3].x, v[i][3].y, v[i][3].z, v[i][3].w};
-                            uint32_t ee = e[i], c = 0u;
-#pragma unroll
-                            for (int k = 0; k < 16; k++) {
-                                ee = k4_next<LAYOUT>(T.k4, ee, x[k]);
-                                c += ee >> K4_CNT_SHIFT;
-                            }
-                            if (c != 0u) {
-                                const uint8_t* q = rp + i * 32 * kStageW;
-                                const uint4 w0 = lds128_fresh(q + ob), w1 = lds128_fresh(q + (ob ^ 16u)),
-                                            w2 = lds128_fresh(q + (ob ^ 32u)), w3 = lds128_fresh(q + (ob ^ 48u));
-                                const uint32_t bad =
-                                    word_bad(p0) | word_bad(p1) | word_bad(w0.x) | word_bad(w0.y) |
-                                    word_bad(w0.z) | word_bad(w0.w) | word_bad(w1.x) | word_bad(w1.y) |
-                                    word_bad(w1.z) | word_bad(w1.w) | word_bad(w2.x) | word_bad(w2.y) |
-                                    word_bad(w2.z) | word_bad(w2.w) | word_bad(w3.x) | word_bad(w3.y) |
-                                    word_bad(w3.z) | word_bad(w3.w);
-                                if (bad != 0u) {
-                                    // a non-base near a count: this stage exactly
-                                    CountSink cs;
-                                    Walker<LAYOUT, false, CountSink> w{
-                                        T, cs, r != 0u ? exact_state8(T, p0, p1) : 0u, 0u};
-                                    w.vec4(w0, w1, w2, w3, r);
-                                    c = w.cnt;
-                                    ee = w.e;
-                                }
-                            }
-                            e[i] = ee;
-                            cnt[i] += c;
+                            CountSink cs;
+                            Walker<LAYOUT, false, CountSink> wc{T, cs, e[i], 0u};
+                            const uint2 map = wc.vec4_relaxed_map(v[i][0], v[i][1], v[i][2], v[i][3]);
+                            if ((map.x | map.y) != 0u)        // accepts: each window tested for bases
+                                cnt[i] += window_exact(map, r, m, p0, p1, rp + i * 32 * kStageW, ob, cs);
+                            e[i] = wc.e;
                         }
                     } else {
                         count_stage<LAYOUT>(T, e, cnt, v, ok, r);
