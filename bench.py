@@ -427,9 +427,12 @@ def run_ours(args):
     value = bytes_per_step * world / (ms_per_step * 1e-3) / 1e9
 
     # dominant kernel roofline: every launch is the same kernel; time each one
-    # over a separate pass of K launches with events on the launching stream
+    # over a separate pass of K launches with events on the launching stream.
+    # An untimed step is queued first, so that the events bracket the finds'
+    # device time and not the host's submission of the first one.
     k_ms = []
     for _ in range(args.steps):
+        step()
         for i, t in enumerate(tables):
             ev[i][0].record(stream)
             dd.dfa_find(text, t, pos[i], cnt[i], ws, cfg=cfgs[i], stream=stream)

@@ -1832,40 +1832,43 @@ __global__ void __launch_bounds__(1024)
     k_tile_offsets(unsigned long long* tile_sum, int64_t ntiles, const unsigned long long* base_in,
                    unsigned long long* count)
 {
+    // one block of 1024 threads; thread i scans its own contiguous run of
+    // tiles (loads issued back to back), then one block scan of the runs
     __shared__ unsigned long long s_warp[32];
-    __shared__ unsigned long long s_carry;
+    __shared__ unsigned long long s_base;     // read before anyone writes *count
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = base_in ? *base_in : 0ull;
+    if (threadIdx.x == 0) s_base = base_in ? *base_in : 0ull;
+    const int64_t per = (ntiles + 1023) / 1024;
+    const int64_t t0 = min((int64_t)threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
+    unsigned long long sum = 0;
+#pragma unroll 4
+    for (int64_t t = t0; t < t1; t++) sum += tile_sum[t];
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
     __syncthreads();
-    for (int64_t t0 = 0; t0 < ntiles; t0 += 1024) {
-        const int64_t t = t0 + threadIdx.x;
-        const unsigned long long v = t < ntiles ? tile_sum[t] : 0ull;
-        unsigned long long x = v;
+    if (warp == 0) {
+        unsigned long long w = s_warp[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
         }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long w = s_warp[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            s_warp[lane] = w;                  // inclusive over warps
-        }
-        __syncthreads();
-        const unsigned long long carry = s_carry;
-        const unsigned long long excl = carry + (warp ? s_warp[warp - 1] : 0ull) + x - v;
-        if (t < ntiles) tile_sum[t] = excl;
-        __syncthreads();
-        if (threadIdx.x == 1023) s_carry = excl + v;
-        __syncthreads();
+        s_warp[lane] = w;                      // inclusive over warps
     }
-    if (threadIdx.x == 0) *count = s_carry;
+    __syncthreads();
+    const unsigned long long base = s_base;
+    unsigned long long run = base + (warp ? s_warp[warp - 1] : 0ull) + x - sum;
+    for (int64_t t = t0; t < t1; t++) {
+        const unsigned long long v = tile_sum[t];
+        tile_sum[t] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) *count = base + s_warp[31];
 }
 
 // Pass 3 of the staged two-pass find, one warp per (tile, walker warp)
