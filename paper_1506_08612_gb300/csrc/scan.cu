@@ -780,16 +780,18 @@ constexpr int kTSlotsDense = 16;                 // staged positions per row (de
 // half the throughput, so the depth is capped here.
 constexpr int kMaxStages = 4;
 constexpr int kRelaxedCountStages = 2;           // ring depth of the relaxed count pass
-// Default row length (stages of 64 bytes) of a long text: relaxed layouts
-// 12 stages (16 below m = 12), exact layouts 15.  Measured on 3.2e9 bytes:
-// finds of m = 16 and 64 0.624 ms at 20 stages (1280 B), 0.553/0.557 at 12,
-// 0.565/0.579 at 10, 0.58-0.60 at 11 and 13; m = 8 0.713 at 12, 0.702 at
-// 15, 0.695 at 16 (more replayed stages, longer rows amortise the tile end);
-// the dense find of m = 4 0.960 at 20, 0.941 at 16, 0.911 at 15, 0.925 at 14.
+// Default row length (stages of 64 bytes) of a long text: relaxed layouts 12
+// stages, layout 1 finds (the staged dense pass) 16, other exact scans 15.
+// Measured on 3.2e9 bytes (device time of one call): finds of m = 8 and 16
+// 0.614/0.550 ms at 12 stages, 0.615/0.562 at 14, 0.623/0.574 at 16, 0.633/0.560
+// at 10, m = 16 and 64 0.62 at 20; the dense find of m = 4 (m = 5) 0.650
+// (0.583) at 16, 0.662 (0.658) at 15, 0.682 (0.639) at 14, 0.696 (0.625) at
+// 12: rows of a multiple of 128 bytes stream better (at 15 stages the dense
+// pass read 1.12x its text from DRAM); counts of m = 4 0.684 at 15, 0.696
+// at 16.
 constexpr int kDefaultStagesRelaxed = 12;
-constexpr int kDefaultStagesRelaxedShort = 16;   // m < kShortRelaxedM
-constexpr int kShortRelaxedM = 12;
 constexpr int kDefaultStagesExact = 15;
+constexpr int kDefaultStagesDenseFind = 16;
 constexpr int kDefer = 4;                        // tiles whose positions wait for their offset
 constexpr int kTicketRing = 8;
 // How many tiles ahead of the slowest walker warp the ticket warp may claim
@@ -2245,7 +2247,8 @@ constexpr int64_t kMinDefaultTile = 256 * 64;   // workspace sizing for cfg == N
 
 // Launch configuration for a scan of n bytes (n_avail readable).  The TMA
 // loader needs a 16-byte aligned text holding at least two full rows.
-int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int sms, int m, Resolved* r)
+int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int sms, int m, bool find,
+            Resolved* r)
 {
     // default layout (the TMA kernel's): short patterns walk the four-step
     // table exactly; from kOptMinM on the relaxed walk takes the flagged
@@ -2273,8 +2276,9 @@ int resolve(const dfa_config* cfg, int64_t n, int64_t n_avail, bool aligned, int
             const int64_t per = (int64_t)kRows * kStageW * 4 * sms;
             int64_t sps = (n + per - 1) / per;
             const bool relaxed = r->layout == kLayoutK4F || r->layout == kLayoutK4S;
-            const int64_t cap = !relaxed ? kDefaultStagesExact
-                                         : (m < kShortRelaxedM ? kDefaultStagesRelaxedShort : kDefaultStagesRelaxed);
+            const int64_t cap = relaxed ? kDefaultStagesRelaxed
+                                : (find && r->layout == kLayoutK4 && m <= 8) ? kDefaultStagesDenseFind
+                                                                            : kDefaultStagesExact;
             sps = std::min<int64_t>(std::max<int64_t>(sps, 2), cap);
             chunk = sps * kStageW;
         }
@@ -2483,7 +2487,7 @@ int launch_count(const uint8_t* d_text, int64_t n, const dfa_table* t, uint64_t*
     if (rc) return rc;
     if (dev != t->device) return DFA_EINVAL;
     Resolved r;
-    rc = resolve(cfg, n, n, ((uintptr_t)d_text & 15u) == 0, di->sms, t->m, &r);
+    rc = resolve(cfg, n, n, ((uintptr_t)d_text & 15u) == 0, di->sms, t->m, false, &r);
     if (rc) return rc;
     CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st));
     if (n < t->m) return DFA_OK;
@@ -2570,7 +2574,7 @@ int launch_find(const uint8_t* d_text, int64_t n, int64_t n_own, const dfa_table
     if (rc) return rc;
     if (dev != t->device) return DFA_EINVAL;
     Resolved r;
-    rc = resolve(cfg, n_own, n, ((uintptr_t)d_text & 15u) == 0, di->sms, t->m, &r);
+    rc = resolve(cfg, n_own, n, ((uintptr_t)d_text & 15u) == 0, di->sms, t->m, true, &r);
     if (rc) return rc;
     ScanArgs a;
     fill_args(&a, d_text, n, n_own, t, r);
@@ -2790,12 +2794,11 @@ int64_t dfa_find_workspace_bytes(int64_t n, const dfa_config* cfg)
         sms = 152;
     }
     // the default layout and rows depend on m (layout 1 below kOptMinM,
-    // shorter relaxed rows from kShortRelaxedM on): size for every pattern
-    // length that takes the staged two-pass find
+    // a relaxed layout from there on): size for both
     int64_t need = single;
-    for (int m : {1, kOptMinM, kShortRelaxedM}) {
+    for (int m : {1, kOptMinM}) {
         Resolved r;
-        if (resolve(cfg, n, n, true, sms, m, &r) == DFA_OK && two_pass_layout(r, m)) {
+        if (resolve(cfg, n, n, true, sms, m, true, &r) == DFA_OK && two_pass_layout(r, m)) {
             const int64_t tile_bytes = (int64_t)kRows * r.chunk;
             need = std::max(need, work_bytes_two_pass((n + tile_bytes - 1) / tile_bytes, r.layout));
         }

@@ -94,15 +94,15 @@ def test_oracle_lib_builds():
 
 def test_workspace_covers_every_default_row_length():
     """With no configuration the workspace must hold the staged two-pass
-    find of every pattern length: below m = 8 layout 1 with 960-byte rows
+    find of every pattern length: below m = 8 layout 1 with 1024-byte rows
     staging up to 16 u16 end offsets a row, from m = 8 the relaxed layout
-    with 1024-byte rows (768 from m = 12 on, the most rows) keeping a u64
-    stage mask a row; one tile is 512 rows; per tile a u64 total (and 16 u32
-    walker-warp totals for layout 1), per row a u16 count."""
+    with 768-byte rows keeping a u64 stage mask a row; one tile is 512 rows;
+    per tile a u64 total (and 16 u32 walker-warp totals for layout 1), per
+    row a u16 count."""
     import paper_1506_08612_gb300 as dd
     n = 3_200_000_000
     need = 0
-    for row_bytes, per_row, per_tile in ((960, 32, 64), (1024, 8, 0), (768, 8, 0)):
+    for row_bytes, per_row, per_tile in ((1024, 32, 64), (768, 8, 0)):
         tiles = -(-n // (512 * row_bytes))
         need = max(need, 8 * (2 + tiles) + tiles * per_tile + tiles * 512 * (2 + per_row))
     assert dd._lib.dfa_find_workspace_bytes(n, None) >= need

@@ -435,7 +435,7 @@ def test_staged_row_end_offsets(gpu, chunk):
         assert _check(gpu, t, pat, cfg) > 0
 
 
-@pytest.mark.parametrize("chunk", [128, 960])
+@pytest.mark.parametrize("chunk", [128, 960, 1024])
 def test_staged_dense_rows_past_their_slots(gpu, chunk):
     # layout 1 stages up to 16 end offsets a row: rows holding 0..23 true
     # copies of a short pattern in turn (rows above 16 are walked again by
