@@ -51,11 +51,12 @@ WORKLOAD = "genome-scale single-pattern scan"
 # one dfa_find per pattern, the two-pass find: pass 1 k_scan_tma (m >= 8:
 # the relaxed count kernel, leaving row counts and the stage masks of its
 # exact replays; m < 8: the relaxed dense walk recording each row's end
-# offsets), k_tile_offsets (scan of the tile totals) and pass 3 (k_place
-# copies the recorded offsets; k_place_masked walks the masked bytes of the
-# rows with accepts); the events time the whole call
+# offsets, then k_tile_offsets scans the tile totals; for m >= 8 the count
+# kernel's last CTA does) and pass 3 (k_place copies the recorded offsets;
+# k_place_masked walks the masked bytes of the rows with accepts); the
+# events time the whole call
 DOMINANT_KERNEL = ("dfa_find = k_scan_tma (TMA-staged pass 1) + k_tile_offsets + k_place (m < 8) "
-                   "or k_place_masked (m >= 8)")
+                   "or k_scan_tma (pass 1, tile scan in its last CTA) + k_place_masked (m >= 8)")
 
 
 def parse():
@@ -98,15 +99,17 @@ def dist_env():
 
 def kernels_per_find(m, cfg):
     """Kernels one dfa_find launches on the TMA path: the staged two-pass
-    find (count pass, tile scan, placement) for the relaxed layouts at any m
-    and for layout 1 up to m = 8 (the library's defaults: layout 1 below
+    find for the relaxed layouts at any m (count pass, its last CTA scanning
+    the tile totals, and placement: two) and for layout 1 up to m = 8 (dense
+    pass, tile scan, copy: three; the library's defaults: layout 1 below
     m = 8, layout 4 from there; the workspace bench.py passes always has
     room for it), else the single-pass find kernel."""
     layout = (cfg or {}).get("layout", 0)
     if layout == 0:
         layout = 4 if m >= 8 else 1
-    staged = layout in (3, 4) or (layout == 1 and m <= 8)
-    return 3 if staged else 1
+    if layout in (3, 4):
+        return 2
+    return 3 if layout == 1 and m <= 8 else 1
 
 
 def config_dict(n, world, cfg):
@@ -869,7 +872,7 @@ def measure_small(dd, dev, stream, reps=20, graph_reps=200):
                          "unit": "GB/s", "frac": round(algo / (med * 1e-6) / 1e9 / peak, 4),
                          "traffic": None, "peak_kind": f"{kind} (hbm_gbs copy bandwidth)",
                          "note": "16 MiB is a few microseconds of HBM time: launch latency bounds it"},
-            "launches_per_find": 3}
+            "launches_per_find": kernels_per_find(8, None)}
 
 
 def run_shard(args):

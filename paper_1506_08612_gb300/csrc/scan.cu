@@ -835,7 +835,55 @@ struct TmaArgs {
     // layout 1: each walker warp's total count of the tile, at
     // warp_sum[t * kWalkWarps + warp]
     uint32_t* warp_sum;
+    // first pass of a two-pass find on a relaxed layout: the last CTA to
+    // finish turns tile_sum into each tile's first index (scan_base added)
+    // and writes the total to scan_count; a.count then counts the finished
+    // CTAs. Null otherwise (layout 1 scans in k_tile_offsets).
+    unsigned long long* scan_count;
+    const unsigned long long* scan_base;
 };
+
+// Exclusive scan of ntiles tile totals by one CTA (blockDim.x a multiple of
+// 32): tile_sum[t] becomes base + the totals of the tiles before t, *count
+// base + all of them. Each thread scans its own contiguous run of tiles,
+// then one block scan of the runs. The totals were added by other CTAs'
+// atomics: read at L2.
+__device__ __forceinline__ void scan_tile_totals(unsigned long long* tile_sum, int64_t ntiles,
+                                                 unsigned long long base, unsigned long long* count)
+{
+    __shared__ unsigned long long s_warp[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    const int64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int64_t t0 = min((int64_t)threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
+    unsigned long long sum = 0;
+#pragma unroll 4
+    for (int64_t t = t0; t < t1; t++) sum += __ldcg(tile_sum + t);
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < nw ? s_warp[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;                      // inclusive over warps
+    }
+    __syncthreads();
+    unsigned long long run = base + (warp ? s_warp[warp - 1] : 0ull) + x - sum;
+    for (int64_t t = t0; t < t1; t++) {
+        const unsigned long long v = __ldcg(tile_sum + t);
+        tile_sum[t] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) *count = base + s_warp[nw - 1];
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -1801,6 +1849,24 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
         if (lane == 0) s_sum[warp] = total;
+        if (OPT && p.scan_count) {
+            // pass 1 of a two-pass find (relaxed layouts): the CTAs count
+            // themselves out; the last one scans the tile totals (every
+            // warp's atomics on them are fenced before its CTA's ticket; no
+            // CTA waits for another)
+            __shared__ int s_last;
+            if (lane == 0) __threadfence();
+            named_sync_walkers();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                s_last = atomicAdd(a.count, 1ull) == (unsigned long long)gridDim.x - 1ull;
+            }
+            named_sync_walkers();
+            if (!s_last) return;
+            __threadfence();
+            scan_tile_totals(p.tile_sum, a.ntiles, p.scan_base ? *p.scan_base : 0ull, p.scan_count);
+            return;
+        }
         named_sync_walkers();
         if (threadIdx.x == 0 && !*abort_flag) {
             unsigned long long v = 0;
@@ -1824,53 +1890,23 @@ __global__ void __launch_bounds__(FIND ? kTmaThreads : kWalkThreads, (!FIND && D
 //
 // For the relaxed-walk layouts a find is: the count kernel writing every
 // row's count and every tile's total (pass 1), an exclusive scan of the tile
-// totals (pass 2), and an exact walk of just the rows that hold an accept,
-// each writing its positions at its own offset (pass 3).  Sparse patterns
-// have few such rows, so the find costs little more than the count.
+// totals (pass 2, done by pass 1's last CTA: scan_tile_totals), and an exact
+// walk of just the rows that hold an accept, each writing its positions at
+// its own offset (pass 3).  Sparse patterns have few such rows, so the find
+// costs little more than the count.
 
-// Pass 2 (one CTA of 1024 threads): tile_sum[t] becomes the global index of
-// tile t's first position (base included); *count becomes base + total.
+// Pass 2 of layout 1's two-pass find (one CTA of 1024 threads): tile_sum[t]
+// becomes the global index of tile t's first position (base included);
+// *count becomes base + total.  (The relaxed layouts scan in pass 1's last
+// CTA; on the dense pass that tail cost more than this launch.)
 __global__ void __launch_bounds__(1024)
     k_tile_offsets(unsigned long long* tile_sum, int64_t ntiles, const unsigned long long* base_in,
                    unsigned long long* count)
 {
-    // one block of 1024 threads; thread i scans its own contiguous run of
-    // tiles (loads issued back to back), then one block scan of the runs
-    __shared__ unsigned long long s_warp[32];
     __shared__ unsigned long long s_base;     // read before anyone writes *count
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_base = base_in ? *base_in : 0ull;
-    const int64_t per = (ntiles + 1023) / 1024;
-    const int64_t t0 = min((int64_t)threadIdx.x * per, ntiles), t1 = min(t0 + per, ntiles);
-    unsigned long long sum = 0;
-#pragma unroll 4
-    for (int64_t t = t0; t < t1; t++) sum += tile_sum[t];
-    unsigned long long x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        unsigned long long w = s_warp[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        s_warp[lane] = w;                      // inclusive over warps
-    }
-    __syncthreads();
-    const unsigned long long base = s_base;
-    unsigned long long run = base + (warp ? s_warp[warp - 1] : 0ull) + x - sum;
-    for (int64_t t = t0; t < t1; t++) {
-        const unsigned long long v = tile_sum[t];
-        tile_sum[t] = run;
-        run += v;
-    }
-    if (threadIdx.x == 0) *count = base + s_warp[31];
+    scan_tile_totals(tile_sum, ntiles, s_base, count);
 }
 
 // Pass 3 of the staged two-pass find, one warp per (tile, walker warp)
@@ -2391,7 +2427,8 @@ int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* fn)
 // Launch the TMA-staged kernel for the filled-in arguments `a`.
 int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool find, int dev,
                const DeviceInfo* di, cudaStream_t st, uint16_t* rows = nullptr, uint16_t* stage = nullptr,
-               unsigned long long* masks = nullptr, uint32_t* warp_sum = nullptr)
+               unsigned long long* masks = nullptr, uint32_t* warp_sum = nullptr,
+               unsigned long long* scan_count = nullptr, const unsigned long long* scan_base = nullptr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 encode;
     int rc = tensor_map_encoder(&encode);
@@ -2411,6 +2448,8 @@ int launch_tma(const Resolved& r, const ScanArgs& a, const dfa_table* t, bool fi
     p.stage = stage;
     p.masks = masks;
     p.warp_sum = warp_sum;
+    p.scan_count = scan_count;
+    p.scan_base = scan_base;
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)p.nrows_full};
     cuuint64_t strides[1] = {(cuuint64_t)C};
@@ -2531,7 +2570,7 @@ bool two_pass_layout(const Resolved& r, int m)
     return r.loader == 2 && (r.layout == kLayoutK4F || r.layout == kLayoutK4S || (r.layout == kLayoutK4 && m <= 8));
 }
 
-// Passes 1-3 of the staged two-pass find (see k_tile_offsets, k_place); the
+// Passes 1-3 of the staged two-pass find (see scan_tile_totals, k_tile_offsets, k_place); the
 // header and tile words of the workspace are already zero.
 int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, int dev, const DeviceInfo* di,
                     cudaStream_t st)
@@ -2543,12 +2582,17 @@ int launch_two_pass(const Resolved& r, const ScanArgs& a, const dfa_table* t, in
     uint16_t* stage = dense ? reinterpret_cast<uint16_t*>(wb + staged_tail_off(a.ntiles)) : nullptr;
     unsigned long long* masks = dense ? nullptr : reinterpret_cast<unsigned long long*>(wb + staged_tail_off(a.ntiles));
     ScanArgs a1 = a;
-    a1.count = a.work;                    // the pass-1 total lands in the unused ticket word
+    // the unused ticket word: pass 1's total (layout 1), else its count of
+    // finished CTAs (pass 2, the tile scan, runs in its last CTA)
+    a1.count = a.work;
     uint32_t* wsum = dense ? reinterpret_cast<uint32_t*>(wb + staged_wsum_off(a.ntiles)) : nullptr;
-    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, stage, masks, wsum);
+    int rc = launch_tma(r, a1, t, false, dev, di, st, rows, stage, masks, wsum, dense ? nullptr : a.count,
+                        a.base_in);
     if (rc) return rc;
-    k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
-    CUDA_TRY(cudaGetLastError());
+    if (dense) {
+        k_tile_offsets<<<1, 1024, 0, st>>>(tile_sum, a.ntiles, a.base_in, a.count);
+        CUDA_TRY(cudaGetLastError());
+    }
     const void* fn = dense ? (const void*)k_place : (const void*)k_place_masked;
     int occ = occupancy(fn, 256, 0, dev, di->smem_optin);
     if (occ <= 0) return fail("placement kernel does not fit on an SM (occupancy 0)");

@@ -9,12 +9,14 @@ import bench
 
 
 def test_kernels_per_find():
-    for m in (4, 7, 8, 16, 64):
-        assert bench.kernels_per_find(m, None) == 3        # count pass, tile scan, placement
+    for m in (4, 7):
+        assert bench.kernels_per_find(m, None) == 3        # dense pass, tile scan, copy
+    for m in (8, 16, 64):
+        assert bench.kernels_per_find(m, None) == 2        # count pass (+ tile scan), placement
     assert bench.kernels_per_find(16, {"layout": 1}) == 1  # single-pass find
     assert bench.kernels_per_find(8, {"layout": 1}) == 3
     assert bench.kernels_per_find(4, {"layout": 2}) == 1
-    assert bench.kernels_per_find(4, {"layout": 4}) == 3
+    assert bench.kernels_per_find(4, {"layout": 4}) == 2
 
 
 def test_measured_peak_and_config():
