@@ -387,13 +387,19 @@ int64_t dfa_multi_smem_bytes(const dfa_multi* table);
  * uint64[nseq * npat], row-major by sequence, overwritten.  Occurrences are
  * owned by the chunk holding their start (Algorithm 1 with patterns of
  * several lengths: each chunk reads m_max - 1 bytes past its end).
- *   cfg: threads (128, 256 or 512 per CTA) and chunk (bytes per thread per
- *        tile, multiple of 16); layout: the table in shared memory, 1 = one
- *        copy (2 bytes an entry), 2 = 32 per-lane copies (4 bytes an entry
- *        each, every warp's lookups conflict-free; DFA_EINVAL when they do
- *        not fit), 0 = the copies when CTAs of 1024 threads a SM still fit
- *        in 200 KiB (about 198 states at 512 threads); other fields
- *        ignored; NULL = 256 x 1024, layout 0.
+ *   cfg: threads (128, 256, 512 or 1024 per CTA) and chunk (bytes per
+ *        thread per tile, multiple of 16); layout: the table in shared
+ *        memory, 1 = one copy (2 bytes an entry), 2 = 32 per-lane copies
+ *        (4 bytes an entry each, every warp's lookups conflict-free;
+ *        DFA_EINVAL when they do not fit), 3, 4, 5 = one table copy and 2,
+ *        4 or 8 copies of every state's output counter, lane l adding to
+ *        copy l % copies so that the atomics of an output-dense automaton
+ *        (a k-mer census) spread over more banks (512 or 1024 threads only;
+ *        shared memory: the table + copies x 4 bytes a state; DFA_EINVAL
+ *        when it does not fit), 0 = the per-lane table copies when CTAs of
+ *        1024 threads a SM still fit in 200 KiB (about 198 states at 512
+ *        threads), else layout 1; other fields ignored; NULL = 256 x 1024,
+ *        layout 0.
  * Asynchronous on `stream`; allocates nothing (capturable in a CUDA graph).
  * Errors: DFA_EINVAL, DFA_ECUDA.
  */

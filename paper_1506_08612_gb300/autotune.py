@@ -18,14 +18,16 @@ the caller's own text and remembers the fastest per key:
   after each new entry;
 * ``DNADFA_CONFIG`` (a JSON object of dfa_config fields) forces one
   configuration for every call and skips tuning; the multi-pattern tuner
-  keeps only the fields dfa_multi_count reads (threads, chunk, a layout of
-  its own 0..2, ctas_per_sm).
+  keeps only the fields dfa_multi_count reads (threads, chunk, ctas_per_sm,
+  and its table layout: ``multi_layout`` 0..5, or ``layout`` when it is
+  0..2, a value the two counts read alike).
 
 Candidates: the multi-pattern count varies threads x chunk x table layout
-(one shared copy, or one copy per lane where the automaton is small enough:
-the library refuses the copies otherwise, and a refused candidate is
-skipped); one pattern varies the table layout x row length of the TMA
-kernel, timed on the call it will serve (dfa_count or dfa_find).
+(one shared copy; one copy per lane where the automaton is small enough;
+one table copy with 2, 4 or 8 copies of each state's counter at 512 or
+1024 threads: the library refuses what does not fit, and a refused
+candidate is skipped); one pattern varies the table layout x row length of
+the TMA kernel, timed on the call it will serve (dfa_count or dfa_find).
 
 Timing and selection are separate from the GPU so that the host logic runs
 (and is tested) without one: ``select_best`` takes any timing callable.
@@ -41,9 +43,12 @@ import threading
 # Candidate grids.  Multi-pattern count: threads per CTA in {128, 256, 512}
 # (the kernel's instantiations) x chunk bytes; the chunk must stay well above
 # m_max - 1 so the overlap re-scan (Algorithm 1) stays a small fraction.
-MULTI_THREADS = (128, 256, 512)
+MULTI_THREADS = (128, 256, 512, 1024)
 MULTI_CHUNKS = (256, 512, 1024, 2048, 4096)
-MULTI_LAYOUTS = (1, 2)            # one shared table copy / 32 per-lane copies
+# one shared table copy / 32 per-lane copies / one table copy with 2, 4, 8
+# counter copies a state (at 512 and 1024 threads)
+MULTI_LAYOUTS = (1, 2, 3, 4, 5)
+MULTI_COPY_THREADS = (512, 1024)
 # One pattern, TMA loader: chunk bytes per row (multiples of 64) x layout
 # (0 = library default for m, 1 = four-step table with accept counts,
 # 3 = four-step states with exact replays, 4 = relaxed walk on the flagged
@@ -51,7 +56,7 @@ MULTI_LAYOUTS = (1, 2)            # one shared table copy / 32 per-lane copies
 SINGLE_CHUNKS = (0, 512, 768, 960, 1024, 1280)
 SINGLE_LAYOUTS = (0, 1, 3, 4)
 # Bumped when a kernel or its candidate space changes.
-KERNEL_VERSION = "v3"
+KERNEL_VERSION = "v4"
 
 _lock = threading.Lock()
 _cache: dict | None = None
@@ -106,14 +111,17 @@ def forced_config(kind: str = "single") -> dict | None:
     d = json.loads(s)
     if not isinstance(d, dict):
         raise ValueError("DNADFA_CONFIG must be a JSON object")
-    allowed = {"layout", "threads", "chunk", "loader", "ctas_per_sm"}
+    allowed = {"layout", "threads", "chunk", "loader", "ctas_per_sm", "multi_layout"}
     bad = set(d) - allowed
     if bad:
         raise ValueError(f"DNADFA_CONFIG: unknown fields {sorted(bad)}")
     out = {k: int(v) for k, v in d.items()}
+    multi_layout = out.pop("multi_layout", None)
     if kind == "multi":
         out.pop("loader", None)
-        if out.get("layout", 0) not in (0, 1, 2):
+        if multi_layout is not None:
+            out["layout"] = multi_layout
+        elif out.get("layout", 0) not in (0, 1, 2):
             out.pop("layout")
     return out
 
@@ -149,6 +157,8 @@ def multi_candidates(mmax: int) -> list[dict]:
     out = []
     for lay in MULTI_LAYOUTS:
         for t in MULTI_THREADS:
+            if lay >= 3 and t not in MULTI_COPY_THREADS:
+                continue
             for c in MULTI_CHUNKS:
                 if c >= 4 * max(mmax - 1, 1):
                     out.append({"threads": t, "chunk": c, "layout": lay})

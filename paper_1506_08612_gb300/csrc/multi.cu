@@ -101,7 +101,8 @@ struct MultiTab {
     const uint16_t* delta;   // 4 * state + code -> 4 * next | (out(next) not empty)
     const uint32_t* rep;     // per-lane copies: entry i of lane l at rep[32 * i + l]
     uint32_t lane;           // threadIdx.x % 32
-    uint32_t* hs;            // per-state counters
+    uint32_t* hs;            // this lane's per-state counters: with 2^CG copies a
+                             // state, copy g = lane % 2^CG of state q at hs[q << CG]
     const MultiArgs* args;
     unsigned long long* row; // this sequence's per-pattern global counts
     const LocateArgs* loc;   // dfa_multi_locate: where occurrences go
@@ -149,13 +150,14 @@ __device__ __noinline__ void locate_out(const LocateArgs* a, uint32_t st, uint32
 // the chunk: an output of length m_p started before the chunk's end (is
 // owned) iff m_p > d.  All of the state's outputs owned: its counter; some:
 // those patterns one by one in global memory.
+template <int CG>
 __device__ __noinline__ void emit_overlap(const MultiArgs* a, uint32_t* hs, unsigned long long* row, uint32_t st,
                                           uint32_t d)
 {
     const uint32_t shortest = __ldg(a->span + 2 * st), longest = __ldg(a->span + 2 * st + 1);
     if (longest <= d) return;
     if (shortest > d) {
-        atomicAdd(hs + st, 1u);
+        atomicAdd(hs + (st << CG), 1u);
         return;
     }
     const uint32_t k1 = __ldg(a->off + st + 1);
@@ -167,15 +169,15 @@ __device__ __noinline__ void emit_overlap(const MultiArgs* a, uint32_t* hs, unsi
 
 // Output flag set on entry e ending at offset j: owned (CHECK false, or
 // j < own) adds one to the state's counter; a locate writes the positions.
-template <bool CHECK, bool LOC = false>
+template <bool CHECK, bool LOC = false, int CG = 0>
 __device__ __forceinline__ void emit(const MultiTab& M, uint32_t e, uint32_t j, uint32_t own)
 {
     if (LOC)
         locate_out(M.loc, e >> 2, j, own, M.s0);
     else if (!CHECK || j < own)
-        atomicAdd(M.hs + (e >> 2), 1u);
+        atomicAdd(M.hs + ((e >> 2) << CG), 1u);
     else
-        emit_overlap(M.args, M.hs, M.row, e >> 2, j - own + 1u);
+        emit_overlap<CG>(M.args, M.hs, M.row, e >> 2, j - own + 1u);
 }
 
 // Four bases of a word w, byte k ending at offset j + k: four dependent
@@ -189,7 +191,7 @@ __device__ __forceinline__ uint32_t lookup(const MultiTab& M, uint32_t idx)
     return M.delta[idx];
 }
 
-template <bool CHECK, bool LOC = false, bool REP = false>
+template <bool CHECK, bool LOC = false, bool REP = false, int CG = 0>
 __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
 {
     const uint32_t c = (w >> 1) & 0x03030303u;
@@ -199,61 +201,63 @@ __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uin
     const uint32_t e3 = lookup<REP>(M, (e2 & ~3u) | (c >> 24));
     ent = e3;
     if ((e0 | e1 | e2 | e3) & 1u) {
-        if (e0 & 1u) emit<CHECK, LOC>(M, e0, j, own);
-        if (e1 & 1u) emit<CHECK, LOC>(M, e1, j + 1, own);
-        if (e2 & 1u) emit<CHECK, LOC>(M, e2, j + 2, own);
-        if (e3 & 1u) emit<CHECK, LOC>(M, e3, j + 3, own);
+        if (e0 & 1u) emit<CHECK, LOC, CG>(M, e0, j, own);
+        if (e1 & 1u) emit<CHECK, LOC, CG>(M, e1, j + 1, own);
+        if (e2 & 1u) emit<CHECK, LOC, CG>(M, e2, j + 2, own);
+        if (e3 & 1u) emit<CHECK, LOC, CG>(M, e3, j + 3, own);
     }
 }
 
 // One byte, any value: a non-base sends the walk back to q0 (Sec. III-B:
 // columns outside the alphabet lead to q0).
-template <bool LOC = false, bool REP = false>
+template <bool LOC = false, bool REP = false, int CG = 0>
 __device__ __forceinline__ void byte_any(const MultiTab& M, uint32_t& ent, uint32_t b, uint32_t j, uint32_t own)
 {
     const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
     if (((b ^ (t * 0x11u)) & 0xD9u) == 0x41u) {
         ent = lookup<REP>(M, (ent & ~3u) | ((b >> 1) & 3u));
-        if (ent & 1u) emit<true, LOC>(M, ent, j, own);
+        if (ent & 1u) emit<true, LOC, CG>(M, ent, j, own);
     } else {
         ent = 0u;
     }
 }
 
 // A word holding bases and non-bases, byte by byte.
-template <bool LOC = false, bool REP = false>
+template <bool LOC = false, bool REP = false, int CG = 0>
 __device__ __forceinline__ uint32_t word_mixed(const MultiTab& M, uint32_t ent, uint32_t w, uint32_t j, uint32_t own)
 {
 #pragma unroll 1
-    for (int k = 0; k < 4; k++) byte_any<LOC, REP>(M, ent, (w >> (8 * k)) & 0xFFu, j + k, own);
+    for (int k = 0; k < 4; k++) byte_any<LOC, REP, CG>(M, ent, (w >> (8 * k)) & 0xFFu, j + k, own);
     return ent;
 }
 
-template <bool CHECK, bool LOC = false, bool REP = false>
+template <bool CHECK, bool LOC = false, bool REP = false, int CG = 0>
 __device__ __forceinline__ void word_any(const MultiTab& M, uint32_t& ent, uint32_t w, uint32_t j, uint32_t own)
 {
     const uint32_t bad = word_bad_m(w);
     if (bad == 0u) {
-        word_bases<CHECK, LOC, REP>(M, ent, w, j, own);
+        word_bases<CHECK, LOC, REP, CG>(M, ent, w, j, own);
     } else if (((bad - 0x01010101u) & ~bad & 0x80808080u) == 0u) {
         ent = 0u;                                   // four non-bases (an N block)
     } else {
-        ent = word_mixed<LOC, REP>(M, ent, w, j, own);
+        ent = word_mixed<LOC, REP, CG>(M, ent, w, j, own);
     }
 }
 
-template <bool CHECK, bool LOC = false, bool REP = false>
+template <bool CHECK, bool LOC = false, bool REP = false, int CG = 0>
 __device__ __forceinline__ void vec_any(const MultiTab& M, uint32_t& ent, uint4 v, uint32_t j, uint32_t own)
 {
-    word_any<CHECK, LOC, REP>(M, ent, v.x, j, own);
-    word_any<CHECK, LOC, REP>(M, ent, v.y, j + 4, own);
-    word_any<CHECK, LOC, REP>(M, ent, v.z, j + 8, own);
-    word_any<CHECK, LOC, REP>(M, ent, v.w, j + 12, own);
+    word_any<CHECK, LOC, REP, CG>(M, ent, v.x, j, own);
+    word_any<CHECK, LOC, REP, CG>(M, ent, v.y, j + 4, own);
+    word_any<CHECK, LOC, REP, CG>(M, ent, v.z, j + 8, own);
+    word_any<CHECK, LOC, REP, CG>(M, ent, v.w, j + 12, own);
 }
 
 // REP: the table as 32 per-lane copies (4 bytes an entry) instead of one
 // (2 bytes an entry), for automata small enough (kMultiRepStates).
-template <int THREADS, bool REP>
+// CG: 2^CG copies of each state's counter, lane l adding to copy l % 2^CG
+// (the lanes' atomics of a dense output then spread over more banks).
+template <int THREADS, bool REP, int CG = 0>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const __grid_constant__ MultiArgs a)
 {
     extern __shared__ __align__(16) uint8_t msm[];
@@ -274,9 +278,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
     M.delta = reinterpret_cast<const uint16_t*>(msm);
     M.rep = reinterpret_cast<const uint32_t*>(msm);
     M.lane = threadIdx.x & 31u;
-    M.hs = reinterpret_cast<uint32_t*>(msm + table_bytes);
+    uint32_t* const hs0 = reinterpret_cast<uint32_t*>(msm + table_bytes);
+    M.hs = hs0 + (M.lane & ((1u << CG) - 1u));
     M.args = &a;
-    for (int q = threadIdx.x; q < a.nstates; q += THREADS) M.hs[q] = 0u;
+    for (int q = threadIdx.x; q < (a.nstates << CG); q += THREADS) hs0[q] = 0u;
     __syncthreads();
 
     // the per-state counters go to the per-pattern counts of sequence sq:
@@ -285,9 +290,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
         __syncthreads();
         unsigned long long* row = a.counts + (int64_t)sq * a.npat;
         for (int q = threadIdx.x; q < a.nstates; q += THREADS) {
-            const uint32_t v = M.hs[q];
+            uint32_t* const hq = hs0 + ((uint32_t)q << CG);
+            uint32_t v = 0u;
+#pragma unroll
+            for (int g = 0; g < (1 << CG); g++) {
+                v += hq[g];
+                hq[g] = 0u;
+            }
             if (v) {
-                M.hs[q] = 0u;
                 const uint32_t k1 = __ldg(a.off + q + 1);
                 for (uint32_t k = __ldg(a.off + q); k < k1; k++)
                     atomicAdd(row + __ldg(a.ids + k), (unsigned long long)v);
@@ -321,7 +331,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
         uint32_t j = 0;
         if ((((uintptr_t)base) & 15u) == 0) {
             if ((((uintptr_t)base) & 31u) != 0 && len >= 16) {
-                vec_any<true, false, REP>(M, ent, *reinterpret_cast<const uint4*>(base), 0u, own);
+                vec_any<true, false, REP, CG>(M, ent, *reinterpret_cast<const uint4*>(base), 0u, own);
                 j = 16;
             }
             // owned 32-byte blocks, the next one in flight while one is walked
@@ -334,16 +344,16 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_multi_count(const _
                     const uint4 c0 = a0, c1 = a1;
                     if (g + 1 < nb) ldg32m(base + j + 32 * (g + 1), a0, a1);
                     const uint32_t jj = j + 32u * g;
-                    vec_any<false, false, REP>(M, ent, c0, jj, own);
-                    vec_any<false, false, REP>(M, ent, c1, jj + 16, own);
+                    vec_any<false, false, REP, CG>(M, ent, c0, jj, own);
+                    vec_any<false, false, REP, CG>(M, ent, c1, jj + 16, own);
                 }
                 j += nb << 5;
             }
             // the rest of the chunk and its overlap, 16 bytes at a time
             for (; j + 16 <= len; j += 16)
-                vec_any<true, false, REP>(M, ent, *reinterpret_cast<const uint4*>(base + j), j, own);
+                vec_any<true, false, REP, CG>(M, ent, *reinterpret_cast<const uint4*>(base + j), j, own);
         }
-        for (; j < len; j++) byte_any<false, REP>(M, ent, base[j], j, own);
+        for (; j < len; j++) byte_any<false, REP, CG>(M, ent, base[j], j, own);
     }
     if (cur >= 0) flush(cur);
 }
@@ -429,16 +439,30 @@ __global__ void __launch_bounds__(512) k_sort_segments(int64_t* pos, const unsig
 
 typedef void (*MultiFn)(const MultiArgs);
 
-MultiFn pick_multi(int threads, bool rep)
+// The instantiation for threads, the per-lane table copies (rep) or 2^cg
+// counter copies (one table copy; cg > 0 only at 512 and 1024 threads,
+// where the copies fit beside the table), else null.
+MultiFn pick_multi(int threads, bool rep, int cg)
 {
     if (rep) {
         if (threads == 128) return k_multi_count<128, true>;
+        if (threads == 256) return k_multi_count<256, true>;
         if (threads == 512) return k_multi_count<512, true>;
-        return k_multi_count<256, true>;
+        if (threads == 1024) return k_multi_count<1024, true>;
+        return nullptr;
     }
-    if (threads == 128) return k_multi_count<128, false>;
-    if (threads == 512) return k_multi_count<512, false>;
-    return k_multi_count<256, false>;
+    if (cg == 0) {
+        if (threads == 128) return k_multi_count<128, false>;
+        if (threads == 256) return k_multi_count<256, false>;
+        if (threads == 512) return k_multi_count<512, false>;
+        if (threads == 1024) return k_multi_count<1024, false>;
+        return nullptr;
+    }
+    if (threads == 512) return cg == 1 ? k_multi_count<512, false, 1> : cg == 2 ? k_multi_count<512, false, 2>
+                                                                              : k_multi_count<512, false, 3>;
+    if (threads == 1024) return cg == 1 ? k_multi_count<1024, false, 1> : cg == 2 ? k_multi_count<1024, false, 2>
+                                                                                : k_multi_count<1024, false, 3>;
+    return nullptr;
 }
 
 int multi_fail(const char* what, cudaError_t err)
@@ -845,14 +869,18 @@ int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32
     if (!t->d_mem) return set_last_error(DFA_EINVAL, "dfa_multi_count: the automaton has no device copy (dfa_multi_attach)");
     const int threads = cfg && cfg->threads ? cfg->threads : 256;
     const int chunk = cfg && cfg->chunk ? cfg->chunk : 1024;
-    if (threads != 128 && threads != 256 && threads != 512) return DFA_EINVAL;
+    if (threads != 128 && threads != 256 && threads != 512 && threads != 1024) return DFA_EINVAL;
     if (chunk < 16 || chunk > 32768 || (chunk & 15)) return DFA_EINVAL;
-    // table layout: 1 = one shared copy, 2 = 32 per-lane copies, 0 = the
-    // copies when the SM still holds 1024 threads' worth of CTAs
+    // table layout: 1 = one shared copy, 2 = 32 per-lane copies, 3..5 = one
+    // shared copy and 2, 4 or 8 copies of each state's counter (lane l adds
+    // to copy l % copies: the lanes' atomics of a dense output spread over
+    // more banks; 512 or 1024 threads), 0 = the per-lane copies when the SM
+    // still holds 1024 threads' worth of CTAs, else layout 1
     const int layout = cfg ? cfg->layout : 0;
-    if (layout < 0 || layout > 2) return DFA_EINVAL;
+    if (layout < 0 || layout > 5) return DFA_EINVAL;
     const int64_t rep_smem = (int64_t)t->nstates * (4 * 32 * 4 + 4);
     const bool rep = layout == 2 || (layout == 0 && rep_smem * (1024 / threads) <= kRepSmemPerSm);
+    const int cg = layout >= 3 ? layout - 2 : 0;
     int dev;
     cudaError_t err;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return multi_fail("dfa_multi_count", err);
@@ -883,8 +911,10 @@ int dfa_multi_count(const uint8_t* const* d_texts, const int64_t* lengths, int32
     if ((err = cudaMemsetAsync(d_counts, 0, (size_t)nseq * t->npat * 8, st)) != cudaSuccess)
         return multi_fail("dfa_multi_count", err);
     if (a.tile0[nseq] == 0) return DFA_OK;
-    MultiFn fn = pick_multi(threads, rep);
-    const int smem = (int)(rep ? rep_smem : dfa_multi_smem_bytes(t));
+    MultiFn fn = pick_multi(threads, rep, cg);
+    if (!fn) return set_last_error(DFA_EINVAL, "dfa_multi_count: counter copies need 512 or 1024 threads");
+    const int64_t smem64 = rep ? rep_smem : (int64_t)t->delta_bytes + ((int64_t)t->nstates << cg) * 4;
+    const int smem = (int)std::min<int64_t>(smem64, INT_MAX);
     int optin = 0, sms = 0;
     if ((err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
         (err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)

@@ -37,12 +37,17 @@ def test_candidates_respect_kernel_limits():
         cands = autotune.multi_candidates(mmax)
         assert cands
         for c in cands:
-            assert c["threads"] in (128, 256, 512)
+            assert c["threads"] in (128, 256, 512, 1024)
             assert c["chunk"] % 16 == 0 and 16 <= c["chunk"] <= 32768
             assert c["chunk"] >= 4 * (mmax - 1)       # overlap at most a quarter of a chunk
-        # both table layouts of the multi-pattern count are timed
-        assert {c["layout"] for c in cands} == {1, 2}
-        assert len({(c["threads"], c["chunk"]) for c in cands if c["layout"] == 1}) == len(cands) // 2
+            # counter copies only where the kernel has them
+            assert c["layout"] < 3 or c["threads"] in (512, 1024)
+        # every table layout of the multi-pattern count is timed
+        assert {c["layout"] for c in cands} == {1, 2, 3, 4, 5}
+        one = {(c["threads"], c["chunk"]) for c in cands if c["layout"] == 1}
+        assert one == {(c["threads"], c["chunk"]) for c in cands if c["layout"] == 2}
+        assert {(c["threads"], c["chunk"]) for c in cands if c["layout"] == 5} == \
+            {(t, ch) for t, ch in one if t in (512, 1024)}
     for m in (4, 7, 8, 64):
         lays = set()
         for c in autotune.single_candidates(m):
@@ -112,6 +117,10 @@ def test_forced_single_pattern_fields_do_not_reach_the_multi_count(monkeypatch):
     assert autotune.forced_config("multi") == {"chunk": 768}
     monkeypatch.setenv("DNADFA_CONFIG", '{"layout": 2, "threads": 256}')
     assert autotune.forced_config("multi") == {"layout": 2, "threads": 256}
+    # the multi-pattern count's own layouts (counter copies) under their own key
+    monkeypatch.setenv("DNADFA_CONFIG", '{"layout": 4, "multi_layout": 5, "threads": 1024}')
+    assert autotune.forced_config("multi") == {"layout": 5, "threads": 1024}
+    assert autotune.forced_config() == {"layout": 4, "threads": 1024}
 
 
 def test_forced_config(monkeypatch):

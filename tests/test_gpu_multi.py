@@ -275,11 +275,13 @@ def test_class_automaton_counts_the_sum_of_its_expansions(gpu):
         assert int(out.item()) == sum(gpu.count(td, e) for e in exp), c
 
 
-@pytest.mark.parametrize("layout", [1, 2])
+@pytest.mark.parametrize("layout", [1, 2, 3, 4, 5])
 def test_table_layouts_agree(gpu, layout):
-    """The table as one shared copy (layout 1) and as 32 per-lane copies
-    (layout 2, conflict-free lookups) count the same, bit-exact against the
-    oracle, for plain and class automata and every block size."""
+    """The table as one shared copy (layout 1), as 32 per-lane copies
+    (layout 2, conflict-free lookups) and as one copy with 2, 4 or 8 counter
+    copies a state (layouts 3-5, 512 and 1024 threads) count the same,
+    bit-exact against the oracle, for plain and class automata and every
+    block size the layout takes."""
     import torch
     texts = [synth.genome_text(n, 760 + i, mask_mean=60, n_gap_mean=30_000, n_run_mean=300)
              for i, n in enumerate((2_000_003, 333_331, 17))]
@@ -289,7 +291,7 @@ def test_table_layouts_agree(gpu, layout):
     for pats, cls in sets:
         mt = gpu.MultiTable(pats, classes=cls)
         want = oracle.multi_count_class(texts, pats) if cls else oracle.multi_count(texts, pats)
-        for threads in (128, 256, 512):
+        for threads in (128, 256, 512, 1024) if layout < 3 else (512, 1024):
             out = torch.zeros(len(texts) * len(pats), dtype=torch.int64, device="cuda")
             gpu.dfa_multi_count([_dev(t) for t in texts], mt, out,
                                 cfg=dict(layout=layout, threads=threads, chunk=256))
@@ -305,3 +307,9 @@ def test_per_lane_copies_refused_when_too_large(gpu):
         gpu.dfa_multi_count([_dev(synth.genome_text(10_000, 3))], mt, out, cfg=dict(layout=2))
     gpu.dfa_multi_count([_dev(synth.genome_text(10_000, 3))], mt, out, cfg=dict(layout=1))
     assert int(out.sum().item()) == oracle.valid_windows(synth.genome_text(10_000, 3), 6)
+    # counter copies: 8 a state beside this table fit one CTA of 1024 threads;
+    # at 256 threads the kernel has none
+    gpu.dfa_multi_count([_dev(synth.genome_text(10_000, 3))], mt, out, cfg=dict(layout=5, threads=1024))
+    assert int(out.sum().item()) == oracle.valid_windows(synth.genome_text(10_000, 3), 6)
+    with pytest.raises(gpu.DfaError):
+        gpu.dfa_multi_count([_dev(synth.genome_text(10_000, 3))], mt, out, cfg=dict(layout=3, threads=256))
