@@ -1070,6 +1070,16 @@ __device__ __forceinline__ uint32_t window_exact(uint2 map, uint32_t r, uint32_t
             const uint32_t jp = j - 4u;
             wl = *reinterpret_cast<const uint32_t*>(q + (ob ^ (jp & 0x30u)) + (jp & 0xCu));
         }
+        if (m <= 4u) {
+            // the window in one word: bytes jl + 1 .. jl + 4 of wl:wh, its
+            // first 4 - m bytes outside the window
+            const uint32_t w = __funnelshift_rc(wl, wh, 8u * (jl + 1u));
+            if ((word_bad(w) & (0xFFFFFFFFu << (8u * (4u - m)))) == 0u) {
+                sink.put(r + j);
+                c++;
+            }
+            continue;
+        }
         // bytes of wl inside the window: from 5 + jl - m on (all of them
         // when that is below 0, none when it is past 3: shl by >= 32 is 0)
         uint32_t keep_l;
