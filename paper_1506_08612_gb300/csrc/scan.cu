@@ -2012,11 +2012,61 @@ __device__ __noinline__ void place_range(const ScanArgs& a, const uint8_t* d1s, 
 constexpr int64_t kLaneRange = 128;
 
 // Every occurrence starting in [s, e), walked by one lane alone (through
-// min(e + m - 1, n)) and written in order from index g.
+// min(e + m - 1, n)) and written in order from index g: the walk of
+// place_slice with the next 16-byte load in flight while a block is walked,
+// and a block's words of four bases stepped without the per-byte base test
+// (out of line, so the calling kernel's own registers do not pay for it).
 __device__ __noinline__ void place_row_lane(const ScanArgs& a, const uint8_t* d1s, int64_t s, int64_t e, int64_t g)
 {
-    int64_t keep[4];
-    place_slice<true>(a, d1s, s, e, min(e + (int64_t)a.m - 1, a.n), g, keep);
+    const int64_t hi = min(e + (int64_t)a.m - 1, a.n);
+    const uint32_t m = (uint32_t)a.m;
+    if (s >= e) return;
+    uint32_t q = 0;
+    auto load16 = [&](int64_t base) -> uint4 {
+        if (base + 16 <= a.n) return ldg16(reinterpret_cast<const uint4*>(a.text + base));
+        uint32_t w[4] = {0u, 0u, 0u, 0u};            // the text's last bytes: no read past n
+        for (int64_t j = base; j < a.n; j++) w[(j - base) >> 2] |= (uint32_t)__ldg(a.text + j) << (8 * ((j - base) & 3));
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    };
+    auto hit = [&](int64_t j) {
+        if (g < a.cap) a.pos[g] = a.pos_base + j - (int64_t)(m - 1);
+        g++;
+    };
+    auto step = [&](uint32_t b) {                   // one byte, any value
+        const uint32_t t = (b >> 2) & ~(b >> 1) & 1u;
+        q = ((b ^ (t * 0x11u)) & 0xD9u) == 0x41u ? (uint32_t)d1s[q * 4u + ((b >> 1) & 3u)] : 0u;
+    };
+    int64_t base = s & ~(int64_t)15;
+    uint4 v = load16(base);
+    for (; base < hi; base += 16) {
+        const uint4 vn = base + 16 < hi ? load16(base + 16) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        if (s <= base && base + 16 <= hi) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (word_bad(w[k]) == 0u) {
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        q = d1s[q * 4u + ((w[k] >> (8 * i + 1)) & 3u)];
+                        if (q == m) hit(base + 4 * k + i);
+                    }
+                } else {
+                    for (int i = 0; i < 4; i++) {
+                        step((w[k] >> (8 * i)) & 0xFFu);
+                        if (q == m) hit(base + 4 * k + i);
+                    }
+                }
+            }
+        } else {
+            const int64_t j0 = max(s, base), j1 = min(hi, base + 16);
+            for (int64_t j = j0; j < j1; j++) {
+                const uint32_t off = (uint32_t)(j - base);
+                step((w[off >> 2] >> (8u * (off & 3u))) & 0xFFu);
+                if (q == m) hit(j);
+            }
+        }
+        v = vn;
+    }
 }
 
 // The single-step table of the pattern, (m+1) x 4 bytes, into shared memory.
