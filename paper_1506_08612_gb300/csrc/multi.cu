@@ -180,6 +180,18 @@ __device__ __forceinline__ void emit(const MultiTab& M, uint32_t e, uint32_t j, 
         emit_overlap<CG>(M.args, M.hs, M.row, e >> 2, j - own + 1u);
 }
 
+// An owned step's output without a branch: the add to the state's counter
+// is predicated on the entry's output flag (most steps of a sparse output
+// set have none, but some lane of a warp usually does, so a branch would
+// send the whole warp through the add).
+template <int CG>
+__device__ __forceinline__ void emit_owned(const MultiTab& M, uint32_t e)
+{
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(M.hs) + (((e >> 2) << CG) << 2);
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
+                 ::"r"(addr), "r"(e & 1u) : "memory");
+}
+
 // Four bases of a word w, byte k ending at offset j + k: four dependent
 // lookups, one test of the output flags.
 // One table lookup.  REP: the lane's own copy of the entry; the 32 copies
@@ -200,7 +212,12 @@ __device__ __forceinline__ void word_bases(const MultiTab& M, uint32_t& ent, uin
     const uint32_t e2 = lookup<REP>(M, (e1 & ~3u) | ((c >> 16) & 3u));
     const uint32_t e3 = lookup<REP>(M, (e2 & ~3u) | (c >> 24));
     ent = e3;
-    if ((e0 | e1 | e2 | e3) & 1u) {
+    if (!CHECK && !LOC) {
+        emit_owned<CG>(M, e0);
+        emit_owned<CG>(M, e1);
+        emit_owned<CG>(M, e2);
+        emit_owned<CG>(M, e3);
+    } else if ((e0 | e1 | e2 | e3) & 1u) {
         if (e0 & 1u) emit<CHECK, LOC, CG>(M, e0, j, own);
         if (e1 & 1u) emit<CHECK, LOC, CG>(M, e1, j + 1, own);
         if (e2 & 1u) emit<CHECK, LOC, CG>(M, e2, j + 2, own);
