@@ -187,9 +187,13 @@ __device__ __forceinline__ void emit(const MultiTab& M, uint32_t e, uint32_t j, 
 template <int CG>
 __device__ __forceinline__ void emit_owned(const MultiTab& M, uint32_t e)
 {
-    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(M.hs) + (((e >> 2) << CG) << 2);
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
-                 ::"r"(addr), "r"(e & 1u) : "memory");
+    // one counter a state: a flagged entry is 4 * next + 1, so e - 1 is the
+    // byte offset of next's counter
+    const uint32_t hs_sa = (uint32_t)__cvta_generic_to_shared(M.hs);
+    const uint32_t addr = CG == 0 ? e + (hs_sa - 1u) : hs_sa + (((e >> 2) << CG) << 2);
+    asm volatile("{\n\t.reg .pred p;\n\t.reg .b32 f;\n\tand.b32 f, %1, 1;\n\tsetp.ne.u32 p, f, 0;\n\t"
+                 "@p red.shared.add.u32 [%0], 1;\n\t}"
+                 ::"r"(addr), "r"(e) : "memory");
 }
 
 // Four bases of a word w, byte k ending at offset j + k: four dependent
