@@ -197,7 +197,8 @@ __device__ __forceinline__ void emit_owned(const MultiTab& M, uint32_t e)
 }
 
 // Four bases of a word w, byte k ending at offset j + k: four dependent
-// lookups, one test of the output flags.
+// lookups; owned outputs by predicated adds, the others behind one test of
+// the output flags.
 // One table lookup.  REP: the lane's own copy of the entry; the 32 copies
 // of an entry sit in the 32 banks, so a warp's 32 lookups never conflict.
 template <bool REP>
