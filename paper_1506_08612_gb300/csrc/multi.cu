@@ -270,8 +270,9 @@ template <bool CHECK, bool LOC = false, bool REP = false, int CG = 0>
 __device__ __forceinline__ void vec_any(const MultiTab& M, uint32_t& ent, uint4 v, uint32_t j, uint32_t own)
 {
     // one base test for the 16 bytes: all bases (nearly every block) take
-    // the four words without a branch between them
-    if ((word_bad_m(v.x) | word_bad_m(v.y) | word_bad_m(v.z) | word_bad_m(v.w)) == 0u) {
+    // the four words without a branch between them (not with the per-lane
+    // table copies, whose walk it left short of registers)
+    if (!REP && (word_bad_m(v.x) | word_bad_m(v.y) | word_bad_m(v.z) | word_bad_m(v.w)) == 0u) {
         word_bases<CHECK, LOC, REP, CG>(M, ent, v.x, j, own);
         word_bases<CHECK, LOC, REP, CG>(M, ent, v.y, j + 4, own);
         word_bases<CHECK, LOC, REP, CG>(M, ent, v.z, j + 8, own);
